@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: one EMPSO generation of the plain elitist-PSO workload.
+
+Workload (the headline configuration): 461 x 151 grid at 20 m with a 40-cell
+damping layer (541 x 231 padded), 8th order in space, 3 s record (1414 steps),
+6 Hz Ricker, seeded synthetic layered/faulted model (1500-4700 m/s), particle =
+4 x 8 control nodes (natural cubic spline), swarm of 32, 16 shots, 461
+receivers, FP32 wavefields.  One step = eval_fitness over all 32 x 16
+(particle, shot) instances in one persistent launch + one EMPSO step.
+
+Prints one JSON line.  value = grid-point updates per second over the padded
+grid (whole job); fitness_evals_per_s alongside.  The L2 is flushed between
+timed steps by writing a 256 MiB buffer outside the timed region.
+
+--impl reference times the FP64 CPU oracle (the method restated plainly, no
+GPU) on a bounded sample of the same workload and prints the same line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1905_12795_gb300 import synth  # noqa: E402
+
+METRIC = ("grid-pt updates/s + PSO fitness evals/s at 1 GB300; wall-clock to target misfit, "
+          "surrogate vs plain")
+WORKLOAD = "empso-461x151-P32-S16"
+BYTES_PER_UPDATE = 16          # read u^n, u^{n-1}, a; write u^{n+1} (FP32)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-particles", type=int, default=2)
+    return ap.parse_args()
+
+
+def _setup(name):
+    wl = synth.workloads()[name]
+    gs = wl.grids[0]
+    S = wl.shots_per_grid[0]
+    Lx = (gs.nx - 1) * gs.hx
+    shots = synth.shot_line(S, Lx, wl.src_z)
+    rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
+    true = synth.layered_faulted_model(gs.nx, gs.nz, gs.hx, gs.hz, seed=wl.seed_model,
+                                       vmin=gs.vmin, vmax=gs.vmax)
+    return wl, gs, S, shots, rec, true
+
+
+def _updates_per_instance(gs, nt):
+    return (gs.nx + 2 * gs.pad) * (gs.nz + 2 * gs.pad) * nt
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _wave_source_hash():
+    h = hashlib.sha256()
+    for f in ("wave.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1905_12795_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile(workload):
+    """DRAM bytes per launch of the modelling kernel from the committed ncu
+    summary, or None when absent or taken on another version of the kernel."""
+    path = os.path.join(ROOT, "profiles", "wave_kernel_empso-461x151.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    hsh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not hsh or hsh.group(1) != _wave_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class _Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _cpu_baseline(wl, gs, S, shots, rec, n_particles, nt_expected):
+    """Time the FP64 oracle on `n_particles` particles x all S shots (host cores)."""
+    import oracle
+    og = oracle.Grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmax)
+    assert og.nt == nt_expected
+    parts = synth.random_particles(n_particles, gs.kx * gs.kz, wl.xmin, wl.xmax,
+                                   seed=wl.seed_pso)
+    nrec = len(rec)
+    zeros = [np.zeros((og.nt, nrec)) for _ in range(S)]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    for p in range(n_particles):
+        vel = oracle.interp_model(parts[p].reshape(gs.kz, gs.kx), gs.nz, gs.nx, 0, gs.vmin,
+                                  gs.vmax)
+        oracle.shot_batch(og, vel, shots, rec, [0] * S, [nrec] * S, dobs=zeros, nthreads=cores)
+    el = time.perf_counter() - t0
+    upd = n_particles * S * _updates_per_instance(gs, og.nt)
+    return {"value": upd / el, "unit": "grid-pt updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_particles} particles x {S} shots of the same grid "
+                      f"({n_particles * S} instances, {upd:.3e} updates) in {el:.1f} s",
+            "fitness_evals_per_s": n_particles / el, "seconds": el}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, gs, S, shots, rec, _ = _setup(a.workload)
+    import oracle
+    og = oracle.Grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmax)
+    steps = []
+    for _ in range(a.warmup + a.steps):
+        steps.append(_cpu_baseline(wl, gs, S, shots, rec, 1, og.nt))
+    timed = steps[a.warmup:]
+    val = float(np.mean([s["value"] for s in timed]))
+    per = _updates_per_instance(gs, og.nt) * S
+    cb = dict(timed[-1])
+    cb["value"] = val
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "grid-pt updates/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * per / val, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": a.workload, "grid": f"{gs.nx}x{gs.nz}", "step_sample":
+                       f"1 particle x {S} shots of the {wl.P}x{S} generation"},
+            "cpu_baseline": cb,
+            "e2e": {"value": val, "unit": "grid-pt updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    wl, gs, S, shots, rec, true = _setup(a.workload)
+    nrec = len(rec)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
+                       gs.vmax, kx=gs.kx, kz=gs.kz, mode=gs.mode)
+    K = gs.kx * gs.kz
+    pso = B.EmpsoPso(wl.P, K, 1.2, 2.9, 0.5, 0.3, 0.25, max(1, wl.gens // 10), 1,
+                     wl.seed_pso + rank)
+    ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
+    dt, nt = ctx.grid_info(0)
+    sh = B.make_shots(shots, [0] * S, [nrec] * S)
+    # observed data of the true model (FP32, on this GPU)
+    dobs = torch.zeros(S * nt * nrec, device=dev)
+    ctx.forward_traces(torch.tensor(true, dtype=torch.float32, device=dev)[None], sh, dobs)
+    x = torch.zeros(wl.P, K, device=dev)
+    mis = torch.zeros(wl.P, dtype=torch.float64, device=dev)
+    ctx.pso_init(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.eval_fitness(x, sh, dobs, mis)
+        ctx.pso_step(mis, x)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    clocks = _Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    step_ms, wave_ms = [], []
+    for _ in range(a.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        wave_ms.append(ctx.read_timing()[1])
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ctx.set_timing(False)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+        dist.barrier()
+
+    # end-to-end through the public API: inputs from pinned host memory each
+    # step, misfit read back each step
+    x_host = x.cpu().pin_memory()
+    dobs_host = dobs.cpu().pin_memory()
+    mis_host = torch.zeros(wl.P, dtype=torch.float64).pin_memory()
+    x_e2e = torch.empty_like(x)
+    dobs_e2e = torch.empty_like(dobs)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(a.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x_e2e.copy_(x_host, non_blocking=True)
+        dobs_e2e.copy_(dobs_host, non_blocking=True)
+        ctx.eval_fitness(x_e2e, sh, dobs_e2e, mis)
+        ctx.pso_step(mis, x_e2e)
+        mis_host.copy_(mis, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = t.item()
+
+    upd_step = wl.P * S * _updates_per_instance(gs, nt)
+    value = world * upd_step * a.steps / (total_ms / 1e3)
+    evals = world * wl.P * a.steps / (total_ms / 1e3)
+    e2e_value = world * upd_step * a.steps / (e2e_total / 1e3)
+    wave_mean = float(np.mean(wave_ms))
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_UPDATE * upd_step / (wave_mean / 1e3) / 1e9
+    traffic = _traffic_from_profile(a.workload)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = _cpu_baseline(wl, gs, S, shots, rec, a.cpu_sample_particles, nt)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "grid-pt updates/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": a.workload, "grid": f"{gs.nx}x{gs.nz} (+{gs.pad} damping)",
+                       "space_order": gs.order, "nt": nt, "particles": wl.P, "shots": S,
+                       "receivers": nrec, "instances_per_step": wl.P * S,
+                       "updates_per_step": upd_step, "l2": "flushed (256 MiB write) between "
+                       "timed steps", "parallelism": f"replicas x{world}"},
+            "fitness_evals_per_s": evals,
+            "e2e": {"value": e2e_value, "unit": "grid-pt updates/s",
+                    "h2d_bytes_per_step": int(x.numel() * 4 + dobs.numel() * 4),
+                    "d2h_bytes_per_step": int(mis.numel() * 8),
+                    "fitness_evals_per_s": world * wl.P * a.steps / (e2e_total / 1e3)},
+            "roofline": {"kernel": "wave_kernel", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": BYTES_PER_UPDATE * upd_step,
+                         "kernel_ms": wave_mean},
+            "gpu_launches": 4 * a.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * empso.h - C ABI of the GB300 EMPSO fitness-evaluation library.
+ *
+ * Method: arXiv 1905.12795 ("Towards automatically building starting models
+ * for FWI using global optimization methods: a PSO approach via DEAP +
+ * Devito").  A particle is a small grid of velocity control nodes; it is
+ * interpolated onto the finite-difference grid (two-grid strategy, section
+ * "Testing approach"), every shot is forward-modelled with a 2nd-order-in-time,
+ * 4th/8th-order-in-space acoustic FD scheme with a damping layer (JSON nbpml)
+ * and a Ricker source, and the L2 misfit against the observed traces is the
+ * particle's fitness.  An elitist-mutated PSO (section "Theory", Eq. 1-3 and
+ * the EMPSO figure) then moves the swarm.
+ *
+ * Conventions shared by every entry point:
+ *  - All device work is enqueued on the caller's `stream` (a cudaStream_t
+ *    passed as void*; NULL = legacy default stream) and is stream-ordered;
+ *    nothing synchronises the host unless stated.
+ *  - Buffers marked "device" are caller-owned device memory; the library
+ *    never frees or keeps them beyond the call.  Buffers marked "host" are
+ *    read before the call returns.
+ *  - The library owns only its context: per-grid tables, workspace (model
+ *    fields, wavefield slots, partial misfits), swarm state and surrogate.
+ *  - No C++ exception crosses this boundary; every call returns a status and
+ *    leaves a message for empso_last_error().  On error nothing is enqueued
+ *    unless the status is EMPSO_CUDA_ERROR.
+ *  - One context serves one host thread at a time.
+ *
+ * Units: metres, seconds, hertz, metres per second.  Float arrays are
+ * row-major with x fastest.
+ */
+#ifndef EMPSO_H
+#define EMPSO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t empso_status;
+#define EMPSO_OK              0
+#define EMPSO_INVALID_ARG     1  /* a size, pointer, position or enum is out of range */
+#define EMPSO_OOM             2  /* device or pinned allocation failed */
+#define EMPSO_CUDA_ERROR      3  /* a CUDA call failed; the context may be unusable */
+#define EMPSO_NONFINITE       4  /* a misfit was NaN/Inf (reported as +inf, strict mode only) */
+#define EMPSO_TIMEOUT         5  /* a bounded device-side wait gave up */
+#define EMPSO_UNSUPPORTED     6  /* e.g. space order not in {2,4,8}, swarm too large */
+#define EMPSO_NOT_INITIALIZED 7  /* swarm or surrogate used before its init call */
+
+typedef struct empso_ctx empso_ctx;
+
+/* One modelling grid ("Testing approach": FD grid, nbpml damping cells, space
+ * order, record length, Ricker peak frequency).  Node (i, j) of the physical
+ * nx x nz grid sits at (i hx, j hz); `pad` damping cells surround it on all
+ * four sides.  dt <= 0 selects dt = T / (nt - 1) with
+ * nt = ceil(T / (0.9 dt_cfl)) + 1, dt_cfl = 2 / (vmax sqrt(rho (1/hx^2 + 1/hz^2)))
+ * and rho the extreme eigenvalue of the 1-D stencil.  Interpolated models are
+ * clipped to [vmin, vmax]; vmax also sets the damping strength.  A particle on
+ * this grid has kz x kx control nodes (index k = kz_i * kx + kx_i) spanning
+ * the physical domain edge to edge, interpolated by a natural cubic spline
+ * (interp_mode 0) or bilinearly (interp_mode 1, the paper's two-grid rule). */
+typedef struct {
+    int32_t nx, nz;
+    int32_t pad;
+    int32_t space_order;
+    float hx, hz;
+    float t_rec;
+    float f0;
+    float dt;
+    float vmin, vmax;
+    int32_t kx, kz;
+    int32_t interp_mode;
+} empso_grid;
+
+/* One shot ("Testing approach": acquisition geometry).  Source at (sx, sz),
+ * receivers rec_xz[rec_begin .. rec_begin + nrec) of the table given to
+ * empso_create, all inside the physical domain.  `weight` scales this shot's
+ * misfit in the particle's sum (1 for the paper's plain sum). */
+typedef struct {
+    float sx, sz;
+    int32_t rec_begin;
+    int32_t nrec;
+    int32_t grid_id;
+    float weight;
+} empso_shot;
+
+/* EMPSO parameters ("Theory": Eq. 1-3, EM figure; "Testing approach": NM,
+ * p_em, start iteration, c1, c2; JSON lambda for the velocity clamp).
+ * P particles of D dimensions; EM on the floor(nm_frac P) worst particles from
+ * generation em_start (1-based) on when em_enabled; seed keys Philox4x32-10. */
+typedef struct {
+    int32_t P, D;
+    double c1, c2, lambda, p_em, nm_frac;
+    int32_t em_start, em_enabled;
+    uint64_t seed;
+} empso_pso;
+
+/* Create a context.  grids: host [ngrids]; rec_xz: host [nrec_total][2]
+ * receiver table (copied); pso: host, may be NULL when no swarm is needed;
+ * xmin/xmax: host [pso->D] search box (ignored when pso is NULL).  On success
+ * *out owns device tables and must be released with empso_destroy.
+ * Errors: INVALID_ARG (bad sizes/positions), UNSUPPORTED (space order),
+ * OOM, CUDA_ERROR. */
+empso_status empso_create(const empso_grid *grids, int32_t ngrids,
+                          const float *rec_xz, int32_t nrec_total,
+                          const empso_pso *pso, const double *xmin,
+                          const double *xmax, empso_ctx **out);
+
+/* Release the context and everything it allocated (synchronises the device). */
+void empso_destroy(empso_ctx *ctx);
+
+/* Time axis chosen for a grid: dt (s) and number of steps/trace samples nt.
+ * dt, nt: host, either may be NULL. */
+empso_status empso_grid_info(const empso_ctx *ctx, int32_t grid_id, float *dt,
+                             int32_t *nt);
+
+/* Two-grid parameterisation ("Testing approach"): particles device [P][K]
+ * (K = kz kx of the grid, m/s) -> vel_out device [P][nz][nx] (m/s), clipped
+ * to [vmin, vmax].  Exposed for tests; eval_fitness does this internally. */
+empso_status empso_interp(empso_ctx *ctx, int32_t grid_id, const float *particles,
+                          int32_t P, float *vel_out, void *stream);
+
+/* Forward-model M gridded models on every shot ("Testing approach": FD
+ * modelling of each shot) and write the traces.  vel: device [M][nz][nx]
+ * (m/s) of the one grid all shots use; shots: host [S]; traces: device, for
+ * each model the concatenation over shots of [nt][nrec_s] float samples, so
+ * model m starts at m * sum_s nt nrec_s.  Trace sample n is the wavefield at
+ * t_{n+1} = (n + 1) dt, bilinearly sampled after step n; the source term of
+ * step n is r(n dt). */
+empso_status forward_traces(empso_ctx *ctx, const float *vel, int32_t M,
+                            const empso_shot *shots, int32_t S, float *traces,
+                            void *stream);
+
+/* Misfit of M gridded models: misfit[m] = sum_s weight_s * phi_ms with
+ * phi = 1/2 sum_n sum_r (d - d_obs)^2 ("Testing approach": l2 norm).
+ * vel: device [M][nz][nx]; d_obs: device, concatenation over shots of
+ * [nt][nrec_s]; misfit: device [M] doubles.  Non-finite misfits become +inf. */
+empso_status eval_models(empso_ctx *ctx, const float *vel, int32_t M,
+                         const empso_shot *shots, int32_t S, const float *d_obs,
+                         double *misfit, void *stream);
+
+/* Fitness of P particles (the method's fitness evaluation): each particle is
+ * interpolated onto the grid of every shot, every (particle, shot) instance
+ * is modelled in one persistent launch, and misfit[p] = sum_s weight_s phi_ps
+ * is reduced in fixed shot order.  particles: device [P][K] (K of the shots'
+ * grids, which must agree); shots: host [S] (grids may differ); d_obs:
+ * device, concatenation over shots of [nt_g(s)][nrec_s]; misfit: device [P]. */
+empso_status eval_fitness(empso_ctx *ctx, const float *particles, int32_t P,
+                          const empso_shot *shots, int32_t S, const float *d_obs,
+                          double *misfit, void *stream);
+
+/* Initialise the swarm ("Theory": random positions, randomized velocities):
+ * x ~ U(xmin, xmax), v ~ U(-vmax, vmax), vmax = lambda (xmax - xmin), pbest
+ * fitness +inf, generation 0.  particles_out: device [P][D] floats (x), may be
+ * NULL.  Errors: NOT_INITIALIZED if the context has no swarm. */
+empso_status pso_init(empso_ctx *ctx, float *particles_out, void *stream);
+
+/* One EMPSO generation given the fitness of the current positions ("Theory",
+ * Eq. 1-3 and the EM figure): generation k += 1; strict personal-best update;
+ * global best = lowest-index argmin; if EM is on and k >= em_start, the
+ * floor(nm_frac P) worst particles of a stable ascending sort of the fitness
+ * take g_d + 0.1 VR_d N(0,1) with probability p_em (else g_d) per coordinate,
+ * velocities unchanged; all others follow Eq. 1 (constriction Eq. 3, clamp to
+ * +-vmax) and Eq. 2; positions are clamped to the box.  misfit: device [P];
+ * particles_out: device [P][D] floats, may be NULL; gbest_out: HOST int, may
+ * be NULL - when given, the call synchronises the stream to fill it. */
+empso_status pso_step(empso_ctx *ctx, const double *misfit, float *particles_out,
+                      int32_t *gbest_out, void *stream);
+
+/* Copy the swarm state into caller buffers (any may be NULL): x, v, p device
+ * [P][D] doubles; pf device [P]; order device [P] ints (the last sort, or the
+ * identity when EM did not run); gk device int[2] = {g, k}. */
+empso_status pso_get_state(empso_ctx *ctx, double *x, double *v, double *p,
+                           double *pf, int32_t *order, int32_t *gk, void *stream);
+
+/* Overwrite the swarm state from caller device buffers (x, v, p [P][D], pf
+ * [P]) with global-best index g and generation k (host values). */
+empso_status pso_set_state(empso_ctx *ctx, const double *x, const double *v,
+                           const double *p, const double *pf, int32_t g,
+                           int32_t k, void *stream);
+
+/* Kernel timing: when enable != 0, eval_fitness / eval_models /
+ * forward_traces record CUDA events on their stream around the model-field
+ * kernels, the persistent modelling launch and the misfit reduction. */
+empso_status empso_set_timing(empso_ctx *ctx, int32_t enable);
+
+/* Durations of the last timed call in milliseconds (host double[3]):
+ * [0] model fields (interpolation), [1] modelling launch, [2] misfit
+ * reduction.  Waits for the last recorded event.  NOT_INITIALIZED if no
+ * timed call ran since timing was enabled. */
+empso_status empso_read_timing(empso_ctx *ctx, double *ms3);
+
+/* Human-readable name of a status code (static storage). */
+const char *empso_status_string(empso_status s);
+
+/* Message of the last failed call on this context (static storage of the
+ * context; empty string if none).  ctx may be NULL for empso_create errors. */
+const char *empso_last_error(const empso_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMPSO_H */

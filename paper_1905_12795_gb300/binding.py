@@ -1,0 +1,215 @@
+"""Thin ctypes binding over the C ABI declared in ``include/empso.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device buffers are passed as ``torch.Tensor`` objects on the
+current CUDA device; the current PyTorch stream is handed to the library.
+If the library has not been built (``paper_1905_12795_gb300.build.build()``
+or ``__graft_entry__.build()``) the first use raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_i32 = ctypes.c_int32
+_f32 = ctypes.c_float
+_f64 = ctypes.c_double
+_vp = ctypes.c_void_p
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
+          5: "TIMEOUT", 6: "UNSUPPORTED", 7: "NOT_INITIALIZED"}
+
+EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "forward_traces",
+           "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
+           "pso_set_state", "empso_set_timing", "empso_read_timing", "empso_status_string",
+           "empso_last_error"]
+
+
+class EmpsoGrid(ctypes.Structure):
+    _fields_ = [("nx", _i32), ("nz", _i32), ("pad", _i32), ("space_order", _i32),
+                ("hx", _f32), ("hz", _f32), ("t_rec", _f32), ("f0", _f32), ("dt", _f32),
+                ("vmin", _f32), ("vmax", _f32), ("kx", _i32), ("kz", _i32),
+                ("interp_mode", _i32)]
+
+
+class EmpsoShot(ctypes.Structure):
+    _fields_ = [("sx", _f32), ("sz", _f32), ("rec_begin", _i32), ("nrec", _i32),
+                ("grid_id", _i32), ("weight", _f32)]
+
+
+class EmpsoPso(ctypes.Structure):
+    _fields_ = [("P", _i32), ("D", _i32), ("c1", _f64), ("c2", _f64), ("lam", _f64),
+                ("p_em", _f64), ("nm_frac", _f64), ("em_start", _i32), ("em_enabled", _i32),
+                ("seed", ctypes.c_uint64)]
+
+
+class EmpsoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Open the built library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"EMPSO CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build())")
+    import torch  # noqa: F401  - load torch's CUDA runtime first so both share it
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    L.empso_create.argtypes = [P(EmpsoGrid), _i32, P(_f32), _i32, P(EmpsoPso), P(_f64), P(_f64),
+                               P(_vp)]
+    L.empso_destroy.argtypes = [_vp]
+    L.empso_destroy.restype = None
+    L.empso_grid_info.argtypes = [_vp, _i32, P(_f32), P(_i32)]
+    L.empso_interp.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp]
+    L.forward_traces.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp]
+    L.eval_models.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp, _vp]
+    L.eval_fitness.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp, _vp]
+    L.pso_init.argtypes = [_vp, _vp, _vp]
+    L.pso_step.argtypes = [_vp, _vp, _vp, P(_i32), _vp]
+    L.pso_get_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.pso_set_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp]
+    L.empso_set_timing.argtypes = [_vp, _i32]
+    L.empso_read_timing.argtypes = [_vp, P(_f64)]
+    L.empso_status_string.argtypes = [_i32]
+    L.empso_status_string.restype = ctypes.c_char_p
+    L.empso_last_error.argtypes = [_vp]
+    L.empso_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("empso_destroy", "empso_status_string", "empso_last_error"):
+            getattr(L, name).restype = _i32
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_grid(nx, nz, hx, hz, pad, order, T, f0, vmin, vmax, kx=8, kz=4, mode=0, dt=0.0):
+    return EmpsoGrid(nx, nz, pad, order, hx, hz, T, f0, dt, vmin, vmax, kx, kz, mode)
+
+
+def make_shots(shot_xz, rec_begin, rec_count, grid_ids=None, weights=None):
+    S = len(shot_xz)
+    arr = (EmpsoShot * S)()
+    for s in range(S):
+        arr[s] = EmpsoShot(float(shot_xz[s][0]), float(shot_xz[s][1]), int(rec_begin[s]),
+                           int(rec_count[s]), 0 if grid_ids is None else int(grid_ids[s]),
+                           1.0 if weights is None else float(weights[s]))
+    return arr
+
+
+class Context:
+    """An EMPSO context: grids (``EmpsoGrid`` list), a receiver table
+    ([N][2] metres) and optionally a swarm (``EmpsoPso`` + bounds)."""
+
+    def __init__(self, grids, rec_xz, pso: EmpsoPso | None = None, xmin=None, xmax=None):
+        L = load()
+        self._L = L
+        ng = len(grids)
+        self._grids = (EmpsoGrid * ng)(*grids)
+        rec = np.ascontiguousarray(np.asarray(rec_xz, dtype=np.float32).reshape(-1, 2))
+        self._rec = rec
+        h = ctypes.c_void_p()
+        self.pso = pso
+        xmn = xmx = None
+        if pso is not None:
+            self._xmin = np.ascontiguousarray(np.broadcast_to(xmin, (pso.D,)), dtype=np.float64)
+            self._xmax = np.ascontiguousarray(np.broadcast_to(xmax, (pso.D,)), dtype=np.float64)
+            xmn = self._xmin.ctypes.data_as(ctypes.POINTER(_f64))
+            xmx = self._xmax.ctypes.data_as(ctypes.POINTER(_f64))
+        rc = L.empso_create(self._grids, ng, rec.ctypes.data_as(ctypes.POINTER(_f32)),
+                            rec.shape[0], ctypes.byref(pso) if pso is not None else None,
+                            xmn, xmx, ctypes.byref(h))
+        if rc != 0:
+            raise EmpsoError(rc, L.empso_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.empso_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise EmpsoError(rc, self._L.empso_last_error(self._h).decode())
+
+    def grid_info(self, gid=0):
+        dt = _f32()
+        nt = _i32()
+        self._check(self._L.empso_grid_info(self._h, gid, ctypes.byref(dt), ctypes.byref(nt)))
+        return dt.value, nt.value
+
+    def interp(self, gid, particles, vel_out):
+        self._check(self._L.empso_interp(self._h, gid, _ptr(particles), particles.shape[0],
+                                         _ptr(vel_out), _stream()))
+
+    def forward_traces(self, vel, shots, traces):
+        self._check(self._L.forward_traces(self._h, _ptr(vel), vel.shape[0], shots, len(shots),
+                                           _ptr(traces), _stream()))
+
+    def eval_models(self, vel, shots, d_obs, misfit):
+        self._check(self._L.eval_models(self._h, _ptr(vel), vel.shape[0], shots, len(shots),
+                                        _ptr(d_obs), _ptr(misfit), _stream()))
+
+    def eval_fitness(self, particles, shots, d_obs, misfit):
+        self._check(self._L.eval_fitness(self._h, _ptr(particles), particles.shape[0], shots,
+                                         len(shots), _ptr(d_obs), _ptr(misfit), _stream()))
+
+    def set_timing(self, enable=True):
+        self._check(self._L.empso_set_timing(self._h, 1 if enable else 0))
+
+    def read_timing(self):
+        """(fields_ms, modelling_ms, reduction_ms) of the last timed call."""
+        ms = (_f64 * 3)()
+        self._check(self._L.empso_read_timing(self._h, ms))
+        return tuple(ms)
+
+    def pso_init(self, particles_out=None):
+        self._check(self._L.pso_init(self._h, _ptr(particles_out), _stream()))
+
+    def pso_step(self, misfit, particles_out=None, want_gbest=False):
+        g = _i32(-1)
+        self._check(self._L.pso_step(self._h, _ptr(misfit), _ptr(particles_out),
+                                     ctypes.byref(g) if want_gbest else None, _stream()))
+        return g.value if want_gbest else None
+
+    def pso_get_state(self, x=None, v=None, p=None, pf=None, order=None, gk=None):
+        self._check(self._L.pso_get_state(self._h, _ptr(x), _ptr(v), _ptr(p), _ptr(pf),
+                                          _ptr(order), _ptr(gk), _stream()))
+
+    def pso_set_state(self, x, v, p, pf, g, k):
+        self._check(self._L.pso_set_state(self._h, _ptr(x), _ptr(v), _ptr(p), _ptr(pf), int(g),
+                                          int(k), _stream()))

@@ -1,0 +1,694 @@
+// C ABI of the EMPSO library (include/empso.h): argument validation, the
+// context (per-grid tables, workspace, swarm state) and the batch builder that
+// turns (model, shot) pairs into one persistent modelling launch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace empso;
+
+struct GridHost {
+    empso_grid spec;
+    GridDev dev;
+    float *ex = nullptr, *ez = nullptr, *wavelet = nullptr, *Wx = nullptr, *Wz = nullptr;
+};
+
+struct empso_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::vector<GridHost> grids;
+    GridDev *grids_dev = nullptr;
+    float2 *rec_dev = nullptr;
+    std::vector<float> rec_host;
+    int nrec_total = 0;
+
+    // workspace, grown on demand
+    float *fields = nullptr;
+    size_t fields_cap = 0;       // floats
+    float *slots = nullptr;
+    size_t slots_cap = 0;        // floats
+    double *partial = nullptr;
+    size_t partial_cap = 0;      // doubles
+    unsigned char *stage_host = nullptr;  // pinned: instance table + shot weights
+    unsigned char *stage_dev = nullptr;
+    size_t stage_cap = 0;        // bytes
+    cudaEvent_t stage_free = nullptr;
+    int *counter = nullptr;
+
+    // launch shape of the modelling kernel
+    int wave_threads = 512;
+    int wave_ctas_per_sm = 1;
+
+    // swarm
+    bool has_pso = false;
+    empso_pso pcfg{};
+    PsoDev pso{};
+    double *pso_mem = nullptr;
+    int *pso_int = nullptr;
+
+    // kernel timing
+    bool timing = false;
+    bool timed = false;
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+empso_status fail(empso_ctx *c, empso_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+#define CK(ctx, call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? EMPSO_OOM : EMPSO_CUDA_ERROR, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+// Centred second-derivative weights of accuracy order 2R (Fornberg 1988).
+bool fd_weights(int order, double *c, int *R)
+{
+    static const double w2[] = {-2.0, 1.0};
+    static const double w4[] = {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
+    static const double w8[] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+    const double *w = nullptr;
+    if (order == 2) { w = w2; *R = 1; }
+    else if (order == 4) { w = w4; *R = 2; }
+    else if (order == 8) { w = w8; *R = 4; }
+    else return false;
+    for (int m = 0; m <= *R; ++m) c[m] = w[m];
+    return true;
+}
+
+empso_status setup_grid(empso_ctx *ctx, GridHost &G, int id)
+{
+    const empso_grid &s = G.spec;
+    char buf[256];
+    if (s.nx < 2 || s.nz < 2 || s.pad < 0 || !(s.hx > 0) || !(s.hz > 0) || !(s.t_rec > 0) ||
+        !(s.f0 > 0) || !(s.vmax > 0) || !(s.vmin <= s.vmax) || s.kx < 2 || s.kz < 2 ||
+        s.kx > 64 || s.kz > 64 || (s.interp_mode != 0 && s.interp_mode != 1)) {
+        snprintf(buf, sizeof buf, "grid %d: invalid sizes/spacings/bounds (need nx,nz>=2, "
+                 "pad>=0, h>0, T>0, f0>0, vmin<=vmax, 2<=kx,kz<=64, mode 0|1)", id);
+        return fail(ctx, EMPSO_INVALID_ARG, buf);
+    }
+    double c[MAX_R + 1];
+    int R = 0;
+    if (!fd_weights(s.space_order, c, &R)) {
+        snprintf(buf, sizeof buf, "grid %d: space order %d not in {2,4,8}", id, s.space_order);
+        return fail(ctx, EMPSO_UNSUPPORTED, buf);
+    }
+    GridDev &g = G.dev;
+    memset(&g, 0, sizeof g);
+    g.nx = s.nx;
+    g.nz = s.nz;
+    g.pad = s.pad;
+    g.R = R;
+    g.NX = s.nx + 2 * s.pad;
+    g.NZ = s.nz + 2 * s.pad;
+    g.NQ = (g.NX + 3) / 4;
+    g.pitch = ((4 * g.NQ + 2 * HALO) + 31) / 32 * 32;
+    g.rows = g.NZ + 2 * HALO;
+    g.field = (long long)g.rows * g.pitch;
+    g.kx = s.kx;
+    g.kz = s.kz;
+    g.mode = s.interp_mode;
+    g.hx = s.hx;
+    g.hz = s.hz;
+    g.vmin = s.vmin;
+    g.vmax = s.vmax;
+    // time axis: dt = T / (nt - 1), nt = ceil(T / (0.9 dt_cfl)) + 1 unless given
+    double dt = s.dt, T = s.t_rec;
+    int nt;
+    if (dt <= 0) {
+        double rho = c[0];
+        for (int m = 1; m <= R; ++m) rho += 2.0 * ((m & 1) ? -c[m] : c[m]);
+        rho = std::fabs(rho);
+        const double hx = s.hx, hz = s.hz;
+        const double dtmax = 2.0 / (s.vmax * std::sqrt(rho * (1.0 / (hx * hx) + 1.0 / (hz * hz))));
+        nt = (int)std::ceil(T / (0.9 * dtmax)) + 1;
+        dt = T / (double)(nt - 1);
+    } else {
+        nt = (int)std::lround(T / dt) + 1;
+    }
+    if (nt < 2 || nt > (1 << 24)) {
+        snprintf(buf, sizeof buf, "grid %d: %d time steps out of range", id, nt);
+        return fail(ctx, EMPSO_INVALID_ARG, buf);
+    }
+    g.nt = nt;
+    g.dt = (float)dt;
+    const double ihx2 = 1.0 / ((double)s.hx * s.hx), ihz2 = 1.0 / ((double)s.hz * s.hz);
+    for (int m = 0; m <= MAX_R; ++m) {
+        const double cm = m <= R ? c[m] : 0.0;
+        g.c[m] = (float)cm;
+        g.cxm[m] = (float)(cm * ihx2);
+        g.czm[m] = (float)(cm * ihz2);
+    }
+    g.cxm[0] = (float)(c[0] * (ihx2 + ihz2));
+    g.czm[0] = 0.f;
+    CK(ctx, cudaMalloc(&G.ex, sizeof(float) * g.pitch));
+    CK(ctx, cudaMalloc(&G.ez, sizeof(float) * g.rows));
+    CK(ctx, cudaMalloc(&G.wavelet, sizeof(float) * nt));
+    CK(ctx, cudaMalloc(&G.Wx, sizeof(float) * s.nx * s.kx));
+    CK(ctx, cudaMalloc(&G.Wz, sizeof(float) * s.nz * s.kz));
+    g.ex = G.ex;
+    g.ez = G.ez;
+    g.wavelet = G.wavelet;
+    g.Wx = G.Wx;
+    g.Wz = G.Wz;
+    CK(ctx, launch_grid_tables(g, G.ex, G.ez, G.wavelet, G.Wx, G.Wz, s.vmax, s.f0, 0));
+    return EMPSO_OK;
+}
+
+empso_status grow(empso_ctx *ctx, void **p, size_t *cap, size_t need_bytes, size_t elem)
+{
+    if (need_bytes <= *cap * elem) return EMPSO_OK;
+    if (*p) {
+        CK(ctx, cudaDeviceSynchronize());
+        CK(ctx, cudaFree(*p));
+        *p = nullptr;
+        *cap = 0;
+    }
+    size_t bytes = need_bytes + need_bytes / 8;
+    CK(ctx, cudaMalloc(p, bytes));
+    *cap = bytes / elem;
+    return EMPSO_OK;
+}
+
+empso_status grow_stage(empso_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->stage_cap) return EMPSO_OK;
+    CK(ctx, cudaEventSynchronize(ctx->stage_free));
+    if (ctx->stage_host) cudaFreeHost(ctx->stage_host);
+    if (ctx->stage_dev) {
+        CK(ctx, cudaDeviceSynchronize());
+        cudaFree(ctx->stage_dev);
+    }
+    ctx->stage_host = nullptr;
+    ctx->stage_dev = nullptr;
+    size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
+    CK(ctx, cudaMallocHost(&ctx->stage_host, cap));
+    CK(ctx, cudaMalloc(&ctx->stage_dev, cap));
+    ctx->stage_cap = cap;
+    return EMPSO_OK;
+}
+
+// Validate shots against the grids and the receiver table.
+empso_status check_shots(empso_ctx *ctx, const empso_shot *shots, int S, int only_grid)
+{
+    if (!shots || S <= 0) return fail(ctx, EMPSO_INVALID_ARG, "need at least one shot");
+    char buf[256];
+    for (int s = 0; s < S; ++s) {
+        const empso_shot &sh = shots[s];
+        if (sh.grid_id < 0 || sh.grid_id >= (int)ctx->grids.size()) {
+            snprintf(buf, sizeof buf, "shot %d: grid_id %d out of range", s, sh.grid_id);
+            return fail(ctx, EMPSO_INVALID_ARG, buf);
+        }
+        if (only_grid >= 0 && sh.grid_id != only_grid) {
+            snprintf(buf, sizeof buf, "shot %d: gridded models need every shot on one grid", s);
+            return fail(ctx, EMPSO_INVALID_ARG, buf);
+        }
+        const empso_grid &g = ctx->grids[sh.grid_id].spec;
+        const float Lx = (g.nx - 1) * g.hx, Lz = (g.nz - 1) * g.hz;
+        if (!(sh.sx >= 0 && sh.sx <= Lx && sh.sz >= 0 && sh.sz <= Lz)) {
+            snprintf(buf, sizeof buf, "shot %d: source (%g, %g) outside the %g x %g m domain", s,
+                     sh.sx, sh.sz, Lx, Lz);
+            return fail(ctx, EMPSO_INVALID_ARG, buf);
+        }
+        if (sh.nrec < 0 || sh.rec_begin < 0 || sh.rec_begin + (long long)sh.nrec > ctx->nrec_total) {
+            snprintf(buf, sizeof buf, "shot %d: receivers [%d, %d) outside the table of %d", s,
+                     sh.rec_begin, sh.rec_begin + sh.nrec, ctx->nrec_total);
+            return fail(ctx, EMPSO_INVALID_ARG, buf);
+        }
+        for (int r = sh.rec_begin; r < sh.rec_begin + sh.nrec; ++r) {
+            const float x = ctx->rec_host[2 * r], z = ctx->rec_host[2 * r + 1];
+            if (!(x >= 0 && x <= Lx && z >= 0 && z <= Lz)) {
+                snprintf(buf, sizeof buf, "shot %d: receiver %d at (%g, %g) outside its grid", s, r,
+                         x, z);
+                return fail(ctx, EMPSO_INVALID_ARG, buf);
+            }
+        }
+        if (!std::isfinite(sh.weight)) {
+            snprintf(buf, sizeof buf, "shot %d: non-finite weight", s);
+            return fail(ctx, EMPSO_INVALID_ARG, buf);
+        }
+    }
+    return EMPSO_OK;
+}
+
+// Model source for a batch: control-node particles or gridded velocities.
+struct Models {
+    const float *particles = nullptr;  // [M][K]
+    const float *vel = nullptr;        // [M][nz][nx]
+    int M = 0;
+};
+
+// Build and run one persistent modelling launch over all M x S instances.
+empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shots, int S,
+                       const float *d_obs, float *traces, double *misfit, cudaStream_t st)
+{
+    const int M = mod.M;
+    const int ng = (int)ctx->grids.size();
+    // per-shot offsets into d_obs / traces (concatenation over shots of [nt][nrec])
+    std::vector<long long> doff(S + 1, 0);
+    for (int s = 0; s < S; ++s)
+        doff[s + 1] = doff[s] + (long long)ctx->grids[shots[s].grid_id].dev.nt * shots[s].nrec;
+    // model fields: for each used grid, M fields
+    std::vector<long long> fbase(ng, -1);
+    long long ftotal = 0, maxfield = 0;
+    for (int s = 0; s < S; ++s) {
+        const int gid = shots[s].grid_id;
+        if (fbase[gid] < 0) {
+            fbase[gid] = ftotal;
+            ftotal += (long long)M * ctx->grids[gid].dev.field;
+            maxfield = std::max(maxfield, ctx->grids[gid].dev.field);
+        }
+    }
+    const long long n_inst = (long long)M * S;
+    if (n_inst > (1LL << 30)) return fail(ctx, EMPSO_INVALID_ARG, "too many instances");
+    const int max_ctas = ctx->sm_count * ctx->wave_ctas_per_sm;
+    const int n_ctas = (int)std::min<long long>(n_inst, max_ctas);
+    empso_status rc;
+    if ((rc = grow(ctx, (void **)&ctx->fields, &ctx->fields_cap, sizeof(float) * ftotal,
+                   sizeof(float))) != EMPSO_OK)
+        return rc;
+    if ((rc = grow(ctx, (void **)&ctx->slots, &ctx->slots_cap,
+                   sizeof(float) * 2 * maxfield * n_ctas, sizeof(float))) != EMPSO_OK)
+        return rc;
+    if ((rc = grow(ctx, (void **)&ctx->partial, &ctx->partial_cap, sizeof(double) * n_inst,
+                   sizeof(double))) != EMPSO_OK)
+        return rc;
+    const size_t inst_bytes = sizeof(Inst) * n_inst;
+    const size_t wofs = (inst_bytes + 255) / 256 * 256;
+    if ((rc = grow_stage(ctx, wofs + sizeof(float) * S)) != EMPSO_OK) return rc;
+
+    // instance table, longest work first so the dynamic queue balances
+    std::vector<long long> order(n_inst);
+    for (long long q = 0; q < n_inst; ++q) order[q] = q;
+    auto work = [&](long long q) {
+        const GridDev &g = ctx->grids[shots[q % S].grid_id].dev;
+        return (double)g.field * g.nt;
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](long long a, long long b) { return work(a) > work(b); });
+    CK(ctx, cudaEventSynchronize(ctx->stage_free));  // previous upload has left the buffer
+    Inst *hi = reinterpret_cast<Inst *>(ctx->stage_host);
+    const long long per_model = doff[S];
+    for (long long k = 0; k < n_inst; ++k) {
+        const long long q = order[k];
+        const int m = (int)(q / S), s = (int)(q % S);
+        const empso_shot &sh = shots[s];
+        const GridDev &g = ctx->grids[sh.grid_id].dev;
+        Inst in{};
+        in.a = ctx->fields + fbase[sh.grid_id] + (long long)m * g.field;
+        in.dobs = d_obs ? d_obs + doff[s] : nullptr;
+        in.traces = traces ? traces + (long long)m * per_model + doff[s] : nullptr;
+        in.rec = ctx->rec_dev + sh.rec_begin;
+        in.grid = sh.grid_id;
+        in.nrec = sh.nrec;
+        in.sx = sh.sx;
+        in.sz = sh.sz;
+        in.out = (int)q;
+        hi[k] = in;
+    }
+    float *wh = reinterpret_cast<float *>(ctx->stage_host + wofs);
+    for (int s = 0; s < S; ++s) wh[s] = shots[s].weight;
+    CK(ctx, cudaMemcpyAsync(ctx->stage_dev, ctx->stage_host, wofs + sizeof(float) * S,
+                            cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaEventRecord(ctx->stage_free, st));
+
+    if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[0], st));
+    // model fields
+    for (int gid = 0; gid < ng; ++gid) {
+        if (fbase[gid] < 0) continue;
+        const GridDev &g = ctx->grids[gid].dev;
+        float *dst = ctx->fields + fbase[gid];
+        if (mod.particles) CK(ctx, launch_interp(g, mod.particles, M, dst, g.field, nullptr, st));
+        else CK(ctx, launch_vel_to_field(g, mod.vel, M, dst, g.field, st));
+    }
+    CK(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int), st));
+    if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[1], st));
+    CK(ctx, launch_wave(ctx->grids_dev, reinterpret_cast<const Inst *>(ctx->stage_dev), (int)n_inst,
+                        ctx->counter, ctx->slots, 2 * maxfield, n_ctas, ctx->wave_threads,
+                        ctx->partial, st));
+    if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[2], st));
+    if (misfit)
+        CK(ctx, launch_finalize(ctx->partial, reinterpret_cast<const float *>(ctx->stage_dev + wofs),
+                                M, S, misfit, st));
+    if (ctx->timing) {
+        CK(ctx, cudaEventRecord(ctx->tev[3], st));
+        ctx->timed = true;
+    }
+    return EMPSO_OK;
+}
+
+void free_ctx(empso_ctx *c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    for (auto &G : c->grids) {
+        cudaFree(G.ex);
+        cudaFree(G.ez);
+        cudaFree(G.wavelet);
+        cudaFree(G.Wx);
+        cudaFree(G.Wz);
+    }
+    cudaFree(c->grids_dev);
+    cudaFree(c->rec_dev);
+    cudaFree(c->fields);
+    cudaFree(c->slots);
+    cudaFree(c->partial);
+    cudaFree(c->stage_dev);
+    cudaFree(c->counter);
+    cudaFree(c->pso_mem);
+    cudaFree(c->pso_int);
+    if (c->stage_host) cudaFreeHost(c->stage_host);
+    if (c->stage_free) cudaEventDestroy(c->stage_free);
+    for (auto &e : c->tev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *empso_status_string(empso_status s)
+{
+    switch (s) {
+    case EMPSO_OK: return "ok";
+    case EMPSO_INVALID_ARG: return "invalid argument";
+    case EMPSO_OOM: return "out of memory";
+    case EMPSO_CUDA_ERROR: return "CUDA error";
+    case EMPSO_NONFINITE: return "non-finite misfit";
+    case EMPSO_TIMEOUT: return "device wait timed out";
+    case EMPSO_UNSUPPORTED: return "unsupported";
+    case EMPSO_NOT_INITIALIZED: return "not initialised";
+    default: return "unknown status";
+    }
+}
+
+const char *empso_last_error(const empso_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *rec_xz,
+                          int32_t nrec_total, const empso_pso *pso, const double *xmin,
+                          const double *xmax, empso_ctx **out)
+{
+    g_create_error.clear();
+    if (!out) return fail(nullptr, EMPSO_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grids || ngrids <= 0 || ngrids > 64)
+        return fail(nullptr, EMPSO_INVALID_ARG, "need 1..64 grids");
+    if (nrec_total < 0 || (nrec_total > 0 && !rec_xz))
+        return fail(nullptr, EMPSO_INVALID_ARG, "bad receiver table");
+    empso_ctx *ctx = new (std::nothrow) empso_ctx();
+    if (!ctx) return fail(nullptr, EMPSO_OOM, "host allocation failed");
+    auto bail = [&](empso_status s) {
+        g_create_error = ctx->err;
+        free_ctx(ctx);
+        return s;
+    };
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device) !=
+            cudaSuccess) {
+        ctx->err = "no CUDA device";
+        return bail(EMPSO_CUDA_ERROR);
+    }
+    empso_status rc;
+    ctx->grids.resize(ngrids);
+    for (int i = 0; i < ngrids; ++i) {
+        ctx->grids[i].spec = grids[i];
+        if ((rc = setup_grid(ctx, ctx->grids[i], i)) != EMPSO_OK) return bail(rc);
+    }
+    std::vector<GridDev> gd(ngrids);
+    for (int i = 0; i < ngrids; ++i) gd[i] = ctx->grids[i].dev;
+    auto ck = [&](cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return EMPSO_OK;
+        ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? EMPSO_OOM : EMPSO_CUDA_ERROR;
+    };
+    if ((rc = ck(cudaMalloc(&ctx->grids_dev, sizeof(GridDev) * ngrids), "grid table")) ||
+        (rc = ck(cudaMemcpy(ctx->grids_dev, gd.data(), sizeof(GridDev) * ngrids,
+                            cudaMemcpyHostToDevice), "grid table copy")))
+        return bail(rc);
+    ctx->nrec_total = nrec_total;
+    ctx->rec_host.assign(rec_xz, rec_xz + 2 * (size_t)nrec_total);
+    if ((rc = ck(cudaMalloc(&ctx->rec_dev, sizeof(float2) * std::max(1, nrec_total)), "receivers")))
+        return bail(rc);
+    if (nrec_total > 0 &&
+        (rc = ck(cudaMemcpy(ctx->rec_dev, rec_xz, sizeof(float2) * nrec_total,
+                            cudaMemcpyHostToDevice), "receiver copy")))
+        return bail(rc);
+    if ((rc = ck(cudaMalloc(&ctx->counter, sizeof(int)), "counter")) ||
+        (rc = ck(cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming), "event")))
+        return bail(rc);
+    ctx->wave_ctas_per_sm = std::max(1, wave_max_ctas_per_sm(ctx->wave_threads));
+
+    if (pso) {
+        const empso_pso &p = *pso;
+        if (p.P < 1 || p.P > MAX_PSO_P || p.D < 1 || p.D > MAX_PSO_D) {
+            ctx->err = "swarm: need 1 <= P <= 2048 and 1 <= D <= 1024";
+            return bail(EMPSO_UNSUPPORTED);
+        }
+        if (!(p.c1 + p.c2 >= 4.0) || !(p.lambda > 0) || !(p.p_em >= 0 && p.p_em <= 1) ||
+            !(p.nm_frac >= 0 && p.nm_frac <= 1) || !xmin || !xmax) {
+            ctx->err = "swarm: need c1 + c2 >= 4 (Eq. 3), lambda > 0, p_em and nm_frac in [0,1], "
+                       "xmin/xmax";
+            return bail(EMPSO_INVALID_ARG);
+        }
+        for (int d = 0; d < p.D; ++d)
+            if (!(xmax[d] > xmin[d])) {
+                ctx->err = "swarm: need xmax > xmin in every dimension";
+                return bail(EMPSO_INVALID_ARG);
+            }
+        ctx->has_pso = true;
+        ctx->pcfg = p;
+        const size_t PD = (size_t)p.P * p.D;
+        if ((rc = ck(cudaMalloc(&ctx->pso_mem, sizeof(double) * (3 * PD + p.P + 2 * p.D)), "swarm")) ||
+            (rc = ck(cudaMalloc(&ctx->pso_int, sizeof(int) * (p.P + 2)), "swarm ints")))
+            return bail(rc);
+        PsoDev &s = ctx->pso;
+        s.P = p.P;
+        s.D = p.D;
+        s.NM = (int)std::floor(p.nm_frac * p.P);
+        s.em_start = p.em_start;
+        s.em_enabled = p.em_enabled;
+        s.c1 = p.c1;
+        s.c2 = p.c2;
+        s.lambda = p.lambda;
+        s.p_em = p.p_em;
+        s.seed = p.seed;
+        s.x = ctx->pso_mem;
+        s.v = s.x + PD;
+        s.p = s.v + PD;
+        s.pf = s.p + PD;
+        double *bounds = s.pf + p.P;
+        s.xmin = bounds;
+        s.xmax = bounds + p.D;
+        s.order = ctx->pso_int;
+        s.gk = ctx->pso_int + p.P;
+        if ((rc = ck(cudaMemcpy(bounds, xmin, sizeof(double) * p.D, cudaMemcpyHostToDevice), "xmin")) ||
+            (rc = ck(cudaMemcpy(bounds + p.D, xmax, sizeof(double) * p.D, cudaMemcpyHostToDevice),
+                     "xmax")) ||
+            (rc = ck(cudaMemset(ctx->pso_int, 0, sizeof(int) * (p.P + 2)), "swarm ints")))
+            return bail(rc);
+    }
+    if ((rc = ck(cudaDeviceSynchronize(), "setup kernels"))) return bail(rc);
+    *out = ctx;
+    return EMPSO_OK;
+}
+
+void empso_destroy(empso_ctx *ctx) { free_ctx(ctx); }
+
+empso_status empso_grid_info(const empso_ctx *ctx, int32_t grid_id, float *dt, int32_t *nt)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size()) return EMPSO_INVALID_ARG;
+    if (dt) *dt = ctx->grids[grid_id].dev.dt;
+    if (nt) *nt = ctx->grids[grid_id].dev.nt;
+    return EMPSO_OK;
+}
+
+empso_status empso_interp(empso_ctx *ctx, int32_t grid_id, const float *particles, int32_t P,
+                          float *vel_out, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size())
+        return fail(ctx, EMPSO_INVALID_ARG, "grid_id out of range");
+    if (P < 0 || (P > 0 && (!particles || !vel_out)))
+        return fail(ctx, EMPSO_INVALID_ARG, "bad particles/vel_out");
+    if (P == 0) return EMPSO_OK;
+    const GridDev &g = ctx->grids[grid_id].dev;
+    empso_status rc = grow(ctx, (void **)&ctx->fields, &ctx->fields_cap,
+                           sizeof(float) * g.field * P, sizeof(float));
+    if (rc) return rc;
+    CK(ctx, launch_interp(g, particles, P, ctx->fields, g.field, vel_out, (cudaStream_t)stream));
+    return EMPSO_OK;
+}
+
+empso_status forward_traces(empso_ctx *ctx, const float *vel, int32_t M, const empso_shot *shots,
+                            int32_t S, float *traces, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (M < 0 || (M > 0 && (!vel || !traces))) return fail(ctx, EMPSO_INVALID_ARG, "bad vel/traces");
+    empso_status rc = check_shots(ctx, shots, S, shots && S > 0 ? shots[0].grid_id : -1);
+    if (rc || M == 0) return rc;
+    Models mod;
+    mod.vel = vel;
+    mod.M = M;
+    return run_batch(ctx, mod, shots, S, nullptr, traces, nullptr, (cudaStream_t)stream);
+}
+
+empso_status eval_models(empso_ctx *ctx, const float *vel, int32_t M, const empso_shot *shots,
+                         int32_t S, const float *d_obs, double *misfit, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (M < 0 || (M > 0 && (!vel || !d_obs || !misfit)))
+        return fail(ctx, EMPSO_INVALID_ARG, "bad vel/d_obs/misfit");
+    empso_status rc = check_shots(ctx, shots, S, shots && S > 0 ? shots[0].grid_id : -1);
+    if (rc || M == 0) return rc;
+    Models mod;
+    mod.vel = vel;
+    mod.M = M;
+    return run_batch(ctx, mod, shots, S, d_obs, nullptr, misfit, (cudaStream_t)stream);
+}
+
+empso_status eval_fitness(empso_ctx *ctx, const float *particles, int32_t P,
+                          const empso_shot *shots, int32_t S, const float *d_obs, double *misfit,
+                          void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (P < 0 || (P > 0 && (!particles || !d_obs || !misfit)))
+        return fail(ctx, EMPSO_INVALID_ARG, "bad particles/d_obs/misfit");
+    empso_status rc = check_shots(ctx, shots, S, -1);
+    if (rc || P == 0) return rc;
+    const int K = ctx->grids[shots[0].grid_id].spec.kx * ctx->grids[shots[0].grid_id].spec.kz;
+    for (int s = 1; s < S; ++s) {
+        const empso_grid &g = ctx->grids[shots[s].grid_id].spec;
+        if (g.kx * g.kz != K)
+            return fail(ctx, EMPSO_INVALID_ARG, "shots' grids disagree on the control nodes");
+    }
+    Models mod;
+    mod.particles = particles;
+    mod.M = P;
+    return run_batch(ctx, mod, shots, S, d_obs, nullptr, misfit, (cudaStream_t)stream);
+}
+
+empso_status pso_init(empso_ctx *ctx, float *particles_out, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm");
+    CK(ctx, launch_pso_init(ctx->pso, particles_out, (cudaStream_t)stream));
+    return EMPSO_OK;
+}
+
+empso_status pso_step(empso_ctx *ctx, const double *misfit, float *particles_out,
+                      int32_t *gbest_out, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm");
+    if (!misfit) return fail(ctx, EMPSO_INVALID_ARG, "misfit is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(ctx, launch_pso_step(ctx->pso, misfit, particles_out, st));
+    if (gbest_out) {
+        CK(ctx, cudaMemcpyAsync(gbest_out, ctx->pso.gk, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaStreamSynchronize(st));
+    }
+    return EMPSO_OK;
+}
+
+empso_status pso_get_state(empso_ctx *ctx, double *x, double *v, double *p, double *pf,
+                           int32_t *order, int32_t *gk, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t PD = sizeof(double) * ctx->pso.P * ctx->pso.D;
+    if (x) CK(ctx, cudaMemcpyAsync(x, ctx->pso.x, PD, cudaMemcpyDeviceToDevice, st));
+    if (v) CK(ctx, cudaMemcpyAsync(v, ctx->pso.v, PD, cudaMemcpyDeviceToDevice, st));
+    if (p) CK(ctx, cudaMemcpyAsync(p, ctx->pso.p, PD, cudaMemcpyDeviceToDevice, st));
+    if (pf)
+        CK(ctx, cudaMemcpyAsync(pf, ctx->pso.pf, sizeof(double) * ctx->pso.P,
+                                cudaMemcpyDeviceToDevice, st));
+    if (order)
+        CK(ctx, cudaMemcpyAsync(order, ctx->pso.order, sizeof(int) * ctx->pso.P,
+                                cudaMemcpyDeviceToDevice, st));
+    if (gk) CK(ctx, cudaMemcpyAsync(gk, ctx->pso.gk, 2 * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    return EMPSO_OK;
+}
+
+empso_status pso_set_state(empso_ctx *ctx, const double *x, const double *v, const double *p,
+                           const double *pf, int32_t g, int32_t k, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm");
+    if (!x || !v || !p || !pf) return fail(ctx, EMPSO_INVALID_ARG, "state buffers are NULL");
+    if (g < 0 || g >= ctx->pso.P || k < 0) return fail(ctx, EMPSO_INVALID_ARG, "bad g or k");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t PD = sizeof(double) * ctx->pso.P * ctx->pso.D;
+    CK(ctx, cudaMemcpyAsync(ctx->pso.x, x, PD, cudaMemcpyDeviceToDevice, st));
+    CK(ctx, cudaMemcpyAsync(ctx->pso.v, v, PD, cudaMemcpyDeviceToDevice, st));
+    CK(ctx, cudaMemcpyAsync(ctx->pso.p, p, PD, cudaMemcpyDeviceToDevice, st));
+    CK(ctx, cudaMemcpyAsync(ctx->pso.pf, pf, sizeof(double) * ctx->pso.P, cudaMemcpyDeviceToDevice,
+                            st));
+    int gk[2] = {g, k};
+    // staged through pinned memory so the copy is stream-ordered
+    CK(ctx, cudaEventSynchronize(ctx->stage_free));
+    empso_status rc = grow_stage(ctx, 64);
+    if (rc) return rc;
+    memcpy(ctx->stage_host, gk, sizeof gk);
+    CK(ctx, cudaMemcpyAsync(ctx->pso.gk, ctx->stage_host, sizeof gk, cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaEventRecord(ctx->stage_free, st));
+    return EMPSO_OK;
+}
+
+empso_status empso_set_timing(empso_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (enable && !ctx->tev[0])
+        for (auto &e : ctx->tev) CK(ctx, cudaEventCreate(&e));
+    ctx->timing = enable != 0;
+    ctx->timed = false;
+    return EMPSO_OK;
+}
+
+empso_status empso_read_timing(empso_ctx *ctx, double *ms3)
+{
+    if (!ctx || !ms3) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->timed) return fail(ctx, EMPSO_NOT_INITIALIZED, "no timed call yet");
+    CK(ctx, cudaEventSynchronize(ctx->tev[3]));
+    for (int i = 0; i < 3; ++i) {
+        float ms = 0.f;
+        CK(ctx, cudaEventElapsedTime(&ms, ctx->tev[i], ctx->tev[i + 1]));
+        ms3[i] = ms;
+    }
+    return EMPSO_OK;
+}
+
+}  // extern "C"

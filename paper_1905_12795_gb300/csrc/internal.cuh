@@ -1,0 +1,88 @@
+// Internal declarations shared by the translation units of the EMPSO CUDA
+// library.  Not part of the public ABI (include/empso.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "empso.h"
+
+namespace empso {
+
+// Every wavefield / model buffer carries HALO zero cells around the padded
+// grid on all sides, enough for the widest stencil (space order 8, radius 4),
+// so the stencil never tests bounds.  Padded node (I, J) lives at
+// buf[(J + HALO) * pitch + I + HALO]; the interior starts 16 bytes into a row,
+// so float4 group q (nodes 4q .. 4q+3) is 16-byte aligned.
+constexpr int HALO = 4;
+constexpr int MAX_R = 4;
+constexpr int MAX_PSO_P = 2048;
+constexpr int MAX_PSO_D = 1024;
+
+// Device-side description of one modelling grid.
+struct GridDev {
+    int nx, nz, pad, R;      // physical nodes, damping cells, stencil radius
+    int NX, NZ;              // padded grid
+    int NQ;                  // float4 groups per row = ceil(NX / 4)
+    int pitch;               // floats per buffer row (multiple of 32)
+    int rows;                // NZ + 2 HALO
+    int nt;                  // time steps = trace samples
+    int kx, kz, mode;        // control nodes and interpolation mode
+    float dt, hx, hz;
+    float vmin, vmax;
+    float c[MAX_R + 1];      // centred 2nd-derivative weights c_0..c_R
+    float cxm[MAX_R + 1];    // c_m / hx^2 (m >= 1), [0] = c_0 (1/hx^2 + 1/hz^2)
+    float czm[MAX_R + 1];    // c_m / hz^2
+    const float *wavelet;    // [nt]      Ricker r(n dt)
+    const float *ex;         // [pitch]   eta_x dt / 2 per buffer column (0 in halo)
+    const float *ez;         // [rows]    eta_z dt / 2 per buffer row (0 in halo)
+    const float *Wx;         // [nx][kx]  interpolation weights along x
+    const float *Wz;         // [nz][kz]  interpolation weights along z
+    long long field;         // floats per buffer = rows * pitch
+};
+
+// One (model, shot) modelling instance of a launch.
+struct Inst {
+    const float *a;          // model field v^2 dt^2, buffer layout of the grid
+    const float *dobs;       // [nt][nrec] observed traces, or null
+    float *traces;           // [nt][nrec] output traces, or null
+    const float2 *rec;       // receiver positions (m) of this shot
+    int grid;                // index into the grid table
+    int nrec;
+    float sx, sz;            // source position (m)
+    int out;                 // slot of the partial misfit
+    int pad_;
+};
+
+// Host-side launchers (each enqueues on `st`).  Return cudaSuccess or the
+// launch error.
+cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wavelet,
+                               float *Wx, float *Wz, double vmax_damp, double f0,
+                               cudaStream_t st);
+cudaError_t launch_interp(const GridDev &g, const float *particles, int P, float *a_fields,
+                          long long field_stride, float *vel_out, cudaStream_t st);
+cudaError_t launch_vel_to_field(const GridDev &g, const float *vel, int M, float *a_fields,
+                                long long field_stride, cudaStream_t st);
+cudaError_t launch_wave(const GridDev *grids_dev, const Inst *insts, int n_inst,
+                        int *counter, float *slots, long long slot_floats, int n_ctas,
+                        int threads, double *partial, cudaStream_t st);
+cudaError_t launch_finalize(const double *partial, const float *weights, int P, int S,
+                            double *misfit, cudaStream_t st);
+int wave_max_ctas_per_sm(int threads);
+
+// Swarm state on the device.
+struct PsoDev {
+    int P, D, NM, em_start, em_enabled;
+    double c1, c2, lambda, p_em;
+    uint64_t seed;
+    const double *xmin, *xmax;   // [D]
+    double *x, *v, *p;           // [P][D]
+    double *pf;                  // [P]
+    int *order;                  // [P]
+    int *gk;                     // {g, k}
+};
+cudaError_t launch_pso_init(const PsoDev &s, float *particles_out, cudaStream_t st);
+cudaError_t launch_pso_step(const PsoDev &s, const double *misfit, float *particles_out,
+                            cudaStream_t st);
+
+}  // namespace empso

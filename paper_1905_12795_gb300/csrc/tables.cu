@@ -1,0 +1,200 @@
+// Per-grid tables and the two-grid parameterisation (section "Testing
+// approach": control nodes interpolated onto the FD grid; JSON nbpml damping
+// layer; Ricker source wavelet).
+#include "internal.cuh"
+
+namespace empso {
+
+// Damping: eta(d) = eta_max (d / L)^2 for a node d metres into the layer
+// (measured from its inner edge), L = pad h, eta_max = 3 vmax ln(1/R) / (2 L),
+// R = 1e-3 (Collino & Tsogka 2001).  Stored pre-multiplied by dt / 2 per
+// buffer column (x) and buffer row (z); halo cells get 0.
+__device__ double damping_eta(int I, int n, int pad, double h, double vmax)
+{
+    if (pad <= 0) return 0.0;
+    double d = 0.0;
+    if (I < pad) d = (double)(pad - I) * h;
+    else if (I > pad + n - 1) d = (double)(I - (pad + n - 1)) * h;
+    if (d <= 0.0) return 0.0;
+    double L = pad * h;
+    double etamax = 3.0 * vmax * log(1000.0) / (2.0 * L);
+    double q = d / L;
+    return etamax * q * q;
+}
+
+__global__ void damping_kernel(GridDev g, float *ex, float *ez, double vmax)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < g.pitch) {
+        int I = t - HALO;
+        float v = 0.f;
+        if (I >= 0 && I < g.NX) v = (float)(damping_eta(I, g.nx, g.pad, g.hx, vmax) * g.dt * 0.5);
+        ex[t] = v;
+    }
+    if (t < g.rows) {
+        int J = t - HALO;
+        float v = 0.f;
+        if (J >= 0 && J < g.NZ) v = (float)(damping_eta(J, g.nz, g.pad, g.hz, vmax) * g.dt * 0.5);
+        ez[t] = v;
+    }
+}
+
+// Ricker wavelet r(t) = (1 - 2 a) e^{-a}, a = (pi f0 (t - 1/f0))^2, sampled at
+// t_n = n dt.
+__global__ void wavelet_kernel(float *w, int nt, double dt, double f0)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nt) return;
+    double tau = n * dt - 1.0 / f0;
+    double a = 3.14159265358979323846 * f0 * tau;
+    a = a * a;
+    w[n] = (float)((1.0 - 2.0 * a) * exp(-a));
+}
+
+// Interpolation weights of K uniformly spaced control nodes (node k at grid
+// index k (n-1)/(K-1)) onto the n grid nodes: column k is the interpolant of
+// the k-th unit vector.  Mode 0: natural cubic spline (second derivatives
+// solved by the Thomas algorithm on the tridiagonal system
+// M_{j-1} + 4 M_j + M_{j+1} = 6 (y_{j+1} - 2 y_j + y_{j-1}) / H^2,
+// M_0 = M_{K-1} = 0).  Mode 1: piecewise linear.  One block per k.
+__global__ void interp_weights_kernel(float *W, int K, int n, int mode)
+{
+    __shared__ double M[64];
+    __shared__ double cp[64];
+    __shared__ double dp[64];
+    const int k = blockIdx.x;
+    const double H = (double)(n - 1) / (double)(K - 1);
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < K; ++j) M[j] = 0.0;
+        if (mode == 0 && K > 2) {
+            // unknowns M_1 .. M_{K-2}; forward sweep
+            int m = K - 2;
+            for (int r = 0; r < m; ++r) {
+                int j = r + 1;
+                double rhs = 6.0 * (((j + 1) == k) - 2.0 * (j == k) + ((j - 1) == k)) / (H * H);
+                double b = 4.0, a = (r > 0) ? 1.0 : 0.0, c = 1.0;
+                double den = b - a * (r > 0 ? cp[r - 1] : 0.0);
+                cp[r] = c / den;
+                dp[r] = (rhs - a * (r > 0 ? dp[r - 1] : 0.0)) / den;
+            }
+            for (int r = m - 1; r >= 0; --r)
+                M[r + 1] = dp[r] - (r < m - 1 ? cp[r] * M[r + 2] : 0.0);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double xi = (double)i;
+        int seg = (int)floor(xi / H);
+        seg = seg > K - 2 ? K - 2 : (seg < 0 ? 0 : seg);
+        double t = (xi - seg * H) / H;
+        double y0 = (seg == k) ? 1.0 : 0.0;
+        double y1 = (seg + 1 == k) ? 1.0 : 0.0;
+        double s = (1.0 - t) * y0 + t * y1;
+        if (mode == 0) {
+            double u = 1.0 - t;
+            s += H * H / 6.0 * ((u * u * u - u) * M[seg] + (t * t * t - t) * M[seg + 1]);
+        }
+        W[(size_t)i * K + k] = (float)s;
+    }
+}
+
+cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wavelet,
+                               float *Wx, float *Wz, double vmax_damp, double f0,
+                               cudaStream_t st)
+{
+    int n = g.pitch > g.rows ? g.pitch : g.rows;
+    damping_kernel<<<(n + 255) / 256, 256, 0, st>>>(g, ex, ez, vmax_damp);
+    wavelet_kernel<<<(g.nt + 255) / 256, 256, 0, st>>>(wavelet, g.nt, (double)g.dt, f0);
+    interp_weights_kernel<<<g.kx, 256, 0, st>>>(Wx, g.kx, g.nx, g.mode);
+    interp_weights_kernel<<<g.kz, 256, 0, st>>>(Wz, g.kz, g.nz, g.mode);
+    return cudaGetLastError();
+}
+
+// Model field a = v^2 dt^2 in buffer layout from the control nodes of one
+// particle per blockIdx.y: v(i, j) = sum_kz Wz[j][kz] sum_kx C[kz][kx] Wx[i][kx],
+// clipped to [vmin, vmax], edge-extended into the damping pad; 0 in the halo
+// and in the alignment columns past NX.  Optionally also writes the physical
+// model [nz][nx] (m/s).
+__global__ void interp_kernel(GridDev g, const float *__restrict__ particles, float *a_fields,
+                              long long field_stride, float *vel_out)
+{
+    extern __shared__ float C[];
+    const int p = blockIdx.y;
+    const int K = g.kx * g.kz;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) C[k] = particles[(size_t)p * K + k];
+    __syncthreads();
+    float *a = a_fields + p * field_stride;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.field;
+         e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e / g.pitch), c = (int)(e % g.pitch);
+        int I = c - HALO, J = r - HALO;
+        float out = 0.f;
+        if (I >= 0 && I < g.NX && J >= 0 && J < g.NZ) {
+            int i = min(max(I - g.pad, 0), g.nx - 1);
+            int j = min(max(J - g.pad, 0), g.nz - 1);
+            const float *wx = g.Wx + (size_t)i * g.kx;
+            const float *wz = g.Wz + (size_t)j * g.kz;
+            float v = 0.f;
+            for (int kz = 0; kz < g.kz; ++kz) {
+                float t = 0.f;
+                for (int kx = 0; kx < g.kx; ++kx) t = fmaf(C[kz * g.kx + kx], wx[kx], t);
+                v = fmaf(wz[kz], t, v);
+            }
+            v = fminf(fmaxf(v, g.vmin), g.vmax);
+            float vd = v * g.dt;
+            out = vd * vd;
+            if (vel_out && I - g.pad == i && J - g.pad == j)
+                vel_out[(size_t)p * g.nx * g.nz + (size_t)j * g.nx + i] = v;
+        }
+        a[e] = out;
+    }
+}
+
+cudaError_t launch_interp(const GridDev &g, const float *particles, int P, float *a_fields,
+                          long long field_stride, float *vel_out, cudaStream_t st)
+{
+    if (P <= 0) return cudaSuccess;
+    int K = g.kx * g.kz;
+    int blocks = (int)((g.field + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    dim3 grid(blocks, P);
+    interp_kernel<<<grid, 256, K * sizeof(float), st>>>(g, particles, a_fields, field_stride,
+                                                         vel_out);
+    return cudaGetLastError();
+}
+
+// Model field from a gridded physical model [nz][nx] (m/s), edge-extended
+// into the pad.
+__global__ void vel_field_kernel(GridDev g, const float *__restrict__ vel, float *a_fields,
+                                 long long field_stride)
+{
+    const int m = blockIdx.y;
+    float *a = a_fields + m * field_stride;
+    const float *v0 = vel + (size_t)m * g.nx * g.nz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.field;
+         e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e / g.pitch), c = (int)(e % g.pitch);
+        int I = c - HALO, J = r - HALO;
+        float out = 0.f;
+        if (I >= 0 && I < g.NX && J >= 0 && J < g.NZ) {
+            int i = min(max(I - g.pad, 0), g.nx - 1);
+            int j = min(max(J - g.pad, 0), g.nz - 1);
+            float vd = v0[(size_t)j * g.nx + i] * g.dt;
+            out = vd * vd;
+        }
+        a[e] = out;
+    }
+}
+
+cudaError_t launch_vel_to_field(const GridDev &g, const float *vel, int M, float *a_fields,
+                                long long field_stride, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    int blocks = (int)((g.field + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    dim3 grid(blocks, M);
+    vel_field_kernel<<<grid, 256, 0, st>>>(g, vel, a_fields, field_stride);
+    return cudaGetLastError();
+}
+
+}  // namespace empso

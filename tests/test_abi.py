@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/empso.h declares; the binding's structures match the header."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "empso.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_]\w*\s*\**\s*([A-Za-z_]\w*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_12795_gb300 import build
+    path = build.build()
+    import torch  # noqa: F401  (CUDA runtime first, as the binding does)
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("empso_create", "eval_fitness", "pso_init", "pso_step", "forward_traces"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_export_list_matches_header():
+    from paper_1905_12795_gb300 import binding
+    assert sorted(binding.EXPORTS) == _declared_functions()
+
+
+def test_struct_layouts():
+    from paper_1905_12795_gb300 import binding as B
+    # sizes follow the C layout of empso.h (natural alignment, no packing)
+    assert ctypes.sizeof(B.EmpsoGrid) == 14 * 4
+    assert ctypes.sizeof(B.EmpsoShot) == 6 * 4
+    assert ctypes.sizeof(B.EmpsoPso) == 8 + 5 * 8 + 8 + 8
+
+
+def test_status_strings(lib):
+    lib.empso_status_string.restype = ctypes.c_char_p
+    assert lib.empso_status_string(0) == b"ok"
+    assert lib.empso_status_string(6) == b"unsupported"
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1905_12795_gb300 import binding as B
+    grid = B.make_grid(41, 31, 10.0, 10.0, 5, 4, 0.2, 10.0, 1500.0, 3000.0)
+    with pytest.raises(B.EmpsoError) as e:
+        B.Context([grid], [[0.0, 0.0]])
+    assert e.value.status == 3
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    from paper_1905_12795_gb300 import binding as B
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "lib_path", lambda: str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        B.load()

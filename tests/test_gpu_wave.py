@@ -1,0 +1,268 @@
+"""GPU parity of the modelling path against the FP64 CPU oracle.
+
+Bar (from the method's accuracy target): traces within 1e-4 relative L2 of the
+oracle; misfits within 1e-4 relative when the residual is at least 1 % of the
+observed data, else |dphi| <= 1e-4 * 1/2 |d_obs|^2.  All inputs are seeded and
+synthetic (layered/faulted or two-layer models, shots and receivers on a line).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_12795_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-4
+MISFIT_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1905_12795_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _check_misfit(got, ref, dobs_energy):
+    for g, r, e in zip(np.atleast_1d(got), np.atleast_1d(ref), np.atleast_1d(dobs_energy)):
+        if r >= 1e-4 * e:      # |r| >= 1 % |d_obs|  <=>  phi >= 1e-4 * 1/2 |d_obs|^2
+            assert abs(g - r) <= MISFIT_TOL * r, (g, r)
+        else:
+            assert abs(g - r) <= MISFIT_TOL * e, (g, r, e)
+
+
+def _geometry(nx, nz, h, S, src_z, rec_z, off_grid=False):
+    Lx = (nx - 1) * h
+    shots = synth.shot_line(S, Lx, src_z)
+    rec = synth.receiver_line(nx, h, rec_z)
+    if off_grid:
+        rec = rec[:-1] + np.array([0.37 * h, 0.0])
+        shots = shots + np.array([0.21 * h, 0.43 * h])
+    return shots, rec
+
+
+@pytest.mark.parametrize("order,nx,nz,pad,h", [
+    (2, 37, 29, 7, 10.0),    # ragged: NX = 51, not a multiple of 4
+    (4, 61, 45, 10, 12.5),
+    (8, 70, 33, 9, 15.0),
+    (8, 23, 19, 0, 10.0),    # no damping layer, rigid edges
+])
+def test_traces_match_oracle(B, order, nx, nz, pad, h):
+    vmax = 3200.0
+    og = oracle.Grid(nx, nz, h, h, pad, order, 0.3, 12.0, vmax)
+    vel = synth.layered_faulted_model(nx, nz, h, h, seed=order + nx, vmin=1500.0, vmax=vmax)
+    shots, rec = _geometry(nx, nz, h, 3, 2.5 * h, 1.5 * h, off_grid=True)
+    nrec = len(rec)
+    _, ref = oracle.shot_batch(og, vel, shots, rec, [0] * 3, [nrec] * 3, want_traces=True)
+    grid = B.make_grid(nx, nz, h, h, pad, order, 0.3, 12.0, 1500.0, vmax)
+    ctx = B.Context([grid], rec)
+    dt, nt = ctx.grid_info(0)
+    assert nt == og.nt and dt == pytest.approx(og.dt, rel=1e-6)
+    out = torch.zeros(3 * og.nt * nrec, device="cuda")
+    ctx.forward_traces(_dev(vel[None]), B.make_shots(shots, [0] * 3, [nrec] * 3), out)
+    got = out.cpu().numpy().reshape(3, og.nt, nrec)
+    for s in range(3):
+        assert _rel_l2(got[s], ref[s]) < TRACE_TOL, (s, _rel_l2(got[s], ref[s]))
+    ctx.close()
+
+
+def test_single_forward_two_layer(B):
+    """Two-layer model (1500/2500 m/s, interface at 500 m) on 101 x 101 at 10 m
+    with a 20-cell damping layer, order 4, 10 Hz Ricker at (500, 20) m, 101
+    receivers at 20 m, 0.5 s; observed data from the model with +5 % velocity."""
+    nx = nz = 101
+    h = 10.0
+    og = oracle.Grid(nx, nz, h, h, 20, 4, 0.5, 10.0, 2625.0)
+    true = synth.two_layer_model(nx, nz, h)
+    obs_model = true * 1.05
+    shots = [(500.0, 20.0)]
+    rec = synth.receiver_line(nx, h, 20.0)
+    _, obs = oracle.shot_batch(og, obs_model, shots, rec, [0], [nx], want_traces=True)
+    phi_ref, _ = oracle.shot_batch(og, true, shots, rec, [0], [nx], dobs=obs)
+    _, tr_ref = oracle.shot_batch(og, true, shots, rec, [0], [nx], want_traces=True)
+    grid = B.make_grid(nx, nz, h, h, 20, 4, 0.5, 10.0, 1500.0, 2625.0)
+    ctx = B.Context([grid], rec)
+    sh = B.make_shots(shots, [0], [nx])
+    tr = torch.zeros(og.nt * nx, device="cuda")
+    ctx.forward_traces(_dev(true[None]), sh, tr)
+    assert _rel_l2(tr.cpu().numpy().reshape(og.nt, nx), tr_ref[0]) < TRACE_TOL
+    mis = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.eval_models(_dev(true[None]), sh, _dev(obs[0].ravel()), mis)
+    _check_misfit(mis.cpu().numpy(), phi_ref[0], 0.5 * np.sum(obs[0] ** 2))
+    # model == observed model: the misfit is round-off only
+    ctx.eval_models(_dev(obs_model[None]), sh, _dev(obs[0].ravel()), mis)
+    assert mis.item() <= MISFIT_TOL * 0.5 * np.sum(obs[0] ** 2)
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_interp_matches_oracle(B, mode):
+    nx, nz, h = 93, 41, 20.0
+    grid = B.make_grid(nx, nz, h, h, 5, 8, 0.2, 6.0, 1500.0, 4700.0, kx=8, kz=4, mode=mode)
+    ctx = B.Context([grid], [[0.0, 0.0]])
+    parts = synth.random_particles(5, 32, 1000.0, 5200.0, seed=9)   # some nodes outside the clip
+    out = torch.zeros(5, nz, nx, device="cuda")
+    ctx.interp(0, _dev(parts), out)
+    got = out.cpu().numpy()
+    for p in range(5):
+        ref = oracle.interp_model(parts[p].reshape(4, 8), nz, nx, mode, 1500.0, 4700.0)
+        assert np.max(np.abs(got[p] - ref) / ref) < 2e-6
+    ctx.close()
+
+
+def _oracle_fitness(og, parts, kz, kx, mode, vmin, vmax, shots, rec, rb, rc, dobs, weights=None):
+    out = []
+    for p in range(len(parts)):
+        vel = oracle.interp_model(parts[p].reshape(kz, kx), og.nz, og.nx, mode, vmin, vmax)
+        phi, _ = oracle.shot_batch(og, vel, shots, rec, rb, rc, dobs=dobs)
+        w = np.ones(len(shots)) if weights is None else np.asarray(weights)
+        out.append(float(np.sum(w * phi[0])))
+    return np.array(out)
+
+
+def test_eval_fitness_particles(B):
+    nx, nz, h, pad = 77, 35, 20.0, 12
+    vmin, vmax = 1500.0, 4700.0
+    og = oracle.Grid(nx, nz, h, h, pad, 8, 0.8, 6.0, vmax)
+    true = synth.layered_faulted_model(nx, nz, h, h, seed=1905, vmin=vmin, vmax=vmax)
+    shots, rec = _geometry(nx, nz, h, 4, 20.0, 20.0)
+    nrec = len(rec)
+    rb, rc = [0] * 4, [nrec] * 4
+    _, obs = oracle.shot_batch(og, true, shots, rec, rb, rc, want_traces=True)
+    parts = synth.random_particles(6, 32, vmin, vmax, seed=3)
+    ref = _oracle_fitness(og, parts, 4, 8, 0, vmin, vmax, shots, rec, rb, rc, obs)
+    grid = B.make_grid(nx, nz, h, h, pad, 8, 0.8, 6.0, vmin, vmax)
+    ctx = B.Context([grid], rec)
+    mis = torch.zeros(6, dtype=torch.float64, device="cuda")
+    dobs = _dev(np.concatenate([o.ravel() for o in obs]))
+    ctx.eval_fitness(_dev(parts), B.make_shots(shots, rb, rc), dobs, mis)
+    e = 0.5 * sum(np.sum(o ** 2) for o in obs)
+    _check_misfit(mis.cpu().numpy(), ref, [e] * 6)
+    # the same call again gives the same bits (fixed reduction order)
+    mis2 = torch.zeros_like(mis)
+    ctx.eval_fitness(_dev(parts), B.make_shots(shots, rb, rc), dobs, mis2)
+    assert torch.equal(mis, mis2)
+    ctx.close()
+
+
+def test_uneven_batch_two_grids(B):
+    """One launch over instances of two grid classes (coarse 40 m / 3 Hz / long
+    record, fine 20 m / 6 Hz), weighted misfit sum in fixed shot order."""
+    vmin, vmax = 1500.0, 4700.0
+    coarse = dict(nx=39, nz=17, h=40.0, pad=6, T=1.2, f0=3.0)
+    fine = dict(nx=77, nz=33, h=20.0, pad=10, T=0.9, f0=6.0)
+    ogs, grids, recs, shots_all, obs_all = [], [], [], [], []
+    rec_table = []
+    for gi, c in enumerate((coarse, fine)):
+        og = oracle.Grid(c["nx"], c["nz"], c["h"], c["h"], c["pad"], 8, c["T"], c["f0"], vmax)
+        ogs.append(og)
+        grids.append(B.make_grid(c["nx"], c["nz"], c["h"], c["h"], c["pad"], 8, c["T"], c["f0"],
+                                 vmin, vmax))
+        sh, rec = _geometry(c["nx"], c["nz"], c["h"], 2, 40.0, 40.0)
+        true = synth.layered_faulted_model(c["nx"], c["nz"], c["h"], c["h"], seed=7, vmin=vmin,
+                                           vmax=vmax)
+        _, obs = oracle.shot_batch(og, true, sh, rec, [0, 0], [len(rec)] * 2, want_traces=True)
+        recs.append(rec)
+        shots_all.append(sh)
+        obs_all.append(obs)
+        rec_table.append(rec)
+    parts = synth.random_particles(5, 32, vmin, vmax, seed=11)
+    w = [0.7, 0.7, 1.3, 1.3]
+    ref = np.zeros(5)
+    for gi in range(2):
+        og = ogs[gi]
+        nrec = len(recs[gi])
+        ref += _oracle_fitness(og, parts, 4, 8, 0, vmin, vmax, shots_all[gi], recs[gi], [0, 0],
+                               [nrec] * 2, obs_all[gi], weights=w[2 * gi:2 * gi + 2])
+    ctx = B.Context(grids, np.concatenate(rec_table))
+    n0 = len(recs[0])
+    xz = np.concatenate(shots_all)
+    sh = B.make_shots(xz, [0, 0, n0, n0], [n0, n0, len(recs[1]), len(recs[1])],
+                      grid_ids=[0, 0, 1, 1], weights=w)
+    dobs = _dev(np.concatenate([o.ravel() for ob in obs_all for o in ob]))
+    mis = torch.zeros(5, dtype=torch.float64, device="cuda")
+    ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+    e = sum(wi * 0.5 * np.sum(o ** 2) for wi, o in zip(w, [o for ob in obs_all for o in ob]))
+    _check_misfit(mis.cpu().numpy(), ref, [e] * 5)
+    ctx.close()
+
+
+def test_edge_cases(B):
+    nx, nz, h = 41, 31, 10.0
+    grid = B.make_grid(nx, nz, h, h, 5, 4, 0.2, 10.0, 1500.0, 3000.0)
+    rec = synth.receiver_line(nx, h, 0.0)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    # zero particles: no work, no error
+    ctx.eval_fitness(torch.zeros(0, 32, device="cuda"), B.make_shots([(200.0, 0.0)], [0], [nx]),
+                     torch.zeros(nt * nx, device="cuda"), torch.zeros(0, dtype=torch.float64,
+                                                                       device="cuda"))
+    # a shot with no receivers has zero misfit; sources on the domain corners are valid
+    sh = B.make_shots([(0.0, 0.0), ((nx - 1) * h, (nz - 1) * h)], [0, 0], [0, nx])
+    vel = torch.full((2, nz, nx), 2000.0, device="cuda")
+    og = oracle.Grid(nx, nz, h, h, 5, 4, 0.2, 10.0, 3000.0)
+    _, ref = oracle.shot_batch(og, np.full((nz, nx), 2000.0), [((nx - 1) * h, (nz - 1) * h)], rec,
+                               [0], [nx], want_traces=True)
+    tr = torch.zeros(2 * nt * nx, device="cuda")
+    ctx.forward_traces(vel, sh, tr)
+    got = tr.cpu().numpy().reshape(2, nt, nx)
+    assert _rel_l2(got[1], ref[0]) < TRACE_TOL and _rel_l2(got[0], ref[0]) < TRACE_TOL
+    mis = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ctx.eval_models(vel, sh, torch.zeros(nt * nx, device="cuda"), mis)
+    assert mis[0].item() == pytest.approx(0.5 * np.sum(ref[0].astype(np.float64) ** 2), rel=1e-4)
+    # invalid arguments are refused before any launch
+    with pytest.raises(B.EmpsoError) as e:
+        ctx.forward_traces(vel, B.make_shots([(-1.0, 0.0)], [0], [nx]), tr)
+    assert e.value.status == 1
+    with pytest.raises(B.EmpsoError):
+        ctx.forward_traces(vel, B.make_shots([(0.0, 0.0)], [5], [nx]), tr)
+    with pytest.raises(B.EmpsoError) as e:
+        B.Context([B.make_grid(nx, nz, h, h, 5, 6, 0.2, 10.0, 1500.0, 3000.0)], rec)
+    assert e.value.status == 6
+    ctx.close()
+
+
+@pytest.mark.parametrize("S_check", [2])
+def test_full_size_sampled(B, S_check):
+    """The 461 x 151 / 20 m / order 8 / 3 s / 6 Hz grid of the plain EMPSO
+    workload with 32 particles x 16 shots in one launch (the benchmarked launch
+    configuration); particles 0 and 31 are recomputed by the oracle (all 16
+    shots each)."""
+    wl = synth.workloads()["empso-461x151-P32-S16"]
+    gs = wl.grids[0]
+    og = oracle.Grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmax)
+    S = wl.shots_per_grid[0]
+    Lx = (gs.nx - 1) * gs.hx
+    shots = synth.shot_line(S, Lx, wl.src_z)
+    rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
+    nrec = len(rec)
+    true = synth.layered_faulted_model(gs.nx, gs.nz, gs.hx, gs.hz, seed=wl.seed_model)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
+                       gs.vmax, kx=gs.kx, kz=gs.kz)
+    ctx = B.Context([grid], rec)
+    sh = B.make_shots(shots, [0] * S, [nrec] * S)
+    _, obs = oracle.shot_batch(og, true, shots, rec, [0] * S, [nrec] * S, want_traces=True)
+    dobs = _dev(np.concatenate([o.ravel() for o in obs]))
+    obs = np.stack(obs)
+    parts = synth.random_particles(wl.P, gs.kx * gs.kz, wl.xmin, wl.xmax, seed=wl.seed_pso)
+    mis = torch.zeros(wl.P, dtype=torch.float64, device="cuda")
+    ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+    got = mis.cpu().numpy()
+    sel = [0, wl.P - 1][:S_check]
+    ref = _oracle_fitness(og, parts[sel], gs.kz, gs.kx, 0, gs.vmin, gs.vmax, shots, rec,
+                          [0] * S, [nrec] * S, list(obs))
+    e = 0.5 * np.sum(obs ** 2)
+    _check_misfit(got[sel], ref, [e] * len(sel))
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    ctx.close()
