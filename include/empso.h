@@ -179,6 +179,29 @@ empso_status pso_set_state(empso_ctx *ctx, const double *x, const double *v,
                            const double *p, const double *pf, int32_t g,
                            int32_t k, void *stream);
 
+/* Modelling kernel selection for the persistent launch:
+ *   EMPSO_KERNEL_AUTO      on-chip variant when every grid of the batch fits a
+ *                          cluster of <= 8 CTAs, else the streaming variant;
+ *   EMPSO_KERNEL_STREAMING wavefields in global memory, one CTA per instance;
+ *   EMPSO_KERNEL_RESIDENT  wavefields in distributed shared memory, one
+ *                          thread-block cluster per instance (calls return
+ *                          UNSUPPORTED when a grid does not fit).
+ * Both compute the same scheme; results agree to FP32 rounding. */
+#define EMPSO_KERNEL_AUTO      0
+#define EMPSO_KERNEL_STREAMING 1
+#define EMPSO_KERNEL_RESIDENT  2
+empso_status empso_set_kernel(empso_ctx *ctx, int32_t kind);
+
+/* Cluster size (CTAs per instance) of the on-chip kernel: 0 lets the library
+ * pick the size that keeps the most SMs busy; 1..16 forces it (calls return
+ * UNSUPPORTED when the batch does not fit that size). */
+empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas);
+
+/* Which modelling kernel the last launch used: *kind = EMPSO_KERNEL_STREAMING
+ * or EMPSO_KERNEL_RESIDENT (0 before any launch), *cluster = CTAs per
+ * instance.  Either pointer may be NULL (host ints). */
+empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *cluster);
+
 /* Kernel timing: when enable != 0, eval_fitness / eval_models /
  * forward_traces record CUDA events on their stream around the model-field
  * kernels, the persistent modelling launch and the misfit reduction. */

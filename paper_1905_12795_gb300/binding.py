@@ -27,7 +27,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
 
 EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "forward_traces",
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
-           "pso_set_state", "empso_set_timing", "empso_read_timing", "empso_status_string",
+           "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_set_timing", "empso_read_timing", "empso_status_string",
            "empso_last_error"]
 
 
@@ -84,6 +84,9 @@ def load():
     L.pso_step.argtypes = [_vp, _vp, _vp, P(_i32), _vp]
     L.pso_get_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.pso_set_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp]
+    L.empso_set_kernel.argtypes = [_vp, _i32]
+    L.empso_set_cluster.argtypes = [_vp, _i32]
+    L.empso_last_launch.argtypes = [_vp, P(_i32), P(_i32)]
     L.empso_set_timing.argtypes = [_vp, _i32]
     L.empso_read_timing.argtypes = [_vp, P(_f64)]
     L.empso_status_string.argtypes = [_i32]
@@ -187,6 +190,20 @@ class Context:
     def eval_fitness(self, particles, shots, d_obs, misfit):
         self._check(self._L.eval_fitness(self._h, _ptr(particles), particles.shape[0], shots,
                                          len(shots), _ptr(d_obs), _ptr(misfit), _stream()))
+
+    KERNEL_AUTO, KERNEL_STREAMING, KERNEL_RESIDENT = 0, 1, 2
+
+    def set_kernel(self, kind: int):
+        self._check(self._L.empso_set_kernel(self._h, int(kind)))
+
+    def set_cluster(self, ctas: int):
+        self._check(self._L.empso_set_cluster(self._h, int(ctas)))
+
+    def last_launch(self):
+        """(kernel kind, CTAs per instance) of the last modelling launch."""
+        k, c = _i32(), _i32()
+        self._check(self._L.empso_last_launch(self._h, ctypes.byref(k), ctypes.byref(c)))
+        return k.value, c.value
 
     def set_timing(self, enable=True):
         self._check(self._L.empso_set_timing(self._h, 1 if enable else 0))

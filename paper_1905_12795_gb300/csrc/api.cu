@@ -42,8 +42,13 @@ struct empso_ctx {
     int *counter = nullptr;
 
     // launch shape of the modelling kernel
+    int kernel_kind = EMPSO_KERNEL_AUTO;
     int wave_threads = 512;
     int wave_ctas_per_sm = 1;
+    size_t smem_optin = 0;          // max dynamic shared memory per block
+    int forced_C = 0;               // 0: choose the cluster size, else use this one
+    int last_path = 0;              // 1 streaming, 2 resident (last modelling launch)
+    int last_C = 0;
 
     // swarm
     bool has_pso = false;
@@ -279,13 +284,60 @@ empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shot
     }
     const long long n_inst = (long long)M * S;
     if (n_inst > (1LL << 30)) return fail(ctx, EMPSO_INVALID_ARG, "too many instances");
+    empso_status rc;
+    // on-chip path: the smallest cluster that every grid of the batch fits
+    int resC = 0, res_threads = 0, res_clusters = 0, resR = -1, ring_pitch = 0;
+    size_t res_smem = 0;
+    for (int gid = 0; gid < ng; ++gid) {   // one stencil radius per on-chip launch
+        if (fbase[gid] < 0) continue;
+        const int R = ctx->grids[gid].dev.R;
+        resR = (resR < 0 || resR == R) ? R : 0;
+    }
+    if (ctx->kernel_kind != EMPSO_KERNEL_STREAMING && resR > 0) {
+        // every cluster size the batch fits; keep the one that keeps the most
+        // SMs busy (co-resident clusters x C, capped by the instance count)
+        long long best_sms = 0;
+        int nrec_max = 0;
+        for (int s = 0; s < S; ++s) nrec_max = std::max(nrec_max, (int)shots[s].nrec);
+        ring_pitch = std::min(nrec_max, resident_max_threads());
+        for (int C = 1; C <= 16; ++C) {
+            if (ctx->forced_C > 0 && C != ctx->forced_C) continue;
+            bool ok = true;
+            size_t sm = 0;
+            int items = 32;
+            for (int gid = 0; gid < ng && ok; ++gid) {
+                if (fbase[gid] < 0) continue;
+                const GridDev &g = ctx->grids[gid].dev;
+                ok = resident_fits(g, C, ring_pitch, ctx->smem_optin);
+                sm = std::max(sm, resident_smem_bytes(g, C, ring_pitch));
+                const int rows_c = (g.NZ + C - 1) / C;
+                const int rpt = resident_rows_per_thread();
+                items = std::max(items, g.NQ * ((rows_c + rpt - 1) / rpt));
+            }
+            if (!ok) continue;
+            const int threads = (items + 31) / 32 * 32;
+            const int nc = (int)std::min<long long>(resident_max_clusters(resR, C, threads, sm), n_inst);
+            const long long sms = (long long)nc * C;
+            if (nc > 0 && sms > best_sms) {
+                best_sms = sms;
+                resC = C;
+                res_smem = sm;
+                res_threads = threads;
+                res_clusters = nc;
+            }
+        }
+    }
+    if (ctx->kernel_kind == EMPSO_KERNEL_RESIDENT && res_clusters <= 0)
+        return fail(ctx, EMPSO_UNSUPPORTED,
+                    "the batch does not fit the on-chip kernel (grid too large or mixed orders)");
+    const bool resident = res_clusters > 0;
     const int max_ctas = ctx->sm_count * ctx->wave_ctas_per_sm;
     const int n_ctas = (int)std::min<long long>(n_inst, max_ctas);
-    empso_status rc;
     if ((rc = grow(ctx, (void **)&ctx->fields, &ctx->fields_cap, sizeof(float) * ftotal,
                    sizeof(float))) != EMPSO_OK)
         return rc;
-    if ((rc = grow(ctx, (void **)&ctx->slots, &ctx->slots_cap,
+    if (!resident &&
+        (rc = grow(ctx, (void **)&ctx->slots, &ctx->slots_cap,
                    sizeof(float) * 2 * maxfield * n_ctas, sizeof(float))) != EMPSO_OK)
         return rc;
     if ((rc = grow(ctx, (void **)&ctx->partial, &ctx->partial_cap, sizeof(double) * n_inst,
@@ -341,9 +393,19 @@ empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shot
     }
     CK(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int), st));
     if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[1], st));
-    CK(ctx, launch_wave(ctx->grids_dev, reinterpret_cast<const Inst *>(ctx->stage_dev), (int)n_inst,
-                        ctx->counter, ctx->slots, 2 * maxfield, n_ctas, ctx->wave_threads,
-                        ctx->partial, st));
+    if (resident) {
+        CK(ctx, launch_wave_resident(resR, ctx->grids_dev, reinterpret_cast<const Inst *>(ctx->stage_dev),
+                                     (int)n_inst, ctx->counter, resC, res_clusters, res_threads,
+                                     ring_pitch, res_smem, ctx->partial, st));
+        ctx->last_path = 2;
+        ctx->last_C = resC;
+    } else {
+        CK(ctx, launch_wave(ctx->grids_dev, reinterpret_cast<const Inst *>(ctx->stage_dev),
+                            (int)n_inst, ctx->counter, ctx->slots, 2 * maxfield, n_ctas,
+                            ctx->wave_threads, ctx->partial, st));
+        ctx->last_path = 1;
+        ctx->last_C = 1;
+    }
     if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[2], st));
     if (misfit)
         CK(ctx, launch_finalize(ctx->partial, reinterpret_cast<const float *>(ctx->stage_dev + wofs),
@@ -459,6 +521,15 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         (rc = ck(cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming), "event")))
         return bail(rc);
     ctx->wave_ctas_per_sm = std::max(1, wave_max_ctas_per_sm(ctx->wave_threads));
+    {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        // keep room for the kernel's static shared memory
+        ctx->smem_optin = optin > 2048 ? (size_t)optin - 2048 : 0;
+        for (int R : {1, 2, 4})
+            if ((rc = ck(resident_configure(R, ctx->smem_optin, 16), "on-chip kernel attributes")))
+                return bail(rc);
+    }
 
     if (pso) {
         const empso_pso &p = *pso;
@@ -663,6 +734,33 @@ empso_status pso_set_state(empso_ctx *ctx, const double *x, const double *v, con
     memcpy(ctx->stage_host, gk, sizeof gk);
     CK(ctx, cudaMemcpyAsync(ctx->pso.gk, ctx->stage_host, sizeof gk, cudaMemcpyHostToDevice, st));
     CK(ctx, cudaEventRecord(ctx->stage_free, st));
+    return EMPSO_OK;
+}
+
+empso_status empso_set_kernel(empso_ctx *ctx, int32_t kind)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (kind != EMPSO_KERNEL_AUTO && kind != EMPSO_KERNEL_STREAMING && kind != EMPSO_KERNEL_RESIDENT)
+        return fail(ctx, EMPSO_INVALID_ARG, "unknown kernel kind");
+    ctx->kernel_kind = kind;
+    return EMPSO_OK;
+}
+
+empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (ctas < 0 || ctas > 16) return fail(ctx, EMPSO_INVALID_ARG, "cluster size must be 0..16");
+    ctx->forced_C = ctas;
+    return EMPSO_OK;
+}
+
+empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *cluster)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    if (kind) *kind = ctx->last_path;
+    if (cluster) *cluster = ctx->last_C;
     return EMPSO_OK;
 }
 

@@ -70,6 +70,17 @@ cudaError_t launch_finalize(const double *partial, const float *weights, int P, 
                             double *misfit, cudaStream_t st);
 int wave_max_ctas_per_sm(int threads);
 
+// On-chip variant (wave_resident.cu): one thread-block cluster per instance.
+int resident_max_threads();
+int resident_rows_per_thread();
+size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch);
+bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit);
+cudaError_t resident_configure(int R, size_t smem_bytes, int C);
+int resident_max_clusters(int R, int C, int threads, size_t smem_bytes);
+cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, int n_inst,
+                                 int *counter, int C, int n_clusters, int threads, int ring_pitch,
+                                 size_t smem_bytes, double *partial, cudaStream_t st);
+
 // Swarm state on the device.
 struct PsoDev {
     int P, D, NM, em_start, em_enabled;

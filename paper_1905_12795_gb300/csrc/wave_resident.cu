@@ -1,0 +1,502 @@
+// On-chip ("resident") variant of the persistent modelling launch: the same
+// scheme and fused source/receiver/misfit work as wave.cu (section "Testing
+// approach": 2nd order in time, 4th/8th order in space, damping layer, Ricker
+// source, l2 misfit), but an instance's two time levels never leave the SMs.
+//
+// A thread-block cluster of C CTAs owns one instance at a time (taken from a
+// global queue by cluster rank 0).  The padded grid is split by rows: CTA c
+// holds rows [c*rows_c, (c+1)*rows_c) of u^n and u^{n-1}/u^{n+1} in its shared
+// memory with R halo rows above and below, and keeps its share of the model
+// field a = v^2 dt^2 in registers.  Every step each thread updates ROWS rows
+// of one float4 column group (z-stencil from a register window, x-stencil from
+// the neighbouring float4s in shared memory), writes u^{n+1} in place of
+// u^{n-1}, and stores its slab's first/last R rows straight into the halo rows
+// of the neighbouring CTAs (distributed shared memory).  One cluster barrier
+// (release/acquire) per step orders it all.  Global memory is touched only for
+// the model field (once per instance), the observed traces and the output.
+#include <cooperative_groups.h>
+
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace empso {
+
+namespace {
+
+constexpr int ROWS = 8;
+
+__device__ __forceinline__ float comp(const float4 &v, int l)
+{
+    return l == 0 ? v.x : (l == 1 ? v.y : (l == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void set_comp(float4 &v, int l, float x)
+{
+    if (l == 0) v.x = x;
+    else if (l == 1) v.y = x;
+    else if (l == 2) v.z = x;
+    else v.w = x;
+}
+
+// 4-byte asynchronous global -> shared copies (cp.async), grouped per step
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Double-buffered shared-memory staging of the wavelet sample and observed
+// record each step needs: step n copies what step n + 1 uses and waits for
+// those copies before its closing barrier, so no copy is in flight across a
+// barrier (a release barrier would wait for it) and the copy latency hides
+// under the stencil work.
+constexpr int DEPTH = 2;
+
+// Bilinear corners of (x, z) metres on the padded grid (lower corner clamped
+// to NX-2 / NZ-2), as global padded indices.
+__device__ __forceinline__ void corners(float x, float z, const GridDev &g, int &i0, int &j0,
+                                        float w[4])
+{
+    const float fx = x / g.hx + (float)g.pad;
+    const float fz = z / g.hz + (float)g.pad;
+    i0 = min(max((int)floorf(fx), 0), g.NX - 2);
+    j0 = min(max((int)floorf(fz), 0), g.NZ - 2);
+    const float ax = fx - (float)i0, az = fz - (float)j0;
+    w[0] = (1.f - ax) * (1.f - az);
+    w[1] = ax * (1.f - az);
+    w[2] = (1.f - ax) * az;
+    w[3] = ax * az;
+}
+
+template <int R>
+__device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
+                                  float4 *M4, float *ezs, float *wring, float *dring, int ring_pitch,
+                                  int C, int crank, cg::cluster_group &cluster, double *cred,
+                                  double *wred, double *partial)
+{
+    const int tid = threadIdx.x;
+    const int nth = blockDim.x;
+    // scalars of the grid in registers (the descriptor lives in shared memory)
+    const int NQ = gs.NQ, NZ = gs.NZ, NX = gs.NX, nt = gs.nt, pitch = gs.pitch;
+    const float *__restrict__ gex = gs.ex;
+    const float *__restrict__ gez = gs.ez;
+    const float *__restrict__ gwav = gs.wavelet;
+    const int sp4 = NQ + 2;                      // float4 per shared row (1 zero group each side)
+    const int rows_c = (NZ + C - 1) / C;
+    const int srows = rows_c + 2 * R;
+    const int z0 = crank * rows_c;
+    const int my_rows = max(0, min(NZ, z0 + rows_c) - z0);
+
+    // zero both time levels (halos included) and load this slab of the model field
+    for (int e = tid; e < 2 * srows * sp4; e += nth) A4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = tid; e < my_rows * NQ; e += nth) {
+        const int r = e / NQ, qq = e % NQ;
+        M4[r * NQ + qq] =
+            __ldg(reinterpret_cast<const float4 *>(in.a + (size_t)(z0 + r + HALO) * pitch + HALO) + qq);
+    }
+    for (int r = tid; r < my_rows; r += nth) ezs[r] = __ldg(gez + z0 + r + HALO);
+
+    // work item: column group q and ROWS consecutive slab rows from r0.  Every
+    // item computes exactly ROWS rows (no per-row conditions): the last item of
+    // a column starts at my_rows - ROWS, overlapping its predecessor, and stores
+    // only rows >= seg * ROWS.  rows_c >= ROWS keeps every read inside the slab
+    // buffers even on a short last CTA.
+    const int nseg = (my_rows + ROWS - 1) / ROWS;
+    const bool active = tid < NQ * nseg;
+    const int q = active ? tid % NQ : 0;
+    const int seg = active ? tid / NQ : 0;
+    const int r0 = active ? max(0, min(seg * ROWS, my_rows - ROWS)) : 0;
+    const int kfirst = seg * ROWS - r0;          // first row this item stores
+    const int klast = my_rows - r0;              // one past the last row it stores
+    const int rc = ROWS;
+
+    float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
+    const bool ex_zero = ex.x == 0.f && ex.y == 0.f && ex.z == 0.f && ex.w == 0.f;
+    // rows without z-damping: t = ex per lane, constant over the instance
+    const float2 d1x01 = make_float2(1.f - ex.x, 1.f - ex.y), d1x23 = make_float2(1.f - ex.z, 1.f - ex.w);
+    const float2 d2x01 = make_float2(__fdividef(1.f, 1.f + ex.x), __fdividef(1.f, 1.f + ex.y));
+    const float2 d2x23 = make_float2(__fdividef(1.f, 1.f + ex.z), __fdividef(1.f, 1.f + ex.w));
+    float cx[R + 1], cz[R + 1];
+#pragma unroll
+    for (int m = 0; m <= R; ++m) {
+        cx[m] = gs.cxm[m];
+        cz[m] = gs.czm[m];
+    }
+
+    // source: weights b / (hx hz) of the (up to) two rows and four lanes of
+    // this item that hold one of its bilinear corners
+    int s_i0, s_j0;
+    float sw[4];
+    corners(in.sx, in.sz, gs, s_i0, s_j0, sw);
+    const float inv_cell = 1.f / (gs.hx * gs.hz);
+    const int ks = s_j0 - (z0 + r0);             // item row of the upper corner row
+    float4 sb0 = make_float4(0.f, 0.f, 0.f, 0.f), sb1 = sb0;
+    bool src_here = false;
+    if (active && s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3 && ks + 1 >= 0 && ks < rc) {
+        src_here = true;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int I = 4 * q + l;
+            const float bx0 = (I == s_i0 ? 1.f : 0.f), bx1 = (I == s_i0 + 1 ? 1.f : 0.f);
+            set_comp(sb0, l, (bx0 * sw[0] + bx1 * sw[1]) * inv_cell);
+            set_comp(sb1, l, (bx0 * sw[2] + bx1 * sw[3]) * inv_cell);
+        }
+    }
+
+    // receivers: one per thread, owned by the CTA holding the lower corner row
+    int rk = 0;
+    float rw[4] = {0.f, 0.f, 0.f, 0.f};
+    bool rec_mine = false;
+    if (tid < in.nrec) {
+        const float2 p = in.rec[tid];
+        int i0, j0;
+        corners(p.x, p.y, gs, i0, j0, rw);
+        rec_mine = j0 >= z0 && j0 < z0 + my_rows;
+        rk = (j0 - z0 + R) * (4 * sp4) + 4 + i0;          // float index in the shared slab
+    }
+    const bool rec_loop = in.nrec > nth;                 // more receivers than threads
+    const float *__restrict__ dobs = in.dobs;
+    const bool ring_rec = rec_mine && dobs && !rec_loop;
+    // staging prologue: the wavelet sample of step 0
+    if (tid == 0 && nt > 0) cp_async4(wring, gwav);
+    cp_async_commit();
+    cp_async_wait<0>();
+    float accf = 0.f;
+    double acc = 0.0;
+    (void)NX;
+
+    cluster.sync();                                      // zeroed everywhere before halo stores
+
+    // neighbours' views of both time-level buffers
+    float4 *prev_A = nullptr, *prev_B = nullptr, *next_A = nullptr, *next_B = nullptr;
+    if (crank > 0) {
+        prev_A = cluster.map_shared_rank(A4, crank - 1);
+        prev_B = cluster.map_shared_rank(B4, crank - 1);
+    }
+    if (crank < C - 1) {
+        next_A = cluster.map_shared_rank(A4, crank + 1);
+        next_B = cluster.map_shared_rank(B4, crank + 1);
+    }
+    const bool top_item = r0 < R;                        // may hold halo rows of the CTA above
+    const bool bot_item = r0 + ROWS > rows_c - R;        // ... of the CTA below
+
+    float4 *cur = A4, *nxt = B4;
+    for (int n = 0; n <= nt; ++n) {
+        // stage wavelet sample n + 1 and record n (sampled in step n + 1); their
+        // slots were last read in step n - 1, which the previous barrier closed
+        {
+            const int iw = n + 1, ir = n;
+            if (tid == 0 && iw < nt) cp_async4(wring + iw % DEPTH, gwav + iw);
+            if (ring_rec && ir < nt)
+                cp_async4(dring + (ir % DEPTH) * ring_pitch + tid, dobs + (size_t)ir * in.nrec + tid);
+            cp_async_commit();
+        }
+        if (n < nt && active) {
+            const float rn = wring[n % DEPTH];
+            const bool even = (n & 1) == 0;           // nxt is B4 on even steps, A4 on odd
+            float4 *prevA = even ? prev_B : prev_A;
+            float4 *nextA = even ? next_B : next_A;
+            float4 w[2 * R + 1];
+#pragma unroll
+            for (int m = 0; m < 2 * R; ++m) w[m] = cur[(r0 + m) * sp4 + 1 + q];
+#pragma unroll
+            for (int k = 0; k < ROWS; ++k) {
+                {
+                    const int lr = R + r0 + k;           // shared row of the output
+                    w[2 * R] = cur[(lr + R) * sp4 + 1 + q];
+                    const float4 lft = cur[lr * sp4 + q];
+                    const float4 rgt = cur[lr * sp4 + 2 + q];
+                    const float4 um = nxt[lr * sp4 + 1 + q];
+                    const float4 av = M4[(r0 + k) * NQ + q];
+                    // Laplacian of lanes (0,1) and (2,3) with packed FP32x2 arithmetic;
+                    // x and z parts accumulate separately (two independent chains)
+                    const float2 c01 = make_float2(w[R].x, w[R].y), c23 = make_float2(w[R].z, w[R].w);
+                    const float s[12] = {lft.x, lft.y, lft.z, lft.w, w[R].x, w[R].y, w[R].z,
+                                         w[R].w, rgt.x, rgt.y, rgt.z, rgt.w};
+                    float2 lx01 = __fmul2_rn(make_float2(cx[0], cx[0]), c01);
+                    float2 lx23 = __fmul2_rn(make_float2(cx[0], cx[0]), c23);
+                    float2 lz01 = make_float2(0.f, 0.f), lz23 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int m = 1; m <= R; ++m) {
+                        const float2 czm = make_float2(cz[m], cz[m]);
+                        const float2 cxm = make_float2(cx[m], cx[m]);
+                        lz01 = __ffma2_rn(czm, __fadd2_rn(make_float2(w[R - m].x, w[R - m].y),
+                                                          make_float2(w[R + m].x, w[R + m].y)), lz01);
+                        lz23 = __ffma2_rn(czm, __fadd2_rn(make_float2(w[R - m].z, w[R - m].w),
+                                                          make_float2(w[R + m].z, w[R + m].w)), lz23);
+                        float2 sx01, sx23;
+                        if ((m & 1) == 0) {    // register pairs line up: packed adds
+                            sx01 = __fadd2_rn(make_float2(s[4 - m], s[5 - m]), make_float2(s[4 + m], s[5 + m]));
+                            sx23 = __fadd2_rn(make_float2(s[6 - m], s[7 - m]), make_float2(s[6 + m], s[7 + m]));
+                        } else {
+                            sx01 = make_float2(s[4 - m] + s[4 + m], s[5 - m] + s[5 + m]);
+                            sx23 = make_float2(s[6 - m] + s[6 + m], s[7 - m] + s[7 + m]);
+                        }
+                        lx01 = __ffma2_rn(cxm, sx01, lx01);
+                        lx23 = __ffma2_rn(cxm, sx23, lx23);
+                    }
+                    float2 lap01 = __fadd2_rn(lx01, lz01), lap23 = __fadd2_rn(lx23, lz23);
+                    if (src_here && (k == ks || k == ks + 1)) {
+                        const float4 sb = (k == ks) ? sb0 : sb1;
+                        lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);
+                        lap23 = __ffma2_rn(make_float2(sb.z, sb.w), make_float2(rn, rn), lap23);
+                    }
+                    const float ezk = ezs[r0 + k];
+                    float4 out;
+                    if (ezk == 0.f && ex_zero) {
+                        // u^{n+1} = 2 u^n - u^{n-1} + a lap
+                        const float2 two = make_float2(2.f, 2.f);
+                        const float2 o01 = __ffma2_rn(make_float2(av.x, av.y), lap01,
+                                                      __ffma2_rn(two, c01, make_float2(-um.x, -um.y)));
+                        const float2 o23 = __ffma2_rn(make_float2(av.z, av.w), lap23,
+                                                      __ffma2_rn(two, c23, make_float2(-um.z, -um.w)));
+                        out = make_float4(o01.x, o01.y, o23.x, o23.y);
+                    } else {
+                        // damped: u^{n+1} = d2 (2 u^n - d1 u^{n-1} + a lap), d1 = 1 - t, d2 = 1 / (1 + t)
+                        float2 e01, e23, f01, f23;
+                        if (ezk == 0.f) {
+                            e01 = d1x01; e23 = d1x23; f01 = d2x01; f23 = d2x23;
+                        } else if (ex_zero) {
+                            const float d1 = 1.f - ezk, d2 = __fdividef(1.f, 1.f + ezk);
+                            e01 = e23 = make_float2(d1, d1);
+                            f01 = f23 = make_float2(d2, d2);
+                        } else {
+                            e01 = make_float2(1.f - (ex.x + ezk), 1.f - (ex.y + ezk));
+                            e23 = make_float2(1.f - (ex.z + ezk), 1.f - (ex.w + ezk));
+                            f01 = make_float2(__fdividef(1.f, 1.f + (ex.x + ezk)), __fdividef(1.f, 1.f + (ex.y + ezk)));
+                            f23 = make_float2(__fdividef(1.f, 1.f + (ex.z + ezk)), __fdividef(1.f, 1.f + (ex.w + ezk)));
+                        }
+                        const float2 two = make_float2(2.f, 2.f);
+                        const float2 m01 = __fmul2_rn(e01, make_float2(-um.x, -um.y));
+                        const float2 m23 = __fmul2_rn(e23, make_float2(-um.z, -um.w));
+                        const float2 o01 = __fmul2_rn(f01, __ffma2_rn(make_float2(av.x, av.y), lap01,
+                                                                      __ffma2_rn(two, c01, m01)));
+                        const float2 o23 = __fmul2_rn(f23, __ffma2_rn(make_float2(av.z, av.w), lap23,
+                                                                      __ffma2_rn(two, c23, m23)));
+                        out = make_float4(o01.x, o01.y, o23.x, o23.y);
+                    }
+                    if (k >= kfirst && k < klast) {
+                        nxt[lr * sp4 + 1 + q] = out;
+                        // halo rows of the neighbours
+                        const int rr = r0 + k;
+                        if (top_item && prevA && rr < R) prevA[(rr + rows_c + R) * sp4 + 1 + q] = out;
+                        if (bot_item && nextA && rr >= rows_c - R)
+                            nextA[(rr - rows_c + R) * sp4 + 1 + q] = out;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
+            }
+        }
+        // receivers sample u^n (record n - 1)
+        if (n >= 1) {
+            const float *cf = reinterpret_cast<const float *>(cur);
+            const int sp = 4 * sp4;
+            if (!rec_loop) {
+                if (rec_mine) {
+                    const float d = rw[0] * cf[rk] + rw[1] * cf[rk + 1] + rw[2] * cf[rk + sp] +
+                                    rw[3] * cf[rk + sp + 1];
+                    if (in.traces) in.traces[(size_t)(n - 1) * in.nrec + tid] = d;
+                    if (dobs) {
+                        const float e = d - dring[((n - 1) % DEPTH) * ring_pitch + tid];
+                        accf = fmaf(e, e, accf);
+                    }
+                }
+            } else {
+                for (int r = tid; r < in.nrec; r += nth) {
+                    const float2 p = in.rec[r];
+                    int i0, j0;
+                    float w4[4];
+                    corners(p.x, p.y, gs, i0, j0, w4);
+                    if (j0 < z0 || j0 >= z0 + my_rows) continue;
+                    const int k0 = (j0 - z0 + R) * sp + 4 + i0;
+                    const float d = w4[0] * cf[k0] + w4[1] * cf[k0 + 1] + w4[2] * cf[k0 + sp] +
+                                    w4[3] * cf[k0 + sp + 1];
+                    const size_t o = (size_t)(n - 1) * in.nrec + r;
+                    if (in.traces) in.traces[o] = d;
+                    if (dobs) {
+                        const float e = d - __ldg(dobs + o);
+                        accf = fmaf(e, e, accf);
+                    }
+                }
+            }
+            if ((n & 31) == 0) {        // keep the FP32 partial short, carry in FP64
+                acc += (double)accf;
+                accf = 0.f;
+            }
+        }
+        // this step's copies have landed; the barrier publishes them
+        cp_async_wait<0>();
+        cluster.sync();
+        float4 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    cp_async_wait<0>();
+    if (!dobs) accf = 0.f, acc = 0.0;
+    acc += (double)accf;
+    // fixed-order reduction: warps -> CTA -> cluster rank 0 (ranks in order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) wred[tid >> 5] = acc;
+    __syncthreads();
+    if (tid < 32) {
+        double v = (tid < nth / 32) ? wred[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (tid == 0) *cluster.map_shared_rank(cred + crank, 0) = v;
+    }
+    cluster.sync();
+    if (crank == 0 && tid == 0) {
+        double sum = 0.0;
+        for (int c = 0; c < C; ++c) sum += cred[c];
+        partial[in.out] = 0.5 * sum;
+    }
+}
+
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, 1)
+wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts,
+                     int n_inst, int *counter, int ring_pitch, double *partial)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ int s_q;
+    __shared__ double cred[16];
+    __shared__ double wred[NT / 32];
+    __shared__ GridDev sg;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    for (;;) {
+        if (crank == 0 && threadIdx.x == 0) {
+            const int q = atomicAdd(counter, 1);
+            for (int c = 0; c < C; ++c) *cluster.map_shared_rank(&s_q, c) = q;
+        }
+        cluster.sync();
+        const int q = s_q;
+        if (q >= n_inst) break;
+        const Inst in = insts[q];
+        if (threadIdx.x == 0) sg = grids[in.grid];
+        __syncthreads();
+        const int rows_c = (sg.NZ + C - 1) / C;
+        float4 *A4 = smem4;
+        float4 *B4 = A4 + (size_t)(rows_c + 2 * R) * (sg.NQ + 2);
+        float4 *M4 = B4 + (size_t)(rows_c + 2 * R) * (sg.NQ + 2);
+        float *ezs = reinterpret_cast<float *>(M4 + (size_t)rows_c * sg.NQ);
+        float *wring = ezs + (rows_c + 3) / 4 * 4;
+        float *dring = wring + 4 * ((DEPTH + 3) / 4);
+        resident_instance<R>(sg, in, A4, B4, M4, ezs, wring, dring, ring_pitch, C, crank, cluster,
+                             cred, wred, partial);
+    }
+}
+
+constexpr int RES_NT = 512;
+
+}  // namespace
+
+int resident_max_threads() { return RES_NT; }
+int resident_rows_per_thread() { return ROWS; }
+
+// two time levels with halo rows, the slab of the model field, its damping
+// rows, and the staging rings (wavelet samples, observed records of up to
+// ring_pitch receivers)
+size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch)
+{
+    const int rows_c = (g.NZ + C - 1) / C;
+    return sizeof(float4) * (2 * (size_t)(rows_c + 2 * g.R) * (g.NQ + 2) + (size_t)rows_c * g.NQ) +
+           sizeof(float) * ((rows_c + 3) / 4 * 4 + 4 * ((DEPTH + 3) / 4) + (size_t)DEPTH * ring_pitch);
+}
+
+// Does grid g run on a cluster of C CTAs?  Each CTA needs at least R rows (so
+// halos come from the nearest neighbour only), no CTA may be empty, the work
+// items must fit one thread each, and the two time levels plus the model slab
+// the shared memory.
+bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit)
+{
+    const int rows_c = (g.NZ + C - 1) / C;
+    if (rows_c < g.R || rows_c < ROWS) return false;
+    if ((C - 1) * rows_c >= g.NZ) return false;
+    const int nseg = (rows_c + ROWS - 1) / ROWS;
+    if (g.NQ * nseg > RES_NT) return false;
+    return resident_smem_bytes(g, C, ring_pitch) <= smem_limit;
+}
+
+namespace {
+template <int R>
+cudaError_t configure_r(size_t smem_bytes, int C)
+{
+    cudaError_t e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (C > 8)
+        e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+using ResidentFn = void (*)(const GridDev *, const Inst *, int, int *, int, double *);
+
+ResidentFn resident_fn(int R)
+{
+    if (R == 4) return wave_resident_kernel<4, RES_NT>;
+    if (R == 2) return wave_resident_kernel<2, RES_NT>;
+    return wave_resident_kernel<1, RES_NT>;
+}
+}  // namespace
+
+cudaError_t resident_configure(int R, size_t smem_bytes, int C)
+{
+    if (R == 4) return configure_r<4>(smem_bytes, C);
+    if (R == 2) return configure_r<2>(smem_bytes, C);
+    return configure_r<1>(smem_bytes, C);
+}
+
+int resident_max_clusters(int R, int C, int threads, size_t smem_bytes)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * 64, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem_bytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, resident_fn(R), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, int n_inst,
+                                 int *counter, int C, int n_clusters, int threads, int ring_pitch,
+                                 size_t smem_bytes, double *partial, cudaStream_t st)
+{
+    if (n_inst <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * n_clusters, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem_bytes;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, resident_fn(R), grids_dev, insts, n_inst, counter, ring_pitch,
+                              partial);
+}
+
+}  // namespace empso

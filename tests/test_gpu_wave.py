@@ -52,13 +52,25 @@ def _geometry(nx, nz, h, S, src_z, rec_z, off_grid=False):
     return shots, rec
 
 
+KINDS = [1, 2]   # streaming, resident (on-chip cluster) variants of the persistent launch
+
+
+def _use(ctx, kind):
+    ctx.set_kernel(kind)
+
+
+def _ran(ctx, kind):
+    assert ctx.last_launch()[0] == kind
+
+
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("order,nx,nz,pad,h", [
     (2, 37, 29, 7, 10.0),    # ragged: NX = 51, not a multiple of 4
     (4, 61, 45, 10, 12.5),
     (8, 70, 33, 9, 15.0),
     (8, 23, 19, 0, 10.0),    # no damping layer, rigid edges
 ])
-def test_traces_match_oracle(B, order, nx, nz, pad, h):
+def test_traces_match_oracle(B, kind, order, nx, nz, pad, h):
     vmax = 3200.0
     og = oracle.Grid(nx, nz, h, h, pad, order, 0.3, 12.0, vmax)
     vel = synth.layered_faulted_model(nx, nz, h, h, seed=order + nx, vmin=1500.0, vmax=vmax)
@@ -67,17 +79,20 @@ def test_traces_match_oracle(B, order, nx, nz, pad, h):
     _, ref = oracle.shot_batch(og, vel, shots, rec, [0] * 3, [nrec] * 3, want_traces=True)
     grid = B.make_grid(nx, nz, h, h, pad, order, 0.3, 12.0, 1500.0, vmax)
     ctx = B.Context([grid], rec)
+    _use(ctx, kind)
     dt, nt = ctx.grid_info(0)
     assert nt == og.nt and dt == pytest.approx(og.dt, rel=1e-6)
     out = torch.zeros(3 * og.nt * nrec, device="cuda")
     ctx.forward_traces(_dev(vel[None]), B.make_shots(shots, [0] * 3, [nrec] * 3), out)
+    _ran(ctx, kind)
     got = out.cpu().numpy().reshape(3, og.nt, nrec)
     for s in range(3):
         assert _rel_l2(got[s], ref[s]) < TRACE_TOL, (s, _rel_l2(got[s], ref[s]))
     ctx.close()
 
 
-def test_single_forward_two_layer(B):
+@pytest.mark.parametrize("kind", KINDS)
+def test_single_forward_two_layer(B, kind):
     """Two-layer model (1500/2500 m/s, interface at 500 m) on 101 x 101 at 10 m
     with a 20-cell damping layer, order 4, 10 Hz Ricker at (500, 20) m, 101
     receivers at 20 m, 0.5 s; observed data from the model with +5 % velocity."""
@@ -93,9 +108,11 @@ def test_single_forward_two_layer(B):
     _, tr_ref = oracle.shot_batch(og, true, shots, rec, [0], [nx], want_traces=True)
     grid = B.make_grid(nx, nz, h, h, 20, 4, 0.5, 10.0, 1500.0, 2625.0)
     ctx = B.Context([grid], rec)
+    _use(ctx, kind)
     sh = B.make_shots(shots, [0], [nx])
     tr = torch.zeros(og.nt * nx, device="cuda")
     ctx.forward_traces(_dev(true[None]), sh, tr)
+    _ran(ctx, kind)
     assert _rel_l2(tr.cpu().numpy().reshape(og.nt, nx), tr_ref[0]) < TRACE_TOL
     mis = torch.zeros(1, dtype=torch.float64, device="cuda")
     ctx.eval_models(_dev(true[None]), sh, _dev(obs[0].ravel()), mis)
@@ -131,7 +148,8 @@ def _oracle_fitness(og, parts, kz, kx, mode, vmin, vmax, shots, rec, rb, rc, dob
     return np.array(out)
 
 
-def test_eval_fitness_particles(B):
+@pytest.mark.parametrize("kind", KINDS)
+def test_eval_fitness_particles(B, kind):
     nx, nz, h, pad = 77, 35, 20.0, 12
     vmin, vmax = 1500.0, 4700.0
     og = oracle.Grid(nx, nz, h, h, pad, 8, 0.8, 6.0, vmax)
@@ -144,9 +162,11 @@ def test_eval_fitness_particles(B):
     ref = _oracle_fitness(og, parts, 4, 8, 0, vmin, vmax, shots, rec, rb, rc, obs)
     grid = B.make_grid(nx, nz, h, h, pad, 8, 0.8, 6.0, vmin, vmax)
     ctx = B.Context([grid], rec)
+    _use(ctx, kind)
     mis = torch.zeros(6, dtype=torch.float64, device="cuda")
     dobs = _dev(np.concatenate([o.ravel() for o in obs]))
     ctx.eval_fitness(_dev(parts), B.make_shots(shots, rb, rc), dobs, mis)
+    _ran(ctx, kind)
     e = 0.5 * sum(np.sum(o ** 2) for o in obs)
     _check_misfit(mis.cpu().numpy(), ref, [e] * 6)
     # the same call again gives the same bits (fixed reduction order)
@@ -156,7 +176,8 @@ def test_eval_fitness_particles(B):
     ctx.close()
 
 
-def test_uneven_batch_two_grids(B):
+@pytest.mark.parametrize("kind", KINDS)
+def test_uneven_batch_two_grids(B, kind):
     """One launch over instances of two grid classes (coarse 40 m / 3 Hz / long
     record, fine 20 m / 6 Hz), weighted misfit sum in fixed shot order."""
     vmin, vmax = 1500.0, 4700.0
@@ -186,6 +207,7 @@ def test_uneven_batch_two_grids(B):
         ref += _oracle_fitness(og, parts, 4, 8, 0, vmin, vmax, shots_all[gi], recs[gi], [0, 0],
                                [nrec] * 2, obs_all[gi], weights=w[2 * gi:2 * gi + 2])
     ctx = B.Context(grids, np.concatenate(rec_table))
+    _use(ctx, kind)
     n0 = len(recs[0])
     xz = np.concatenate(shots_all)
     sh = B.make_shots(xz, [0, 0, n0, n0], [n0, n0, len(recs[1]), len(recs[1])],
@@ -193,6 +215,7 @@ def test_uneven_batch_two_grids(B):
     dobs = _dev(np.concatenate([o.ravel() for ob in obs_all for o in ob]))
     mis = torch.zeros(5, dtype=torch.float64, device="cuda")
     ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+    _ran(ctx, kind)
     e = sum(wi * 0.5 * np.sum(o ** 2) for wi, o in zip(w, [o for ob in obs_all for o in ob]))
     _check_misfit(mis.cpu().numpy(), ref, [e] * 5)
     ctx.close()
@@ -233,36 +256,52 @@ def test_edge_cases(B):
     ctx.close()
 
 
-@pytest.mark.parametrize("S_check", [2])
-def test_full_size_sampled(B, S_check):
+_FULL = {}
+
+
+def _full_size_reference():
+    """Oracle observed data and the misfits of particles 0 and P-1 for the
+    plain EMPSO workload (computed once per session: 48 full-size shots)."""
+    if not _FULL:
+        wl = synth.workloads()["empso-461x151-P32-S16"]
+        gs = wl.grids[0]
+        og = oracle.Grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmax)
+        S = wl.shots_per_grid[0]
+        shots = synth.shot_line(S, (gs.nx - 1) * gs.hx, wl.src_z)
+        rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
+        nrec = len(rec)
+        true = synth.layered_faulted_model(gs.nx, gs.nz, gs.hx, gs.hz, seed=wl.seed_model)
+        _, obs = oracle.shot_batch(og, true, shots, rec, [0] * S, [nrec] * S, want_traces=True)
+        parts = synth.random_particles(wl.P, gs.kx * gs.kz, wl.xmin, wl.xmax, seed=wl.seed_pso)
+        sel = [0, wl.P - 1]
+        ref = _oracle_fitness(og, parts[sel], gs.kz, gs.kx, 0, gs.vmin, gs.vmax, shots, rec,
+                              [0] * S, [nrec] * S, obs)
+        _FULL.update(wl=wl, gs=gs, og=og, S=S, shots=shots, rec=rec, obs=np.stack(obs),
+                     parts=parts, sel=sel, ref=ref)
+    return _FULL
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_full_size_sampled(B, kind):
     """The 461 x 151 / 20 m / order 8 / 3 s / 6 Hz grid of the plain EMPSO
     workload with 32 particles x 16 shots in one launch (the benchmarked launch
     configuration); particles 0 and 31 are recomputed by the oracle (all 16
     shots each)."""
-    wl = synth.workloads()["empso-461x151-P32-S16"]
-    gs = wl.grids[0]
-    og = oracle.Grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmax)
-    S = wl.shots_per_grid[0]
-    Lx = (gs.nx - 1) * gs.hx
-    shots = synth.shot_line(S, Lx, wl.src_z)
-    rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
+    F = _full_size_reference()
+    wl, gs, S, rec, obs = F["wl"], F["gs"], F["S"], F["rec"], F["obs"]
     nrec = len(rec)
-    true = synth.layered_faulted_model(gs.nx, gs.nz, gs.hx, gs.hz, seed=wl.seed_model)
     grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
                        gs.vmax, kx=gs.kx, kz=gs.kz)
     ctx = B.Context([grid], rec)
-    sh = B.make_shots(shots, [0] * S, [nrec] * S)
-    _, obs = oracle.shot_batch(og, true, shots, rec, [0] * S, [nrec] * S, want_traces=True)
-    dobs = _dev(np.concatenate([o.ravel() for o in obs]))
-    obs = np.stack(obs)
-    parts = synth.random_particles(wl.P, gs.kx * gs.kz, wl.xmin, wl.xmax, seed=wl.seed_pso)
+    _use(ctx, kind)
+    sh = B.make_shots(F["shots"], [0] * S, [nrec] * S)
+    dobs = _dev(obs.ravel())
     mis = torch.zeros(wl.P, dtype=torch.float64, device="cuda")
-    ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+    ctx.eval_fitness(_dev(F["parts"]), sh, dobs, mis)
+    # the default picks the on-chip kernel for this grid
+    assert ctx.last_launch()[0] == (2 if kind == 0 else kind)
     got = mis.cpu().numpy()
-    sel = [0, wl.P - 1][:S_check]
-    ref = _oracle_fitness(og, parts[sel], gs.kz, gs.kx, 0, gs.vmin, gs.vmax, shots, rec,
-                          [0] * S, [nrec] * S, list(obs))
-    e = 0.5 * np.sum(obs ** 2)
-    _check_misfit(got[sel], ref, [e] * len(sel))
+    e = 0.5 * np.sum(obs.astype(np.float64) ** 2)
+    _check_misfit(got[F["sel"]], F["ref"], [e] * 2)
     assert np.all(np.isfinite(got)) and np.all(got > 0)
     ctx.close()
