@@ -26,11 +26,6 @@ namespace {
 
 constexpr int ROWS = 8;
 
-__device__ __forceinline__ float comp(const float4 &v, int l)
-{
-    return l == 0 ? v.x : (l == 1 ? v.y : (l == 2 ? v.z : v.w));
-}
-
 __device__ __forceinline__ void set_comp(float4 &v, int l, float x)
 {
     if (l == 0) v.x = x;
