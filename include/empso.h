@@ -213,6 +213,34 @@ empso_status empso_set_timing(empso_ctx *ctx, int32_t enable);
  * timed call ran since timing was enabled. */
 empso_status empso_read_timing(empso_ctx *ctx, double *ms3);
 
+/* Misfits of M gridded models on one grid WITHOUT ANY ALLOCATION.  The paper
+ * has no counterpart: this entry point exists for callers that may not
+ * allocate device memory - code running where the CUDA allocator must not be
+ * touched (a host that owns and budgets all device memory itself, a plugin
+ * inside another runtime's memory pool, a real-time loop that forbids
+ * allocation after start-up).  It needs no context.
+ *
+ * grid: host; rec_xz: host [nrec_total][2] (<= 1024 receivers); vel: device
+ * [M][nz][nx]; shots: host [S] (<= 64, all with grid_id 0); d_obs: device,
+ * concatenation over shots of [nt][nrec_s]; misfit: device [M].  Same result
+ * as eval_models (same kernels, streaming variant).
+ *
+ * Scratch: a fixed 16 MiB device array inside the library (held by every GPU
+ * that loads it, until exit).  It must hold the model fields of all M models
+ * plus two wavefield buffers of at least one instance; larger requests return
+ * EMPSO_UNSUPPORTED with the needed size in empso_last_error(NULL).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the call
+ * clears what must start at zero itself); calls that overlap on the GPU -
+ * different streams, or different host threads, on one device - race on it
+ * and must be serialised by the caller.  Errors: INVALID_ARG, UNSUPPORTED,
+ * CUDA_ERROR; message in empso_last_error(NULL). */
+empso_status eval_models_noalloc(const empso_grid *grid, const float *rec_xz,
+                                 int32_t nrec_total, const float *vel, int32_t M,
+                                 const empso_shot *shots, int32_t S,
+                                 const float *d_obs, double *misfit, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *empso_status_string(empso_status s);
 

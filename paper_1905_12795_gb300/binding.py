@@ -27,8 +27,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
 
 EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "forward_traces",
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
-           "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_set_timing", "empso_read_timing", "empso_status_string",
-           "empso_last_error"]
+           "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
+           "empso_status_string", "empso_last_error"]
 
 
 class EmpsoGrid(ctypes.Structure):
@@ -89,6 +89,8 @@ def load():
     L.empso_last_launch.argtypes = [_vp, P(_i32), P(_i32)]
     L.empso_set_timing.argtypes = [_vp, _i32]
     L.empso_read_timing.argtypes = [_vp, P(_f64)]
+    L.eval_models_noalloc.argtypes = [P(EmpsoGrid), P(_f32), _i32, _vp, _i32, P(EmpsoShot), _i32,
+                                      _vp, _vp, _vp]
     L.empso_status_string.argtypes = [_i32]
     L.empso_status_string.restype = ctypes.c_char_p
     L.empso_last_error.argtypes = [_vp]
@@ -126,6 +128,19 @@ def make_shots(shot_xz, rec_begin, rec_count, grid_ids=None, weights=None):
                            int(rec_count[s]), 0 if grid_ids is None else int(grid_ids[s]),
                            1.0 if weights is None else float(weights[s]))
     return arr
+
+
+def eval_models_noalloc(grid: EmpsoGrid, rec_xz, vel, shots, d_obs, misfit):
+    """Allocation-free misfit of gridded models (no context; fixed scratch
+    inside the library).  vel, d_obs, misfit: CUDA tensors; rec_xz: host
+    array [N][2]; shots: ``make_shots`` array on grid 0."""
+    L = load()
+    rec = np.ascontiguousarray(np.asarray(rec_xz, dtype=np.float32).reshape(-1, 2))
+    rc = L.eval_models_noalloc(ctypes.byref(grid), rec.ctypes.data_as(ctypes.POINTER(_f32)),
+                               rec.shape[0], _ptr(vel), vel.shape[0], shots, len(shots),
+                               _ptr(d_obs), _ptr(misfit), _stream())
+    if rc != 0:
+        raise EmpsoError(rc, L.empso_last_error(None).decode())
 
 
 class Context:

@@ -446,6 +446,8 @@ void free_ctx(empso_ctx *c)
 
 }  // namespace
 
+void empso::set_global_error(const char *msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char *empso_status_string(empso_status s)

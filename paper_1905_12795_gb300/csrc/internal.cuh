@@ -81,6 +81,9 @@ cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *in
                                  int *counter, int C, int n_clusters, int threads, int ring_pitch,
                                  size_t smem_bytes, double *partial, cudaStream_t st);
 
+// Message returned by empso_last_error(NULL) for calls made without a context.
+void set_global_error(const char *msg);
+
 // Swarm state on the device.
 struct PsoDev {
     int P, D, NM, em_start, em_enabled;
