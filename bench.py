@@ -5,8 +5,11 @@ Workload (the headline configuration): 461 x 151 grid at 20 m with a 40-cell
 damping layer (541 x 231 padded), 8th order in space, 3 s record (1414 steps),
 6 Hz Ricker, seeded synthetic layered/faulted model (1500-4700 m/s), particle =
 4 x 8 control nodes (natural cubic spline), swarm of 32, 16 shots, 461
-receivers, FP32 wavefields.  One step = eval_fitness over all 32 x 16
-(particle, shot) instances in one persistent launch + one EMPSO step.
+receivers, FP32 wavefields.  One step = one EMPSO generation through the
+public API (empso_generation): a replay of one CUDA graph that interpolates
+the 32 particles, models all 32 x 16 (particle, shot) instances in one
+persistent launch (kernel and cluster size picked by the autotuner on this
+batch first), reduces the misfits and runs the EMPSO step.
 
 Prints one JSON line.  value = grid-point updates per second over the padded
 grid (whole job); fitness_evals_per_s alongside.  The L2 is flushed between
@@ -53,6 +56,10 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-particles", type=int, default=2)
+    ap.add_argument("--case", default=None,
+                    help="P,S: small profiling case on the workload's grid (no JSON line)")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 streaming, 2 on-chip")
+    ap.add_argument("--reps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -82,25 +89,28 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _wave_source_hash():
+_KERNEL_SOURCES = {"wave_kernel": "wave.cu", "wave_resident_kernel": "wave_resident.cu"}
+
+
+def _wave_source_hash(kernel):
     h = hashlib.sha256()
-    for f in ("wave.cu", "internal.cuh"):
+    for f in (_KERNEL_SOURCES[kernel], "internal.cuh"):
         with open(os.path.join(ROOT, "paper_1905_12795_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile(workload):
-    """DRAM bytes per launch of the modelling kernel from the committed ncu
+def _traffic_from_profile(kernel):
+    """DRAM bytes per launch of the modelling kernel from its committed ncu
     summary, or None when absent or taken on another version of the kernel."""
-    path = os.path.join(ROOT, "profiles", "wave_kernel_empso-461x151.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_empso-461x151.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
     hsh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    if not m or not hsh or hsh.group(1) != _wave_source_hash():
+    if not m or not hsh or hsh.group(1) != _wave_source_hash(kernel):
         return None
     return float(m.group(1))
 
@@ -235,17 +245,21 @@ def run_ours(a):
     x = torch.zeros(wl.P, K, device=dev)
     mis = torch.zeros(wl.P, dtype=torch.float64, device=dev)
     ctx.pso_init(x)
+    # pick the kernel / cluster size on this batch, then run generations as
+    # replays of one captured CUDA graph (fitness of all instances + EMPSO step)
+    tuned = ctx.autotune(x, sh, dobs, mis)
+    ctx.pso_init(x)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    ctx.set_timing(True)
 
     def step():
-        ctx.eval_fitness(x, sh, dobs, mis)
-        ctx.pso_step(mis, x)
+        ctx.generation(sh, dobs, mis)
 
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
-    ctx.set_timing(True)
+    launch = ctx.last_launch()
     clocks = _Clocks(torch.cuda.current_device()) if rank == 0 else None
     if dist:
         dist.barrier()
@@ -265,7 +279,6 @@ def run_ours(a):
         wave_ms.append(ctx.read_timing()[1])
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    ctx.set_timing(False)
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], device=dev)
@@ -273,13 +286,10 @@ def run_ours(a):
         total_ms = t.item()
         dist.barrier()
 
-    # end-to-end through the public API: inputs from pinned host memory each
-    # step, misfit read back each step
-    x_host = x.cpu().pin_memory()
+    # end-to-end through the public API: the step's input (the observed
+    # traces) copied from pinned host memory every step, the fitness read back
     dobs_host = dobs.cpu().pin_memory()
     mis_host = torch.zeros(wl.P, dtype=torch.float64).pin_memory()
-    x_e2e = torch.empty_like(x)
-    dobs_e2e = torch.empty_like(dobs)
     torch.cuda.synchronize()
     e2e_ms = []
     for _ in range(a.steps):
@@ -287,14 +297,13 @@ def run_ours(a):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        x_e2e.copy_(x_host, non_blocking=True)
-        dobs_e2e.copy_(dobs_host, non_blocking=True)
-        ctx.eval_fitness(x_e2e, sh, dobs_e2e, mis)
-        ctx.pso_step(mis, x_e2e)
+        dobs.copy_(dobs_host, non_blocking=True)
+        ctx.generation(sh, dobs, mis)
         mis_host.copy_(mis, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
+    ctx.set_timing(False)
     e2e_total = sum(e2e_ms)
     if dist:
         t = torch.tensor([e2e_total], device=dev)
@@ -308,7 +317,8 @@ def run_ours(a):
     wave_mean = float(np.mean(wave_ms))
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_UPDATE * upd_step / (wave_mean / 1e3) / 1e9
-    traffic = _traffic_from_profile(a.workload)
+    kname = "wave_resident_kernel" if launch[0] == 2 else "wave_kernel"
+    traffic = _traffic_from_profile(kname)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -327,10 +337,15 @@ def run_ours(a):
                        "timed steps", "parallelism": f"replicas x{world}"},
             "fitness_evals_per_s": evals,
             "e2e": {"value": e2e_value, "unit": "grid-pt updates/s",
-                    "h2d_bytes_per_step": int(x.numel() * 4 + dobs.numel() * 4),
+                    "h2d_bytes_per_step": int(dobs.numel() * 4),
                     "d2h_bytes_per_step": int(mis.numel() * 8),
                     "fitness_evals_per_s": world * wl.P * a.steps / (e2e_total / 1e3)},
-            "roofline": {"kernel": "wave_kernel", "bound": "hbm", "achieved": achieved,
+            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
+                       "cluster_ctas": launch[1], "autotuned": list(tuned),
+                       "step": "CUDA graph: interpolation, persistent modelling launch, "
+                               "misfit reduction, EMPSO step"},
+            "roofline": {"kernel": kname,
+                         "bound": "hbm", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": BYTES_PER_UPDATE * upd_step,
@@ -345,9 +360,40 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_case(a):
+    """P particles x S shots of the workload's grid through eval_fitness, with
+    the kernel time of each repetition (used for profiler captures)."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    P, S = (int(v) for v in a.case.split(","))
+    wl, gs, _, _, rec, _ = _setup(a.workload)
+    shots = synth.shot_line(S, (gs.nx - 1) * gs.hx, wl.src_z)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
+                       gs.vmax, kx=gs.kx, kz=gs.kz, mode=gs.mode)
+    ctx = B.Context([grid], rec)
+    ctx.set_kernel(a.kernel)
+    _, nt = ctx.grid_info(0)
+    sh = B.make_shots(shots, [0] * S, [len(rec)] * S)
+    dobs = torch.zeros(S * nt * len(rec), device="cuda")
+    x = torch.tensor(synth.random_particles(P, gs.kx * gs.kz, wl.xmin, wl.xmax, 1),
+                     dtype=torch.float32, device="cuda")
+    mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+    ctx.set_timing(True)
+    upd = P * S * _updates_per_instance(gs, nt)
+    for r in range(a.reps):
+        ctx.eval_fitness(x, sh, dobs, mis)
+        torch.cuda.synchronize()
+        ms = ctx.read_timing()[1]
+        print(f"rep {r}: modelling kernel {ms:.3f} ms, {upd / ms / 1e6:.1f} G updates/s, "
+              f"launch {ctx.last_launch()}", flush=True)
+    ctx.close()
+
+
 def main():
     a = _args()
-    if a.impl == "reference":
+    if a.case:
+        run_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -179,6 +179,35 @@ empso_status pso_set_state(empso_ctx *ctx, const double *x, const double *v,
                            const double *p, const double *pf, int32_t g,
                            int32_t k, void *stream);
 
+/* One whole EMPSO generation as a CUDA graph: fitness of the swarm's current
+ * positions (as eval_fitness, on every shot) followed by pso_step.  The first
+ * call for a given shot list, d_obs and misfit_out pointer (and kernel
+ * settings) plans the launch - it may allocate workspace and synchronises
+ * `stream` - and captures the work into a graph; later calls replay that
+ * graph on `stream` with one launch.  d_obs: device, as for eval_fitness;
+ * misfit_out: device [P] doubles receiving this generation's fitness, or
+ * NULL.  The swarm dimension must equal the grids' control-node count.
+ * The shots' host array is read at capture time only. */
+empso_status empso_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S,
+                              const float *d_obs, double *misfit_out, void *stream);
+
+/* Autotuner: times the streaming kernel and the on-chip kernel at every
+ * cluster size the batch fits (one warm-up and one timed launch each, CUDA
+ * events on `stream`) on this exact batch (particles device [P][K], shots,
+ * d_obs; misfit device [P] is used as scratch output), and keeps the fastest
+ * for every later batch with the same grids, shot counts and P.  The choice
+ * is returned in *kind_out / *cluster_out (host, may be NULL) and appended to
+ * the tuning cache file if one is set.  Synchronises `stream`. */
+empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
+                            const empso_shot *shots, int32_t S, const float *d_obs,
+                            double *misfit, int32_t *kind_out, int32_t *cluster_out,
+                            void *stream);
+
+/* Tuning cache: a JSON-lines file (one object per tuned batch: gpu, key,
+ * kind, cluster, ms).  Entries of this GPU are loaded now and used for
+ * matching batches; empso_autotune appends to it.  NULL or "" disables it. */
+empso_status empso_set_tuning_cache(empso_ctx *ctx, const char *path);
+
 /* Modelling kernel selection for the persistent launch:
  *   EMPSO_KERNEL_AUTO      on-chip variant when every grid of the batch fits a
  *                          cluster of <= 8 CTAs, else the streaming variant;

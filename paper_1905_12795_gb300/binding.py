@@ -28,6 +28,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
 EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "forward_traces",
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
            "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
+           "empso_generation", "empso_autotune", "empso_set_tuning_cache",
            "empso_status_string", "empso_last_error"]
 
 
@@ -89,6 +90,9 @@ def load():
     L.empso_last_launch.argtypes = [_vp, P(_i32), P(_i32)]
     L.empso_set_timing.argtypes = [_vp, _i32]
     L.empso_read_timing.argtypes = [_vp, P(_f64)]
+    L.empso_generation.argtypes = [_vp, P(EmpsoShot), _i32, _vp, _vp, _vp]
+    L.empso_autotune.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp, P(_i32), P(_i32), _vp]
+    L.empso_set_tuning_cache.argtypes = [_vp, ctypes.c_char_p]
     L.eval_models_noalloc.argtypes = [P(EmpsoGrid), P(_f32), _i32, _vp, _i32, P(EmpsoShot), _i32,
                                       _vp, _vp, _vp]
     L.empso_status_string.argtypes = [_i32]
@@ -228,6 +232,24 @@ class Context:
         ms = (_f64 * 3)()
         self._check(self._L.empso_read_timing(self._h, ms))
         return tuple(ms)
+
+    def generation(self, shots, d_obs, misfit_out=None):
+        """One EMPSO generation (fitness + step), captured as a CUDA graph on
+        the first call for these shots/buffers and replayed afterwards."""
+        self._check(self._L.empso_generation(self._h, shots, len(shots), _ptr(d_obs),
+                                             _ptr(misfit_out), _stream()))
+
+    def autotune(self, particles, shots, d_obs, misfit):
+        """Time every kernel / cluster size on this batch; keep the fastest.
+        Returns (kind, cluster)."""
+        k, c = _i32(), _i32()
+        self._check(self._L.empso_autotune(self._h, _ptr(particles), particles.shape[0], shots,
+                                           len(shots), _ptr(d_obs), _ptr(misfit), ctypes.byref(k),
+                                           ctypes.byref(c), _stream()))
+        return k.value, c.value
+
+    def set_tuning_cache(self, path):
+        self._check(self._L.empso_set_tuning_cache(self._h, (path or "").encode()))
 
     def pso_init(self, particles_out=None):
         self._check(self._L.pso_init(self._h, _ptr(particles_out), _stream()))

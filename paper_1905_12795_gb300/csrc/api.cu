@@ -5,7 +5,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -56,6 +59,21 @@ struct empso_ctx {
     PsoDev pso{};
     double *pso_mem = nullptr;
     int *pso_int = nullptr;
+
+    // tuned (kind, cluster) choices by batch signature, and the cache file
+    std::map<std::string, std::pair<int, int>> tuned;
+    std::string tune_cache;
+
+    // captured generations (eval + EMPSO step), one per shape and buffers
+    struct GraphEntry {
+        std::string key;
+        cudaGraphExec_t exec = nullptr;
+        unsigned char *table = nullptr;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
+    float *xf = nullptr;            // float copy of the swarm positions [P][D]
+    double *gen_misfit = nullptr;   // misfit of the last captured generation [P]
 
     // kernel timing
     bool timing = false;
@@ -261,52 +279,93 @@ struct Models {
     int M = 0;
 };
 
-// Build and run one persistent modelling launch over all M x S instances.
-empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shots, int S,
-                       const float *d_obs, float *traces, double *misfit, cudaStream_t st)
+// Everything the host decides about one persistent modelling launch.
+struct Plan {
+    int M = 0, S = 0;
+    long long n_inst = 0, maxfield = 0;
+    std::vector<long long> fbase;      // per grid: offset of its M model fields, -1 if unused
+    bool resident = false;
+    int resR = 0, resC = 0, res_threads = 0, res_clusters = 0, ring_pitch = 0;
+    size_t res_smem = 0;
+    int n_ctas = 0;
+    const Inst *insts = nullptr;       // device instance table
+    const float *weights = nullptr;    // device shot weights
+};
+
+// Signature of a batch for the tuned-choice table: the grids its shots use
+// (with their sizes and orders), their shot counts, and the model count.
+std::string batch_key(const empso_ctx *ctx, const empso_shot *shots, int S, int M)
+{
+    std::vector<int> count(ctx->grids.size(), 0);
+    for (int s = 0; s < S; ++s) ++count[shots[s].grid_id];
+    std::string k = "M" + std::to_string(M);
+    for (size_t g = 0; g < count.size(); ++g) {
+        if (!count[g]) continue;
+        const GridDev &d = ctx->grids[g].dev;
+        k += "|" + std::to_string(d.NX) + "x" + std::to_string(d.NZ) + "o" + std::to_string(2 * d.R) +
+             "t" + std::to_string(d.nt) + "s" + std::to_string(count[g]);
+    }
+    return k;
+}
+
+// Choose the kernel, size the workspace and build the instance table.  With
+// `table` the table is copied synchronously into that device buffer (graph
+// capture); otherwise it goes through the pinned staging buffer on `st`.
+empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shots, int S,
+                        const float *d_obs, float *traces, Plan &p, unsigned char *table,
+                        cudaStream_t st)
 {
     const int M = mod.M;
     const int ng = (int)ctx->grids.size();
-    // per-shot offsets into d_obs / traces (concatenation over shots of [nt][nrec])
+    p.M = M;
+    p.S = S;
     std::vector<long long> doff(S + 1, 0);
     for (int s = 0; s < S; ++s)
         doff[s + 1] = doff[s] + (long long)ctx->grids[shots[s].grid_id].dev.nt * shots[s].nrec;
-    // model fields: for each used grid, M fields
-    std::vector<long long> fbase(ng, -1);
-    long long ftotal = 0, maxfield = 0;
+    p.fbase.assign(ng, -1);
+    long long ftotal = 0;
+    p.maxfield = 0;
     for (int s = 0; s < S; ++s) {
         const int gid = shots[s].grid_id;
-        if (fbase[gid] < 0) {
-            fbase[gid] = ftotal;
+        if (p.fbase[gid] < 0) {
+            p.fbase[gid] = ftotal;
             ftotal += (long long)M * ctx->grids[gid].dev.field;
-            maxfield = std::max(maxfield, ctx->grids[gid].dev.field);
+            p.maxfield = std::max(p.maxfield, ctx->grids[gid].dev.field);
         }
     }
-    const long long n_inst = (long long)M * S;
-    if (n_inst > (1LL << 30)) return fail(ctx, EMPSO_INVALID_ARG, "too many instances");
+    p.n_inst = (long long)M * S;
+    if (p.n_inst > (1LL << 30)) return fail(ctx, EMPSO_INVALID_ARG, "too many instances");
     empso_status rc;
-    // on-chip path: the smallest cluster that every grid of the batch fits
-    int resC = 0, res_threads = 0, res_clusters = 0, resR = -1, ring_pitch = 0;
-    size_t res_smem = 0;
+
+    // kernel and cluster size: explicit settings, else the tuned choice, else
+    // the on-chip kernel with the cluster size that keeps the most SMs busy
+    int kind = ctx->kernel_kind, forcedC = ctx->forced_C;
+    if (kind == EMPSO_KERNEL_AUTO && forcedC == 0) {
+        auto it = ctx->tuned.find(batch_key(ctx, shots, S, M));
+        if (it != ctx->tuned.end()) {
+            kind = it->second.first;
+            forcedC = it->second.second;
+        }
+    }
+    int resR = -1;
     for (int gid = 0; gid < ng; ++gid) {   // one stencil radius per on-chip launch
-        if (fbase[gid] < 0) continue;
+        if (p.fbase[gid] < 0) continue;
         const int R = ctx->grids[gid].dev.R;
         resR = (resR < 0 || resR == R) ? R : 0;
     }
-    if (ctx->kernel_kind != EMPSO_KERNEL_STREAMING && resR > 0) {
-        // every cluster size the batch fits; keep the one that keeps the most
-        // SMs busy (co-resident clusters x C, capped by the instance count)
+    p.resident = false;
+    if (kind != EMPSO_KERNEL_STREAMING && resR > 0) {
         long long best_sms = 0;
         int nrec_max = 0;
         for (int s = 0; s < S; ++s) nrec_max = std::max(nrec_max, (int)shots[s].nrec);
-        ring_pitch = std::min(nrec_max, resident_max_threads());
+        const int ring_pitch = nrec_max;
         for (int C = 1; C <= 16; ++C) {
-            if (ctx->forced_C > 0 && C != ctx->forced_C) continue;
+            if (forcedC > 0 && C != forcedC) continue;
             bool ok = true;
             size_t sm = 0;
             int items = 32;
             for (int gid = 0; gid < ng && ok; ++gid) {
-                if (fbase[gid] < 0) continue;
+                if (p.fbase[gid] < 0) continue;
                 const GridDev &g = ctx->grids[gid].dev;
                 ok = resident_fits(g, C, ring_pitch, ctx->smem_optin);
                 sm = std::max(sm, resident_smem_bytes(g, C, ring_pitch));
@@ -316,40 +375,42 @@ empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shot
             }
             if (!ok) continue;
             const int threads = (items + 31) / 32 * 32;
-            const int nc = (int)std::min<long long>(resident_max_clusters(resR, C, threads, sm), n_inst);
+            const int nc = (int)std::min<long long>(resident_max_clusters(resR, C, threads, sm), p.n_inst);
             const long long sms = (long long)nc * C;
             if (nc > 0 && sms > best_sms) {
                 best_sms = sms;
-                resC = C;
-                res_smem = sm;
-                res_threads = threads;
-                res_clusters = nc;
+                p.resident = true;
+                p.resR = resR;
+                p.resC = C;
+                p.res_smem = sm;
+                p.res_threads = threads;
+                p.res_clusters = nc;
+                p.ring_pitch = ring_pitch;
             }
         }
     }
-    if (ctx->kernel_kind == EMPSO_KERNEL_RESIDENT && res_clusters <= 0)
+    if (kind == EMPSO_KERNEL_RESIDENT && !p.resident)
         return fail(ctx, EMPSO_UNSUPPORTED,
                     "the batch does not fit the on-chip kernel (grid too large or mixed orders)");
-    const bool resident = res_clusters > 0;
     const int max_ctas = ctx->sm_count * ctx->wave_ctas_per_sm;
-    const int n_ctas = (int)std::min<long long>(n_inst, max_ctas);
+    p.n_ctas = (int)std::min<long long>(p.n_inst, max_ctas);
     if ((rc = grow(ctx, (void **)&ctx->fields, &ctx->fields_cap, sizeof(float) * ftotal,
                    sizeof(float))) != EMPSO_OK)
         return rc;
-    if (!resident &&
+    if (!p.resident &&
         (rc = grow(ctx, (void **)&ctx->slots, &ctx->slots_cap,
-                   sizeof(float) * 2 * maxfield * n_ctas, sizeof(float))) != EMPSO_OK)
+                   sizeof(float) * 2 * p.maxfield * p.n_ctas, sizeof(float))) != EMPSO_OK)
         return rc;
-    if ((rc = grow(ctx, (void **)&ctx->partial, &ctx->partial_cap, sizeof(double) * n_inst,
+    if ((rc = grow(ctx, (void **)&ctx->partial, &ctx->partial_cap, sizeof(double) * p.n_inst,
                    sizeof(double))) != EMPSO_OK)
         return rc;
-    const size_t inst_bytes = sizeof(Inst) * n_inst;
+    const size_t inst_bytes = sizeof(Inst) * p.n_inst;
     const size_t wofs = (inst_bytes + 255) / 256 * 256;
     if ((rc = grow_stage(ctx, wofs + sizeof(float) * S)) != EMPSO_OK) return rc;
 
     // instance table, longest work first so the dynamic queue balances
-    std::vector<long long> order(n_inst);
-    for (long long q = 0; q < n_inst; ++q) order[q] = q;
+    std::vector<long long> order(p.n_inst);
+    for (long long q = 0; q < p.n_inst; ++q) order[q] = q;
     auto work = [&](long long q) {
         const GridDev &g = ctx->grids[shots[q % S].grid_id].dev;
         return (double)g.field * g.nt;
@@ -359,13 +420,13 @@ empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shot
     CK(ctx, cudaEventSynchronize(ctx->stage_free));  // previous upload has left the buffer
     Inst *hi = reinterpret_cast<Inst *>(ctx->stage_host);
     const long long per_model = doff[S];
-    for (long long k = 0; k < n_inst; ++k) {
+    for (long long k = 0; k < p.n_inst; ++k) {
         const long long q = order[k];
         const int m = (int)(q / S), s = (int)(q % S);
         const empso_shot &sh = shots[s];
         const GridDev &g = ctx->grids[sh.grid_id].dev;
         Inst in{};
-        in.a = ctx->fields + fbase[sh.grid_id] + (long long)m * g.field;
+        in.a = ctx->fields + p.fbase[sh.grid_id] + (long long)m * g.field;
         in.dobs = d_obs ? d_obs + doff[s] : nullptr;
         in.traces = traces ? traces + (long long)m * per_model + doff[s] : nullptr;
         in.rec = ctx->rec_dev + sh.rec_begin;
@@ -378,43 +439,79 @@ empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shot
     }
     float *wh = reinterpret_cast<float *>(ctx->stage_host + wofs);
     for (int s = 0; s < S; ++s) wh[s] = shots[s].weight;
-    CK(ctx, cudaMemcpyAsync(ctx->stage_dev, ctx->stage_host, wofs + sizeof(float) * S,
-                            cudaMemcpyHostToDevice, st));
-    CK(ctx, cudaEventRecord(ctx->stage_free, st));
+    unsigned char *dst = table ? table : ctx->stage_dev;
+    if (table) {
+        CK(ctx, cudaMemcpy(table, ctx->stage_host, wofs + sizeof(float) * S, cudaMemcpyHostToDevice));
+    } else {
+        CK(ctx, cudaMemcpyAsync(ctx->stage_dev, ctx->stage_host, wofs + sizeof(float) * S,
+                                cudaMemcpyHostToDevice, st));
+        CK(ctx, cudaEventRecord(ctx->stage_free, st));
+    }
+    p.insts = reinterpret_cast<const Inst *>(dst);
+    p.weights = reinterpret_cast<const float *>(dst + wofs);
+    return EMPSO_OK;
+}
 
-    if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[0], st));
-    // model fields
+size_t table_bytes(long long n_inst, int S)
+{
+    return (sizeof(Inst) * n_inst + 255) / 256 * 256 + sizeof(float) * S;
+}
+
+// Timing event on `st`; inside a stream capture it becomes an event-record
+// node that records whenever the graph runs.
+cudaError_t mark(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    return cudaEventRecord(ev, st);
+}
+
+// Enqueue the planned launch: model fields, queue reset, persistent
+// modelling kernel, misfit reduction (when `misfit` is given).
+empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, double *misfit,
+                           cudaStream_t st)
+{
+    const int ng = (int)ctx->grids.size();
+    if (ctx->timing) CK(ctx, mark(ctx->tev[0], st));
     for (int gid = 0; gid < ng; ++gid) {
-        if (fbase[gid] < 0) continue;
+        if (p.fbase[gid] < 0) continue;
         const GridDev &g = ctx->grids[gid].dev;
-        float *dst = ctx->fields + fbase[gid];
-        if (mod.particles) CK(ctx, launch_interp(g, mod.particles, M, dst, g.field, nullptr, st));
-        else CK(ctx, launch_vel_to_field(g, mod.vel, M, dst, g.field, st));
+        float *dst = ctx->fields + p.fbase[gid];
+        if (mod.particles) CK(ctx, launch_interp(g, mod.particles, p.M, dst, g.field, nullptr, st));
+        else CK(ctx, launch_vel_to_field(g, mod.vel, p.M, dst, g.field, st));
     }
     CK(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int), st));
-    if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[1], st));
-    if (resident) {
-        CK(ctx, launch_wave_resident(resR, ctx->grids_dev, reinterpret_cast<const Inst *>(ctx->stage_dev),
-                                     (int)n_inst, ctx->counter, resC, res_clusters, res_threads,
-                                     ring_pitch, res_smem, ctx->partial, st));
+    if (ctx->timing) CK(ctx, mark(ctx->tev[1], st));
+    if (p.resident) {
+        CK(ctx, launch_wave_resident(p.resR, ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter,
+                                     p.resC, p.res_clusters, p.res_threads, p.ring_pitch, p.res_smem,
+                                     ctx->partial, st));
         ctx->last_path = 2;
-        ctx->last_C = resC;
+        ctx->last_C = p.resC;
     } else {
-        CK(ctx, launch_wave(ctx->grids_dev, reinterpret_cast<const Inst *>(ctx->stage_dev),
-                            (int)n_inst, ctx->counter, ctx->slots, 2 * maxfield, n_ctas,
-                            ctx->wave_threads, ctx->partial, st));
+        CK(ctx, launch_wave(ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter, ctx->slots,
+                            2 * p.maxfield, p.n_ctas, ctx->wave_threads, ctx->partial, st));
         ctx->last_path = 1;
         ctx->last_C = 1;
     }
-    if (ctx->timing) CK(ctx, cudaEventRecord(ctx->tev[2], st));
-    if (misfit)
-        CK(ctx, launch_finalize(ctx->partial, reinterpret_cast<const float *>(ctx->stage_dev + wofs),
-                                M, S, misfit, st));
+    if (ctx->timing) CK(ctx, mark(ctx->tev[2], st));
+    if (misfit) CK(ctx, launch_finalize(ctx->partial, p.weights, p.M, p.S, misfit, st));
     if (ctx->timing) {
-        CK(ctx, cudaEventRecord(ctx->tev[3], st));
+        CK(ctx, mark(ctx->tev[3], st));
         ctx->timed = true;
     }
     return EMPSO_OK;
+}
+
+empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shots, int S,
+                       const float *d_obs, float *traces, double *misfit, cudaStream_t st)
+{
+    Plan p;
+    empso_status rc = plan_batch(ctx, mod, shots, S, d_obs, traces, p, nullptr, st);
+    if (rc) return rc;
+    return enqueue_batch(ctx, mod, p, misfit, st);
 }
 
 void free_ctx(empso_ctx *c)
@@ -437,6 +534,13 @@ void free_ctx(empso_ctx *c)
     cudaFree(c->counter);
     cudaFree(c->pso_mem);
     cudaFree(c->pso_int);
+    cudaFree(c->xf);
+    cudaFree(c->gen_misfit);
+    for (auto &e : c->graphs) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        cudaFree(e.table);
+    }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->stage_host) cudaFreeHost(c->stage_host);
     if (c->stage_free) cudaEventDestroy(c->stage_free);
     for (auto &e : c->tev)
@@ -554,7 +658,9 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         ctx->pcfg = p;
         const size_t PD = (size_t)p.P * p.D;
         if ((rc = ck(cudaMalloc(&ctx->pso_mem, sizeof(double) * (3 * PD + p.P + 2 * p.D)), "swarm")) ||
-            (rc = ck(cudaMalloc(&ctx->pso_int, sizeof(int) * (p.P + 2)), "swarm ints")))
+            (rc = ck(cudaMalloc(&ctx->pso_int, sizeof(int) * (p.P + 2)), "swarm ints")) ||
+            (rc = ck(cudaMalloc(&ctx->xf, sizeof(float) * PD), "positions")) ||
+            (rc = ck(cudaMalloc(&ctx->gen_misfit, sizeof(double) * p.P), "generation misfit")))
             return bail(rc);
         PsoDev &s = ctx->pso;
         s.P = p.P;
@@ -576,12 +682,15 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         s.xmax = bounds + p.D;
         s.order = ctx->pso_int;
         s.gk = ctx->pso_int + p.P;
+        s.xf = ctx->xf;
         if ((rc = ck(cudaMemcpy(bounds, xmin, sizeof(double) * p.D, cudaMemcpyHostToDevice), "xmin")) ||
             (rc = ck(cudaMemcpy(bounds + p.D, xmax, sizeof(double) * p.D, cudaMemcpyHostToDevice),
                      "xmax")) ||
             (rc = ck(cudaMemset(ctx->pso_int, 0, sizeof(int) * (p.P + 2)), "swarm ints")))
             return bail(rc);
     }
+    if ((rc = ck(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream")))
+        return bail(rc);
     if ((rc = ck(cudaDeviceSynchronize(), "setup kernels"))) return bail(rc);
     *out = ctx;
     return EMPSO_OK;
@@ -736,6 +845,201 @@ empso_status pso_set_state(empso_ctx *ctx, const double *x, const double *v, con
     memcpy(ctx->stage_host, gk, sizeof gk);
     CK(ctx, cudaMemcpyAsync(ctx->pso.gk, ctx->stage_host, sizeof gk, cudaMemcpyHostToDevice, st));
     CK(ctx, cudaEventRecord(ctx->stage_free, st));
+    CK(ctx, launch_xf_from_x(ctx->pso, st));
+    return EMPSO_OK;
+}
+
+empso_status empso_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S,
+                              const float *d_obs, double *misfit_out, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm");
+    if (!d_obs) return fail(ctx, EMPSO_INVALID_ARG, "d_obs is NULL");
+    empso_status rc = check_shots(ctx, shots, S, -1);
+    if (rc) return rc;
+    for (int s = 0; s < S; ++s) {
+        const empso_grid &g = ctx->grids[shots[s].grid_id].spec;
+        if (g.kx * g.kz != ctx->pso.D)
+            return fail(ctx, EMPSO_INVALID_ARG, "swarm dimension differs from the grids' control nodes");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // the captured graph depends on the shots, the buffers, the kernel choice
+    // and whether kernel timing is on
+    std::string key = batch_key(ctx, shots, S, ctx->pso.P);
+    {
+        std::ostringstream os;
+        os << "|" << (const void *)d_obs << "|" << (const void *)misfit_out << "|k" << ctx->kernel_kind
+           << "c" << ctx->forced_C << "t" << ctx->timing;
+        for (int s = 0; s < S; ++s)
+            os << "|" << shots[s].sx << "," << shots[s].sz << "," << shots[s].rec_begin << ","
+               << shots[s].nrec << "," << shots[s].grid_id << "," << shots[s].weight;
+        key += os.str();
+    }
+    empso_ctx::GraphEntry *ge = nullptr;
+    for (auto &e : ctx->graphs)
+        if (e.key == key) ge = &e;
+    if (!ge) {
+        Models mod;
+        mod.particles = ctx->xf;
+        mod.M = ctx->pso.P;
+        empso_ctx::GraphEntry e;
+        e.key = key;
+        CK(ctx, cudaMalloc(&e.table, table_bytes((long long)ctx->pso.P * S, S)));
+        Plan p;
+        // planning allocates and uploads outside the capture; the graph holds
+        // only kernels and a memset
+        CK(ctx, cudaStreamSynchronize(st));
+        if ((rc = plan_batch(ctx, mod, shots, S, d_obs, nullptr, p, e.table, ctx->cap_stream))) {
+            cudaFree(e.table);
+            return rc;
+        }
+        cudaGraph_t graph = nullptr;
+        CK(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_batch(ctx, mod, p, ctx->gen_misfit, ctx->cap_stream);
+        cudaError_t ce = cudaSuccess;
+        if (!rc) ce = launch_pso_step(ctx->pso, ctx->gen_misfit, nullptr, ctx->cap_stream);
+        if (!rc && ce == cudaSuccess && misfit_out)
+            ce = cudaMemcpyAsync(misfit_out, ctx->gen_misfit, sizeof(double) * ctx->pso.P,
+                                 cudaMemcpyDeviceToDevice, ctx->cap_stream);
+        cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc || ce != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaFree(e.table);
+            if (rc) return rc;
+            return fail(ctx, EMPSO_CUDA_ERROR, std::string("graph capture: ") +
+                                                  cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        }
+        ce = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            cudaFree(e.table);
+            return fail(ctx, EMPSO_CUDA_ERROR, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        ctx->graphs.push_back(e);
+        ge = &ctx->graphs.back();
+    }
+    CK(ctx, cudaGraphLaunch(ge->exec, st));
+    return EMPSO_OK;
+}
+
+namespace {
+
+// JSON-lines tuning cache: one {"gpu", "key", "kind", "cluster", "ms"} object
+// per line; later lines override earlier ones.
+std::string gpu_name(int dev)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    return prop.name;
+}
+
+std::string json_str(const std::string &line, const std::string &field)
+{
+    const std::string pat = "\"" + field + "\": \"";
+    size_t a = line.find(pat);
+    if (a == std::string::npos) return "";
+    a += pat.size();
+    size_t b = line.find('"', a);
+    return b == std::string::npos ? "" : line.substr(a, b - a);
+}
+
+long json_int(const std::string &line, const std::string &field, long dflt)
+{
+    const std::string pat = "\"" + field + "\": ";
+    size_t a = line.find(pat);
+    if (a == std::string::npos) return dflt;
+    return strtol(line.c_str() + a + pat.size(), nullptr, 10);
+}
+
+void load_tune_cache(empso_ctx *ctx)
+{
+    std::ifstream in(ctx->tune_cache);
+    const std::string gpu = gpu_name(ctx->device);
+    std::string line;
+    while (std::getline(in, line)) {
+        if (json_str(line, "gpu") != gpu) continue;
+        const std::string key = json_str(line, "key");
+        if (key.empty()) continue;
+        ctx->tuned[key] = {(int)json_int(line, "kind", 0), (int)json_int(line, "cluster", 0)};
+    }
+}
+
+}  // namespace
+
+empso_status empso_set_tuning_cache(empso_ctx *ctx, const char *path)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    ctx->tune_cache = path ? path : "";
+    if (!ctx->tune_cache.empty()) load_tune_cache(ctx);
+    return EMPSO_OK;
+}
+
+empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
+                            const empso_shot *shots, int32_t S, const float *d_obs,
+                            double *misfit, int32_t *kind_out, int32_t *cluster_out, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (P <= 0 || !particles || !d_obs || !misfit)
+        return fail(ctx, EMPSO_INVALID_ARG, "bad particles/d_obs/misfit");
+    empso_status rc = check_shots(ctx, shots, S, -1);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const std::string key = batch_key(ctx, shots, S, P);
+    ctx->tuned.erase(key);
+    const int save_kind = ctx->kernel_kind, save_C = ctx->forced_C;
+    Models mod;
+    mod.particles = particles;
+    mod.M = P;
+    cudaEvent_t e0, e1;
+    CK(ctx, cudaEventCreate(&e0));
+    CK(ctx, cudaEventCreate(&e1));
+    // candidates: the streaming kernel and every cluster size of the on-chip one
+    std::vector<std::pair<int, int>> cand = {{EMPSO_KERNEL_STREAMING, 0}};
+    for (int C = 1; C <= 16; ++C) cand.push_back({EMPSO_KERNEL_RESIDENT, C});
+    float best = 1e30f;
+    std::pair<int, int> choice = {EMPSO_KERNEL_AUTO, 0};
+    for (auto &c : cand) {
+        ctx->kernel_kind = c.first;
+        ctx->forced_C = c.second;
+        Plan p;
+        rc = plan_batch(ctx, mod, shots, S, d_obs, nullptr, p, nullptr, st);
+        if (rc == EMPSO_UNSUPPORTED) continue;   // this size does not fit the batch
+        if (rc) break;
+        if ((rc = enqueue_batch(ctx, mod, p, misfit, st))) break;   // warm-up
+        cudaEventRecord(e0, st);
+        if ((rc = enqueue_batch(ctx, mod, p, misfit, st))) break;
+        cudaEventRecord(e1, st);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) {
+            rc = fail(ctx, EMPSO_CUDA_ERROR, cudaGetErrorString(ce));
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            choice = {c.first, p.resident ? p.resC : 0};
+        }
+    }
+    ctx->err.clear();
+    ctx->kernel_kind = save_kind;
+    ctx->forced_C = save_C;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc && rc != EMPSO_UNSUPPORTED) return rc;
+    if (choice.first == EMPSO_KERNEL_AUTO) return fail(ctx, EMPSO_UNSUPPORTED, "no kernel fits the batch");
+    ctx->tuned[key] = choice;
+    if (kind_out) *kind_out = choice.first;
+    if (cluster_out) *cluster_out = choice.second;
+    if (!ctx->tune_cache.empty()) {
+        std::ofstream out(ctx->tune_cache, std::ios::app);
+        out << "{\"gpu\": \"" << gpu_name(ctx->device) << "\", \"key\": \"" << key
+            << "\", \"kind\": " << choice.first << ", \"cluster\": " << choice.second
+            << ", \"ms\": " << best << "}\n";
+    }
     return EMPSO_OK;
 }
 

@@ -94,9 +94,11 @@ struct PsoDev {
     double *pf;                  // [P]
     int *order;                  // [P]
     int *gk;                     // {g, k}
+    float *xf;                   // [P][D] float copy of x (what generations evaluate)
 };
 cudaError_t launch_pso_init(const PsoDev &s, float *particles_out, cudaStream_t st);
 cudaError_t launch_pso_step(const PsoDev &s, const double *misfit, float *particles_out,
                             cudaStream_t st);
+cudaError_t launch_xf_from_x(const PsoDev &s, cudaStream_t st);
 
 }  // namespace empso

@@ -6,6 +6,8 @@
 // functions the method needs (log and cos for Box-Muller normals) are written
 // here from their series, so the same inputs give the same bits on any IEEE
 // machine that evaluates the same sequence.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace empso {
@@ -154,6 +156,7 @@ __global__ void pso_init_kernel(PsoDev s, float *particles_out)
         s.x[e] = x;
         s.v[e] = vm * (2.0 * uv - 1.0);
         s.p[e] = x;
+        s.xf[e] = (float)x;
         if (particles_out) particles_out[e] = (float)x;
         if (d == 0) {
             s.pf[i] = __longlong_as_double(0x7ff0000000000000LL);
@@ -311,6 +314,7 @@ pso_step_kernel(PsoDev s, const double *misfit, float *particles_out)
             x = clampd(xi + vn, lo, hi);
         }
         s.x[e] = x;
+        s.xf[e] = (float)x;
         if (particles_out) particles_out[e] = (float)x;
     }
     if (tid == 0) {
@@ -328,6 +332,22 @@ cudaError_t launch_pso_init(const PsoDev &s, float *particles_out, cudaStream_t 
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
     pso_init_kernel<<<blocks, 256, 0, st>>>(s, particles_out);
+    return cudaGetLastError();
+}
+
+__global__ void xf_from_x_kernel(PsoDev s)
+{
+    const long long n = (long long)s.P * s.D;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        s.xf[e] = (float)s.x[e];
+}
+
+cudaError_t launch_xf_from_x(const PsoDev &s, cudaStream_t st)
+{
+    long long n = (long long)s.P * s.D;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    xf_from_x_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(s);
     return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ __device__ __forceinline__ void corners(float x, float z, const GridDev &g, int 
 
 template <int R>
 __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
-                                  float4 *M4, float *ezs, float *wring, float *dring, int ring_pitch,
+                                  float4 *M4, float *ezs, float *wring, float *dring, float4 *rec_w,
+                                  int *rec_k, int ring_pitch,
                                   int C, int crank, cg::cluster_group &cluster, double *cred,
                                   double *wred, double *partial)
 {
@@ -88,10 +89,16 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
 
     // zero both time levels (halos included) and load this slab of the model field
     for (int e = tid; e < 2 * srows * sp4; e += nth) A4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // model slab pre-scaled by f = 1 / (1 + t), t = (eta_x + eta_z) dt / 2, so
+    // that the damped update needs no division per point (see below)
     for (int e = tid; e < my_rows * NQ; e += nth) {
         const int r = e / NQ, qq = e % NQ;
-        M4[r * NQ + qq] =
+        const float4 av =
             __ldg(reinterpret_cast<const float4 *>(in.a + (size_t)(z0 + r + HALO) * pitch + HALO) + qq);
+        const float4 exq = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + qq);
+        const float ez = __ldg(gez + z0 + r + HALO);
+        M4[r * NQ + qq] = make_float4(av.x / (1.f + (exq.x + ez)), av.y / (1.f + (exq.y + ez)),
+                                      av.z / (1.f + (exq.z + ez)), av.w / (1.f + (exq.w + ez)));
     }
     for (int r = tid; r < my_rows; r += nth) ezs[r] = __ldg(gez + z0 + r + HALO);
 
@@ -111,11 +118,10 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
 
     float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
-    const bool ex_zero = ex.x == 0.f && ex.y == 0.f && ex.z == 0.f && ex.w == 0.f;
-    // rows without z-damping: t = ex per lane, constant over the instance
-    const float2 d1x01 = make_float2(1.f - ex.x, 1.f - ex.y), d1x23 = make_float2(1.f - ex.z, 1.f - ex.w);
-    const float2 d2x01 = make_float2(__fdividef(1.f, 1.f + ex.x), __fdividef(1.f, 1.f + ex.y));
-    const float2 d2x23 = make_float2(__fdividef(1.f, 1.f + ex.z), __fdividef(1.f, 1.f + ex.w));
+    // update weight g = 2 / (1 + t) of rows without z-damping: per lane,
+    // constant over the instance (g = 2 in the interior)
+    const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));
+    const float2 gx23 = make_float2(2.f / (1.f + ex.z), 2.f / (1.f + ex.w));
     float cx[R + 1], cz[R + 1];
 #pragma unroll
     for (int m = 0; m <= R; ++m) {
@@ -143,20 +149,20 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         }
     }
 
-    // receivers: one per thread, owned by the CTA holding the lower corner row
-    int rk = 0;
-    float rw[4] = {0.f, 0.f, 0.f, 0.f};
-    bool rec_mine = false;
-    if (tid < in.nrec) {
-        const float2 p = in.rec[tid];
-        int i0, j0;
-        corners(p.x, p.y, gs, i0, j0, rw);
-        rec_mine = j0 >= z0 && j0 < z0 + my_rows;
-        rk = (j0 - z0 + R) * (4 * sp4) + 4 + i0;          // float index in the shared slab
-    }
-    const bool rec_loop = in.nrec > nth;                 // more receivers than threads
+    // receivers: bilinear corners and weights of every receiver, computed once
+    // per instance; rec_k = float index of the lower-left corner in this CTA's
+    // slab, or -1 when another CTA holds the receiver's lower corner row
+    const int nrec = in.nrec;
     const float *__restrict__ dobs = in.dobs;
-    const bool ring_rec = rec_mine && dobs && !rec_loop;
+    for (int r = tid; r < nrec; r += nth) {
+        const float2 pr = in.rec[r];
+        int i0, j0;
+        float w4[4];
+        corners(pr.x, pr.y, gs, i0, j0, w4);
+        const bool mine = j0 >= z0 && j0 < z0 + my_rows;
+        rec_k[r] = mine ? (j0 - z0 + R) * (4 * sp4) + 4 + i0 : -1;
+        rec_w[r] = make_float4(w4[0], w4[1], w4[2], w4[3]);
+    }
     // staging prologue: the wavelet sample of step 0
     if (tid == 0 && nt > 0) cp_async4(wring, gwav);
     cp_async_commit();
@@ -164,6 +170,7 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     float accf = 0.f;
     double acc = 0.0;
     (void)NX;
+    (void)ring_pitch;
 
     cluster.sync();                                      // zeroed everywhere before halo stores
 
@@ -187,8 +194,10 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         {
             const int iw = n + 1, ir = n;
             if (tid == 0 && iw < nt) cp_async4(wring + iw % DEPTH, gwav + iw);
-            if (ring_rec && ir < nt)
-                cp_async4(dring + (ir % DEPTH) * ring_pitch + tid, dobs + (size_t)ir * in.nrec + tid);
+            if (dobs && ir < nt)
+                for (int r = tid; r < nrec; r += nth)
+                    if (rec_k[r] >= 0)
+                        cp_async4(dring + (ir % DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
             cp_async_commit();
         }
         if (n < nt && active) {
@@ -241,40 +250,22 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
                         lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);
                         lap23 = __ffma2_rn(make_float2(sb.z, sb.w), make_float2(rn, rn), lap23);
                     }
+                    // u^{n+1} = [2 u^n - (1 - t) u^{n-1} + a lap] / (1 + t)
+                    //         = g (u^n - u^{n-1}) + u^{n-1} + (a f) lap,  g = 2 f, f = 1 / (1 + t)
+                    // (a f is the pre-scaled model slab); one branch-free form for
+                    // interior and damping layer, g per lane and row
                     const float ezk = ezs[r0 + k];
-                    float4 out;
-                    if (ezk == 0.f && ex_zero) {
-                        // u^{n+1} = 2 u^n - u^{n-1} + a lap
-                        const float2 two = make_float2(2.f, 2.f);
-                        const float2 o01 = __ffma2_rn(make_float2(av.x, av.y), lap01,
-                                                      __ffma2_rn(two, c01, make_float2(-um.x, -um.y)));
-                        const float2 o23 = __ffma2_rn(make_float2(av.z, av.w), lap23,
-                                                      __ffma2_rn(two, c23, make_float2(-um.z, -um.w)));
-                        out = make_float4(o01.x, o01.y, o23.x, o23.y);
-                    } else {
-                        // damped: u^{n+1} = d2 (2 u^n - d1 u^{n-1} + a lap), d1 = 1 - t, d2 = 1 / (1 + t)
-                        float2 e01, e23, f01, f23;
-                        if (ezk == 0.f) {
-                            e01 = d1x01; e23 = d1x23; f01 = d2x01; f23 = d2x23;
-                        } else if (ex_zero) {
-                            const float d1 = 1.f - ezk, d2 = __fdividef(1.f, 1.f + ezk);
-                            e01 = e23 = make_float2(d1, d1);
-                            f01 = f23 = make_float2(d2, d2);
-                        } else {
-                            e01 = make_float2(1.f - (ex.x + ezk), 1.f - (ex.y + ezk));
-                            e23 = make_float2(1.f - (ex.z + ezk), 1.f - (ex.w + ezk));
-                            f01 = make_float2(__fdividef(1.f, 1.f + (ex.x + ezk)), __fdividef(1.f, 1.f + (ex.y + ezk)));
-                            f23 = make_float2(__fdividef(1.f, 1.f + (ex.z + ezk)), __fdividef(1.f, 1.f + (ex.w + ezk)));
-                        }
-                        const float2 two = make_float2(2.f, 2.f);
-                        const float2 m01 = __fmul2_rn(e01, make_float2(-um.x, -um.y));
-                        const float2 m23 = __fmul2_rn(e23, make_float2(-um.z, -um.w));
-                        const float2 o01 = __fmul2_rn(f01, __ffma2_rn(make_float2(av.x, av.y), lap01,
-                                                                      __ffma2_rn(two, c01, m01)));
-                        const float2 o23 = __fmul2_rn(f23, __ffma2_rn(make_float2(av.z, av.w), lap23,
-                                                                      __ffma2_rn(two, c23, m23)));
-                        out = make_float4(o01.x, o01.y, o23.x, o23.y);
+                    float2 g01 = gx01, g23 = gx23;
+                    if (ezk != 0.f) {
+                        g01 = make_float2(__fdividef(2.f, 1.f + (ex.x + ezk)), __fdividef(2.f, 1.f + (ex.y + ezk)));
+                        g23 = make_float2(__fdividef(2.f, 1.f + (ex.z + ezk)), __fdividef(2.f, 1.f + (ex.w + ezk)));
                     }
+                    const float2 um01 = make_float2(um.x, um.y), um23 = make_float2(um.z, um.w);
+                    const float2 o01 = __ffma2_rn(g01, __fadd2_rn(c01, make_float2(-um.x, -um.y)),
+                                                  __ffma2_rn(make_float2(av.x, av.y), lap01, um01));
+                    const float2 o23 = __ffma2_rn(g23, __fadd2_rn(c23, make_float2(-um.z, -um.w)),
+                                                  __ffma2_rn(make_float2(av.z, av.w), lap23, um23));
+                    const float4 out = make_float4(o01.x, o01.y, o23.x, o23.y);
                     if (k >= kfirst && k < klast) {
                         nxt[lr * sp4 + 1 + q] = out;
                         // halo rows of the neighbours
@@ -292,32 +283,16 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         if (n >= 1) {
             const float *cf = reinterpret_cast<const float *>(cur);
             const int sp = 4 * sp4;
-            if (!rec_loop) {
-                if (rec_mine) {
-                    const float d = rw[0] * cf[rk] + rw[1] * cf[rk + 1] + rw[2] * cf[rk + sp] +
-                                    rw[3] * cf[rk + sp + 1];
-                    if (in.traces) in.traces[(size_t)(n - 1) * in.nrec + tid] = d;
-                    if (dobs) {
-                        const float e = d - dring[((n - 1) % DEPTH) * ring_pitch + tid];
-                        accf = fmaf(e, e, accf);
-                    }
-                }
-            } else {
-                for (int r = tid; r < in.nrec; r += nth) {
-                    const float2 p = in.rec[r];
-                    int i0, j0;
-                    float w4[4];
-                    corners(p.x, p.y, gs, i0, j0, w4);
-                    if (j0 < z0 || j0 >= z0 + my_rows) continue;
-                    const int k0 = (j0 - z0 + R) * sp + 4 + i0;
-                    const float d = w4[0] * cf[k0] + w4[1] * cf[k0 + 1] + w4[2] * cf[k0 + sp] +
-                                    w4[3] * cf[k0 + sp + 1];
-                    const size_t o = (size_t)(n - 1) * in.nrec + r;
-                    if (in.traces) in.traces[o] = d;
-                    if (dobs) {
-                        const float e = d - __ldg(dobs + o);
-                        accf = fmaf(e, e, accf);
-                    }
+            for (int r = tid; r < nrec; r += nth) {
+                const int k0 = rec_k[r];
+                if (k0 < 0) continue;
+                const float4 w4 = rec_w[r];
+                const float d = w4.x * cf[k0] + w4.y * cf[k0 + 1] + w4.z * cf[k0 + sp] +
+                                w4.w * cf[k0 + sp + 1];
+                if (in.traces) in.traces[(size_t)(n - 1) * nrec + r] = d;
+                if (dobs) {
+                    const float e = d - dring[((n - 1) % DEPTH) * nrec + r];
+                    accf = fmaf(e, e, accf);
                 }
             }
             if ((n & 31) == 0) {        // keep the FP32 partial short, carry in FP64
@@ -385,8 +360,10 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float *ezs = reinterpret_cast<float *>(M4 + (size_t)rows_c * sg.NQ);
         float *wring = ezs + (rows_c + 3) / 4 * 4;
         float *dring = wring + 4 * ((DEPTH + 3) / 4);
-        resident_instance<R>(sg, in, A4, B4, M4, ezs, wring, dring, ring_pitch, C, crank, cluster,
-                             cred, wred, partial);
+        float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
+        int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
+        resident_instance<R>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, ring_pitch, C,
+                             crank, cluster, cred, wred, partial);
     }
 }
 
@@ -398,13 +375,15 @@ int resident_max_threads() { return RES_NT; }
 int resident_rows_per_thread() { return ROWS; }
 
 // two time levels with halo rows, the slab of the model field, its damping
-// rows, and the staging rings (wavelet samples, observed records of up to
-// ring_pitch receivers)
+// rows, the staging buffers (wavelet samples, observed records) and the
+// receiver tables, for shots of up to ring_pitch receivers
 size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch)
 {
     const int rows_c = (g.NZ + C - 1) / C;
     return sizeof(float4) * (2 * (size_t)(rows_c + 2 * g.R) * (g.NQ + 2) + (size_t)rows_c * g.NQ) +
-           sizeof(float) * ((rows_c + 3) / 4 * 4 + 4 * ((DEPTH + 3) / 4) + (size_t)DEPTH * ring_pitch);
+           sizeof(float) * ((rows_c + 3) / 4 * 4 + 4 * ((DEPTH + 3) / 4) +
+                            ((size_t)DEPTH * ring_pitch + 3) / 4 * 4) +
+           (sizeof(float4) + sizeof(int)) * (size_t)ring_pitch;
 }
 
 // Does grid g run on a cluster of C CTAs?  Each CTA needs at least R rows (so
