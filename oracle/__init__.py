@@ -29,7 +29,10 @@ itself lives in ``tests/test_oracle_*.py``):
   at phi = 4.
 * ``Swarm`` (EMPSO) - pinned: invariants of the EM rule and of Eq. 1-2,
   statistics of the mutation, sphere and Rastrigin minima reached.
-* ``mlp`` - pinned: central finite differences, closed-form first Adam step.
+* ``mlp`` (surrogate network, FP64 numpy) - pinned: central finite
+  differences, closed-form first Adam step, fit of a known function.
+* ``Swarm.step(f, rank)`` - EM sort keyed by ``rank`` (surrogate pre-screen)
+  while bests follow f - pinned by its invariants.
 """
 from __future__ import annotations
 
@@ -108,7 +111,7 @@ def lib():
         L.eo_chi.restype = _d
         L.eo_pso_init.argtypes = [ctypes.POINTER(_EoPso), _pd, _pd, _pd, _pd, _pd, _pd,
                                   _pi, _pi]
-        L.eo_pso_step.argtypes = [ctypes.POINTER(_EoPso), _pd, _pd, _pd, _pd, _pd, _pd,
+        L.eo_pso_step.argtypes = [ctypes.POINTER(_EoPso), _pd, _pd, _pd, _pd, _pd, _pd, _pd,
                                   _pd, _pi, _pi, _pi, _pi]
         _lib = L
     return _lib
@@ -334,10 +337,15 @@ class Swarm:
         self._g.value = int(g)
         self._k.value = int(k)
 
-    def step(self, f):
+    def step(self, f, rank=None):
+        """One generation; `rank` (optional) keys the EM sort instead of f."""
         f = _f64(f)
+        rk = None
+        if rank is not None:
+            rank = _f64(rank)
+            rk = _p(rank)
         em = ctypes.c_int(0)
-        lib().eo_pso_step(ctypes.byref(self.cfg), _p(self.xmin), _p(self.xmax), _p(f),
+        lib().eo_pso_step(ctypes.byref(self.cfg), _p(self.xmin), _p(self.xmax), _p(f), rk,
                           _p(self.x), _p(self.v), _p(self.p), _p(self.pf),
                           ctypes.byref(self._g), ctypes.byref(self._k),
                           _p(self.order, _pi), ctypes.byref(em))

@@ -619,21 +619,30 @@ void eo_pso_init(const eo_pso *c, const double *xmin, const double *xmax,
  *   1. k <- k + 1; non-finite fitness counts as +inf.
  *   2. personal bests: if f_i < pf_i (strict) then pf_i = f_i, p_i = x_i.
  *   3. global best g = argmin pf, ties to the lowest index.
- *   4. if EM is enabled and k >= em_start: ASF = stable ascending sort of f;
+ *   4. if EM is enabled and k >= em_start: ASF = stable ascending sort of f
+ *      (or of the rank keys, see below);
  *      its last NM = floor(nm_frac P) entries are the worst particles, whose
  *      positions become x_ld = g_d + 0.1 VR_d randn with probability p_em,
  *      else g_d; their velocities are unchanged.
  *   5. every other particle: Eq. 1 with constriction chi (Eq. 3), velocity
  *      clamped to [-vmax, vmax], Eq. 2, position clamped to [xmin, xmax].
- * `order` receives ASF (P ints) when EM ran, else the identity. */
+ * `order` receives ASF (P ints) when EM ran, else the identity.
+ * `rank_in` (may be NULL) replaces f as the key of the EM sort only: with a
+ * surrogate pre-screen, particles that were not modelled carry +inf fitness
+ * (no best update) and their predicted misfit as sort key. */
 void eo_pso_step(const eo_pso *c, const double *xmin, const double *xmax,
-                 const double *f_in, double *x, double *v, double *p, double *pf,
-                 int *g, int *k, int *order, int *em_ran)
+                 const double *f_in, const double *rank_in, double *x, double *v, double *p,
+                 double *pf, int *g, int *k, int *order, int *em_ran)
 {
     int P = c->P, D = c->D;
     *k = *k + 1;
     double *f = malloc(sizeof(double) * P);
+    double *key = malloc(sizeof(double) * P);
     for (int i = 0; i < P; ++i) f[i] = isfinite(f_in[i]) ? f_in[i] : INFINITY;
+    for (int i = 0; i < P; ++i) {
+        double r = rank_in ? rank_in[i] : f_in[i];
+        key[i] = isfinite(r) ? r : INFINITY;
+    }
     for (int i = 0; i < P; ++i) {
         if (f[i] < pf[i]) {
             pf[i] = f[i];
@@ -654,7 +663,7 @@ void eo_pso_step(const eo_pso *c, const double *xmin, const double *xmax,
         for (int a = 1; a < P; ++a) {
             int cur = order[a];
             int b = a - 1;
-            while (b >= 0 && f[order[b]] > f[cur]) {
+            while (b >= 0 && key[order[b]] > key[cur]) {
                 order[b + 1] = order[b];
                 --b;
             }
@@ -691,4 +700,5 @@ void eo_pso_step(const eo_pso *c, const double *xmin, const double *xmax,
     }
     free(mut);
     free(f);
+    free(key);
 }

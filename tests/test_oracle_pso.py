@@ -209,3 +209,25 @@ def test_paper_run_counts(orc):
             assert set(mut.tolist()) == set(np.argsort(f, kind="stable")[P - len(mut):].tolist())
     assert evals == int(gd["model_evaluations"])
     assert em_gens == G - int(gd["em_first_iteration"]) + 1
+
+
+def test_rank_keys_drive_em_only(orc):
+    # surrogate pre-screen: unevaluated particles have +inf fitness (no best
+    # update) and their predicted misfit as EM sort key
+    P, D = 12, 4
+    rng = np.random.default_rng(9)
+    s = orc.Swarm(P, D, -5.0, 5.0, em_start=1, nm_frac=0.25, seed=8)
+    x, v, p, pf = _state(P, D, rng)
+    s.set_state(x, v, p, pf, int(np.argmin(pf)), 3)
+    f = np.full(P, np.inf)
+    ev = np.array([0, 3, 7])
+    f[ev] = rng.uniform(0.5, 2.0, 3)
+    rank = rng.uniform(0, 10, P)
+    rank[ev] = f[ev]
+    s.step(f, rank)
+    improved = f < pf
+    assert np.array_equal(s.pf, np.where(improved, f, pf))
+    assert np.array_equal(s.order, np.argsort(rank, kind="stable"))
+    mutated = set(np.argsort(rank, kind="stable")[P - 3:].tolist())
+    for i in range(P):
+        assert np.array_equal(s.v[i], v[i]) == (i in mutated)
