@@ -208,6 +208,67 @@ empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
  * matching batches; empso_autotune appends to it.  NULL or "" disables it. */
 empso_status empso_set_tuning_cache(empso_ctx *ctx, const char *path);
 
+/* pso_step with a separate key for the elitist-mutation sort: `rank` (device
+ * [P], may be NULL = misfit) orders the particles for EM while `misfit` alone
+ * drives the personal and global bests.  Used by surrogate pre-screening,
+ * where particles that were not modelled carry misfit +inf and their
+ * predicted misfit as rank key. */
+empso_status pso_step_ranked(empso_ctx *ctx, const double *misfit, const double *rank,
+                             float *particles_out, int32_t *gbest_out, void *stream);
+
+/* ---- Surrogate pre-screening (not in the paper) ----------------------------
+ * A K -> H -> H -> 1 ReLU perceptron (K = swarm dimension) predicts the log
+ * misfit of a particle from its control nodes scaled to [-1, 1] with the
+ * swarm's bounds.  Dense layers run on BF16 tensor cores with FP32
+ * accumulation; master weights and Adam moments are FP32.  It is trained
+ * online on a device replay buffer of (particle, log misfit) pairs,
+ * standardised with the buffer's mean and deviation.  Parameters, flat FP32,
+ * in the order W1 [H][K], b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1]. */
+
+/* Create the network: hidden width H (multiple of 16, <= 1024), replay
+ * capacity (pairs), Adam learning rate, seed of the weights and minibatches.
+ * Needs a swarm.  Allocates; synchronises the device. */
+empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, float lr,
+                            uint64_t seed);
+
+/* Predicted log misfit: particles device [P][K] -> logphi device [P]. */
+empso_status surrogate_predict(empso_ctx *ctx, const float *particles, int32_t P, float *logphi,
+                               void *stream);
+
+/* Append pairs to the replay buffer (ring): particles device [n][K], misfit
+ * device [n]; pairs with a non-finite or non-positive misfit are skipped. */
+empso_status surrogate_add(empso_ctx *ctx, const float *particles, const double *misfit,
+                           int32_t n, void *stream);
+
+/* `steps` Adam steps on minibatches of `batch` pairs drawn uniformly from the
+ * buffer (Philox stream of the seed); refreshes the standardisation first. */
+empso_status surrogate_train(empso_ctx *ctx, int32_t steps, int32_t batch, void *stream);
+
+/* Read (get, device [n_params]) and/or overwrite (set) the FP32 parameters;
+ * *n_params (host, may be NULL) receives their count. */
+empso_status surrogate_params(empso_ctx *ctx, float *get, const float *set, int32_t *n_params,
+                              void *stream);
+
+/* Gradient of L = 1/(2n) sum (y - target)^2 on one batch, without updating:
+ * particles device [n][K] (raw positions), target device [n] (standardised
+ * units), grad device [n_params], loss device [1] (may be NULL). */
+empso_status surrogate_grad(empso_ctx *ctx, const float *particles, const float *target,
+                            int32_t n, float *grad, float *loss, void *stream);
+
+/* One surrogate-assisted EMPSO generation.  While the replay buffer holds
+ * fewer than `warm` pairs, every particle is modelled; afterwards only the
+ * round(keep_frac P) particles with the smallest predicted misfit are
+ * modelled (eval_fitness on them), their pairs join the buffer, the network
+ * takes `train_steps` Adam steps of `batch`, and pso_step_ranked moves the
+ * swarm with +inf fitness for the others and their predictions as EM keys.
+ * misfit_out: device [P] (may be NULL) = the fitness used (+inf where not
+ * modelled); *n_modelled (host, may be NULL) = particles modelled.
+ * Synchronises `stream` once (to read the buffer count). */
+empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S,
+                                  const float *d_obs, double keep_frac, int32_t warm,
+                                  int32_t train_steps, int32_t batch, double *misfit_out,
+                                  int32_t *n_modelled, void *stream);
+
 /* Modelling kernel selection for the persistent launch:
  *   EMPSO_KERNEL_AUTO      on-chip variant when every grid of the batch fits a
  *                          cluster of <= 8 CTAs, else the streaming variant;

@@ -29,6 +29,8 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
            "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
            "empso_generation", "empso_autotune", "empso_set_tuning_cache",
+           "pso_step_ranked", "surrogate_init", "surrogate_predict", "surrogate_add",
+           "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
            "empso_status_string", "empso_last_error"]
 
 
@@ -93,6 +95,15 @@ def load():
     L.empso_generation.argtypes = [_vp, P(EmpsoShot), _i32, _vp, _vp, _vp]
     L.empso_autotune.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp, P(_i32), P(_i32), _vp]
     L.empso_set_tuning_cache.argtypes = [_vp, ctypes.c_char_p]
+    L.pso_step_ranked.argtypes = [_vp, _vp, _vp, _vp, P(_i32), _vp]
+    L.surrogate_init.argtypes = [_vp, _i32, _i32, _f32, ctypes.c_uint64]
+    L.surrogate_predict.argtypes = [_vp, _vp, _i32, _vp, _vp]
+    L.surrogate_add.argtypes = [_vp, _vp, _vp, _i32, _vp]
+    L.surrogate_train.argtypes = [_vp, _i32, _i32, _vp]
+    L.surrogate_params.argtypes = [_vp, _vp, _vp, P(_i32), _vp]
+    L.surrogate_grad.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp]
+    L.surrogate_generation.argtypes = [_vp, P(EmpsoShot), _i32, _vp, _f64, _i32, _i32, _i32, _vp,
+                                       P(_i32), _vp]
     L.eval_models_noalloc.argtypes = [P(EmpsoGrid), P(_f32), _i32, _vp, _i32, P(EmpsoShot), _i32,
                                       _vp, _vp, _vp]
     L.empso_status_string.argtypes = [_i32]
@@ -250,6 +261,50 @@ class Context:
 
     def set_tuning_cache(self, path):
         self._check(self._L.empso_set_tuning_cache(self._h, (path or "").encode()))
+
+    def pso_step_ranked(self, misfit, rank, particles_out=None):
+        self._check(self._L.pso_step_ranked(self._h, _ptr(misfit), _ptr(rank), _ptr(particles_out),
+                                            None, _stream()))
+
+    # surrogate pre-screening
+    def surrogate_init(self, hidden=256, capacity=50000, lr=1e-3, seed=1):
+        self._check(self._L.surrogate_init(self._h, hidden, capacity, lr, seed))
+
+    def surrogate_predict(self, particles, logphi):
+        self._check(self._L.surrogate_predict(self._h, _ptr(particles), particles.shape[0],
+                                              _ptr(logphi), _stream()))
+
+    def surrogate_add(self, particles, misfit):
+        self._check(self._L.surrogate_add(self._h, _ptr(particles), _ptr(misfit),
+                                          particles.shape[0], _stream()))
+
+    def surrogate_train(self, steps, batch):
+        self._check(self._L.surrogate_train(self._h, steps, batch, _stream()))
+
+    def surrogate_n_params(self):
+        n = _i32()
+        self._check(self._L.surrogate_params(self._h, None, None, ctypes.byref(n), _stream()))
+        return n.value
+
+    def surrogate_get(self, out):
+        self._check(self._L.surrogate_params(self._h, _ptr(out), None, None, _stream()))
+
+    def surrogate_set(self, params):
+        self._check(self._L.surrogate_params(self._h, None, _ptr(params), None, _stream()))
+
+    def surrogate_grad(self, particles, target, grad, loss=None):
+        self._check(self._L.surrogate_grad(self._h, _ptr(particles), _ptr(target),
+                                           particles.shape[0], _ptr(grad), _ptr(loss), _stream()))
+
+    def surrogate_generation(self, shots, d_obs, keep_frac=0.25, warm=None, train_steps=20,
+                             batch=256, misfit_out=None):
+        """One surrogate-assisted generation; returns how many particles were modelled."""
+        n = _i32()
+        warm = self.pso.P if warm is None else warm
+        self._check(self._L.surrogate_generation(self._h, shots, len(shots), _ptr(d_obs), keep_frac,
+                                                 warm, train_steps, batch, _ptr(misfit_out),
+                                                 ctypes.byref(n), _stream()))
+        return n.value
 
     def pso_init(self, particles_out=None):
         self._check(self._L.pso_init(self._h, _ptr(particles_out), _stream()))

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <random>
 #include <map>
 #include <new>
 #include <sstream>
@@ -74,6 +75,17 @@ struct empso_ctx {
     cudaStream_t cap_stream = nullptr;
     float *xf = nullptr;            // float copy of the swarm positions [P][D]
     double *gen_misfit = nullptr;   // misfit of the last captured generation [P]
+
+    // surrogate network and the buffers of surrogate-assisted generations
+    bool has_sur = false;
+    SurDev sur;
+    std::vector<void *> sur_mem;
+    int *sel_rows = nullptr;        // [P] indices of the modelled particles
+    float *xk = nullptr;            // [P][D] their positions
+    double *fk = nullptr;           // [P] their misfits
+    double *fit_full = nullptr;     // [P] fitness, +inf where not modelled
+    double *rank_full = nullptr;    // [P] EM sort keys
+    float *logphi = nullptr;        // [P] predictions
 
     // kernel timing
     bool timing = false;
@@ -541,6 +553,7 @@ void free_ctx(empso_ctx *c)
         cudaFree(e.table);
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (void *p : c->sur_mem) cudaFree(p);
     if (c->stage_host) cudaFreeHost(c->stage_host);
     if (c->stage_free) cudaEventDestroy(c->stage_free);
     for (auto &e : c->tev)
@@ -1092,6 +1105,222 @@ empso_status empso_read_timing(empso_ctx *ctx, double *ms3)
         CK(ctx, cudaEventElapsedTime(&ms, ctx->tev[i], ctx->tev[i + 1]));
         ms3[i] = ms;
     }
+    return EMPSO_OK;
+}
+
+empso_status pso_step_ranked(empso_ctx *ctx, const double *misfit, const double *rank,
+                             float *particles_out, int32_t *gbest_out, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm");
+    if (!misfit) return fail(ctx, EMPSO_INVALID_ARG, "misfit is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(ctx, launch_pso_step(ctx->pso, misfit, particles_out, st, rank));
+    if (gbest_out) {
+        CK(ctx, cudaMemcpyAsync(gbest_out, ctx->pso.gk, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaStreamSynchronize(st));
+    }
+    return EMPSO_OK;
+}
+
+empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, float lr, uint64_t seed)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "the surrogate needs a swarm (its bounds)");
+    if (ctx->has_sur) return fail(ctx, EMPSO_INVALID_ARG, "surrogate already initialised");
+    if (hidden < 16 || hidden > 1024 || hidden % 16 || capacity < 1 || !(lr > 0))
+        return fail(ctx, EMPSO_INVALID_ARG, "need 16 <= hidden <= 1024 (multiple of 16), capacity >= 1, lr > 0");
+    SurDev &s = ctx->sur;
+    const int K = ctx->pso.D, H = hidden, P = ctx->pso.P;
+    s.K = K;
+    s.H = H;
+    s.cap = capacity;
+    s.rows_max = std::max(P, 1024);
+    s.off_W1 = 0;
+    s.off_b1 = (long long)H * K;
+    s.off_W2 = s.off_b1 + H;
+    s.off_b2 = s.off_W2 + (long long)H * H;
+    s.off_w3 = s.off_b2 + H;
+    s.off_b3 = s.off_w3 + H;
+    s.n_params = s.off_b3 + 1;
+    s.lr = lr;
+    s.seed = seed;
+    s.xmin = ctx->pso.xmin;
+    s.xmax = ctx->pso.xmax;
+    auto alloc = [&](void **p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess) ctx->sur_mem.push_back(*p);
+        return e;
+    };
+    const size_t R = s.rows_max;
+    const size_t np = s.n_params;
+    CK(ctx, alloc((void **)&s.p, 4 * np));
+    CK(ctx, alloc((void **)&s.g, 4 * np));
+    CK(ctx, alloc((void **)&s.m, 4 * np));
+    CK(ctx, alloc((void **)&s.v, 4 * np));
+    CK(ctx, alloc((void **)&s.W1b, 2 * (size_t)H * K));
+    CK(ctx, alloc((void **)&s.W2b, 2 * (size_t)H * H));
+    CK(ctx, alloc((void **)&s.Xb, 2 * R * K));
+    CK(ctx, alloc((void **)&s.A1b, 2 * R * H));
+    CK(ctx, alloc((void **)&s.dZb, 2 * R * H));
+    CK(ctx, alloc((void **)&s.Z1, 4 * R * H));
+    CK(ctx, alloc((void **)&s.Z2, 4 * R * H));
+    CK(ctx, alloc((void **)&s.dZf, 4 * R * H));
+    CK(ctx, alloc((void **)&s.dA, 4 * R * H));
+    CK(ctx, alloc((void **)&s.y, 4 * R));
+    CK(ctx, alloc((void **)&s.dy, 4 * R));
+    CK(ctx, alloc((void **)&s.tb, 4 * R));
+    CK(ctx, alloc((void **)&s.rows, 4 * R));
+    CK(ctx, alloc((void **)&s.loss, 4));
+    CK(ctx, alloc((void **)&s.stats, 8));
+    CK(ctx, alloc((void **)&s.xbuf, 4 * (size_t)capacity * K));
+    CK(ctx, alloc((void **)&s.ybuf, 4 * (size_t)capacity));
+    CK(ctx, alloc((void **)&s.count, 4));
+    CK(ctx, alloc((void **)&ctx->sel_rows, 4 * (size_t)P));
+    CK(ctx, alloc((void **)&ctx->xk, 4 * (size_t)P * K));
+    CK(ctx, alloc((void **)&ctx->fk, 8 * (size_t)P));
+    CK(ctx, alloc((void **)&ctx->fit_full, 8 * (size_t)P));
+    CK(ctx, alloc((void **)&ctx->rank_full, 8 * (size_t)P));
+    CK(ctx, alloc((void **)&ctx->logphi, 4 * (size_t)P));
+    // He-uniform weights (limit sqrt(6 / fan_in)), zero biases, from the seed
+    std::vector<float> h(np, 0.f);
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> u(-1.0, 1.0);
+    const double l1 = std::sqrt(6.0 / K), l2 = std::sqrt(6.0 / H);
+    for (long long i = 0; i < (long long)H * K; ++i) h[s.off_W1 + i] = (float)(l1 * u(rng));
+    for (long long i = 0; i < (long long)H * H; ++i) h[s.off_W2 + i] = (float)(l2 * u(rng));
+    for (long long i = 0; i < H; ++i) h[s.off_w3 + i] = (float)(l2 * u(rng));
+    const float stats0[2] = {0.f, 1.f};
+    CK(ctx, cudaMemcpy(s.p, h.data(), 4 * np, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemset(s.m, 0, 4 * np));
+    CK(ctx, cudaMemset(s.v, 0, 4 * np));
+    CK(ctx, cudaMemset(s.count, 0, 4));
+    CK(ctx, cudaMemcpy(s.stats, stats0, 8, cudaMemcpyHostToDevice));
+    CK(ctx, sur_refresh_bf16(s, 0));
+    CK(ctx, cudaDeviceSynchronize());
+    ctx->has_sur = true;
+    return EMPSO_OK;
+}
+
+#define NEED_SUR(ctx)                                                                   \
+    do {                                                                                \
+        if (!ctx) return EMPSO_INVALID_ARG;                                             \
+        ctx->err.clear();                                                               \
+        if (!ctx->has_sur) return fail(ctx, EMPSO_NOT_INITIALIZED, "no surrogate");      \
+    } while (0)
+
+empso_status surrogate_predict(empso_ctx *ctx, const float *particles, int32_t P, float *logphi,
+                               void *stream)
+{
+    NEED_SUR(ctx);
+    if (P < 0 || P > ctx->sur.rows_max || (P > 0 && (!particles || !logphi)))
+        return fail(ctx, EMPSO_INVALID_ARG, "bad particles/logphi or too many rows");
+    if (P == 0) return EMPSO_OK;
+    CK(ctx, sur_predict(ctx->sur, particles, P, logphi, (cudaStream_t)stream));
+    return EMPSO_OK;
+}
+
+empso_status surrogate_add(empso_ctx *ctx, const float *particles, const double *misfit, int32_t n,
+                           void *stream)
+{
+    NEED_SUR(ctx);
+    if (n < 0 || (n > 0 && (!particles || !misfit))) return fail(ctx, EMPSO_INVALID_ARG, "bad particles/misfit");
+    if (n == 0) return EMPSO_OK;
+    CK(ctx, sur_append(ctx->sur, particles, misfit, nullptr, n, (cudaStream_t)stream));
+    return EMPSO_OK;
+}
+
+empso_status surrogate_train(empso_ctx *ctx, int32_t steps, int32_t batch, void *stream)
+{
+    NEED_SUR(ctx);
+    if (steps < 0 || batch < 1 || batch > ctx->sur.rows_max)
+        return fail(ctx, EMPSO_INVALID_ARG, "need steps >= 0 and 1 <= batch <= max rows");
+    CK(ctx, sur_train(ctx->sur, steps, batch, (cudaStream_t)stream));
+    return EMPSO_OK;
+}
+
+empso_status surrogate_params(empso_ctx *ctx, float *get, const float *set, int32_t *n_params,
+                              void *stream)
+{
+    NEED_SUR(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 4 * (size_t)ctx->sur.n_params;
+    if (n_params) *n_params = (int32_t)ctx->sur.n_params;
+    if (get) CK(ctx, cudaMemcpyAsync(get, ctx->sur.p, bytes, cudaMemcpyDeviceToDevice, st));
+    if (set) {
+        CK(ctx, cudaMemcpyAsync(ctx->sur.p, set, bytes, cudaMemcpyDeviceToDevice, st));
+        CK(ctx, sur_refresh_bf16(ctx->sur, st));
+    }
+    return EMPSO_OK;
+}
+
+empso_status surrogate_grad(empso_ctx *ctx, const float *particles, const float *target, int32_t n,
+                            float *grad, float *loss, void *stream)
+{
+    NEED_SUR(ctx);
+    if (n < 1 || n > ctx->sur.rows_max || !particles || !target || !grad)
+        return fail(ctx, EMPSO_INVALID_ARG, "bad particles/target/grad");
+    cudaStream_t st = (cudaStream_t)stream;
+    SurDev &s = ctx->sur;
+    CK(ctx, sur_normalize(s, particles, nullptr, n, s.Xb, st));
+    CK(ctx, sur_backward(s, s.Xb, target, n, loss ? loss : s.loss, st));
+    CK(ctx, cudaMemcpyAsync(grad, s.g, 4 * (size_t)s.n_params, cudaMemcpyDeviceToDevice, st));
+    return EMPSO_OK;
+}
+
+empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S,
+                                  const float *d_obs, double keep_frac, int32_t warm,
+                                  int32_t train_steps, int32_t batch, double *misfit_out,
+                                  int32_t *n_modelled, void *stream)
+{
+    NEED_SUR(ctx);
+    if (!d_obs || !(keep_frac > 0 && keep_frac <= 1) || train_steps < 0 || batch < 1 ||
+        batch > ctx->sur.rows_max)
+        return fail(ctx, EMPSO_INVALID_ARG, "bad d_obs, keep fraction or training settings");
+    empso_status rc = check_shots(ctx, shots, S, -1);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    SurDev &s = ctx->sur;
+    const int P = ctx->pso.P, K = ctx->pso.D;
+    for (int i = 0; i < S; ++i) {
+        const empso_grid &g = ctx->grids[shots[i].grid_id].spec;
+        if (g.kx * g.kz != K)
+            return fail(ctx, EMPSO_INVALID_ARG, "swarm dimension differs from the grids' control nodes");
+    }
+    // how many pairs the replay buffer holds (host read: decides the branch)
+    int have = 0;
+    CK(ctx, cudaMemcpyAsync(&have, s.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    Models mod;
+    int k;
+    if (have < warm) {
+        // warm-up: model every particle
+        k = P;
+        mod.particles = ctx->xf;
+        mod.M = P;
+        if ((rc = run_batch(ctx, mod, shots, S, d_obs, nullptr, ctx->fit_full, st))) return rc;
+        CK(ctx, sur_append(s, ctx->xf, ctx->fit_full, nullptr, P, st));
+        CK(ctx, sur_train(s, train_steps, batch, st));
+        CK(ctx, launch_pso_step(ctx->pso, ctx->fit_full, nullptr, st, nullptr));
+    } else {
+        // pre-screen: model the keep_frac fraction with the smallest predictions
+        k = std::max(1, (int)std::lround(keep_frac * P));
+        CK(ctx, sur_predict(s, ctx->xf, P, ctx->logphi, st));
+        CK(ctx, sur_select(ctx->logphi, P, k, ctx->sel_rows, st));
+        CK(ctx, sur_gather(ctx->xf, ctx->sel_rows, k, K, ctx->xk, st));
+        mod.particles = ctx->xk;
+        mod.M = k;
+        if ((rc = run_batch(ctx, mod, shots, S, d_obs, nullptr, ctx->fk, st))) return rc;
+        CK(ctx, sur_append(s, ctx->xf, ctx->fk, ctx->sel_rows, k, st));
+        CK(ctx, sur_scatter(ctx->sel_rows, ctx->fk, k, ctx->logphi, P, ctx->fit_full, ctx->rank_full, st));
+        CK(ctx, sur_train(s, train_steps, batch, st));
+        CK(ctx, launch_pso_step(ctx->pso, ctx->fit_full, nullptr, st, ctx->rank_full));
+    }
+    if (misfit_out)
+        CK(ctx, cudaMemcpyAsync(misfit_out, ctx->fit_full, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
+    if (n_modelled) *n_modelled = k;
     return EMPSO_OK;
 }
 

@@ -2,6 +2,7 @@
 // library.  Not part of the public ABI (include/empso.h is).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -98,7 +99,41 @@ struct PsoDev {
 };
 cudaError_t launch_pso_init(const PsoDev &s, float *particles_out, cudaStream_t st);
 cudaError_t launch_pso_step(const PsoDev &s, const double *misfit, float *particles_out,
-                            cudaStream_t st);
+                            cudaStream_t st, const double *rank = nullptr);
 cudaError_t launch_xf_from_x(const PsoDev &s, cudaStream_t st);
+
+// Surrogate network (surrogate.cu): flat FP32 parameters in the order
+// W1 [H][K], b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1]; BF16 copies of W1, W2.
+struct SurDev {
+    int K = 0, H = 0, cap = 0, rows_max = 0;
+    long long n_params = 0, off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_w3 = 0, off_b3 = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+    const double *xmin = nullptr, *xmax = nullptr;
+    __nv_bfloat16 *Xb = nullptr, *A1b = nullptr, *dZb = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *y = nullptr, *dy = nullptr, *dZf = nullptr, *dA = nullptr;
+    float *tb = nullptr, *loss = nullptr, *stats = nullptr;
+    int *rows = nullptr;
+    float *xbuf = nullptr, *ybuf = nullptr;
+    int *count = nullptr;
+    uint64_t seed = 0;
+    int sample_step = 0, t = 0;
+    float lr = 1e-3f, beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+};
+cudaError_t sur_forward(const SurDev &s, const __nv_bfloat16 *Xb, int n, float *y, cudaStream_t st);
+cudaError_t sur_backward(const SurDev &s, const __nv_bfloat16 *Xb, const float *t, int n, float *loss,
+                         cudaStream_t st);
+cudaError_t sur_adam(SurDev &s, cudaStream_t st);
+cudaError_t sur_refresh_bf16(const SurDev &s, cudaStream_t st);
+cudaError_t sur_normalize(const SurDev &s, const float *x, const int *rows, int n, __nv_bfloat16 *out,
+                          cudaStream_t st);
+cudaError_t sur_predict(const SurDev &s, const float *x, int n, float *logphi, cudaStream_t st);
+cudaError_t sur_append(const SurDev &s, const float *x, const double *misfit, const int *rows, int n,
+                       cudaStream_t st);
+cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st);
+cudaError_t sur_select(const float *key, int P, int k, int *rows, cudaStream_t st);
+cudaError_t sur_gather(const float *x, const int *rows, int k, int K, float *out, cudaStream_t st);
+cudaError_t sur_scatter(const int *rows, const double *fk, int k, const float *logphi, int P,
+                        double *fit, double *rank, cudaStream_t st);
 
 }  // namespace empso

@@ -180,7 +180,7 @@ __device__ __forceinline__ bool before(double fa, int ia, double fb, int ib)
 
 // One generation in one CTA: bests, global best, EM sort, EM and Eq. 1-2.
 __global__ void __launch_bounds__(STEP_THREADS)
-pso_step_kernel(PsoDev s, const double *misfit, float *particles_out)
+pso_step_kernel(PsoDev s, const double *misfit, const double *rank, float *particles_out)
 {
     __shared__ double key[MAX_PSO_P];
     __shared__ int idx[MAX_PSO_P];
@@ -200,7 +200,10 @@ pso_step_kernel(PsoDev s, const double *misfit, float *particles_out)
         if (i < P) {
             double f = misfit[i];
             if (!isfinite(f)) f = inf;
-            key[i] = f;
+            // EM sort key: the fitness, or the given rank key (surrogate pre-screen)
+            double r = rank ? rank[i] : misfit[i];
+            if (!isfinite(r)) r = inf;
+            key[i] = r;
             idx[i] = i;
             if (f < s.pf[i]) {
                 s.pf[i] = f;
@@ -352,9 +355,9 @@ cudaError_t launch_xf_from_x(const PsoDev &s, cudaStream_t st)
 }
 
 cudaError_t launch_pso_step(const PsoDev &s, const double *misfit, float *particles_out,
-                            cudaStream_t st)
+                            cudaStream_t st, const double *rank)
 {
-    pso_step_kernel<<<1, STEP_THREADS, 0, st>>>(s, misfit, particles_out);
+    pso_step_kernel<<<1, STEP_THREADS, 0, st>>>(s, misfit, rank, particles_out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,573 @@
+// Surrogate network that pre-screens EMPSO particles (the paper has none; it
+// serves the pre-screening pattern the library adds): a K -> H -> H -> 1
+// ReLU perceptron predicting the standardised log-misfit of a particle from
+// its control nodes scaled to [-1, 1].  Dense layers run on the tensor cores
+// (BF16 operands, FP32 accumulation), master weights and Adam moments are
+// FP32, and the training set is a device-side replay buffer filled with the
+// (particle, misfit) pairs the fitness evaluation produces.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace empso {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// C[M][N] = sum_k A(m, k) B(k, n) (+ bias[n], ReLU) with BF16 operands and
+// FP32 accumulation on mma.sync m16n8k16.  A(m, k) = A[m lda + k] (a_mk) or
+// A[k lda + m]; B(k, n) = B[n ldb + k] (b_nk) or B[k ldb + n].  Tiles of
+// 64 x 64 per 128-thread block, 32-deep k-steps staged in shared memory
+// (zero-filled past M, N, K).  Outputs: FP32 Cf and/or BF16 Cb.
+// ---------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128)
+gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda, int a_mk,
+                 const __nv_bfloat16 *__restrict__ B, int ldb, int b_nk,
+                 const float *__restrict__ bias, int relu, float *Cf, int ldc, __nv_bfloat16 *Cb,
+                 int ldcb)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];   // (m, k)
+    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];   // (n, k)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+        for (int e = tid; e < GBM * GBK; e += 128) {
+            int mm, kk;
+            if (a_mk) { mm = e / GBK; kk = e % GBK; } else { kk = e / GBM; mm = e % GBM; }
+            const int m = m0 + mm, k = k0 + kk;
+            __nv_bfloat16 v = zero;
+            if (m < M && k < K) v = a_mk ? A[(size_t)m * lda + k] : A[(size_t)k * lda + m];
+            As[mm][kk] = v;
+        }
+        for (int e = tid; e < GBN * GBK; e += 128) {
+            int nn, kk;
+            if (b_nk) { nn = e / GBK; kk = e % GBK; } else { kk = e / GBN; nn = e % GBN; }
+            const int n = n0 + nn, k = k0 + kk;
+            __nv_bfloat16 v = zero;
+            if (n < N && k < K) v = b_nk ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+            Bs[nn][kk] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < GBK; ks += 16) {
+            unsigned af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + 16 * i + g;
+                af[i][0] = *reinterpret_cast<const unsigned *>(&As[r][ks + 2 * t]);
+                af[i][1] = *reinterpret_cast<const unsigned *>(&As[r + 8][ks + 2 * t]);
+                af[i][2] = *reinterpret_cast<const unsigned *>(&As[r][ks + 2 * t + 8]);
+                af[i][3] = *reinterpret_cast<const unsigned *>(&As[r + 8][ks + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + 8 * j + g;
+                bf[j][0] = *reinterpret_cast<const unsigned *>(&Bs[c][ks + 2 * t]);
+                bf[j][1] = *reinterpret_cast<const unsigned *>(&Bs[c][ks + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int m = m0 + wm + 16 * i + g + (e >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * j + 2 * t + (e & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][e];
+                if (bias) v += bias[n];
+                if (relu) v = fmaxf(v, 0.f);
+                if (Cf) Cf[(size_t)m * ldc + n] = v;
+                if (Cb) Cb[(size_t)m * ldcb + n] = __float2bfloat16(v);
+            }
+}
+
+cudaError_t gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16 *A, int lda, int a_mk,
+                 const __nv_bfloat16 *B, int ldb, int b_nk, const float *bias, int relu, float *Cf,
+                 int ldc, __nv_bfloat16 *Cb, int ldcb)
+{
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+    gemm_bf16_kernel<<<grid, 128, 0, st>>>(M, N, K, A, lda, a_mk, B, ldb, b_nk, bias, relu, Cf, ldc,
+                                           Cb, ldcb);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// elementwise and reduction kernels
+// ---------------------------------------------------------------------------
+
+// x_n = 2 (x - xmin) / (xmax - xmin) - 1, as BF16 rows of the batch
+__global__ void normalize_kernel(const float *__restrict__ x, const int *__restrict__ rows, int n,
+                                 int K, const double *__restrict__ xmin,
+                                 const double *__restrict__ xmax, __nv_bfloat16 *out)
+{
+    const long long tot = (long long)n * K;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / K), k = (int)(e % K);
+        const int src = rows ? rows[b] : b;
+        const float lo = (float)xmin[k], hi = (float)xmax[k];
+        out[e] = __float2bfloat16(2.f * (x[(size_t)src * K + k] - lo) / (hi - lo) - 1.f);
+    }
+}
+
+// y[b] = sum_h relu(Z2[b][h]) w3[h] + b3, one warp per row (fixed order)
+__global__ void head_kernel(const float *__restrict__ Z2, int n, int H, const float *__restrict__ w3,
+                            const float *__restrict__ b3, float *y)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    float s = 0.f;
+    for (int h = lane; h < H; h += 32) s = fmaf(fmaxf(Z2[(size_t)warp * H + h], 0.f), w3[h], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[warp] = s + b3[0];
+}
+
+// dy = (y - t) / n and the loss 1/(2n) sum (y - t)^2 (one block, fixed order)
+__global__ void loss_kernel(const float *__restrict__ y, const float *__restrict__ t, int n,
+                            float *dy, float *loss)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const float r = y[b] - t[b];
+        dy[b] = r / (float)n;
+        s += (double)r * r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) v += red[w];
+        if (loss) *loss = (float)(0.5 * v / n);
+    }
+}
+
+// dZ2[b][h] = dy[b] w3[h] [Z2 > 0] (FP32 and BF16 copies)
+__global__ void dz2_kernel(const float *__restrict__ dy, const float *__restrict__ Z2,
+                           const float *__restrict__ w3, int n, int H, float *dZf,
+                           __nv_bfloat16 *dZb)
+{
+    const long long tot = (long long)n * H;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / H), h = (int)(e % H);
+        const float v = Z2[e] > 0.f ? dy[b] * w3[h] : 0.f;
+        dZf[e] = v;
+        dZb[e] = __float2bfloat16(v);
+    }
+}
+
+// dZ1 = dA1 [Z1 > 0] (FP32 in place and BF16 copy)
+__global__ void relu_back_kernel(float *dA, const float *__restrict__ Z, long long tot,
+                                 __nv_bfloat16 *dZb)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float v = Z[e] > 0.f ? dA[e] : 0.f;
+        dA[e] = v;
+        dZb[e] = __float2bfloat16(v);
+    }
+}
+
+// column sums of an [n][H] FP32 matrix, optionally weighted per row by relu(Z)
+// (g[h] = sum_b X[b][h], fixed order per column)
+__global__ void colsum_kernel(const float *__restrict__ X, const float *__restrict__ wrow,
+                              const float *__restrict__ Zrelu, int n, int H, float *g)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    float s = 0.f;
+    for (int b = 0; b < n; ++b) {
+        float v = X ? X[(size_t)b * H + h] : fmaxf(Zrelu[(size_t)b * H + h], 0.f);
+        if (wrow) v *= wrow[b];
+        s += v;
+    }
+    g[h] = s;
+}
+
+__global__ void sum_kernel(const float *__restrict__ v, int n, float *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; i < n; ++i) s += v[i];
+        *out = s;
+    }
+}
+
+// Adam on FP32 master weights, then BF16 copies of the two hidden matrices
+__global__ void adam_kernel(float *p, const float *__restrict__ g, float *m, float *v, long long n,
+                            float lr, float b1, float b2, float eps, float c1, float c2,
+                            __nv_bfloat16 *w1b, long long n_w1, __nv_bfloat16 *w2b, long long off_w2,
+                            long long n_w2)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[e];
+        const float mi = b1 * m[e] + (1.f - b1) * gi;
+        const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+        m[e] = mi;
+        v[e] = vi;
+        const float w = p[e] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[e] = w;
+        if (e < n_w1) w1b[e] = __float2bfloat16(w);
+        else if (e >= off_w2 && e < off_w2 + n_w2) w2b[e - off_w2] = __float2bfloat16(w);
+    }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ src, __nv_bfloat16 *dst, long long n)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        dst[e] = __float2bfloat16(src[e]);
+}
+
+// Philox4x32-10 (Salmon et al. 2011) for minibatch sampling
+__device__ __forceinline__ uint4 philox_s(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// batch rows drawn uniformly from the filled part of the replay buffer
+__global__ void sample_kernel(int *rows, int B, const int *count, int cap, uint64_t seed, int step)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int have = min(*count, cap);
+    const uint4 w = philox_s(make_uint4((uint32_t)step, (uint32_t)b, 0x5u, 0x7u), (uint32_t)seed,
+                             (uint32_t)(seed >> 32));
+    rows[b] = have > 0 ? (int)(((unsigned long long)w.x * (unsigned long long)have) >> 32) : 0;
+}
+
+// standardised targets of the batch: (log phi - mu) / sigma
+__global__ void targets_kernel(const float *__restrict__ ybuf, const int *__restrict__ rows, int B,
+                               const float *__restrict__ stats, float *t)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) t[b] = (ybuf[rows[b]] - stats[0]) / stats[1];
+}
+
+// mean and standard deviation of the filled replay targets (one block)
+__global__ void stats_kernel(const float *__restrict__ ybuf, const int *count, int cap, float *stats)
+{
+    __shared__ double s1[32], s2[32];
+    const int n = min(*count, cap);
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += ybuf[i];
+        b += (double)ybuf[i] * ybuf[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s1[threadIdx.x >> 5] = a;
+        s2[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, Bs = 0.0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+            A += s1[w];
+            Bs += s2[w];
+        }
+        double mu = n > 0 ? A / n : 0.0;
+        double var = n > 1 ? Bs / n - mu * mu : 1.0;
+        stats[0] = (float)mu;
+        stats[1] = (float)sqrt(var > 1e-12 ? var : 1e-12);
+    }
+}
+
+// append (particle, log misfit) pairs; rows with a non-finite misfit are skipped
+__global__ void append_kernel(const float *__restrict__ x, const double *__restrict__ misfit,
+                              const int *__restrict__ rows, int n, int K, float *xbuf, float *ybuf,
+                              int *count, int cap)
+{
+    // single block, sequential slots keep the buffer order deterministic
+    __shared__ int base;
+    __shared__ int ok[1024];
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+        const int m = min(1024, n - c0);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double f = misfit[c0 + i];
+            ok[i] = (isfinite(f) && f > 0.0) ? 1 : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int c = *count;
+            for (int i = 0; i < m; ++i) {
+                const int v = ok[i];
+                ok[i] = v ? c % cap : -1;
+                c += v;
+            }
+            base = c;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const int slot = ok[i];
+            if (slot < 0) continue;
+            const int src = rows ? rows[c0 + i] : c0 + i;
+            ybuf[slot] = (float)log(misfit[c0 + i]);
+            for (int k = 0; k < K; ++k) xbuf[(size_t)slot * K + k] = x[(size_t)src * K + k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *count = base;
+        __syncthreads();
+    }
+}
+
+// predictions back to log-misfit: out = y sigma + mu
+__global__ void destandardize_kernel(const float *__restrict__ y, int n, const float *__restrict__ stats,
+                                     float *out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) out[b] = y[b] * stats[1] + stats[0];
+}
+
+// indices of the k smallest keys (ties to the lower index), one block, P <= 2048
+__global__ void __launch_bounds__(1024) select_kernel(const float *__restrict__ key, int P, int k, int *out)
+{
+    __shared__ float kv[2048];
+    __shared__ int iv[2048];
+    int N = 1;
+    while (N < P) N <<= 1;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        float v = i < P ? key[i] : __int_as_float(0x7f800000);
+        if (!(v == v)) v = __int_as_float(0x7f800000);
+        kv[i] = v;
+        iv[i] = i < P ? i : 0x7fffffff;
+    }
+    __syncthreads();
+    for (int size = 2; size <= N; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const bool lt = kv[hi] < kv[lo] || (kv[hi] == kv[lo] && iv[hi] < iv[lo]);
+                const bool gt = kv[lo] < kv[hi] || (kv[lo] == kv[hi] && iv[lo] < iv[hi]);
+                if (up ? lt : gt) {
+                    const float a = kv[lo];
+                    kv[lo] = kv[hi];
+                    kv[hi] = a;
+                    const int b = iv[lo];
+                    iv[lo] = iv[hi];
+                    iv[hi] = b;
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) out[i] = iv[i];
+}
+
+// gather selected particles into a compact [k][K] array
+__global__ void gather_kernel(const float *__restrict__ x, const int *__restrict__ rows, int k, int K,
+                              float *out)
+{
+    const long long tot = (long long)k * K;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x)
+        out[e] = x[(size_t)rows[e / K] * K + e % K];
+}
+
+// full-swarm fitness (+inf where not modelled) and EM sort keys (modelled:
+// true misfit, others: predicted misfit exp(log phi))
+__global__ void scatter_kernel(const int *__restrict__ rows, const double *__restrict__ fk, int k,
+                               const float *__restrict__ logphi, int P, double *fit, double *rank)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) {
+        fit[i] = __longlong_as_double(0x7ff0000000000000LL);
+        rank[i] = exp((double)logphi[i]);
+    }
+}
+
+__global__ void scatter_fill_kernel(const int *__restrict__ rows, const double *__restrict__ fk, int k,
+                                    double *fit, double *rank)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) {
+        fit[rows[j]] = fk[j];
+        rank[rows[j]] = fk[j];
+    }
+}
+
+inline int blocks_for(long long n, int per = 256)
+{
+    long long b = (n + per - 1) / per;
+    return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host-side launchers used by api.cu
+// ---------------------------------------------------------------------------
+
+cudaError_t sur_forward(const SurDev &s, const __nv_bfloat16 *Xb, int n, float *y, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = gemm(st, n, s.H, s.K, Xb, s.K, 1, s.W1b, s.K, 1, s.p + s.off_b1, 1, s.Z1, s.H, s.A1b,
+                  s.H)))
+        return e;
+    if ((e = gemm(st, n, s.H, s.H, s.A1b, s.H, 1, s.W2b, s.H, 1, s.p + s.off_b2, 0, s.Z2, s.H,
+                  nullptr, 0)))
+        return e;
+    head_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(s.Z2, n, s.H, s.p + s.off_w3, s.p + s.off_b3, y);
+    return cudaGetLastError();
+}
+
+// gradient of the half-MSE on batch (Xb [n][K] BF16, t [n]) into s.g; loss
+// to *loss (device float, may be null)
+cudaError_t sur_backward(const SurDev &s, const __nv_bfloat16 *Xb, const float *t, int n,
+                         float *loss, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = sur_forward(s, Xb, n, s.y, st))) return e;
+    loss_kernel<<<1, 256, 0, st>>>(s.y, t, n, s.dy, loss);
+    // head: g_w3 = sum_b relu(Z2) dy, g_b3 = sum_b dy
+    colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(nullptr, s.dy, s.Z2, n, s.H, s.g + s.off_w3);
+    sum_kernel<<<1, 32, 0, st>>>(s.dy, n, s.g + s.off_b3);
+    // layer 2
+    dz2_kernel<<<blocks_for((long long)n * s.H), 256, 0, st>>>(s.dy, s.Z2, s.p + s.off_w3, n, s.H,
+                                                             s.dZf, s.dZb);
+    colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(s.dZf, nullptr, nullptr, n, s.H, s.g + s.off_b2);
+    // g_W2[h][h'] = sum_b dZ2[b][h] A1[b][h']
+    if ((e = gemm(st, s.H, s.H, n, s.dZb, s.H, 0, s.A1b, s.H, 0, nullptr, 0, s.g + s.off_W2, s.H,
+                  nullptr, 0)))
+        return e;
+    // dA1 = dZ2 W2  -> dZ1 = dA1 [Z1 > 0]
+    if ((e = gemm(st, n, s.H, s.H, s.dZb, s.H, 1, s.W2b, s.H, 0, nullptr, 0, s.dA, s.H, nullptr, 0)))
+        return e;
+    relu_back_kernel<<<blocks_for((long long)n * s.H), 256, 0, st>>>(s.dA, s.Z1, (long long)n * s.H,
+                                                                     s.dZb);
+    colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(s.dA, nullptr, nullptr, n, s.H, s.g + s.off_b1);
+    // g_W1[h][k] = sum_b dZ1[b][h] X[b][k]
+    if ((e = gemm(st, s.H, s.K, n, s.dZb, s.H, 0, Xb, s.K, 0, nullptr, 0, s.g + s.off_W1, s.K,
+                  nullptr, 0)))
+        return e;
+    return cudaGetLastError();
+}
+
+cudaError_t sur_adam(SurDev &s, cudaStream_t st)
+{
+    s.t += 1;
+    const float c1 = 1.f - powf(s.beta1, (float)s.t), c2 = 1.f - powf(s.beta2, (float)s.t);
+    adam_kernel<<<blocks_for(s.n_params), 256, 0, st>>>(s.p, s.g, s.m, s.v, s.n_params, s.lr, s.beta1,
+                                                        s.beta2, s.eps, c1, c2, s.W1b,
+                                                        (long long)s.H * s.K, s.W2b, s.off_W2,
+                                                        (long long)s.H * s.H);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_refresh_bf16(const SurDev &s, cudaStream_t st)
+{
+    to_bf16_kernel<<<blocks_for((long long)s.H * s.K), 256, 0, st>>>(s.p + s.off_W1, s.W1b,
+                                                                     (long long)s.H * s.K);
+    to_bf16_kernel<<<blocks_for((long long)s.H * s.H), 256, 0, st>>>(s.p + s.off_W2, s.W2b,
+                                                                     (long long)s.H * s.H);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_normalize(const SurDev &s, const float *x, const int *rows, int n, __nv_bfloat16 *out,
+                          cudaStream_t st)
+{
+    normalize_kernel<<<blocks_for((long long)n * s.K), 256, 0, st>>>(x, rows, n, s.K, s.xmin, s.xmax,
+                                                                     out);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_predict(const SurDev &s, const float *x, int n, float *logphi, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = sur_normalize(s, x, nullptr, n, s.Xb, st))) return e;
+    if ((e = sur_forward(s, s.Xb, n, s.y, st))) return e;
+    destandardize_kernel<<<(n + 255) / 256, 256, 0, st>>>(s.y, n, s.stats, logphi);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_append(const SurDev &s, const float *x, const double *misfit, const int *rows, int n,
+                       cudaStream_t st)
+{
+    append_kernel<<<1, 256, 0, st>>>(x, misfit, rows, n, s.K, s.xbuf, s.ybuf, s.count, s.cap);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st)
+{
+    cudaError_t e;
+    stats_kernel<<<1, 256, 0, st>>>(s.ybuf, s.count, s.cap, s.stats);
+    for (int i = 0; i < steps; ++i) {
+        sample_kernel<<<(B + 255) / 256, 256, 0, st>>>(s.rows, B, s.count, s.cap, s.seed, s.sample_step++);
+        targets_kernel<<<(B + 255) / 256, 256, 0, st>>>(s.ybuf, s.rows, B, s.stats, s.tb);
+        // the buffer holds raw positions: scale the batch rows to [-1, 1] in BF16
+        if ((e = sur_normalize(s, s.xbuf, s.rows, B, s.Xb, st))) return e;
+        if ((e = sur_backward(s, s.Xb, s.tb, B, s.loss, st))) return e;
+        if ((e = sur_adam(s, st))) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t sur_select(const float *key, int P, int k, int *rows, cudaStream_t st)
+{
+    select_kernel<<<1, 1024, 0, st>>>(key, P, k, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_gather(const float *x, const int *rows, int k, int K, float *out, cudaStream_t st)
+{
+    gather_kernel<<<blocks_for((long long)k * K), 256, 0, st>>>(x, rows, k, K, out);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_scatter(const int *rows, const double *fk, int k, const float *logphi, int P,
+                        double *fit, double *rank, cudaStream_t st)
+{
+    scatter_kernel<<<(P + 255) / 256, 256, 0, st>>>(rows, fk, k, logphi, P, fit, rank);
+    scatter_fill_kernel<<<(k + 255) / 256, 256, 0, st>>>(rows, fk, k, fit, rank);
+    return cudaGetLastError();
+}
+
+}  // namespace empso

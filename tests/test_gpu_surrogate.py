@@ -1,0 +1,238 @@
+"""GPU surrogate network against the FP64 oracle (oracle/mlp.py), and what the
+trained network gains the EMPSO search.
+
+Tolerances: the dense layers use BF16 operands (8 significant bits, unit
+round-off 2^-9 ~ 2e-3 per rounded value) with FP32 accumulation.  A layer
+output sums K or H such products with independent rounding, so its relative
+error stays within a few 1e-3; through two layers and the head we allow
+2e-2 relative L2 on predictions and 3e-2 on the gradient vector (cosine
+> 0.999), measured against the exact FP64 network on the same FP32 weights.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1905_12795_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1905_12795_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _ctx(B, P=64, K=32, H=256, lo=1500.0, hi=4700.0, seed=5):
+    grid = B.make_grid(41, 31, 10.0, 10.0, 5, 4, 0.2, 10.0, 1500.0, 4700.0, kx=8, kz=K // 8)
+    pso = B.EmpsoPso(P, K, 1.2, 2.9, 0.5, 0.3, 0.25, 2, 1, seed)
+    ctx = B.Context([grid], synth.receiver_line(41, 10.0, 0.0), pso, lo, hi)
+    ctx.surrogate_init(hidden=H, capacity=4096, lr=1e-3, seed=seed)
+    return ctx
+
+
+def _normalise(x, lo, hi):
+    return 2.0 * (x - lo) / (hi - lo) - 1.0
+
+
+def _set_oracle_params(ctx, p):
+    flat = torch.tensor(mlp.flatten(p), dtype=torch.float32, device="cuda")
+    ctx.surrogate_set(flat)
+    # the network holds FP32 weights: the oracle uses exactly those values
+    return mlp.unflatten(flat.cpu().numpy().astype(np.float64), p["W1"].shape[1], p["W1"].shape[0])
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_forward_matches_oracle(B):
+    K, H = 32, 256
+    ctx = _ctx(B, K=K, H=H)
+    p = mlp.init_params(K, H, seed=11)
+    rng = np.random.default_rng(12)
+    for k in ("b1", "b2"):
+        p[k] = rng.uniform(-0.2, 0.2, H)
+    p["b3"] = np.array([0.3])
+    p = _set_oracle_params(ctx, p)
+    x = rng.uniform(1500.0, 4700.0, (300, K)).astype(np.float32)
+    out = torch.zeros(300, device="cuda")
+    ctx.surrogate_predict(torch.tensor(x, device="cuda"), out)
+    y, _ = mlp.forward(p, _normalise(x.astype(np.float64), 1500.0, 4700.0))
+    assert _rel(out.cpu().numpy(), y) < 2e-2
+    ctx.close()
+
+
+def test_gradient_matches_oracle(B):
+    K, H, n = 32, 256, 192
+    ctx = _ctx(B, K=K, H=H)
+    p = mlp.init_params(K, H, seed=21)
+    rng = np.random.default_rng(22)
+    for k in ("b1", "b2"):
+        p[k] = rng.uniform(-0.2, 0.2, H)
+    p = _set_oracle_params(ctx, p)
+    x = rng.uniform(1500.0, 4700.0, (n, K)).astype(np.float32)
+    t = rng.normal(size=n).astype(np.float32)
+    npar = ctx.surrogate_n_params()
+    assert npar == mlp.flatten(p).size
+    g = torch.zeros(npar, device="cuda")
+    L = torch.zeros(1, device="cuda")
+    ctx.surrogate_grad(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"), g, L)
+    go, Lo = mlp.backward(p, _normalise(x.astype(np.float64), 1500.0, 4700.0), t.astype(np.float64))
+    gv, gov = g.cpu().numpy().astype(np.float64), mlp.flatten(go)
+    assert L.item() == pytest.approx(Lo, rel=2e-2)
+    assert _rel(gv, gov) < 3e-2
+    assert gv @ gov / (np.linalg.norm(gv) * np.linalg.norm(gov)) > 0.999
+    # per block too: every layer's gradient is right, not only the big ones
+    for k in mlp.ORDER:
+        a = mlp.unflatten(gv, K, H)[k].ravel()
+        b = go[k].ravel()
+        assert _rel(a, b) < 5e-2, k
+    ctx.close()
+
+
+def _misfit_surface(x):
+    # a smooth positive misfit of the normalised nodes with one minimum
+    z = _normalise(x, 1500.0, 4700.0)
+    c = np.linspace(-0.5, 0.5, x.shape[1])
+    return np.exp(0.5 * np.sum((z - c) ** 2, axis=1)) - 0.9
+
+
+def _rank_corr(a, b):
+    return np.corrcoef(np.argsort(np.argsort(a)), np.argsort(np.argsort(b)))[0, 1]
+
+
+def test_training_matches_oracle_training(B):
+    """Online training on the GPU reaches the held-out ranking quality of the
+    same network trained in FP64 by the oracle (same data, steps, batch,
+    learning rate; the minibatch draws differ)."""
+    K, H, steps, batch = 32, 256, 600, 256
+    ctx = _ctx(B, K=K, H=H)
+    rng = np.random.default_rng(31)
+    xtr = rng.uniform(1500.0, 4700.0, (2048, K)).astype(np.float32)
+    ftr = _misfit_surface(xtr.astype(np.float64))
+    ctx.surrogate_add(torch.tensor(xtr, device="cuda"), torch.tensor(ftr, device="cuda"))
+    xte = rng.uniform(1500.0, 4700.0, (512, K)).astype(np.float32)
+    fte = np.log(_misfit_surface(xte.astype(np.float64)))
+    pred = torch.zeros(512, device="cuda")
+    ctx.surrogate_predict(torch.tensor(xte, device="cuda"), pred)
+    e0 = np.mean((pred.cpu().numpy() - fte) ** 2)
+    ctx.surrogate_train(steps, batch)
+    ctx.surrogate_predict(torch.tensor(xte, device="cuda"), pred)
+    pr = pred.cpu().numpy()
+    e1 = np.mean((pr - fte) ** 2)
+    ctx.close()
+    # the FP64 oracle, same recipe: standardised log-misfit targets, Adam
+    ytr = np.log(ftr)
+    mu, sd = ytr.mean(), ytr.std()
+    p = mlp.init_params(K, H, seed=5)
+    opt = mlp.Adam(p, lr=1e-3)
+    nrm = lambda x: _normalise(x.astype(np.float64), 1500.0, 4700.0)  # noqa: E731
+    r2 = np.random.default_rng(32)
+    for _ in range(steps):
+        idx = r2.integers(0, 2048, batch)
+        g, _ = mlp.backward(p, nrm(xtr[idx]), (ytr[idx] - mu) / sd)
+        opt.step(p, g)
+    po = mlp.forward(p, nrm(xte))[0] * sd + mu
+    assert e1 < 0.1 * e0
+    assert np.mean((po - fte) ** 2) < 0.1 * e0
+    rho_gpu, rho_or = _rank_corr(pr, fte), _rank_corr(po, fte)
+    assert rho_gpu > 0.5 and rho_gpu >= rho_or - 0.05, (rho_gpu, rho_or)
+
+
+def test_ranked_step_bit_exact(B):
+    P, D = 40, 6
+    grid = B.make_grid(11, 11, 10.0, 10.0, 0, 2, 0.05, 10.0, 1.0, 2.0, kx=2, kz=3)
+    pso = B.EmpsoPso(P, D, 1.2, 2.9, 0.5, 0.3, 0.25, 1, 1, 77)
+    ctx = B.Context([grid], [[0.0, 0.0]], pso, -5.0, 5.0)
+    sw = oracle.Swarm(P, D, -5.0, 5.0, em_start=1, seed=77)
+    rng = np.random.default_rng(3)
+    ctx.pso_init()
+    for _ in range(5):
+        f = np.full(P, np.inf)
+        ev = rng.choice(P, P // 4, replace=False)
+        f[ev] = rng.uniform(0.1, 5.0, ev.size)
+        rank = rng.uniform(0.1, 5.0, P)
+        rank[ev] = f[ev]
+        ctx.pso_step_ranked(torch.tensor(f, device="cuda"), torch.tensor(rank, device="cuda"))
+        sw.step(f, rank)
+    x = torch.zeros(P, D, dtype=torch.float64, device="cuda")
+    order = torch.zeros(P, dtype=torch.int32, device="cuda")
+    pf = torch.zeros(P, dtype=torch.float64, device="cuda")
+    ctx.pso_get_state(x=x, pf=pf, order=order)
+    assert np.array_equal(x.cpu().numpy(), sw.x)
+    assert np.array_equal(order.cpu().numpy(), sw.order)
+    assert np.array_equal(pf.cpu().numpy(), sw.pf)
+    ctx.close()
+
+
+def _search_problem(B, P, seed):
+    nx, nz, h, pad = 61, 41, 10.0, 10
+    grid = B.make_grid(nx, nz, h, h, pad, 4, 0.3, 15.0, 1200.0, 3200.0)
+    rec = synth.receiver_line(nx, h, 20.0)
+    shots_xz = synth.shot_line(2, (nx - 1) * h, 20.0)
+    sh = B.make_shots(shots_xz, [0, 0], [nx, nx])
+    og = oracle.Grid(nx, nz, h, h, pad, 4, 0.3, 15.0, 3200.0)
+    true = synth.two_layer_model(nx, nz, h, 1500.0, 2500.0, 200.0)
+    _, obs = oracle.shot_batch(og, true, shots_xz, rec, [0, 0], [nx, nx], want_traces=True)
+    dobs = torch.tensor(np.concatenate([o.ravel() for o in obs]), dtype=torch.float32,
+                        device="cuda")
+    pso = B.EmpsoPso(P, 32, 1.2, 2.9, 0.5, 0.3, 0.25, 3, 1, seed)
+    ctx = B.Context([grid], rec, pso, 1200.0, 3200.0)
+    return ctx, sh, dobs
+
+
+def test_prescreen_models_the_predicted_best_quarter(B):
+    P = 64
+    ctx, sh, dobs = _search_problem(B, P, 4)
+    ctx.surrogate_init(hidden=64, capacity=4096, lr=1e-3, seed=4)
+    ctx.pso_init()
+    mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+    assert ctx.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=50, batch=64,
+                                    misfit_out=mis) == P
+    assert torch.isfinite(mis).all()
+    # next generation: predictions first (same positions the call will see)
+    x = torch.zeros(P, 32, dtype=torch.float64, device="cuda")
+    ctx.pso_get_state(x=x)
+    pred = torch.zeros(P, device="cuda")
+    ctx.surrogate_predict(x.float(), pred)
+    n = ctx.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=10, batch=64, misfit_out=mis)
+    assert n == 16
+    modelled = torch.isfinite(mis).cpu().numpy()
+    assert modelled.sum() == 16
+    order = np.lexsort((np.arange(P), pred.cpu().numpy()))
+    assert set(np.where(modelled)[0]) == set(order[:16].tolist())
+    ctx.close()
+
+
+def test_surrogate_gains_at_equal_modelling_budget(B):
+    """Plain EMPSO for G generations models G P particles; the surrogate-assisted
+    run, after a one-generation warm-up, models a quarter per generation and
+    gets (G - 1) * 4 + 1 generations for the same budget.  It must reach a
+    lower best misfit (what the trained network gains the method)."""
+    P, G = 128, 10
+    wins = 0
+    for seed in (1, 2, 3):
+        plain, sh, dobs = _search_problem(B, P, seed)
+        plain.pso_init()
+        best_plain = np.inf
+        mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+        for _ in range(G):
+            plain.generation(sh, dobs, mis)
+            best_plain = min(best_plain, mis.min().item())
+        plain.close()
+        sur, sh, dobs = _search_problem(B, P, seed)
+        sur.surrogate_init(hidden=256, capacity=8192, lr=1e-3, seed=seed)
+        sur.pso_init()
+        budget, best_sur = 0, np.inf
+        while budget < G * P:
+            budget += sur.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=30, batch=128,
+                                               misfit_out=mis)
+            best_sur = min(best_sur, mis.min().item())
+        sur.close()
+        wins += best_sur < best_plain
+    assert wins >= 2
