@@ -60,6 +60,11 @@ def _args():
                     help="P,S: small profiling case on the workload's grid (no JSON line)")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 streaming, 2 on-chip")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the surrogate-vs-plain wall-clock comparison")
+    ap.add_argument("--surrogate-seeds", type=int, default=3)
+    ap.add_argument("--particles", type=int, default=0,
+                    help="hires workload: particles in the bounded sample (default 8)")
     return ap.parse_args()
 
 
@@ -323,6 +328,9 @@ def run_ours(a):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = _cpu_baseline(wl, gs, S, shots, rec, a.cpu_sample_particles, nt)
+    sur = None
+    if rank == 0 and not a.no_surrogate:
+        sur = surrogate_vs_plain(a.surrogate_seeds)
 
     if rank == 0:
         line = {
@@ -353,11 +361,239 @@ def run_ours(a):
             "gpu_launches": 4 * a.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "surrogate_vs_plain": sur,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=20, batch=256):
+    """Wall-clock to a target misfit, surrogate-assisted vs plain EMPSO.
+
+    Problem: the 101 x 101 / 10 m / order-4 / 0.5 s / 10 Hz grid with a
+    20-cell damping layer, one shot at (500, 20) m, 101 receivers at 20 m,
+    observed data of the two-layer model (1500 / 2500 m/s, interface 500 m)
+    with +5 % velocity; particles of 4 x 8 nodes in [1200, 3200] m/s, swarm
+    1024.  The plain run does `gens` generations (graph replays); its final
+    best misfit is the target.  The surrogate run models the predicted-best
+    quarter each generation (after a one-generation warm-up) and stops when
+    it reaches the target.  Both times include a host read of the best
+    misfit every generation."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    wl = synth.workloads()["surrogate-101x101-P1024"]
+    gs = wl.grids[0]
+    rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
+    shots = synth.shot_line(1, (gs.nx - 1) * gs.hx, wl.src_z)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
+                       gs.vmax, kx=gs.kx, kz=gs.kz)
+    sh = B.make_shots(shots, [0], [len(rec)])
+    true = synth.two_layer_model(gs.nx, gs.nz, gs.hz) * 1.05
+    K = gs.kx * gs.kz
+    runs = []
+    for seed in range(seeds):
+        pso = B.EmpsoPso(P, K, 1.2, 2.9, 0.5, 0.3, 0.25, max(1, gens // 10), 1, 12795 + seed)
+        # plain
+        ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
+        _, nt = ctx.grid_info(0)
+        dobs = torch.zeros(nt * len(rec), device="cuda")
+        ctx.forward_traces(torch.tensor(true, dtype=torch.float32, device="cuda")[None], sh, dobs)
+        mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+        ctx.pso_init()
+        ctx.generation(sh, dobs, mis)          # capture outside the clock
+        ctx.pso_init()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, hist = float("inf"), []
+        for g in range(gens):
+            ctx.generation(sh, dobs, mis)
+            best = min(best, mis.min().item())
+            hist.append((time.perf_counter() - t0, best))
+        ctx.close()
+        target = best
+        t_plain = next(t for t, b in hist if b <= target)
+        # surrogate-assisted
+        ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
+        ctx.surrogate_init(hidden=256, capacity=50000, lr=1e-3, seed=seed + 1)
+        ctx.pso_init()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best_s, modelled, g, t_sur = float("inf"), 0, 0, None
+        while g < 4 * gens:
+            modelled += ctx.surrogate_generation(sh, dobs, keep, warm=P, train_steps=train_steps,
+                                                 batch=batch, misfit_out=mis)
+            g += 1
+            best_s = min(best_s, mis.min().item())
+            if best_s <= target:
+                t_sur = time.perf_counter() - t0
+                break
+        ctx.close()
+        runs.append({"seed": seed, "target_misfit": target, "plain_s": t_plain,
+                     "plain_models": P * gens, "surrogate_s": t_sur, "surrogate_generations": g,
+                     "surrogate_models": modelled, "surrogate_best": best_s})
+    reached = [r for r in runs if r["surrogate_s"] is not None]
+    med = lambda v: float(np.median(v)) if v else None  # noqa: E731
+    return {"problem": "101x101 order 4, 1 shot, swarm 1024, 100 plain generations, keep 25 %",
+            "seeds": seeds, "reached": len(reached),
+            "median_plain_s": med([r["plain_s"] for r in runs]),
+            "median_surrogate_s": med([r["surrogate_s"] for r in reached]),
+            "median_speedup": med([r["plain_s"] / r["surrogate_s"] for r in reached]),
+            "runs": runs}
+
+
+def run_uneven(a):
+    """Uneven batching: 256 particles x 32 shots, 16 shots on a 40 m / 3 Hz /
+    4 s grid and 16 on a 20 m / 6 Hz / 3 s grid, in one persistent launch per
+    generation (graph replay); shot weights 1 / E of each band."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    wl = synth.workloads()[a.workload]
+    coarse, fine = wl.grids
+    grids = [B.make_grid(g.nx, g.nz, g.hx, g.hz, g.pad, g.order, g.T, g.f0, g.vmin, g.vmax,
+                         kx=g.kx, kz=g.kz) for g in (coarse, fine)]
+    recs = [synth.receiver_line(g.nx, g.hx, wl.rec_z) for g in (coarse, fine)]
+    shots = [synth.shot_line(S, (g.nx - 1) * g.hx, wl.src_z)
+             for g, S in zip((coarse, fine), wl.shots_per_grid)]
+    K = coarse.kx * coarse.kz
+    pso = B.EmpsoPso(wl.P, K, 1.2, 2.9, 0.5, 0.3, 0.25, 10, 1, wl.seed_pso)
+    ctx = B.Context(grids, np.concatenate(recs), pso, wl.xmin, wl.xmax)
+    nts = [ctx.grid_info(i)[1] for i in range(2)]
+    n0 = len(recs[0])
+    S0, S1 = wl.shots_per_grid
+    xz = np.concatenate(shots)
+    rb = [0] * S0 + [n0] * S1
+    rc = [n0] * S0 + [len(recs[1])] * S1
+    gid = [0] * S0 + [1] * S1
+    # observed data per band from the true model of each grid, then 1/E weights
+    obs = []
+    for i, g in enumerate((coarse, fine)):
+        true = synth.layered_faulted_model(g.nx, g.nz, g.hx, g.hz, seed=wl.seed_model)
+        sh_i = B.make_shots(shots[i], [rb[0] if i == 0 else n0] * len(shots[i]),
+                            [len(recs[i])] * len(shots[i]), grid_ids=[i] * len(shots[i]))
+        tr = torch.zeros(len(shots[i]) * nts[i] * len(recs[i]), device="cuda")
+        ctx.forward_traces(torch.tensor(true, dtype=torch.float32, device="cuda")[None], sh_i, tr)
+        obs.append(tr)
+    energy = [0.5 * float((o.double() ** 2).sum()) for o in obs]
+    w = [1.0 / energy[0]] * S0 + [1.0 / energy[1]] * S1
+    sh = B.make_shots(xz, rb, rc, grid_ids=gid, weights=w)
+    dobs = torch.cat(obs)
+    mis = torch.zeros(wl.P, dtype=torch.float64, device="cuda")
+    x = torch.zeros(wl.P, K, device="cuda")
+    ctx.pso_init(x)
+    tuned = ctx.autotune(x, sh, dobs, mis)
+    ctx.pso_init()
+    ctx.set_timing(True)
+    for _ in range(a.warmup):
+        ctx.generation(sh, dobs, mis)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = _Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms, wave = [], []
+    for _ in range(a.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.generation(sh, dobs, mis)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        wave.append(ctx.read_timing()[1])
+    clk = clocks.stop()
+    launch = ctx.last_launch()
+    upd = wl.P * sum(S * _updates_per_instance(g, nt)
+                     for g, S, nt in zip((coarse, fine), wl.shots_per_grid, nts))
+    total = sum(ms)
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_UPDATE * upd / (np.mean(wave) / 1e3) / 1e9
+    line = {"metric": METRIC, "value": upd * a.steps / (total / 1e3), "unit": "grid-pt updates/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": total / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": a.workload, "grids": [f"{g.nx}x{g.nz}@{g.hx:g}m/{g.f0:g}Hz/"
+                                                         f"{g.T:g}s nt={nt}" for g, nt in
+                                                         zip((coarse, fine), nts)],
+                       "particles": wl.P, "shots": list(wl.shots_per_grid),
+                       "instances_per_step": wl.P * sum(wl.shots_per_grid),
+                       "updates_per_step": upd, "l2": "flushed between timed steps"},
+            "fitness_evals_per_s": wl.P * a.steps / (total / 1e3),
+            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
+                       "cluster_ctas": launch[1], "autotuned": list(tuned)},
+            "roofline": {"kernel": "wave_resident_kernel" if launch[0] == 2 else "wave_kernel",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "kernel_ms": float(np.mean(wave))},
+            "gpu_launches": 4 * a.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_hires(a):
+    """High-resolution grid (921 x 301 at 10 m + 60 damping cells, order 8,
+    12 Hz, 4 s): a bounded sample of the generation, `--particles` x 64 shots
+    in one launch (the streaming kernel: the instance does not fit on chip)."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    wl = synth.workloads()[a.workload]
+    gs = wl.grids[0]
+    P = a.particles or 8
+    S = wl.shots_per_grid[0]
+    rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
+    shots = synth.shot_line(S, (gs.nx - 1) * gs.hx, wl.src_z)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
+                       gs.vmax, kx=gs.kx, kz=gs.kz)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    sh = B.make_shots(shots, [0] * S, [len(rec)] * S)
+    true = synth.layered_faulted_model(gs.nx, gs.nz, gs.hx, gs.hz, seed=wl.seed_model)
+    dobs = torch.zeros(S * nt * len(rec), device="cuda")
+    ctx.forward_traces(torch.tensor(true, dtype=torch.float32, device="cuda")[None], sh, dobs)
+    x = torch.tensor(synth.random_particles(P, gs.kx * gs.kz, wl.xmin, wl.xmax, wl.seed_pso),
+                     dtype=torch.float32, device="cuda")
+    mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+    ctx.set_timing(True)
+    for _ in range(a.warmup):
+        ctx.eval_fitness(x, sh, dobs, mis)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms, wave = [], []
+    clocks = _Clocks(torch.cuda.current_device())
+    clocks.start()
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.eval_fitness(x, sh, dobs, mis)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        wave.append(ctx.read_timing()[1])
+    clk = clocks.stop()
+    launch = ctx.last_launch()
+    upd = P * S * _updates_per_instance(gs, nt)
+    total = sum(ms)
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_UPDATE * upd / (np.mean(wave) / 1e3) / 1e9
+    line = {"metric": METRIC, "value": upd * a.steps / (total / 1e3), "unit": "grid-pt updates/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": total / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": a.workload, "grid": f"{gs.nx}x{gs.nz} (+{gs.pad} damping)",
+                       "nt": nt, "sample": f"{P} particles x {S} shots of the {wl.P} x {S} "
+                                           "generation (bounded sample)",
+                       "updates_per_step": upd, "l2": "inputs larger than L2"},
+            "fitness_evals_per_s": P * a.steps / (total / 1e3),
+            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
+                       "cluster_ctas": launch[1]},
+            "roofline": {"kernel": "wave_resident_kernel" if launch[0] == 2 else "wave_kernel",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "kernel_ms": float(np.mean(wave))},
+            "gpu_launches": 3 * a.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def run_case(a):
@@ -393,6 +629,10 @@ def main():
     a = _args()
     if a.case:
         run_case(a)
+    elif a.impl != "reference" and a.workload.startswith("uneven"):
+        run_uneven(a)
+    elif a.impl != "reference" and a.workload.startswith("hires"):
+        run_hires(a)
     elif a.impl == "reference":
         run_reference(a)
     else:
