@@ -168,6 +168,21 @@ class _Clocks:
                 "samples": len(rows)}
 
 
+def aggregate(total_ms: float, updates_per_rank: float, dist=None, device=None):
+    """Whole-job throughput over N replicas: every rank runs its own swarm (the
+    method has no exchange step, so replicas only); the job time is the
+    slowest rank's, value = N x updates per rank / that time.  Returns
+    (max_ms, value, world)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * updates_per_rank / (total_ms / 1e3), world
+
+
 def _cpu_baseline(wl, gs, S, shots, rec, n_particles, nt_expected):
     """Time the FP64 oracle on `n_particles` particles x all S shots (host cores)."""
     import oracle
@@ -285,10 +300,9 @@ def run_ours(a):
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
     total_ms = sum(step_ms)
+    upd_step = wl.P * S * _updates_per_instance(gs, nt)
+    total_ms, value, _ = aggregate(total_ms, upd_step * a.steps, dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
         dist.barrier()
 
     # end-to-end through the public API: the step's input (the observed
@@ -309,16 +323,9 @@ def run_ours(a):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     ctx.set_timing(False)
-    e2e_total = sum(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = t.item()
+    e2e_total, e2e_value, _ = aggregate(sum(e2e_ms), upd_step * a.steps, dist, dev)
 
-    upd_step = wl.P * S * _updates_per_instance(gs, nt)
-    value = world * upd_step * a.steps / (total_ms / 1e3)
     evals = world * wl.P * a.steps / (total_ms / 1e3)
-    e2e_value = world * upd_step * a.steps / (e2e_total / 1e3)
     wave_mean = float(np.mean(wave_ms))
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_UPDATE * upd_step / (wave_mean / 1e3) / 1e9

@@ -140,3 +140,32 @@ def test_uninitialised_swarm(B):
                   0.0, 1.0)
     assert e.value.status == 1
     ctx.close()
+
+
+def test_checkpoint_resume_bit_exact(B):
+    """Checkpoint/resume: the swarm state (x, v, p, pf, g, k) is the whole
+    state of a run because the random numbers are counter-based; restoring it
+    into a fresh context continues the run bit for bit."""
+    P, D = 24, 8
+    ctx, _ = _ctx(B, P, D, -5.12, 5.12, em_start=3)
+    ctx.pso_init()
+    xs = torch.zeros(P, D, dtype=torch.float64, device="cuda")
+
+    def run(c, gens):
+        for _ in range(gens):
+            c.pso_get_state(x=xs)
+            c.pso_step(torch.tensor(_rastrigin(xs.cpu().numpy()), device="cuda"))
+
+    run(ctx, 6)
+    x, v, p, pf, order, gk = _state(ctx, P, D)
+    run(ctx, 6)
+    ref = _state(ctx, P, D)
+    ctx2, _ = _ctx(B, P, D, -5.12, 5.12, em_start=3)
+    ctx2.pso_set_state(*(torch.tensor(a, device="cuda") for a in (x, v, p, pf)), int(gk[0]),
+                       int(gk[1]))
+    run(ctx2, 6)
+    got = _state(ctx2, P, D)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+    ctx.close()
+    ctx2.close()

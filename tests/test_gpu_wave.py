@@ -305,3 +305,33 @@ def test_full_size_sampled(B, kind):
     _check_misfit(got[F["sel"]], F["ref"], [e] * 2)
     assert np.all(np.isfinite(got)) and np.all(got > 0)
     ctx.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_nonfinite_model_gives_inf_misfit(B, kind):
+    """Failure handling: a model whose wavefield blows up (a NaN velocity node)
+    gets misfit +inf, the other models of the launch are unaffected, and
+    pso_step never takes it as a best."""
+    nx, nz, h = 41, 31, 10.0
+    grid = B.make_grid(nx, nz, h, h, 5, 4, 0.2, 10.0, 1500.0, 3000.0)
+    rec = synth.receiver_line(nx, h, 20.0)
+    pso = B.EmpsoPso(3, 32, 1.2, 2.9, 0.5, 0.3, 0.25, 10, 1, 1)
+    ctx = B.Context([grid], rec, pso, 1500.0, 3000.0)
+    _use(ctx, kind)
+    _, nt = ctx.grid_info(0)
+    sh = B.make_shots([(200.0, 20.0)], [0], [nx])
+    vel = np.full((3, nz, nx), 2000.0, dtype=np.float32)
+    vel[1, 10, 10] = np.nan
+    dobs = torch.zeros(nt * nx, device="cuda")
+    mis = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx.eval_models(_dev(vel), sh, dobs, mis)
+    m = mis.cpu().numpy()
+    assert np.isinf(m[1]) and m[1] > 0
+    assert np.isfinite(m[0]) and m[0] == m[2]
+    ctx.pso_init()
+    ctx.pso_step(mis)
+    pf = torch.zeros(3, dtype=torch.float64, device="cuda")
+    gk = torch.zeros(2, dtype=torch.int32, device="cuda")
+    ctx.pso_get_state(pf=pf, gk=gk)
+    assert np.isinf(pf.cpu().numpy()[1]) and gk.cpu().numpy()[0] == 0
+    ctx.close()
