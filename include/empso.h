@@ -292,6 +292,12 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas);
  * instance.  Either pointer may be NULL (host ints). */
 empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *cluster);
 
+/* Device-side status of the launches since the last call: a bounded wait
+ * inside a kernel that gave up (EMPSO_TIMEOUT) - the instance concerned then
+ * reports misfit +inf.  Synchronises `stream`, then clears the word.
+ * status: host int. */
+empso_status empso_device_error(empso_ctx *ctx, int32_t *status, void *stream);
+
 /* Kernel timing: when enable != 0, eval_fitness / eval_models /
  * forward_traces record CUDA events on their stream around the model-field
  * kernels, the persistent modelling launch and the misfit reduction. */

@@ -53,6 +53,7 @@ struct empso_ctx {
     int forced_C = 0;               // 0: choose the cluster size, else use this one
     int last_path = 0;              // 1 streaming, 2 resident (last modelling launch)
     int last_C = 0;
+    int *dev_err = nullptr;         // device status word set by bounded waits that give up
 
     // swarm
     bool has_pso = false;
@@ -300,6 +301,9 @@ struct Plan {
     int resR = 0, resC = 0, res_threads = 0, res_clusters = 0, ring_pitch = 0;
     size_t res_smem = 0;
     int n_ctas = 0;
+    bool stream_tma = false;           // streaming path: row-pipelined bulk-copy kernel
+    int st_threads = 0, st_R = 0, rec_max = 0;
+    size_t st_smem = 0;
     const Inst *insts = nullptr;       // device instance table
     const float *weights = nullptr;    // device shot weights
 };
@@ -404,7 +408,28 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
     if (kind == EMPSO_KERNEL_RESIDENT && !p.resident)
         return fail(ctx, EMPSO_UNSUPPORTED,
                     "the batch does not fit the on-chip kernel (grid too large or mixed orders)");
-    const int max_ctas = ctx->sm_count * ctx->wave_ctas_per_sm;
+    int max_ctas = ctx->sm_count * ctx->wave_ctas_per_sm;
+    if (!p.resident && resR > 0) {
+        // row-pipelined streaming kernel: one thread per float4 column group
+        int nq = 0, pitch = 0, nrec_max = 0;
+        for (int gid = 0; gid < ng; ++gid) {
+            if (p.fbase[gid] < 0) continue;
+            nq = std::max(nq, ctx->grids[gid].dev.NQ);
+            pitch = std::max(pitch, ctx->grids[gid].dev.pitch);
+        }
+        for (int s = 0; s < S; ++s) nrec_max = std::max(nrec_max, (int)shots[s].nrec);
+        const size_t sm = stream_smem_bytes(resR, pitch, nrec_max);
+        if (nq <= stream_max_threads() && sm <= ctx->smem_optin) {
+            p.stream_tma = true;
+            p.st_R = resR;
+            p.st_threads = std::max(64, (nq + 31) / 32 * 32);
+            p.st_smem = sm;
+            p.rec_max = nrec_max;
+            // shared memory decides how many of these CTAs share an SM
+            const int per_sm = std::max(1, (int)(ctx->smem_optin / std::max<size_t>(sm, 1)));
+            max_ctas = ctx->sm_count * std::min(per_sm, 2);
+        }
+    }
     p.n_ctas = (int)std::min<long long>(p.n_inst, max_ctas);
     if ((rc = grow(ctx, (void **)&ctx->fields, &ctx->fields_cap, sizeof(float) * ftotal,
                    sizeof(float))) != EMPSO_OK)
@@ -502,6 +527,12 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
                                      ctx->partial, st));
         ctx->last_path = 2;
         ctx->last_C = p.resC;
+    } else if (p.stream_tma) {
+        CK(ctx, launch_wave_stream(p.st_R, ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter,
+                                   ctx->slots, 2 * p.maxfield, p.n_ctas, p.st_threads, p.st_smem,
+                                   p.rec_max, ctx->dev_err, ctx->partial, st));
+        ctx->last_path = 1;
+        ctx->last_C = 1;
     } else {
         CK(ctx, launch_wave(ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter, ctx->slots,
                             2 * p.maxfield, p.n_ctas, ctx->wave_threads, ctx->partial, st));
@@ -544,6 +575,7 @@ void free_ctx(empso_ctx *c)
     cudaFree(c->partial);
     cudaFree(c->stage_dev);
     cudaFree(c->counter);
+    cudaFree(c->dev_err);
     cudaFree(c->pso_mem);
     cudaFree(c->pso_int);
     cudaFree(c->xf);
@@ -645,9 +677,15 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
         // keep room for the kernel's static shared memory
         ctx->smem_optin = optin > 2048 ? (size_t)optin - 2048 : 0;
-        for (int R : {1, 2, 4})
+        for (int R : {1, 2, 4}) {
             if ((rc = ck(resident_configure(R, ctx->smem_optin, 16), "on-chip kernel attributes")))
                 return bail(rc);
+            if ((rc = ck(stream_configure(R, ctx->smem_optin), "streaming kernel attributes")))
+                return bail(rc);
+        }
+        if ((rc = ck(cudaMalloc(&ctx->dev_err, sizeof(int)), "error word")) ||
+            (rc = ck(cudaMemset(ctx->dev_err, 0, sizeof(int)), "error word")))
+            return bail(rc);
     }
 
     if (pso) {
@@ -1080,6 +1118,19 @@ empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *clu
     if (!ctx) return EMPSO_INVALID_ARG;
     if (kind) *kind = ctx->last_path;
     if (cluster) *cluster = ctx->last_C;
+    return EMPSO_OK;
+}
+
+empso_status empso_device_error(empso_ctx *ctx, int32_t *status, void *stream)
+{
+    if (!ctx || !status) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    CK(ctx, cudaMemcpyAsync(&v, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    CK(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), st));
+    *status = v;
     return EMPSO_OK;
 }
 

@@ -82,6 +82,15 @@ cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *in
                                  int *counter, int C, int n_clusters, int threads, int ring_pitch,
                                  size_t smem_bytes, double *partial, cudaStream_t st);
 
+// TMA-pipelined streaming variant (wave_stream.cu).
+int stream_max_threads();
+size_t stream_smem_bytes(int R, int pitch, int rec_max);
+cudaError_t stream_configure(int R, size_t smem);
+cudaError_t launch_wave_stream(int R, const GridDev *grids_dev, const Inst *insts, int n_inst,
+                               int *counter, float *slots, long long slot_floats, int n_ctas,
+                               int threads, size_t smem, int rec_max, int *err, double *partial,
+                               cudaStream_t st);
+
 // Message returned by empso_last_error(NULL) for calls made without a context.
 void set_global_error(const char *msg);
 

@@ -1,0 +1,410 @@
+// Streaming variant of the persistent modelling launch for grids that do not
+// fit on chip (section "Testing approach": same scheme, source, receivers and
+// l2 misfit as the other variants).
+//
+// A CTA owns one instance at a time (global queue).  Each time step it sweeps
+// the rows of the padded grid top to bottom.  Whole rows move global ->
+// shared memory with 1-D bulk asynchronous copies (cp.async.bulk, completion
+// counted on an mbarrier per ring slot), D rows ahead of the row being
+// computed: a ring of D + 2R rows of u^n (the z-window of D rows in flight)
+// and a ring of D (u^{n-1}, a) row pairs.  Thread q owns float4 column group q
+// and keeps its z-window in registers; x-neighbours come from the shared row.
+// u^{n+1} is stored straight to global memory in place of u^{n-1} (that row
+// is already in shared memory).  One CTA barrier per row releases the ring
+// slots; no wait is unbounded (a wait that times out sets an error flag and
+// the instance is abandoned with misfit NaN -> +inf).
+#include "internal.cuh"
+
+namespace empso {
+
+namespace {
+
+constexpr int SD = 12;  // rows in flight
+constexpr int RB = 4;   // rows computed between two CTA barriers
+
+__device__ __forceinline__ unsigned saddr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            saddr(dst)),
+        "l"(src), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for phase `parity` of `bar`; false after ~2^22 attempts
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+struct Corner {
+    int i0, j0;
+    float w[4];
+};
+
+__device__ __forceinline__ Corner corner_of(float x, float z, const GridDev &g)
+{
+    Corner c;
+    const float fx = x / g.hx + (float)g.pad, fz = z / g.hz + (float)g.pad;
+    c.i0 = min(max((int)floorf(fx), 0), g.NX - 2);
+    c.j0 = min(max((int)floorf(fz), 0), g.NZ - 2);
+    const float ax = fx - (float)c.i0, az = fz - (float)c.j0;
+    c.w[0] = (1.f - ax) * (1.f - az);
+    c.w[1] = ax * (1.f - az);
+    c.w[2] = (1.f - ax) * az;
+    c.w[3] = ax * az;
+    return c;
+}
+
+__device__ __forceinline__ float lane4(const float4 &v, int l)
+{
+    return l == 0 ? v.x : (l == 1 ? v.y : (l == 2 ? v.z : v.w));
+}
+
+// ring geometry: u^n ring of RU rows (RU >= SD + 2R, a multiple of RB) and
+// a (u^{n-1}, a) ring of SD rows; copies move RB consecutive rows at once
+template <int R>
+struct Rings {
+    static constexpr int RU = (SD + 2 * R + RB - 1) / RB * RB;
+    static constexpr int UC = RU / RB;    // u^n chunk slots
+    static constexpr int MC = SD / RB;    // (u^{n-1}, a) chunk slots
+};
+
+template <int R>
+__device__ void stream_instance(const GridDev &g, const Inst &in, float *bufA, float *bufB,
+                                float4 *uring, float4 *mring, float4 *aring, float4 *rec_w,
+                                int *rec_j, int *rec_i, unsigned long long *ubar,
+                                unsigned long long *mbar, unsigned &ucount, unsigned &mcount,
+                                volatile int *abort_flag, int *err, double *red, double *partial)
+{
+    using RG = Rings<R>;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int NQ = g.NQ, NZ = g.NZ, nt = g.nt;
+    const int sp4 = g.pitch / 4;                          // float4 per row
+    const unsigned rowb = (unsigned)(g.pitch * sizeof(float));
+    // zero both time levels (interior, halo rows and columns)
+    {
+        float4 *z4 = reinterpret_cast<float4 *>(bufA);
+        const long long n4 = (2 * g.field) / 4;
+        for (long long e = tid; e < n4; e += nth) z4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool active = tid < NQ;
+    const int q = tid;
+    float cx[R + 1], cz[R + 1];
+#pragma unroll
+    for (int m = 0; m <= R; ++m) {
+        cx[m] = g.cxm[m];
+        cz[m] = g.czm[m];
+    }
+    float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) ex = __ldg(reinterpret_cast<const float4 *>(g.ex + HALO) + q);
+    const Corner sc = corner_of(in.sx, in.sz, g);
+    const float inv_cell = 1.f / (g.hx * g.hz);
+    const bool src_cols = active && sc.i0 >= 4 * q - 1 && sc.i0 <= 4 * q + 3;
+    // receiver corners and weights, once per instance
+    for (int r = tid; r < in.nrec; r += nth) {
+        const float2 pr = in.rec[r];
+        const Corner c = corner_of(pr.x, pr.y, g);
+        rec_j[r] = c.j0;
+        rec_i[r] = c.i0;
+        rec_w[r] = make_float4(c.w[0], c.w[1], c.w[2], c.w[3]);
+    }
+    float accf = 0.f;
+    double acc = 0.0;
+    // make the zeroed buffers visible to the bulk copies (async proxy)
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    __syncthreads();
+
+    float *cur = bufA, *nxt = bufB;   // u^n, u^{n-1} (-> u^{n+1})
+    const int nu = NZ + 2 * R;        // u^n rows a step reads: padded rows -R .. NZ-1+R
+    // u^n chunk c of this step: rows -R + RB c .. (sequence numbers RB c ..)
+    auto issue_u = [&](int c) {
+        const unsigned cnt = ucount + (unsigned)c;          // running chunk number
+        const unsigned slot = cnt % RG::UC;
+        const int r0 = c * RB, rows = min(RB, nu - r0);
+        mbar_expect(&ubar[slot], rows * rowb);
+        bulk_copy(uring + (size_t)slot * RB * sp4, cur + (size_t)(r0 - R + HALO) * g.pitch, rows * rowb,
+                  &ubar[slot]);
+    };
+    // (u^{n-1}, a) chunk c: rows RB c ..
+    auto issue_m = [&](int c) {
+        const unsigned cnt = mcount + (unsigned)c;
+        const unsigned slot = cnt % RG::MC;
+        const int r0 = c * RB, rows = min(RB, NZ - r0);
+        mbar_expect(&mbar[slot], 2 * rows * rowb);
+        bulk_copy(mring + (size_t)slot * RB * sp4, nxt + (size_t)(r0 + HALO) * g.pitch, rows * rowb,
+                  &mbar[slot]);
+        bulk_copy(aring + (size_t)slot * RB * sp4, in.a + (size_t)(r0 + HALO) * g.pitch, rows * rowb,
+                  &mbar[slot]);
+    };
+    const int n_uc = (nu + RB - 1) / RB, n_mc = (NZ + RB - 1) / RB;
+    auto wait_u = [&](int c) {
+        const unsigned cnt = ucount + (unsigned)c;
+        if (!mbar_wait(&ubar[cnt % RG::UC], (cnt / RG::UC) & 1)) {
+            *abort_flag = 1;
+            atomicExch(err, EMPSO_TIMEOUT);
+        }
+    };
+    auto wait_m = [&](int c) {
+        const unsigned cnt = mcount + (unsigned)c;
+        if (!mbar_wait(&mbar[cnt % RG::MC], (cnt / RG::MC) & 1)) {
+            *abort_flag = 1;
+            atomicExch(err, EMPSO_TIMEOUT);
+        }
+    };
+    // u^n row J lives in ring row (ucount RB + J + R) % RU
+    auto urow = [&](int J) {
+        return uring + (size_t)((ucount * RB + (unsigned)(J + R)) % RG::RU) * sp4;
+    };
+
+    for (int n = 0; n < nt && !*abort_flag; ++n) {
+        const float rn = __ldg(g.wavelet + n) * inv_cell;
+        if (tid == 0) {
+            for (int c = 0; c < RG::UC && c < n_uc; ++c) issue_u(c);
+            for (int c = 0; c < RG::MC && c < n_mc; ++c) issue_m(c);
+        }
+        int u_ready = -1;             // highest u^n chunk waited for
+        float4 w[2 * R + 1];
+        for (int k = 0; k < n_mc; ++k) {
+            const int J0 = k * RB;
+            // u^n rows up to J0 + RB - 1 + R, i.e. chunk (J0 + RB - 1 + 2R) / RB
+            const int need = min((J0 + RB - 1 + 2 * R) / RB, n_uc - 1);
+            while (u_ready < need) wait_u(++u_ready);
+            wait_m(k);
+            if (k == 0 && active) {
+#pragma unroll
+                for (int m = 0; m < 2 * R; ++m) w[m] = urow(m - R)[1 + q];
+            }
+            const unsigned ms = (mcount + (unsigned)k) % RG::MC;
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                const int J = J0 + b;
+                const bool live = J < NZ;
+                if (active) {
+                    w[2 * R] = urow(J + R)[1 + q];
+                    const float4 *crow = urow(J);
+                    const float4 lft = crow[q];
+                    const float4 rgt = crow[2 + q];
+                    const float4 um = mring[((size_t)ms * RB + b) * sp4 + 1 + q];
+                    const float4 av = aring[((size_t)ms * RB + b) * sp4 + 1 + q];
+                    const float ezj = live ? __ldg(g.ez + J + HALO) : 0.f;
+                    const float s[12] = {lft.x, lft.y, lft.z, lft.w, w[R].x, w[R].y, w[R].z, w[R].w,
+                                         rgt.x, rgt.y, rgt.z, rgt.w};
+                    float o[4];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        float lap = cx[0] * s[4 + l];
+#pragma unroll
+                        for (int m = 1; m <= R; ++m) {
+                            lap = fmaf(cx[m], s[4 + l - m] + s[4 + l + m], lap);
+                            lap = fmaf(cz[m], lane4(w[R - m], l) + lane4(w[R + m], l), lap);
+                        }
+                        if (src_cols && (J == sc.j0 || J == sc.j0 + 1)) {
+                            const int I = 4 * q + l;
+                            float bw = 0.f;
+                            if (J == sc.j0) bw += (I == sc.i0 ? sc.w[0] : 0.f) + (I == sc.i0 + 1 ? sc.w[1] : 0.f);
+                            else bw += (I == sc.i0 ? sc.w[2] : 0.f) + (I == sc.i0 + 1 ? sc.w[3] : 0.f);
+                            lap = fmaf(bw, rn, lap);
+                        }
+                        const float t = lane4(ex, l) + ezj;
+                        const float num = fmaf(lane4(av, l), lap, fmaf(2.f, s[4 + l], -(1.f - t) * lane4(um, l)));
+                        o[l] = (t == 0.f) ? num : __fdividef(num, 1.f + t);
+                    }
+                    if (live)
+                        reinterpret_cast<float4 *>(nxt + (size_t)(J + HALO) * g.pitch)[1 + q] =
+                            make_float4(o[0], o[1], o[2], o[3]);
+                }
+                // receivers with lower corner row J sample u^n (record n - 1)
+                if (n >= 1 && live) {
+                    const float *r0 = reinterpret_cast<const float *>(urow(J));
+                    const float *r1 = reinterpret_cast<const float *>(urow(J + 1));
+                    for (int r = tid; r < in.nrec; r += nth) {
+                        if (rec_j[r] != J) continue;
+                        const int k0 = HALO + rec_i[r];
+                        const float4 cw = rec_w[r];
+                        const float d = cw.x * r0[k0] + cw.y * r0[k0 + 1] + cw.z * r1[k0] + cw.w * r1[k0 + 1];
+                        const size_t o2 = (size_t)(n - 1) * in.nrec + r;
+                        if (in.traces) in.traces[o2] = d;
+                        if (in.dobs) {
+                            const float e = d - __ldg(in.dobs + o2);
+                            accf = fmaf(e, e, accf);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
+            }
+            __syncthreads();   // (u^{n-1}, a) chunk k and u^n rows < J0 + RB - R are free
+            if (tid == 0) {
+                // refill: u^n chunks are released once all their rows are below
+                // the next window; (u^{n-1}, a) chunk k is released now
+                const int u_next = k + RG::UC;   // u^n chunk that may enter now
+                const int lo_row = J0 + RB - R;  // lowest u^n row still needed
+                // chunk u_next reuses the slot of chunk u_next - UC, whose rows
+                // end at (u_next - UC) RB + RB - 1 - R < lo_row
+                if (u_next < n_uc && (u_next - RG::UC) * RB + RB - 1 - R < lo_row) issue_u(u_next);
+                if (k + RG::MC < n_mc) issue_m(k + RG::MC);
+            }
+        }
+        ucount += (unsigned)n_uc;
+        mcount += (unsigned)n_mc;
+        if ((n & 31) == 0) {
+            acc += (double)accf;
+            accf = 0.f;
+        }
+        // u^{n+1} was written with ordinary stores; the next step reads it with
+        // bulk copies
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        __syncthreads();
+        float *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (*abort_flag && tid == 0) {
+        // abandoned instance: let every copy already issued land (bounded)
+        // before the ring is reused or the block exits
+        // (the step was cut short: waits of up to one ring of chunks)
+        for (int i = 0; i < RG::UC; ++i) mbar_wait(&ubar[i], 0), mbar_wait(&ubar[i], 1);
+        for (int i = 0; i < RG::MC; ++i) mbar_wait(&mbar[i], 0), mbar_wait(&mbar[i], 1);
+    }
+    // the last record: receivers sample u^{nt} from global memory
+    if (!*abort_flag) {
+        for (int r = tid; r < in.nrec; r += nth) {
+            const float4 cw = rec_w[r];
+            const float *b0 = cur + (size_t)(rec_j[r] + HALO) * g.pitch + HALO + rec_i[r];
+            const float d = cw.x * b0[0] + cw.y * b0[1] + cw.z * b0[g.pitch] + cw.w * b0[g.pitch + 1];
+            const size_t o2 = (size_t)(nt - 1) * in.nrec + r;
+            if (in.traces) in.traces[o2] = d;
+            if (in.dobs) {
+                const float e = d - __ldg(in.dobs + o2);
+                accf = fmaf(e, e, accf);
+            }
+        }
+    }
+    acc += (double)accf;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int wi = 0; wi < (nth + 31) / 32; ++wi) v += red[wi];
+        partial[in.out] = *abort_flag ? __longlong_as_double(0x7ff8000000000000LL) : 0.5 * v;
+    }
+    __syncthreads();
+}
+
+constexpr int STREAM_NT = 512;
+
+template <int R>
+__global__ void __launch_bounds__(STREAM_NT, 1)
+wave_stream_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts, int n_inst,
+                   int *counter, float *slots, long long slot_floats, int rec_max, int *err,
+                   double *partial)
+{
+    extern __shared__ __align__(128) float4 sm4[];
+    __shared__ __align__(8) unsigned long long ubar[Rings<R>::UC];
+    __shared__ __align__(8) unsigned long long mbar[Rings<R>::MC];
+    __shared__ int s_q;
+    __shared__ int s_abort;
+    __shared__ double red[32];
+    __shared__ GridDev sg;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < Rings<R>::UC; ++i) mbar_init(&ubar[i], 1);
+        for (int i = 0; i < Rings<R>::MC; ++i) mbar_init(&mbar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+    unsigned ucount = 0, mcount = 0;
+    float *bufA = slots + (size_t)blockIdx.x * slot_floats;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = s_abort ? n_inst : atomicAdd(counter, 1);
+        __syncthreads();
+        const int q = s_q;
+        if (q >= n_inst) break;
+        const Inst in = insts[q];
+        if (threadIdx.x == 0) sg = grids[in.grid];
+        __syncthreads();
+        const int sp4 = sg.pitch / 4;
+        float4 *uring = sm4;
+        float4 *mring = uring + (size_t)Rings<R>::RU * sp4;
+        float4 *aring = mring + (size_t)SD * sp4;
+        float4 *rec_w = aring + (size_t)SD * sp4;
+        int *rec_j = reinterpret_cast<int *>(rec_w + rec_max);
+        int *rec_i = rec_j + rec_max;
+        stream_instance<R>(sg, in, bufA, bufA + sg.field, uring, mring, aring, rec_w, rec_j, rec_i,
+                           ubar, mbar, ucount, mcount, &s_abort, err, red, partial);
+    }
+}
+
+using StreamFn = void (*)(const GridDev *, const Inst *, int, int *, float *, long long, int, int *,
+                          double *);
+
+StreamFn stream_fn(int R)
+{
+    if (R == 4) return wave_stream_kernel<4>;
+    if (R == 2) return wave_stream_kernel<2>;
+    return wave_stream_kernel<1>;
+}
+
+}  // namespace
+
+int stream_max_threads() { return STREAM_NT; }
+
+// row rings (u^n: SD + 2R rows; (u^{n-1}, a): SD row pairs) and the receiver
+// tables of up to rec_max receivers
+size_t stream_smem_bytes(int R, int pitch, int rec_max)
+{
+    const int RU = (SD + 2 * R + RB - 1) / RB * RB;
+    return sizeof(float) * (size_t)pitch * (RU + 2 * SD) +
+           (sizeof(float4) + 2 * sizeof(int)) * (size_t)rec_max;
+}
+
+cudaError_t stream_configure(int R, size_t smem)
+{
+    return cudaFuncSetAttribute(stream_fn(R), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_wave_stream(int R, const GridDev *grids_dev, const Inst *insts, int n_inst,
+                               int *counter, float *slots, long long slot_floats, int n_ctas,
+                               int threads, size_t smem, int rec_max, int *err, double *partial,
+                               cudaStream_t st)
+{
+    if (n_inst <= 0) return cudaSuccess;
+    stream_fn(R)<<<n_ctas, threads, smem, st>>>(grids_dev, insts, n_inst, counter, slots, slot_floats,
+                                                 rec_max, err, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace empso
