@@ -231,6 +231,11 @@ empso_status pso_step_ranked(empso_ctx *ctx, const double *misfit, const double 
 empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, float lr,
                             uint64_t seed);
 
+/* Tensor-core path of this context's dense layers: 1 = tcgen05.mma with
+ * the accumulator in tensor memory (default), 0 = mma.sync.  Both compute
+ * BF16 products with FP32 accumulation. */
+empso_status surrogate_set_backend(empso_ctx *ctx, int32_t kind);
+
 /* Predicted log misfit: particles device [P][K] -> logphi device [P]. */
 empso_status surrogate_predict(empso_ctx *ctx, const float *particles, int32_t P, float *logphi,
                                void *stream);

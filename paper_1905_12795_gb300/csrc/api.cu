@@ -1250,6 +1250,9 @@ empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, fl
     CK(ctx, cudaMemset(s.count, 0, 4));
     CK(ctx, cudaMemcpy(s.stats, stats0, 8, cudaMemcpyHostToDevice));
     CK(ctx, sur_refresh_bf16(s, 0));
+    CK(ctx, sur_prepare_tc());
+    s.tc = 1;
+    s.err = ctx->dev_err;
     CK(ctx, cudaDeviceSynchronize());
     ctx->has_sur = true;
     return EMPSO_OK;
@@ -1261,6 +1264,14 @@ empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, fl
         ctx->err.clear();                                                               \
         if (!ctx->has_sur) return fail(ctx, EMPSO_NOT_INITIALIZED, "no surrogate");      \
     } while (0)
+
+empso_status surrogate_set_backend(empso_ctx *ctx, int32_t kind)
+{
+    NEED_SUR(ctx);
+    if (kind != 0 && kind != 1) return fail(ctx, EMPSO_INVALID_ARG, "backend must be 0 or 1");
+    ctx->sur.tc = kind;
+    return EMPSO_OK;
+}
 
 empso_status surrogate_predict(empso_ctx *ctx, const float *particles, int32_t P, float *logphi,
                                void *stream)

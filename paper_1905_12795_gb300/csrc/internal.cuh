@@ -20,6 +20,18 @@ constexpr int MAX_R = 4;
 constexpr int MAX_PSO_P = 2048;
 constexpr int MAX_PSO_D = 1024;
 
+// Wall-clock limit of every device-side wait (mbarrier phases): a wait that
+// runs past it records EMPSO_TIMEOUT in the context's status word instead of
+// spinning on.
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
 // Device-side description of one modelling grid.
 struct GridDev {
     int nx, nz, pad, R;      // physical nodes, damping cells, stencil radius
@@ -128,6 +140,8 @@ struct SurDev {
     uint64_t seed = 0;
     int sample_step = 0, t = 0;
     float lr = 1e-3f, beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+    int tc = 1;              // dense layers: 1 = tcgen05 (TMEM accumulator), 0 = mma.sync
+    int *err = nullptr;      // status word for a tcgen05 completion wait that gives up
 };
 cudaError_t sur_forward(const SurDev &s, const __nv_bfloat16 *Xb, int n, float *y, cudaStream_t st);
 cudaError_t sur_backward(const SurDev &s, const __nv_bfloat16 *Xb, const float *t, int n, float *loss,
@@ -141,6 +155,7 @@ cudaError_t sur_append(const SurDev &s, const float *x, const double *misfit, co
                        cudaStream_t st);
 cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st);
 cudaError_t sur_select(const float *key, int P, int k, int *rows, cudaStream_t st);
+cudaError_t sur_prepare_tc();
 cudaError_t sur_gather(const float *x, const int *rows, int k, int K, float *out, cudaStream_t st);
 cudaError_t sur_scatter(const int *rows, const double *fk, int k, const float *logphi, int P,
                         double *fit, double *rank, cudaStream_t st);

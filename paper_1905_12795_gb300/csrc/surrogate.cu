@@ -110,10 +110,178 @@ gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int l
             }
 }
 
-cudaError_t gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16 *A, int lda, int a_mk,
+// ---------------------------------------------------------------------------
+// The same product on the 5th-generation tensor cores: tcgen05.mma with BF16
+// operands from shared memory and the FP32 accumulator in tensor memory.
+// One CTA (4 warps) computes a 128 x NT tile (NT <= 256, multiple of 16):
+// threads stage 64-deep k-chunks of A and B into shared memory in the
+// K-major canonical layout without swizzle (8-row x 16-byte core matrices;
+// the two 8-element halves of a 16-deep k-slice 128 bytes apart, successive
+// 8-row groups 256 bytes apart), one thread issues four 128 x NT x 16 MMAs
+// per chunk and commits them to an mbarrier, and after the last chunk every
+// warp reads its 32 accumulator rows with tcgen05.ld for the epilogue.
+// ---------------------------------------------------------------------------
+constexpr int TM = 128, TKC = 64, TNMAX = 256;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// no-swizzle K-major descriptor: start >> 4, LBO (k-direction core stride) >> 4,
+// SBO (m/n-direction core stride) >> 4, descriptor version 1
+__device__ __forceinline__ unsigned long long umma_desc(const void *p, unsigned lbo, unsigned sbo)
+{
+    unsigned long long d = 0;
+    d |= (unsigned long long)((smem_u32(p) >> 4) & 0x3FFF);
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ unsigned umma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+// byte offset of element (row r, k) inside a 16-deep k-slice of a K-major tile
+__device__ __forceinline__ int canon_off(int r, int k)
+{
+    return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(addr), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(128)
+gemm_tc_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda, int a_mk,
+               const __nv_bfloat16 *__restrict__ B, int ldb, int b_nk, const float *__restrict__ bias,
+               int relu, float *Cf, int ldc, __nv_bfloat16 *Cb, int ldcb, int NT, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_base;
+    __shared__ int s_fail;
+    unsigned char *As = tsm;                                   // TKC/16 slices of 128 x 16
+    unsigned char *Bs = tsm + (TKC / 16) * TM * 16 * 2;        // TKC/16 slices of NT x 16
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * NT;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TNMAX)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = tmem_base;
+    const unsigned idesc = umma_idesc(TM, NT);
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    unsigned phase = 0;
+    for (int k0 = 0; k0 < K; k0 += TKC) {
+        // stage A (128 x TKC) and B (NT x TKC) into the canonical layout
+        for (int e = tid; e < TM * TKC; e += 128) {
+            int mm, kk;
+            if (a_mk) { mm = e / TKC; kk = e % TKC; } else { kk = e / TM; mm = e % TM; }
+            const int m = m0 + mm, k = k0 + kk;
+            __nv_bfloat16 v = zero;
+            if (m < M && k < K) v = a_mk ? A[(size_t)m * lda + k] : A[(size_t)k * lda + m];
+            *reinterpret_cast<__nv_bfloat16 *>(As + (kk >> 4) * (TM * 32) + canon_off(mm, kk & 15)) = v;
+        }
+        for (int e = tid; e < NT * TKC; e += 128) {
+            int nn, kk;
+            if (b_nk) { nn = e / TKC; kk = e % TKC; } else { kk = e / NT; nn = e % NT; }
+            const int n = n0 + nn, k = k0 + kk;
+            __nv_bfloat16 v = zero;
+            if (n < N && k < K) v = b_nk ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+            *reinterpret_cast<__nv_bfloat16 *>(Bs + (kk >> 4) * (NT * 32) + canon_off(nn, kk & 15)) = v;
+        }
+        // thread-written shared memory -> visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            for (int s = 0; s < TKC / 16; ++s) {
+                const unsigned long long ad = umma_desc(As + s * (TM * 32), 128, 256);
+                const unsigned long long bd = umma_desc(Bs + s * (NT * 32), 128, 256);
+                const unsigned acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                             "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        // the MMAs of this chunk are done before the tiles are restaged (bounded wait)
+        bool done = mbar_try(smem_u32(&mbar), phase);
+        const unsigned long long t0 = global_ns();
+        while (!done && global_ns() - t0 <= WAIT_LIMIT_NS) done = mbar_try(smem_u32(&mbar), phase);
+        if (!done) s_fail = 1;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        __syncthreads();
+    }
+    // epilogue: warp w reads accumulator rows 32 w .. 32 w + 31 (TMEM lanes)
+    const int row = m0 + 32 * warp + (tid & 31);
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+        unsigned r[16];
+        const unsigned taddr = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                       "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                       "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                     : "r"(taddr)
+                     : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (row < M && !s_fail) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = n0 + c0 + j;
+                if (n >= N || c0 + j >= NT) continue;
+                float v = __uint_as_float(r[j]);
+                if (bias) v += bias[n];
+                if (relu) v = fmaxf(v, 0.f);
+                if (Cf) Cf[(size_t)row * ldc + n] = v;
+                if (Cb) Cb[(size_t)row * ldcb + n] = __float2bfloat16(v);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TNMAX) : "memory");
+    if (tid == 0 && s_fail) atomicExch(err, EMPSO_TIMEOUT);
+}
+
+cudaError_t gemm(const SurDev &s, cudaStream_t st, int M, int N, int K, const __nv_bfloat16 *A, int lda, int a_mk,
                  const __nv_bfloat16 *B, int ldb, int b_nk, const float *bias, int relu, float *Cf,
                  int ldc, __nv_bfloat16 *Cb, int ldcb)
 {
+    if (s.tc && s.err) {
+        const int NT = N >= TNMAX ? TNMAX : ((N + 15) / 16) * 16;
+        dim3 grid((N + NT - 1) / NT, (M + TM - 1) / TM);
+        const size_t smem = (size_t)(TKC / 16) * (TM + NT) * 32;
+        gemm_tc_kernel<<<grid, 128, smem, st>>>(M, N, K, A, lda, a_mk, B, ldb, b_nk, bias, relu, Cf,
+                                                ldc, Cb, ldcb, NT, s.err);
+        return cudaGetLastError();
+    }
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
     gemm_bf16_kernel<<<grid, 128, 0, st>>>(M, N, K, A, lda, a_mk, B, ldb, b_nk, bias, relu, Cf, ldc,
                                            Cb, ldcb);
@@ -446,13 +614,20 @@ inline int blocks_for(long long n, int per = 256)
 // host-side launchers used by api.cu
 // ---------------------------------------------------------------------------
 
+// opt the tcgen05 GEMM into its 48 KiB of dynamic shared memory (current device)
+cudaError_t sur_prepare_tc()
+{
+    return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (TKC / 16) * (TM + TNMAX) * 32);
+}
+
 cudaError_t sur_forward(const SurDev &s, const __nv_bfloat16 *Xb, int n, float *y, cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = gemm(st, n, s.H, s.K, Xb, s.K, 1, s.W1b, s.K, 1, s.p + s.off_b1, 1, s.Z1, s.H, s.A1b,
+    if ((e = gemm(s, st, n, s.H, s.K, Xb, s.K, 1, s.W1b, s.K, 1, s.p + s.off_b1, 1, s.Z1, s.H, s.A1b,
                   s.H)))
         return e;
-    if ((e = gemm(st, n, s.H, s.H, s.A1b, s.H, 1, s.W2b, s.H, 1, s.p + s.off_b2, 0, s.Z2, s.H,
+    if ((e = gemm(s, st, n, s.H, s.H, s.A1b, s.H, 1, s.W2b, s.H, 1, s.p + s.off_b2, 0, s.Z2, s.H,
                   nullptr, 0)))
         return e;
     head_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(s.Z2, n, s.H, s.p + s.off_w3, s.p + s.off_b3, y);
@@ -475,17 +650,17 @@ cudaError_t sur_backward(const SurDev &s, const __nv_bfloat16 *Xb, const float *
                                                              s.dZf, s.dZb);
     colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(s.dZf, nullptr, nullptr, n, s.H, s.g + s.off_b2);
     // g_W2[h][h'] = sum_b dZ2[b][h] A1[b][h']
-    if ((e = gemm(st, s.H, s.H, n, s.dZb, s.H, 0, s.A1b, s.H, 0, nullptr, 0, s.g + s.off_W2, s.H,
+    if ((e = gemm(s, st, s.H, s.H, n, s.dZb, s.H, 0, s.A1b, s.H, 0, nullptr, 0, s.g + s.off_W2, s.H,
                   nullptr, 0)))
         return e;
     // dA1 = dZ2 W2  -> dZ1 = dA1 [Z1 > 0]
-    if ((e = gemm(st, n, s.H, s.H, s.dZb, s.H, 1, s.W2b, s.H, 0, nullptr, 0, s.dA, s.H, nullptr, 0)))
+    if ((e = gemm(s, st, n, s.H, s.H, s.dZb, s.H, 1, s.W2b, s.H, 0, nullptr, 0, s.dA, s.H, nullptr, 0)))
         return e;
     relu_back_kernel<<<blocks_for((long long)n * s.H), 256, 0, st>>>(s.dA, s.Z1, (long long)n * s.H,
                                                                      s.dZb);
     colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(s.dA, nullptr, nullptr, n, s.H, s.g + s.off_b1);
     // g_W1[h][k] = sum_b dZ1[b][h] X[b][k]
-    if ((e = gemm(st, s.H, s.K, n, s.dZb, s.H, 0, Xb, s.K, 0, nullptr, 0, s.g + s.off_W1, s.K,
+    if ((e = gemm(s, st, s.H, s.K, n, s.dZb, s.H, 0, Xb, s.K, 0, nullptr, 0, s.g + s.off_W1, s.K,
                   nullptr, 0)))
         return e;
     return cudaGetLastError();

@@ -62,9 +62,12 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned pari
 // bounded wait for phase `parity` of `bar`; false after ~2^22 attempts
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
 {
-    for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         if (mbar_test(bar, parity)) return true;
-    return false;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
 }
 
 struct Corner {

@@ -67,6 +67,32 @@ def test_forward_matches_oracle(B):
     ctx.close()
 
 
+@pytest.mark.parametrize("K,n", [(32, 300), (192, 64), (32, 1024)])
+def test_tcgen05_equals_mma_sync(B, K, n):
+    """The tcgen05 (TMEM accumulator) and mma.sync paths compute the same BF16
+    products with FP32 accumulation: predictions and gradients agree to FP32
+    summation-order rounding."""
+    H = 256
+    ctx = _ctx(B, K=K, H=H, P=max(n, 64))
+    rng = np.random.default_rng(K + n)
+    x = torch.tensor(rng.uniform(1500.0, 4700.0, (n, K)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.normal(size=n), dtype=torch.float32, device="cuda")
+    npar = ctx.surrogate_n_params()
+    out = {}
+    for kind in (0, 1):
+        ctx.surrogate_set_backend(kind)
+        y = torch.zeros(n, device="cuda")
+        g = torch.zeros(npar, device="cuda")
+        ctx.surrogate_predict(x, y)
+        ctx.surrogate_grad(x, t, g)
+        torch.cuda.synchronize()
+        out[kind] = (y.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64))
+    assert ctx.device_error() == 0
+    assert _rel(out[1][0], out[0][0]) < 1e-5
+    assert _rel(out[1][1], out[0][1]) < 1e-4
+    ctx.close()
+
+
 def test_gradient_matches_oracle(B):
     K, H, n = 32, 256, 192
     ctx = _ctx(B, K=K, H=H)
