@@ -46,6 +46,7 @@ typedef int32_t empso_status;
 #define EMPSO_TIMEOUT         5  /* a bounded device-side wait gave up */
 #define EMPSO_UNSUPPORTED     6  /* e.g. space order not in {2,4,8}, swarm too large */
 #define EMPSO_NOT_INITIALIZED 7  /* swarm or surrogate used before its init call */
+#define EMPSO_IO_ERROR        8  /* checkpoint file unreadable, unwritable or invalid */
 
 typedef struct empso_ctx empso_ctx;
 
@@ -348,6 +349,41 @@ const char *empso_status_string(empso_status s);
 /* Message of the last failed call on this context (static storage of the
  * context; empty string if none).  ctx may be NULL for empso_create errors. */
 const char *empso_last_error(const empso_ctx *ctx);
+
+/* ---- non-finite misfits ------------------------------------------------
+ * A particle whose misfit sum is NaN or infinite (a diverging or
+ * non-finite model) gets misfit +inf, so it never becomes a personal or
+ * global best (Eq. 1-2 compare misfits), and is counted. */
+
+/* Running count of non-finite misfits since the context was created (or
+ * last reset): read after the work already queued on `stream`, which this
+ * call synchronises; reset != 0 zeroes the count after reading it. */
+empso_status empso_nonfinite_count(empso_ctx *ctx, int64_t *count, int32_t reset, void *stream);
+
+/* Strict mode (off by default).  When on, eval_models, eval_fitness,
+ * empso_generation and surrogate_generation synchronise their stream after
+ * the work and return EMPSO_NONFINITE when that call produced a non-finite
+ * misfit; the outputs are still written, those misfits as +inf. */
+empso_status empso_set_strict(empso_ctx *ctx, int32_t enable);
+
+/* ---- checkpoints ------------------------------------------------------
+ * empso_save writes the swarm state (positions x, velocities v, personal
+ * bests p and their misfits pf, global-best index g, generation counter k,
+ * the last sort order) and, when the surrogate is initialised, its
+ * parameters, Adam moments and step, replay buffer and target statistics to
+ * `path` (written to `path`.tmp and renamed, so an existing checkpoint is
+ * replaced only by a complete one).  The RNG needs no state: its streams are
+ * counters keyed by (seed, k, particle, dimension).  empso_load restores
+ * them into a context created with the same swarm (P, D, seed, xmin, xmax)
+ * and, if the file holds a surrogate, the same surrogate shape (K, hidden,
+ * capacity); a run resumed from a checkpoint continues bit for bit as the
+ * uninterrupted run would.  Both synchronise the device.  Errors:
+ * EMPSO_IO_ERROR (file cannot be opened, read, written or renamed; bad
+ * magic, version, length or checksum), EMPSO_INVALID_ARG (shape, seed or
+ * bounds mismatch), EMPSO_NOT_INITIALIZED (no swarm, or a surrogate in the
+ * file but none in the context).  The context is left unchanged on error. */
+empso_status empso_save(empso_ctx *ctx, const char *path);
+empso_status empso_load(empso_ctx *ctx, const char *path);
 
 #ifdef __cplusplus
 }

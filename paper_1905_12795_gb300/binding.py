@@ -23,7 +23,7 @@ _f64 = ctypes.c_double
 _vp = ctypes.c_void_p
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
-          5: "TIMEOUT", 6: "UNSUPPORTED", 7: "NOT_INITIALIZED"}
+          5: "TIMEOUT", 6: "UNSUPPORTED", 7: "NOT_INITIALIZED", 8: "IO_ERROR"}
 
 EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "forward_traces",
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
@@ -31,6 +31,7 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "empso_generation", "empso_autotune", "empso_set_tuning_cache",
            "pso_step_ranked", "surrogate_init", "surrogate_set_backend", "surrogate_predict", "surrogate_add",
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
+           "empso_nonfinite_count", "empso_set_strict", "empso_save", "empso_load",
            "empso_status_string", "empso_last_error"]
 
 
@@ -99,6 +100,10 @@ def load():
     L.pso_step_ranked.argtypes = [_vp, _vp, _vp, _vp, P(_i32), _vp]
     L.surrogate_init.argtypes = [_vp, _i32, _i32, _f32, ctypes.c_uint64]
     L.surrogate_set_backend.argtypes = [_vp, _i32]
+    L.empso_nonfinite_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _i32, _vp]
+    L.empso_set_strict.argtypes = [_vp, _i32]
+    L.empso_save.argtypes = [_vp, ctypes.c_char_p]
+    L.empso_load.argtypes = [_vp, ctypes.c_char_p]
     L.surrogate_predict.argtypes = [_vp, _vp, _i32, _vp, _vp]
     L.surrogate_add.argtypes = [_vp, _vp, _vp, _i32, _vp]
     L.surrogate_train.argtypes = [_vp, _i32, _i32, _vp]
@@ -242,6 +247,25 @@ class Context:
         k, c = _i32(), _i32()
         self._check(self._L.empso_last_launch(self._h, ctypes.byref(k), ctypes.byref(c)))
         return k.value, c.value
+
+    def nonfinite_count(self, reset=False):
+        """Non-finite misfits (returned as +inf) since creation or the last reset."""
+        n = ctypes.c_int64()
+        self._check(self._L.empso_nonfinite_count(self._h, ctypes.byref(n), 1 if reset else 0,
+                                                  _stream()))
+        return n.value
+
+    def set_strict(self, enable=True):
+        """Evaluation calls raise EmpsoError(NONFINITE) when they produce a non-finite misfit."""
+        self._check(self._L.empso_set_strict(self._h, 1 if enable else 0))
+
+    def save(self, path):
+        """Checkpoint the swarm (and surrogate) state to a file."""
+        self._check(self._L.empso_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Restore a checkpoint written by save() into a context of the same shape."""
+        self._check(self._L.empso_load(self._h, os.fsencode(path)))
 
     def set_timing(self, enable=True):
         self._check(self._L.empso_set_timing(self._h, 1 if enable else 0))

@@ -54,6 +54,8 @@ struct empso_ctx {
     int last_path = 0;              // 1 streaming, 2 resident (last modelling launch)
     int last_C = 0;
     int *dev_err = nullptr;         // device status word set by bounded waits that give up
+    unsigned long long *nonfinite = nullptr;  // non-finite misfits: {running, this call}
+    bool strict = false;            // report non-finite misfits as EMPSO_NONFINITE
 
     // swarm
     bool has_pso = false;
@@ -540,7 +542,8 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
         ctx->last_C = 1;
     }
     if (ctx->timing) CK(ctx, mark(ctx->tev[2], st));
-    if (misfit) CK(ctx, launch_finalize(ctx->partial, p.weights, p.M, p.S, misfit, st));
+    if (misfit)
+        CK(ctx, launch_finalize(ctx->partial, p.weights, p.M, p.S, misfit, ctx->nonfinite, st));
     if (ctx->timing) {
         CK(ctx, mark(ctx->tev[3], st));
         ctx->timed = true;
@@ -555,6 +558,26 @@ empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shot
     empso_status rc = plan_batch(ctx, mod, shots, S, d_obs, traces, p, nullptr, st);
     if (rc) return rc;
     return enqueue_batch(ctx, mod, p, misfit, st);
+}
+
+// Strict mode: zero the per-call count of non-finite misfits before the
+// work, read it back (synchronising the stream) after it.
+empso_status strict_begin(empso_ctx *ctx, cudaStream_t st)
+{
+    if (ctx->strict) CK(ctx, cudaMemsetAsync(ctx->nonfinite + 1, 0, sizeof(unsigned long long), st));
+    return EMPSO_OK;
+}
+
+empso_status strict_end(empso_ctx *ctx, empso_status rc, cudaStream_t st)
+{
+    if (rc || !ctx->strict) return rc;
+    unsigned long long n = 0;
+    CK(ctx, cudaMemcpyAsync(&n, ctx->nonfinite + 1, sizeof n, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    if (n)
+        return fail(ctx, EMPSO_NONFINITE,
+                    std::to_string(n) + " non-finite misfit(s), returned as +inf");
+    return EMPSO_OK;
 }
 
 void free_ctx(empso_ctx *c)
@@ -576,6 +599,7 @@ void free_ctx(empso_ctx *c)
     cudaFree(c->stage_dev);
     cudaFree(c->counter);
     cudaFree(c->dev_err);
+    cudaFree(c->nonfinite);
     cudaFree(c->pso_mem);
     cudaFree(c->pso_int);
     cudaFree(c->xf);
@@ -610,6 +634,7 @@ const char *empso_status_string(empso_status s)
     case EMPSO_TIMEOUT: return "device wait timed out";
     case EMPSO_UNSUPPORTED: return "unsupported";
     case EMPSO_NOT_INITIALIZED: return "not initialised";
+    case EMPSO_IO_ERROR: return "file error";
     default: return "unknown status";
     }
 }
@@ -684,7 +709,9 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
                 return bail(rc);
         }
         if ((rc = ck(cudaMalloc(&ctx->dev_err, sizeof(int)), "error word")) ||
-            (rc = ck(cudaMemset(ctx->dev_err, 0, sizeof(int)), "error word")))
+            (rc = ck(cudaMemset(ctx->dev_err, 0, sizeof(int)), "error word")) ||
+            (rc = ck(cudaMalloc(&ctx->nonfinite, 2 * sizeof(unsigned long long)), "counters")) ||
+            (rc = ck(cudaMemset(ctx->nonfinite, 0, 2 * sizeof(unsigned long long)), "counters")))
             return bail(rc);
     }
 
@@ -802,7 +829,9 @@ empso_status eval_models(empso_ctx *ctx, const float *vel, int32_t M, const emps
     Models mod;
     mod.vel = vel;
     mod.M = M;
-    return run_batch(ctx, mod, shots, S, d_obs, nullptr, misfit, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = strict_begin(ctx, st))) return rc;
+    return strict_end(ctx, run_batch(ctx, mod, shots, S, d_obs, nullptr, misfit, st), st);
 }
 
 empso_status eval_fitness(empso_ctx *ctx, const float *particles, int32_t P,
@@ -824,7 +853,9 @@ empso_status eval_fitness(empso_ctx *ctx, const float *particles, int32_t P,
     Models mod;
     mod.particles = particles;
     mod.M = P;
-    return run_batch(ctx, mod, shots, S, d_obs, nullptr, misfit, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = strict_begin(ctx, st))) return rc;
+    return strict_end(ctx, run_batch(ctx, mod, shots, S, d_obs, nullptr, misfit, st), st);
 }
 
 empso_status pso_init(empso_ctx *ctx, float *particles_out, void *stream)
@@ -970,8 +1001,9 @@ empso_status empso_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S
         ctx->graphs.push_back(e);
         ge = &ctx->graphs.back();
     }
+    if ((rc = strict_begin(ctx, st))) return rc;
     CK(ctx, cudaGraphLaunch(ge->exec, st));
-    return EMPSO_OK;
+    return strict_end(ctx, EMPSO_OK, st);
 }
 
 namespace {
@@ -1355,6 +1387,7 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
     int have = 0;
     CK(ctx, cudaMemcpyAsync(&have, s.count, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaStreamSynchronize(st));
+    if ((rc = strict_begin(ctx, st))) return rc;
     Models mod;
     int k;
     if (have < warm) {
@@ -1383,6 +1416,262 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
     if (misfit_out)
         CK(ctx, cudaMemcpyAsync(misfit_out, ctx->fit_full, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
     if (n_modelled) *n_modelled = k;
+    return strict_end(ctx, EMPSO_OK, st);
+}
+
+empso_status empso_set_strict(empso_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    ctx->strict = enable != 0;
+    return EMPSO_OK;
+}
+
+empso_status empso_nonfinite_count(empso_ctx *ctx, int64_t *count, int32_t reset, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!count) return fail(ctx, EMPSO_INVALID_ARG, "count is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long n = 0;
+    CK(ctx, cudaMemcpyAsync(&n, ctx->nonfinite, sizeof n, cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    if (reset) CK(ctx, cudaMemsetAsync(ctx->nonfinite, 0, sizeof n, st));
+    *count = (int64_t)n;
+    return EMPSO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints.  File layout (native byte order, no padding):
+//   "EMPSOCK1" | u32 version | u32 parts (1 swarm, 2 surrogate)
+//   swarm:     i32 P, D | u64 seed | i32 g, k | f64 xmin[D], xmax[D]
+//              | f64 x[P D], v[P D], p[P D], pf[P] | i32 order[P]
+//   surrogate: i32 K, H, cap | u64 seed | i32 t, sample_step, count
+//              | f32 stats[2] | f32 params[n], m[n], v[n]
+//              | f32 xbuf[rows K], ybuf[rows] with rows = min(count, cap)
+//   u64 FNV-1a hash of every preceding byte
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+const char CK_MAGIC[8] = {'E', 'M', 'P', 'S', 'O', 'C', 'K', '1'};
+constexpr uint32_t CK_VERSION = 1;
+
+uint64_t fnv1a(const unsigned char *p, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct CkOut {
+    std::vector<unsigned char> b;
+    void put(const void *p, size_t n)
+    {
+        const unsigned char *c = (const unsigned char *)p;
+        b.insert(b.end(), c, c + n);
+    }
+    template <class T> void val(T v) { put(&v, sizeof v); }
+};
+
+struct CkIn {
+    const std::vector<unsigned char> &b;
+    size_t pos = 0;
+    bool get(void *p, size_t n)
+    {
+        if (n > b.size() - pos) return false;
+        memcpy(p, b.data() + pos, n);
+        pos += n;
+        return true;
+    }
+    template <class T> bool val(T &v) { return get(&v, sizeof v); }
+};
+
+// append n elements of device array d to the checkpoint
+template <class T> cudaError_t dev_put(CkOut &o, const T *d, size_t n)
+{
+    std::vector<T> h(n);
+    cudaError_t e = n ? cudaMemcpy(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost) : cudaSuccess;
+    if (e == cudaSuccess) o.put(h.data(), n * sizeof(T));
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+empso_status empso_save(empso_ctx *ctx, const char *path)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!path || !*path) return fail(ctx, EMPSO_INVALID_ARG, "path is empty");
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm to save");
+    CK(ctx, cudaDeviceSynchronize());
+    CkOut o;
+    o.put(CK_MAGIC, 8);
+    o.val<uint32_t>(CK_VERSION);
+    o.val<uint32_t>(1u | (ctx->has_sur ? 2u : 0u));
+    const PsoDev &q = ctx->pso;
+    const size_t PD = (size_t)q.P * q.D;
+    int gk[2];
+    CK(ctx, cudaMemcpy(gk, q.gk, sizeof gk, cudaMemcpyDeviceToHost));
+    o.val<int32_t>(q.P);
+    o.val<int32_t>(q.D);
+    o.val<uint64_t>(q.seed);
+    o.val<int32_t>(gk[0]);
+    o.val<int32_t>(gk[1]);
+    CK(ctx, dev_put(o, q.xmin, q.D));
+    CK(ctx, dev_put(o, q.xmax, q.D));
+    CK(ctx, dev_put(o, q.x, PD));
+    CK(ctx, dev_put(o, q.v, PD));
+    CK(ctx, dev_put(o, q.p, PD));
+    CK(ctx, dev_put(o, q.pf, (size_t)q.P));
+    CK(ctx, dev_put(o, q.order, (size_t)q.P));
+    if (ctx->has_sur) {
+        const SurDev &s = ctx->sur;
+        int count = 0;
+        CK(ctx, cudaMemcpy(&count, s.count, sizeof count, cudaMemcpyDeviceToHost));
+        const size_t rows = (size_t)std::min(count, s.cap);
+        o.val<int32_t>(s.K);
+        o.val<int32_t>(s.H);
+        o.val<int32_t>(s.cap);
+        o.val<uint64_t>(s.seed);
+        o.val<int32_t>(s.t);
+        o.val<int32_t>(s.sample_step);
+        o.val<int32_t>(count);
+        CK(ctx, dev_put(o, s.stats, 2));
+        CK(ctx, dev_put(o, s.p, (size_t)s.n_params));
+        CK(ctx, dev_put(o, s.m, (size_t)s.n_params));
+        CK(ctx, dev_put(o, s.v, (size_t)s.n_params));
+        CK(ctx, dev_put(o, s.xbuf, rows * s.K));
+        CK(ctx, dev_put(o, s.ybuf, rows));
+    }
+    o.val<uint64_t>(fnv1a(o.b.data(), o.b.size()));
+    // write beside the target and rename, so a crash never leaves half a file
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(ctx, EMPSO_IO_ERROR, "cannot open " + tmp + " for writing");
+    const bool ok = fwrite(o.b.data(), 1, o.b.size(), f) == o.b.size();
+    if ((fclose(f) != 0) || !ok) {
+        remove(tmp.c_str());
+        return fail(ctx, EMPSO_IO_ERROR, "short write to " + tmp);
+    }
+    if (rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return fail(ctx, EMPSO_IO_ERROR, std::string("cannot rename onto ") + path);
+    }
+    return EMPSO_OK;
+}
+
+empso_status empso_load(empso_ctx *ctx, const char *path)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!path || !*path) return fail(ctx, EMPSO_INVALID_ARG, "path is empty");
+    if (!ctx->has_pso) return fail(ctx, EMPSO_NOT_INITIALIZED, "context has no swarm to restore");
+    std::vector<unsigned char> b;
+    {
+        FILE *f = fopen(path, "rb");
+        if (!f) return fail(ctx, EMPSO_IO_ERROR, std::string("cannot open ") + path);
+        unsigned char buf[1 << 16];
+        size_t n;
+        while ((n = fread(buf, 1, sizeof buf, f)) > 0) b.insert(b.end(), buf, buf + n);
+        const bool bad = ferror(f) != 0;
+        fclose(f);
+        if (bad) return fail(ctx, EMPSO_IO_ERROR, std::string("read error on ") + path);
+    }
+    const auto corrupt = [&](const char *what) {
+        return fail(ctx, EMPSO_IO_ERROR, std::string("not a valid checkpoint (") + what + "): " + path);
+    };
+    if (b.size() < 8 + 8 + 8) return corrupt("too short");
+    uint64_t stored;
+    memcpy(&stored, b.data() + b.size() - 8, 8);
+    if (stored != fnv1a(b.data(), b.size() - 8)) return corrupt("checksum");
+    b.resize(b.size() - 8);
+    CkIn in{b};
+    char magic[8];
+    uint32_t version = 0, parts = 0;
+    if (!in.get(magic, 8) || memcmp(magic, CK_MAGIC, 8) != 0) return corrupt("magic");
+    if (!in.val(version) || version != CK_VERSION) return corrupt("version");
+    if (!in.val(parts) || !(parts & 1u)) return corrupt("parts");
+    const PsoDev &q = ctx->pso;
+    int32_t P, D, g, k;
+    uint64_t seed;
+    if (!in.val(P) || !in.val(D) || !in.val(seed) || !in.val(g) || !in.val(k)) return corrupt("swarm header");
+    if (P != q.P || D != q.D || seed != q.seed)
+        return fail(ctx, EMPSO_INVALID_ARG, "checkpoint swarm (P, D, seed) differs from this context's");
+    if (g < 0 || g >= P || k < 0) return corrupt("swarm g, k");
+    const size_t PD = (size_t)P * D;
+    std::vector<double> lo(D), hi(D), x(PD), v(PD), pp(PD), pf(P);
+    std::vector<int32_t> order(P);
+    if (!in.get(lo.data(), 8 * lo.size()) || !in.get(hi.data(), 8 * hi.size()) ||
+        !in.get(x.data(), 8 * PD) || !in.get(v.data(), 8 * PD) || !in.get(pp.data(), 8 * PD) ||
+        !in.get(pf.data(), 8 * pf.size()) || !in.get(order.data(), 4 * order.size()))
+        return corrupt("swarm arrays");
+    {
+        std::vector<double> clo(D), chi(D);
+        CK(ctx, cudaMemcpy(clo.data(), q.xmin, 8 * (size_t)D, cudaMemcpyDeviceToHost));
+        CK(ctx, cudaMemcpy(chi.data(), q.xmax, 8 * (size_t)D, cudaMemcpyDeviceToHost));
+        if (memcmp(clo.data(), lo.data(), 8 * (size_t)D) || memcmp(chi.data(), hi.data(), 8 * (size_t)D))
+            return fail(ctx, EMPSO_INVALID_ARG, "checkpoint search bounds differ from this context's");
+    }
+    // surrogate part: validated in full before anything is written
+    int32_t sK = 0, sH = 0, scap = 0, st_t = 0, st_step = 0, count = 0;
+    uint64_t sseed = 0;
+    float stats[2];
+    std::vector<float> sp, sm, sv, xb, yb;
+    const bool file_sur = (parts & 2u) != 0;
+    if (file_sur) {
+        if (!ctx->has_sur)
+            return fail(ctx, EMPSO_NOT_INITIALIZED, "checkpoint holds a surrogate; call surrogate_init first");
+        const SurDev &s = ctx->sur;
+        if (!in.val(sK) || !in.val(sH) || !in.val(scap) || !in.val(sseed) || !in.val(st_t) ||
+            !in.val(st_step) || !in.val(count) || !in.get(stats, sizeof stats))
+            return corrupt("surrogate header");
+        if (sK != s.K || sH != s.H || scap != s.cap)
+            return fail(ctx, EMPSO_INVALID_ARG, "checkpoint surrogate (K, H, capacity) differs from this context's");
+        if (count < 0 || st_t < 0 || st_step < 0) return corrupt("surrogate counters");
+        const size_t np = (size_t)s.n_params, rows = (size_t)std::min(count, scap);
+        sp.resize(np);
+        sm.resize(np);
+        sv.resize(np);
+        xb.resize(rows * sK);
+        yb.resize(rows);
+        if (!in.get(sp.data(), 4 * np) || !in.get(sm.data(), 4 * np) || !in.get(sv.data(), 4 * np) ||
+            !in.get(xb.data(), 4 * xb.size()) || !in.get(yb.data(), 4 * yb.size()))
+            return corrupt("surrogate arrays");
+    }
+    if (in.pos != b.size()) return corrupt("trailing bytes");
+    CK(ctx, cudaDeviceSynchronize());
+    CK(ctx, cudaMemcpy(q.x, x.data(), 8 * PD, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(q.v, v.data(), 8 * PD, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(q.p, pp.data(), 8 * PD, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(q.pf, pf.data(), 8 * (size_t)P, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(q.order, order.data(), 4 * (size_t)P, cudaMemcpyHostToDevice));
+    const int gk[2] = {g, k};
+    CK(ctx, cudaMemcpy(q.gk, gk, sizeof gk, cudaMemcpyHostToDevice));
+    CK(ctx, launch_xf_from_x(q, 0));
+    if (file_sur) {
+        SurDev &s = ctx->sur;
+        CK(ctx, cudaMemcpy(s.p, sp.data(), 4 * sp.size(), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(s.m, sm.data(), 4 * sm.size(), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(s.v, sv.data(), 4 * sv.size(), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(s.stats, stats, sizeof stats, cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(s.count, &count, sizeof count, cudaMemcpyHostToDevice));
+        if (!xb.empty()) {
+            CK(ctx, cudaMemcpy(s.xbuf, xb.data(), 4 * xb.size(), cudaMemcpyHostToDevice));
+            CK(ctx, cudaMemcpy(s.ybuf, yb.data(), 4 * yb.size(), cudaMemcpyHostToDevice));
+        }
+        s.seed = sseed;
+        s.t = st_t;
+        s.sample_step = st_step;
+        CK(ctx, sur_refresh_bf16(s, 0));
+    }
+    CK(ctx, cudaDeviceSynchronize());
     return EMPSO_OK;
 }
 

@@ -80,7 +80,7 @@ cudaError_t launch_wave(const GridDev *grids_dev, const Inst *insts, int n_inst,
                         int *counter, float *slots, long long slot_floats, int n_ctas,
                         int threads, double *partial, cudaStream_t st);
 cudaError_t launch_finalize(const double *partial, const float *weights, int P, int S,
-                            double *misfit, cudaStream_t st);
+                            double *misfit, unsigned long long *nf, cudaStream_t st);
 int wave_max_ctas_per_sm(int threads);
 
 // On-chip variant (wave_resident.cu): one thread-block cluster per instance.

@@ -282,7 +282,7 @@ extern "C" empso_status eval_models_noalloc(const empso_grid *grid, const float 
         (e = cudaMemsetAsync(L.counter, 0, sizeof(int), st)) != cudaSuccess ||
         (e = launch_wave(L.grid, L.insts, (int)n_inst, L.counter, L.slots, 2 * p.g.field, (int)n_slots,
                          512, L.partial, st)) != cudaSuccess ||
-        (e = launch_finalize(L.partial, L.weights, M, S, misfit, st)) != cudaSuccess)
+        (e = launch_finalize(L.partial, L.weights, M, S, misfit, nullptr, st)) != cudaSuccess)
         return nfail(EMPSO_CUDA_ERROR, cudaGetErrorString(e));
     return EMPSO_OK;
 }

@@ -225,23 +225,29 @@ cudaError_t launch_wave(const GridDev *grids_dev, const Inst *insts, int n_inst,
 }
 
 // misfit[p] = sum_s weight_s partial[p][s] in fixed shot order; non-finite
-// sums become +inf.
+// sums become +inf and are counted in nf[0] (running) and nf[1] (per call).
 __global__ void finalize_kernel(const double *partial, const float *weights, int P, int S,
-                                double *misfit)
+                                double *misfit, unsigned long long *nf)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     double s = 0.0;
     for (int k = 0; k < S; ++k) s += (double)weights[k] * partial[(size_t)p * S + k];
-    if (!isfinite(s)) s = __longlong_as_double(0x7ff0000000000000LL);
+    if (!isfinite(s)) {
+        s = __longlong_as_double(0x7ff0000000000000LL);
+        if (nf) {
+            atomicAdd(nf, 1ull);
+            atomicAdd(nf + 1, 1ull);
+        }
+    }
     misfit[p] = s;
 }
 
 cudaError_t launch_finalize(const double *partial, const float *weights, int P, int S,
-                            double *misfit, cudaStream_t st)
+                            double *misfit, unsigned long long *nf, cudaStream_t st)
 {
     if (P <= 0) return cudaSuccess;
-    finalize_kernel<<<(P + 127) / 128, 128, 0, st>>>(partial, weights, P, S, misfit);
+    finalize_kernel<<<(P + 127) / 128, 128, 0, st>>>(partial, weights, P, S, misfit, nf);
     return cudaGetLastError();
 }
 

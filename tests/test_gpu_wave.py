@@ -328,6 +328,17 @@ def test_nonfinite_model_gives_inf_misfit(B, kind):
     m = mis.cpu().numpy()
     assert np.isinf(m[1]) and m[1] > 0
     assert np.isfinite(m[0]) and m[0] == m[2]
+    assert ctx.nonfinite_count() == 1
+    # strict mode: the call reports it, the outputs are still written
+    ctx.set_strict(True)
+    mis.zero_()
+    with pytest.raises(B.EmpsoError) as e:
+        ctx.eval_models(_dev(vel), sh, dobs, mis)
+    assert e.value.status == 4
+    assert np.array_equal(mis.cpu().numpy(), m)
+    assert ctx.nonfinite_count(reset=True) == 2 and ctx.nonfinite_count() == 0
+    ctx.eval_models(_dev(vel[[0, 2]]), sh, dobs, torch.zeros_like(mis[:2]))   # finite: no error
+    ctx.set_strict(False)
     ctx.pso_init()
     ctx.pso_step(mis)
     pf = torch.zeros(3, dtype=torch.float64, device="cuda")
