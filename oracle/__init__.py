@@ -22,6 +22,10 @@ itself lives in ``tests/test_oracle_*.py``):
   CFL limit; closed-form eigenvalue of the checkerboard mode.
 * ``interp_matrix`` / ``interp_model`` - pinned: node interpolation, linear
   reproduction, scipy natural ``CubicSpline``, ``numpy.interp``.
+* ``interp_levels`` / ``level_bounds`` (irregular level-wise control grid,
+  water layer, depth-dependent ranges) - pinned: ``numpy.interp`` along each
+  level and between levels, the tensor-product bilinear mode on a regular
+  layout, node reproduction, constant extension, straight-line ranges.
 * ``philox`` - pinned: published known-answer vectors of Philox4x32-10.
 * ``log`` / ``cos2pi`` / ``normal`` - pinned: ``math.log`` / ``math.cos``
   within 2 ulp, normality (KS test).
@@ -98,6 +102,9 @@ def lib():
                                     _i]
         L.eo_interp_matrix.argtypes = [_i, _i, _i, _pd]
         L.eo_interp_model.argtypes = [_pd, _i, _i, _i, _i, _i, _d, _d, _pd]
+        L.eo_interp_levels.argtypes = [_i, _pd, _pi, _pd, _pd, _i, _i, _d, _d, _d, _d, _d, _d,
+                                       _pd]
+        L.eo_level_bounds.argtypes = [_i, _pd, _pi, _d, _d, _d, _d, _d, _d, _pd, _pd]
         L.eo_philox.argtypes = [_pu32, _pu32, _pu32]
         L.eo_uniform.argtypes = [_u64, _u32, _u32, _u32, _u32]
         L.eo_uniform.restype = _d
@@ -265,6 +272,32 @@ def interp_model(C, nz: int, nx: int, mode: int = 0, vmin: float = -np.inf,
 # --------------------------------------------------------------------------
 
 INIT_X, INIT_V, U1, U2, EM_U, EM_N = range(6)
+
+
+def interp_levels(level_z, level_n, node_x, C, nz: int, nx: int, hx: float, hz: float,
+                  water_z: float = 0.0, v_water: float = 1500.0, vmin: float = -np.inf,
+                  vmax: float = np.inf) -> np.ndarray:
+    """Velocity [nz][nx] from an irregular level-wise control grid (bilinear
+    two-grid rule, optional fixed water layer, clip)."""
+    lz, nx_ = _f64(level_z), _f64(node_x)
+    ln = np.ascontiguousarray(level_n, dtype=np.int32)
+    Cc = _f64(C)
+    assert Cc.size == nx_.size == ln.sum()
+    V = np.zeros((nz, nx))
+    lib().eo_interp_levels(len(lz), _p(lz), _p(ln, _pi), _p(nx_), _p(Cc), nz, nx, hx, hz,
+                           water_z, v_water, vmin, vmax, _p(V))
+    return V
+
+
+def level_bounds(level_z, level_n, v_first, v_last, lo_first, hi_first, lo_last, hi_last):
+    """Per-node search ranges (xmin, xmax) of an irregular level grid."""
+    lz = _f64(level_z)
+    ln = np.ascontiguousarray(level_n, dtype=np.int32)
+    K = int(ln.sum())
+    lo, hi = np.zeros(K), np.zeros(K)
+    lib().eo_level_bounds(len(lz), _p(lz), _p(ln, _pi), v_first, v_last, lo_first, hi_first,
+                          lo_last, hi_last, _p(lo), _p(hi))
+    return lo, hi
 
 
 def philox(ctr, key) -> np.ndarray:

@@ -425,6 +425,83 @@ void eo_interp_model(const double *C, int Kz, int Kx, int nz, int nx, int mode,
     free(Wx);
 }
 
+/* Irregular control grid of the paper's "Testing approach" (two-grid
+ * strategy with a variable node spacing): L depth levels at z_l (strictly
+ * increasing, metres), level l holding n_l nodes at x positions
+ * node_x[off_l .. off_l + n_l) (strictly increasing) with values
+ * C[off_l ..].  The FD-grid velocity at (x, z) = (i hx, j hz) is the
+ * bilinear rule taken level-wise: along each of the two levels bracketing
+ * z, linear interpolation in x between that level's neighbouring nodes
+ * (the end values held beyond the first/last node), then linear
+ * interpolation in z between the two levels (the first/last level held
+ * above/below).  Points at depth z <= water_z (when water_z > 0) take the
+ * fixed water velocity v_water (the water layer the prior information
+ * fixes).  The result is clipped to [vmin, vmax]. */
+static double eo_level_profile(const double *xs, const double *cs, int n, double x)
+{
+    if (n == 1 || x <= xs[0]) return cs[0];
+    if (x >= xs[n - 1]) return cs[n - 1];
+    int i = 0;
+    while (!(x < xs[i + 1])) ++i;
+    double a = (x - xs[i]) / (xs[i + 1] - xs[i]);
+    return (1.0 - a) * cs[i] + a * cs[i + 1];
+}
+
+void eo_interp_levels(int L, const double *level_z, const int *level_n, const double *node_x,
+                      const double *C, int nz, int nx, double hx, double hz, double water_z,
+                      double v_water, double vmin, double vmax, double *V)
+{
+    int *off = malloc(sizeof(int) * (L + 1));
+    off[0] = 0;
+    for (int l = 0; l < L; ++l) off[l + 1] = off[l] + level_n[l];
+    for (int j = 0; j < nz; ++j) {
+        double z = j * hz;
+        int la, lb;
+        double b;
+        if (z <= level_z[0]) { la = lb = 0; b = 0.0; }
+        else if (z >= level_z[L - 1]) { la = lb = L - 1; b = 0.0; }
+        else {
+            la = 0;
+            while (!(z < level_z[la + 1])) ++la;
+            lb = la + 1;
+            b = (z - level_z[la]) / (level_z[lb] - level_z[la]);
+        }
+        for (int i = 0; i < nx; ++i) {
+            double x = i * hx;
+            double va = eo_level_profile(node_x + off[la], C + off[la], level_n[la], x);
+            double vb = eo_level_profile(node_x + off[lb], C + off[lb], level_n[lb], x);
+            double v = (1.0 - b) * va + b * vb;
+            if (water_z > 0.0 && z <= water_z) v = v_water;
+            if (v < vmin) v = vmin;
+            if (v > vmax) v = vmax;
+            V[(size_t)j * nx + i] = v;
+        }
+    }
+    free(off);
+}
+
+/* Depth-dependent search ranges ("Testing approach"): the first and last
+ * levels get [v (1 - lo), v (1 + hi)] around the prior 1-D velocity v of that
+ * level; the limits of every intermediate level lie on the straight lines (in
+ * depth) through the first and last levels' minima and maxima.  Every node
+ * of a level shares its level's range.  xmin, xmax: [sum n_l]. */
+void eo_level_bounds(int L, const double *level_z, const int *level_n, double v_first,
+                     double v_last, double lo_first, double hi_first, double lo_last,
+                     double hi_last, double *xmin, double *xmax)
+{
+    double min0 = v_first * (1.0 - lo_first), max0 = v_first * (1.0 + hi_first);
+    double min1 = v_last * (1.0 - lo_last), max1 = v_last * (1.0 + hi_last);
+    int k = 0;
+    for (int l = 0; l < L; ++l) {
+        double s = L > 1 ? (level_z[l] - level_z[0]) / (level_z[L - 1] - level_z[0]) : 0.0;
+        double lo = min0 + s * (min1 - min0), hi = max0 + s * (max1 - max0);
+        for (int i = 0; i < level_n[l]; ++i, ++k) {
+            xmin[k] = lo;
+            xmax[k] = hi;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Counter-based random numbers                                              */
 /* ------------------------------------------------------------------------ */
