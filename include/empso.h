@@ -350,6 +350,42 @@ const char *empso_status_string(empso_status s);
  * context; empty string if none).  ctx may be NULL for empso_create errors. */
 const char *empso_last_error(const empso_ctx *ctx);
 
+/* ---- irregular control grid ("Testing approach") -----------------------
+ * The paper's two-grid strategy with a variable node spacing: L depth
+ * levels at level_z[l] (metres, strictly increasing), level l holding
+ * level_count[l] >= 1 nodes at x positions node_x[o_l .. o_l + level_count[l])
+ * (strictly increasing; o_l = sum of the earlier counts).  A particle on
+ * this grid has K = sum level_count values in that order.  The FD-grid
+ * velocity at (x, z) is bilinear level-wise: on the two levels bracketing
+ * z, linear in x between that level's neighbouring nodes (end values held
+ * beyond the ends), then linear in z between the two levels (the first or
+ * last level held above or below); then clipped to [vmin, vmax].
+ * empso_set_levels switches grid `grid_id` to this rule (interp_mode 2),
+ * computing its per-point taps on the device; it synchronises the device
+ * and drops captured generations.  K <= 1024.  Errors: INVALID_ARG,
+ * UNSUPPORTED (K > 1024), OOM/CUDA_ERROR. */
+empso_status empso_set_levels(empso_ctx *ctx, int32_t grid_id, int32_t n_levels,
+                              const float *level_z, const int32_t *level_count,
+                              const float *node_x);
+
+/* Fixed water layer (the prior information of "Testing approach"): every
+ * FD point of grid `grid_id` at depth z <= water_depth takes v_water (then
+ * the clip), whatever the particle; water_depth <= 0 removes the layer.
+ * Applies to every interpolation mode; synchronises the device and drops
+ * captured generations. */
+empso_status empso_set_water(empso_ctx *ctx, int32_t grid_id, float water_depth, float v_water);
+
+/* Depth-dependent search ranges ("Testing approach"): the first and last
+ * levels get [v (1 - lo), v (1 + hi)] around the prior 1-D velocity v_first
+ * / v_last of that level; every intermediate level's limits lie on the
+ * straight lines, in depth, through the first and last levels' minima and
+ * maxima.  All nodes of a level share its range.  Host function (no
+ * context): xmin, xmax host [sum level_count].  INVALID_ARG on bad input. */
+empso_status empso_level_bounds(int32_t n_levels, const float *level_z,
+                                const int32_t *level_count, double v_first, double v_last,
+                                double lo_first, double hi_first, double lo_last,
+                                double hi_last, double *xmin, double *xmax);
+
 /* ---- non-finite misfits ------------------------------------------------
  * A particle whose misfit sum is NaN or infinite (a diverging or
  * non-finite model) gets misfit +inf, so it never becomes a personal or

@@ -32,6 +32,7 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "pso_step_ranked", "surrogate_init", "surrogate_set_backend", "surrogate_predict", "surrogate_add",
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
            "empso_nonfinite_count", "empso_set_strict", "empso_save", "empso_load",
+           "empso_set_levels", "empso_set_water", "empso_level_bounds",
            "empso_status_string", "empso_last_error"]
 
 
@@ -57,6 +58,20 @@ class EmpsoError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+def level_bounds(level_z, level_count, v_first, v_last, lo_first, hi_first, lo_last, hi_last):
+    """Depth-dependent search ranges (xmin, xmax) of an irregular level grid."""
+    lz = np.ascontiguousarray(level_z, dtype=np.float32)
+    lc = np.ascontiguousarray(level_count, dtype=np.int32)
+    K = int(lc.sum())
+    lo, hi = np.zeros(K), np.zeros(K)
+    rc = load().empso_level_bounds(len(lz), lz.ctypes.data, lc.ctypes.data, v_first, v_last,
+                                   lo_first, hi_first, lo_last, hi_last, lo.ctypes.data,
+                                   hi.ctypes.data)
+    if rc != 0:
+        raise EmpsoError(rc, "invalid level layout or ranges")
+    return lo, hi
 
 
 def lib_path() -> str:
@@ -102,6 +117,9 @@ def load():
     L.surrogate_set_backend.argtypes = [_vp, _i32]
     L.empso_nonfinite_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _i32, _vp]
     L.empso_set_strict.argtypes = [_vp, _i32]
+    L.empso_set_levels.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
+    L.empso_set_water.argtypes = [_vp, _i32, _f32, _f32]
+    L.empso_level_bounds.argtypes = [_i32, _vp, _vp, _f64, _f64, _f64, _f64, _f64, _f64, _vp, _vp]
     L.empso_save.argtypes = [_vp, ctypes.c_char_p]
     L.empso_load.argtypes = [_vp, ctypes.c_char_p]
     L.surrogate_predict.argtypes = [_vp, _vp, _i32, _vp, _vp]
@@ -247,6 +265,18 @@ class Context:
         k, c = _i32(), _i32()
         self._check(self._L.empso_last_launch(self._h, ctypes.byref(k), ctypes.byref(c)))
         return k.value, c.value
+
+    def set_levels(self, grid_id, level_z, level_count, node_x):
+        """Irregular level-wise control grid on grid `grid_id` (interp mode 2)."""
+        lz = np.ascontiguousarray(level_z, dtype=np.float32)
+        lc = np.ascontiguousarray(level_count, dtype=np.int32)
+        nx = np.ascontiguousarray(node_x, dtype=np.float32)
+        self._check(self._L.empso_set_levels(self._h, int(grid_id), len(lz), lz.ctypes.data,
+                                             lc.ctypes.data, nx.ctypes.data))
+
+    def set_water(self, grid_id, water_depth, v_water=1500.0):
+        self._check(self._L.empso_set_water(self._h, int(grid_id), float(water_depth),
+                                            float(v_water)))
 
     def nonfinite_count(self, reset=False):
         """Non-finite misfits (returned as +inf) since creation or the last reset."""

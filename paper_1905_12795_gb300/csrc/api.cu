@@ -21,6 +21,11 @@ struct GridHost {
     empso_grid spec;
     GridDev dev;
     float *ex = nullptr, *ez = nullptr, *wavelet = nullptr, *Wx = nullptr, *Wz = nullptr;
+    // irregular level grid (empso_set_levels)
+    float *level_z = nullptr, *node_x = nullptr;
+    int *level_off = nullptr;
+    int4 *lidx = nullptr;
+    float4 *lw = nullptr;
 };
 
 struct empso_ctx {
@@ -163,6 +168,7 @@ empso_status setup_grid(empso_ctx *ctx, GridHost &G, int id)
     g.field = (long long)g.rows * g.pitch;
     g.kx = s.kx;
     g.kz = s.kz;
+    g.K = s.kx * s.kz;
     g.mode = s.interp_mode;
     g.hx = s.hx;
     g.hz = s.hz;
@@ -580,6 +586,22 @@ empso_status strict_end(empso_ctx *ctx, empso_status rc, cudaStream_t st)
     return EMPSO_OK;
 }
 
+// Re-upload one grid's device record after a change of its parameterisation
+// and drop the captured generations (their interpolation launches hold the
+// old record by value).
+empso_status grid_changed(empso_ctx *ctx, int gid)
+{
+    CK(ctx, cudaDeviceSynchronize());
+    CK(ctx, cudaMemcpy(ctx->grids_dev + gid, &ctx->grids[gid].dev, sizeof(GridDev),
+                       cudaMemcpyHostToDevice));
+    for (auto &e : ctx->graphs) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        cudaFree(e.table);
+    }
+    ctx->graphs.clear();
+    return EMPSO_OK;
+}
+
 void free_ctx(empso_ctx *c)
 {
     if (!c) return;
@@ -590,6 +612,11 @@ void free_ctx(empso_ctx *c)
         cudaFree(G.wavelet);
         cudaFree(G.Wx);
         cudaFree(G.Wz);
+        cudaFree(G.level_z);
+        cudaFree(G.node_x);
+        cudaFree(G.level_off);
+        cudaFree(G.lidx);
+        cudaFree(G.lw);
     }
     cudaFree(c->grids_dev);
     cudaFree(c->rec_dev);
@@ -785,6 +812,95 @@ empso_status empso_grid_info(const empso_ctx *ctx, int32_t grid_id, float *dt, i
     return EMPSO_OK;
 }
 
+empso_status empso_set_levels(empso_ctx *ctx, int32_t grid_id, int32_t n_levels,
+                              const float *level_z, const int32_t *level_count, const float *node_x)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size()) return fail(ctx, EMPSO_INVALID_ARG, "bad grid id");
+    if (n_levels < 1 || n_levels > MAX_PSO_D || !level_z || !level_count || !node_x)
+        return fail(ctx, EMPSO_INVALID_ARG, "need 1 <= n_levels <= 1024 and non-NULL tables");
+    std::vector<int> off(n_levels + 1, 0);
+    for (int l = 0; l < n_levels; ++l) {
+        if (level_count[l] < 1) return fail(ctx, EMPSO_INVALID_ARG, "every level needs a node");
+        if (!std::isfinite(level_z[l]) || (l > 0 && !(level_z[l] > level_z[l - 1])))
+            return fail(ctx, EMPSO_INVALID_ARG, "level depths must be finite and strictly increasing");
+        off[l + 1] = off[l] + level_count[l];
+        if (off[l + 1] > MAX_PSO_D) return fail(ctx, EMPSO_UNSUPPORTED, "more than 1024 control nodes");
+    }
+    for (int l = 0; l < n_levels; ++l)
+        for (int k = off[l]; k < off[l + 1]; ++k)
+            if (!std::isfinite(node_x[k]) || (k > off[l] && !(node_x[k] > node_x[k - 1])))
+                return fail(ctx, EMPSO_INVALID_ARG,
+                            "node positions must be finite and strictly increasing within a level");
+    const int K = off[n_levels];
+    GridHost &G = ctx->grids[grid_id];
+    const size_t npts = (size_t)G.dev.nx * G.dev.nz;
+    CK(ctx, cudaDeviceSynchronize());
+    cudaFree(G.level_z);
+    cudaFree(G.node_x);
+    cudaFree(G.level_off);
+    cudaFree(G.lidx);
+    cudaFree(G.lw);
+    G.level_z = G.node_x = nullptr;
+    G.level_off = nullptr;
+    G.lidx = nullptr;
+    G.lw = nullptr;
+    G.dev.mode = G.spec.interp_mode;   // unchanged until the tables are in place
+    CK(ctx, cudaMalloc(&G.level_z, sizeof(float) * n_levels));
+    CK(ctx, cudaMalloc(&G.node_x, sizeof(float) * K));
+    CK(ctx, cudaMalloc(&G.level_off, sizeof(int) * (n_levels + 1)));
+    CK(ctx, cudaMalloc(&G.lidx, sizeof(int4) * npts));
+    CK(ctx, cudaMalloc(&G.lw, sizeof(float4) * npts));
+    CK(ctx, cudaMemcpy(G.level_z, level_z, sizeof(float) * n_levels, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(G.node_x, node_x, sizeof(float) * K, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(G.level_off, off.data(), sizeof(int) * (n_levels + 1), cudaMemcpyHostToDevice));
+    G.dev.lidx = G.lidx;
+    G.dev.lw = G.lw;
+    CK(ctx, launch_level_taps(G.dev, n_levels, G.level_z, G.level_off, G.node_x, G.lidx, G.lw, 0));
+    G.dev.mode = 2;
+    G.dev.K = K;
+    G.spec.interp_mode = 2;
+    return grid_changed(ctx, grid_id);
+}
+
+empso_status empso_set_water(empso_ctx *ctx, int32_t grid_id, float water_depth, float v_water)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (grid_id < 0 || grid_id >= (int)ctx->grids.size()) return fail(ctx, EMPSO_INVALID_ARG, "bad grid id");
+    if (!std::isfinite(water_depth) || !(v_water > 0) || !std::isfinite(v_water))
+        return fail(ctx, EMPSO_INVALID_ARG, "need a finite depth and a positive velocity");
+    GridHost &G = ctx->grids[grid_id];
+    G.dev.water_z = water_depth > 0.f ? water_depth : 0.f;
+    G.dev.v_water = v_water;
+    return grid_changed(ctx, grid_id);
+}
+
+empso_status empso_level_bounds(int32_t n_levels, const float *level_z, const int32_t *level_count,
+                                double v_first, double v_last, double lo_first, double hi_first,
+                                double lo_last, double hi_last, double *xmin, double *xmax)
+{
+    if (n_levels < 1 || !level_z || !level_count || !xmin || !xmax) return EMPSO_INVALID_ARG;
+    for (int l = 0; l < n_levels; ++l)
+        if (level_count[l] < 1 || (l > 0 && !(level_z[l] > level_z[l - 1]))) return EMPSO_INVALID_ARG;
+    const double min0 = v_first * (1.0 - lo_first), max0 = v_first * (1.0 + hi_first);
+    const double min1 = v_last * (1.0 - lo_last), max1 = v_last * (1.0 + hi_last);
+    if (!(min0 <= max0) || !(min1 <= max1)) return EMPSO_INVALID_ARG;
+    const double span = (double)level_z[n_levels - 1] - (double)level_z[0];
+    long long k = 0;
+    for (int l = 0; l < n_levels; ++l) {
+        // position of the level between the first (0) and the last (1) in depth
+        const double s = n_levels > 1 ? ((double)level_z[l] - (double)level_z[0]) / span : 0.0;
+        const double lo = min0 + s * (min1 - min0), hi = max0 + s * (max1 - max0);
+        for (int i = 0; i < level_count[l]; ++i, ++k) {
+            xmin[k] = lo;
+            xmax[k] = hi;
+        }
+    }
+    return EMPSO_OK;
+}
+
 empso_status empso_interp(empso_ctx *ctx, int32_t grid_id, const float *particles, int32_t P,
                           float *vel_out, void *stream)
 {
@@ -844,10 +960,9 @@ empso_status eval_fitness(empso_ctx *ctx, const float *particles, int32_t P,
         return fail(ctx, EMPSO_INVALID_ARG, "bad particles/d_obs/misfit");
     empso_status rc = check_shots(ctx, shots, S, -1);
     if (rc || P == 0) return rc;
-    const int K = ctx->grids[shots[0].grid_id].spec.kx * ctx->grids[shots[0].grid_id].spec.kz;
+    const int K = ctx->grids[shots[0].grid_id].dev.K;
     for (int s = 1; s < S; ++s) {
-        const empso_grid &g = ctx->grids[shots[s].grid_id].spec;
-        if (g.kx * g.kz != K)
+        if (ctx->grids[shots[s].grid_id].dev.K != K)
             return fail(ctx, EMPSO_INVALID_ARG, "shots' grids disagree on the control nodes");
     }
     Models mod;
@@ -941,8 +1056,7 @@ empso_status empso_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S
     empso_status rc = check_shots(ctx, shots, S, -1);
     if (rc) return rc;
     for (int s = 0; s < S; ++s) {
-        const empso_grid &g = ctx->grids[shots[s].grid_id].spec;
-        if (g.kx * g.kz != ctx->pso.D)
+        if (ctx->grids[shots[s].grid_id].dev.K != ctx->pso.D)
             return fail(ctx, EMPSO_INVALID_ARG, "swarm dimension differs from the grids' control nodes");
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -1379,8 +1493,7 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
     SurDev &s = ctx->sur;
     const int P = ctx->pso.P, K = ctx->pso.D;
     for (int i = 0; i < S; ++i) {
-        const empso_grid &g = ctx->grids[shots[i].grid_id].spec;
-        if (g.kx * g.kz != K)
+        if (ctx->grids[shots[i].grid_id].dev.K != K)
             return fail(ctx, EMPSO_INVALID_ARG, "swarm dimension differs from the grids' control nodes");
     }
     // how many pairs the replay buffer holds (host read: decides the branch)

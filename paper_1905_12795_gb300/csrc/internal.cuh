@@ -40,7 +40,9 @@ struct GridDev {
     int pitch;               // floats per buffer row (multiple of 32)
     int rows;                // NZ + 2 HALO
     int nt;                  // time steps = trace samples
-    int kx, kz, mode;        // control nodes and interpolation mode
+    int kx, kz, mode;        // control nodes and interpolation mode (2: level grid)
+    int K;                   // control nodes per particle (kx kz, or the level grid's count)
+    float water_z, v_water;  // fixed water layer: depth <= water_z (when > 0) takes v_water
     float dt, hx, hz;
     float vmin, vmax;
     float c[MAX_R + 1];      // centred 2nd-derivative weights c_0..c_R
@@ -51,6 +53,8 @@ struct GridDev {
     const float *ez;         // [rows]    eta_z dt / 2 per buffer row (0 in halo)
     const float *Wx;         // [nx][kx]  interpolation weights along x
     const float *Wz;         // [nz][kz]  interpolation weights along z
+    const int4 *lidx;        // [nz][nx]  level grid: the four nodes of each point
+    const float4 *lw;        // [nz][nx]  and their weights
     long long field;         // floats per buffer = rows * pitch
 };
 
@@ -72,6 +76,8 @@ struct Inst {
 cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wavelet,
                                float *Wx, float *Wz, double vmax_damp, double f0,
                                cudaStream_t st);
+cudaError_t launch_level_taps(const GridDev &g, int L, const float *level_z, const int *level_off,
+                              const float *node_x, int4 *lidx, float4 *lw, cudaStream_t st);
 cudaError_t launch_interp(const GridDev &g, const float *particles, int P, float *a_fields,
                           long long field_stride, float *vel_out, cudaStream_t st);
 cudaError_t launch_vel_to_field(const GridDev &g, const float *vel, int M, float *a_fields,

@@ -146,6 +146,7 @@ bool derive_grid(const empso_grid &s, GridDev &g, std::string &err)
     g.field = (long long)g.rows * g.pitch;
     g.kx = s.kx;
     g.kz = s.kz;
+    g.K = s.kx * s.kz;
     g.mode = s.interp_mode;
     g.hx = s.hx;
     g.hz = s.hz;

@@ -110,6 +110,68 @@ cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wa
     return cudaGetLastError();
 }
 
+// Taps of the irregular level-wise control grid ("Testing approach": a
+// variable node spacing, nodes bilinearly interpolated to the FD grid).
+// Level l lies at depth level_z[l] and holds the nodes level_off[l] ..
+// level_off[l+1]-1 at increasing x positions node_x[..].  For physical node
+// (i, j) at (x, z) = (i hx, j hz): the two levels bracketing z (the first or
+// last level alone above/below them) with weight 1 - b and b, and on each
+// level the two nodes bracketing x (the end node alone beyond the ends) with
+// weight 1 - a and a.  One thread per point, positions in FP64.
+__global__ void level_taps_kernel(int nx, int nz, double hx, double hz, int L,
+                                  const float *__restrict__ level_z, const int *__restrict__ level_off,
+                                  const float *__restrict__ node_x, int4 *lidx, float4 *lw)
+{
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)nx * nz) return;
+    const int i = (int)(e % nx), j = (int)(e / nx);
+    const double x = i * hx, z = j * hz;
+    int la, lb;
+    double b = 0.0;
+    if (z <= (double)level_z[0]) {
+        la = lb = 0;
+    } else if (z >= (double)level_z[L - 1]) {
+        la = lb = L - 1;
+    } else {
+        la = 0;
+        while (!(z < (double)level_z[la + 1])) ++la;
+        lb = la + 1;
+        b = (z - level_z[la]) / ((double)level_z[lb] - (double)level_z[la]);
+    }
+    int n0[2], n1[2];
+    double a[2];
+    const int lv[2] = {la, lb};
+    for (int s = 0; s < 2; ++s) {
+        const int o = level_off[lv[s]], n = level_off[lv[s] + 1] - o;
+        const float *xs = node_x + o;
+        if (n == 1 || x <= (double)xs[0]) {
+            n0[s] = n1[s] = o;
+            a[s] = 0.0;
+        } else if (x >= (double)xs[n - 1]) {
+            n0[s] = n1[s] = o + n - 1;
+            a[s] = 0.0;
+        } else {
+            int k = 0;
+            while (!(x < (double)xs[k + 1])) ++k;
+            n0[s] = o + k;
+            n1[s] = o + k + 1;
+            a[s] = (x - xs[k]) / ((double)xs[k + 1] - (double)xs[k]);
+        }
+    }
+    lidx[e] = make_int4(n0[0], n1[0], n0[1], n1[1]);
+    lw[e] = make_float4((float)((1.0 - b) * (1.0 - a[0])), (float)((1.0 - b) * a[0]),
+                        (float)(b * (1.0 - a[1])), (float)(b * a[1]));
+}
+
+cudaError_t launch_level_taps(const GridDev &g, int L, const float *level_z, const int *level_off,
+                              const float *node_x, int4 *lidx, float4 *lw, cudaStream_t st)
+{
+    const long long n = (long long)g.nx * g.nz;
+    level_taps_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g.nx, g.nz, g.hx, g.hz, L, level_z,
+                                                                  level_off, node_x, lidx, lw);
+    return cudaGetLastError();
+}
+
 // Model field a = v^2 dt^2 in buffer layout from the control nodes of one
 // particle per blockIdx.y: v(i, j) = sum_kz Wz[j][kz] sum_kx C[kz][kx] Wx[i][kx],
 // clipped to [vmin, vmax], edge-extended into the damping pad; 0 in the halo
@@ -120,7 +182,7 @@ __global__ void interp_kernel(GridDev g, const float *__restrict__ particles, fl
 {
     extern __shared__ float C[];
     const int p = blockIdx.y;
-    const int K = g.kx * g.kz;
+    const int K = g.K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) C[k] = particles[(size_t)p * K + k];
     __syncthreads();
     float *a = a_fields + p * field_stride;
@@ -132,14 +194,21 @@ __global__ void interp_kernel(GridDev g, const float *__restrict__ particles, fl
         if (I >= 0 && I < g.NX && J >= 0 && J < g.NZ) {
             int i = min(max(I - g.pad, 0), g.nx - 1);
             int j = min(max(J - g.pad, 0), g.nz - 1);
-            const float *wx = g.Wx + (size_t)i * g.kx;
-            const float *wz = g.Wz + (size_t)j * g.kz;
             float v = 0.f;
-            for (int kz = 0; kz < g.kz; ++kz) {
-                float t = 0.f;
-                for (int kx = 0; kx < g.kx; ++kx) t = fmaf(C[kz * g.kx + kx], wx[kx], t);
-                v = fmaf(wz[kz], t, v);
+            if (g.mode == 2) {
+                const int4 q = g.lidx[(size_t)j * g.nx + i];
+                const float4 w = g.lw[(size_t)j * g.nx + i];
+                v = fmaf(w.x, C[q.x], fmaf(w.y, C[q.y], fmaf(w.z, C[q.z], w.w * C[q.w])));
+            } else {
+                const float *wx = g.Wx + (size_t)i * g.kx;
+                const float *wz = g.Wz + (size_t)j * g.kz;
+                for (int kz = 0; kz < g.kz; ++kz) {
+                    float t = 0.f;
+                    for (int kx = 0; kx < g.kx; ++kx) t = fmaf(C[kz * g.kx + kx], wx[kx], t);
+                    v = fmaf(wz[kz], t, v);
+                }
             }
+            if (g.water_z > 0.f && (double)j * g.hz <= (double)g.water_z) v = g.v_water;
             v = fminf(fmaxf(v, g.vmin), g.vmax);
             float vd = v * g.dt;
             out = vd * vd;
@@ -154,7 +223,7 @@ cudaError_t launch_interp(const GridDev &g, const float *particles, int P, float
                           long long field_stride, float *vel_out, cudaStream_t st)
 {
     if (P <= 0) return cudaSuccess;
-    int K = g.kx * g.kz;
+    int K = g.K;
     int blocks = (int)((g.field + 255) / 256);
     if (blocks > 1024) blocks = 1024;
     dim3 grid(blocks, P);

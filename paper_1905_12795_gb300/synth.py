@@ -58,6 +58,32 @@ def two_layer_model(nx: int, nz: int, hz: float, v_top: float = 1500.0,
     return np.broadcast_to(v, (nz, nx)).astype(np.float64).copy()
 
 
+def level_layout(Lx: float, Lz: float, water_depth: float, v_top: float = 1500.0,
+                 v_bottom: float = 3500.0, f0: float = 6.0, frac: float = 0.5):
+    """Irregular level-wise control grid whose spacing grows with depth, the
+    structure of the paper's 176-node grid (its resolution criteria are only
+    in a cited work): the prior is the 1-D model linear from v_top at z = 0 to
+    v_bottom at z = Lz; the first level lies at the water bottom, each next
+    level `frac` local wavelengths v(z)/f0 deeper, the last at Lz; level l
+    holds nodes evenly spread over [0, Lx] at a horizontal spacing of twice
+    its vertical spacing.  Returns (level_z, level_count, node_x, v1d) with
+    v1d(z) the prior."""
+    def v1d(z):
+        return v_top + (v_bottom - v_top) * np.asarray(z, dtype=float) / Lz
+    z = [max(water_depth, 0.0)]
+    while True:
+        dz = frac * float(v1d(z[-1])) / f0
+        if z[-1] + 1.5 * dz >= Lz:
+            break
+        z.append(z[-1] + dz)
+    z.append(Lz)
+    level_z = np.array(z)
+    spacing = frac * v1d(level_z) / f0
+    counts = [max(2, int(np.ceil(Lx / (2.0 * d))) + 1) for d in spacing]
+    node_x = np.concatenate([np.linspace(0.0, Lx, n) for n in counts])
+    return level_z, np.array(counts, dtype=np.int32), node_x, v1d
+
+
 def shot_line(S: int, Lx: float, z: float) -> np.ndarray:
     """S sources evenly spread over [0, Lx]: x_s = (s + 1/2) Lx / S, depth z."""
     xs = (np.arange(S) + 0.5) * Lx / S
