@@ -62,7 +62,10 @@ def _args():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-vs-plain wall-clock comparison")
-    ap.add_argument("--surrogate-seeds", type=int, default=3)
+    ap.add_argument("--surrogate-seeds", type=int, default=5)
+    ap.add_argument("--trials", type=int, default=5, help="PSO vs EMPSO comparison trials")
+    ap.add_argument("--generations", type=int, default=0,
+                    help="PSO vs EMPSO comparison generations (0: the workload's)")
     ap.add_argument("--particles", type=int, default=0,
                     help="hires workload: particles in the bounded sample (default 8)")
     return ap.parse_args()
@@ -603,6 +606,89 @@ def run_hires(a):
     ctx.close()
 
 
+def run_compare(a):
+    """Standard PSO against EMPSO (the paper's Results comparison of
+    convergence), seeded trials on the paper-faithful parameterisation: the
+    plain workload's grid, true model and 16 shots, a 200 m water layer, a
+    level-wise irregular control grid (levels 0.75 local wavelengths apart,
+    bilinear), depth-dependent search ranges around a 1-D prior linear from
+    1500 to 4500 m/s.  Both variants start from the same swarm (same seed);
+    PSO has the EM step switched off.  Per trial: best misfit after every
+    generation, the longest stretch without improvement, and the relative
+    L2 error of the final global-best model against the true model."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    wl = synth.workloads()["compare-461x151-P32-S16"]
+    gs, S, ex = wl.grids[0], wl.shots_per_grid[0], wl.extra
+    Lx, Lz = (gs.nx - 1) * gs.hx, (gs.nz - 1) * gs.hz
+    lz, lc, node_x, v1d = synth.level_layout(Lx, Lz, ex["water"], *ex["v_prior"], f0=gs.f0,
+                                             frac=ex["frac"])
+    K = int(lc.sum())
+    lo, hi = B.level_bounds(lz, lc, float(v1d(lz[0])), float(v1d(lz[-1])), *ex["ranges"])
+    true = synth.layered_faulted_model(gs.nx, gs.nz, gs.hx, gs.hz, seed=wl.seed_model,
+                                       vmin=gs.vmin, vmax=gs.vmax, water_depth=ex["water"])
+    rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
+    shots = synth.shot_line(S, Lx, wl.src_z)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
+                       gs.vmax, mode=gs.mode)
+    sh = B.make_shots(shots, [0] * S, [len(rec)] * S)
+    gens, trials, P = a.generations or wl.gens, a.trials, wl.P
+    em_start = max(1, gens // 10)
+    true_t = torch.tensor(true, dtype=torch.float32, device="cuda")
+    dobs = None
+    out = {}
+    t_start = time.perf_counter()
+    for name, em in (("pso", 0), ("empso", 1)):
+        curves, finals, stalls, errors = [], [], [], []
+        for t in range(trials):
+            pso = B.EmpsoPso(P, K, 1.2, 2.9, 0.5, 0.3, 0.25, em_start, em, wl.seed_pso + t)
+            ctx = B.Context([grid], rec, pso, lo, hi)
+            ctx.set_levels(0, lz, lc, node_x)
+            ctx.set_water(0, ex["water"], 1500.0)
+            _, nt = ctx.grid_info(0)
+            if dobs is None:
+                dobs = torch.zeros(S * nt * len(rec), device="cuda")
+                ctx.forward_traces(true_t[None], sh, dobs)
+            mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+            ctx.pso_init()
+            best, curve = float("inf"), []
+            for _ in range(gens):
+                ctx.generation(sh, dobs, mis)
+                best = min(best, mis.min().item())
+                curve.append(best)
+            # global best after the last update: p[g]
+            p = torch.zeros(P, K, dtype=torch.float64, device="cuda")
+            gk = torch.zeros(2, dtype=torch.int32, device="cuda")
+            ctx.pso_get_state(p=p, gk=gk)
+            g = int(gk[0].item())
+            vel = torch.zeros(1, gs.nz, gs.nx, device="cuda")
+            ctx.interp(0, p[g:g + 1].float().contiguous(), vel)
+            errors.append(float(torch.linalg.norm(vel[0] - true_t) / torch.linalg.norm(true_t)))
+            ctx.close()
+            run, longest = 0, 0
+            for i in range(1, gens):
+                run = run + 1 if curve[i] >= curve[i - 1] else 0
+                longest = max(longest, run)
+            curves.append(curve)
+            finals.append(curve[-1])
+            stalls.append(longest)
+        c = np.array(curves)
+        out[name] = {"final_best": finals, "median_final": float(np.median(finals)),
+                     "median_curve": [float(v) for v in np.median(c, axis=0)],
+                     "longest_stall_gens": stalls, "model_rel_l2": errors,
+                     "median_model_rel_l2": float(np.median(errors))}
+    wins = int(sum(e < p for e, p in zip(out["empso"]["final_best"], out["pso"]["final_best"])))
+    line = {"metric": "best misfit after G generations, standard PSO vs EMPSO (seeded trials)",
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": wl.name, "grid": f"{gs.nx}x{gs.nz}@{gs.hx:g}m", "shots": S,
+                       "swarm": P, "generations": gens, "trials": trials, "nodes": K,
+                       "levels": len(lz), "water_m": ex["water"], "em_start": em_start,
+                       "c1": 1.2, "c2": 2.9, "nm_frac": 0.25, "p_em": 0.3},
+            "empso_wins": wins, "pso": out["pso"], "empso": out["empso"],
+            "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line), flush=True)
+
+
 def run_case(a):
     """P particles x S shots of the workload's grid through eval_fitness, with
     the kernel time of each repetition (used for profiler captures)."""
@@ -640,6 +726,8 @@ def main():
         run_uneven(a)
     elif a.impl != "reference" and a.workload.startswith("hires"):
         run_hires(a)
+    elif a.impl != "reference" and a.workload.startswith("compare"):
+        run_compare(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

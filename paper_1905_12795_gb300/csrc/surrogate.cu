@@ -113,15 +113,20 @@ gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int l
 // ---------------------------------------------------------------------------
 // The same product on the 5th-generation tensor cores: tcgen05.mma with BF16
 // operands from shared memory and the FP32 accumulator in tensor memory.
-// One CTA (4 warps) computes a 128 x NT tile (NT <= 256, multiple of 16):
-// threads stage 64-deep k-chunks of A and B into shared memory in the
-// K-major canonical layout without swizzle (8-row x 16-byte core matrices;
-// the two 8-element halves of a 16-deep k-slice 128 bytes apart, successive
-// 8-row groups 256 bytes apart), one thread issues four 128 x NT x 16 MMAs
-// per chunk and commits them to an mbarrier, and after the last chunk every
-// warp reads its 32 accumulator rows with tcgen05.ld for the epilogue.
+// One CTA (4 warps) computes a 128 x NT tile (NT = 64, or N rounded up to 16
+// when N < 64) over 64-deep k-chunks, double-buffered: while the tensor core
+// works on chunk c, the threads stage chunk c + 1 into the other buffer.
+// Staging writes the K-major canonical layout without swizzle (8-row x
+// 16-byte core matrices; the two 8-element halves of a 16-deep k-slice 128
+// bytes apart, successive 8-row groups 256 bytes apart): rows stored k-fastest
+// are copied 16 bytes at a time, operands stored m/n-fastest are transposed
+// in registers 8 x 8 elements at a time.  One thread issues four
+// 128 x NT x 16 MMAs per chunk and commits them to the buffer's mbarrier;
+// after the last chunk every warp reads its 32 accumulator rows with
+// tcgen05.ld for the epilogue (bias, ReLU, FP32 and/or BF16 stores).
 // ---------------------------------------------------------------------------
-constexpr int TM = 128, TKC = 64, TNMAX = 256;
+constexpr int TM = 128, TKC = 64, TNT = 64;
+constexpr int TC_SMEM = 2 * (TKC / 16) * (TM + TNT) * 32;   // two k-chunk buffers
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -161,28 +166,112 @@ __device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity)
     return ok != 0;
 }
 
+// wait (at most WAIT_LIMIT_NS) for the phase of `parity` of an mbarrier
+__device__ __forceinline__ bool mbar_wait_tc(unsigned addr, unsigned parity)
+{
+    if (mbar_try(addr, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(addr, parity)) return true;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+}
+
+// Stage rows r0 .. r0 + R - 1 (of M) x k-chunk k0 .. k0 + 63 (of K) of an
+// operand into the canonical layout at dst (4 slices of R x 16 elements).
+// kmajor: element (r, k) at src[r ld + k]; otherwise at src[k ld + r].
+// vec: ld % 8 == 0 and src 16-byte aligned (16-byte accesses allowed).
+__device__ __forceinline__ void stage_operand(unsigned char *dst, const __nv_bfloat16 *__restrict__ src,
+                                              int ld, int kmajor, bool vec, int r0, int R, int M,
+                                              int k0, int K)
+{
+    const int tid = threadIdx.x;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    if (vec && kmajor) {
+        // one 16-byte vector = 8 consecutive k of one row
+        for (int v = tid; v < R * (TKC / 8); v += blockDim.x) {
+            const int r = v / (TKC / 8), kv = (v % (TKC / 8)) * 8;
+            const int row = r0 + r, k = k0 + kv;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (row < M) {
+                const __nv_bfloat16 *p = src + (size_t)row * ld + k;
+                if (k + 8 <= K) {
+                    val = *reinterpret_cast<const uint4 *>(p);
+                } else if (k < K) {
+                    __nv_bfloat16 t[8];
+                    for (int e = 0; e < 8; ++e) t[e] = (k + e < K) ? p[e] : zero;
+                    val = *reinterpret_cast<const uint4 *>(t);
+                }
+            }
+            *reinterpret_cast<uint4 *>(dst + (kv >> 4) * (R * 32) + canon_off(r, kv & 15)) = val;
+        }
+    } else if (vec && (M & 7) == 0) {
+        // 8 (rows) x 8 (k) blocks: eight 16-byte loads along the rows, a
+        // register transpose, eight 16-byte stores along k
+        for (int b = tid; b < (R / 8) * (TKC / 8); b += blockDim.x) {
+            const int rb = (b % (R / 8)) * 8, kb = (b / (R / 8)) * 8;
+            const int row = r0 + rb;
+            uint4 in[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = k0 + kb + i;
+                in[i] = (row < M && k < K)
+                            ? *reinterpret_cast<const uint4 *>(src + (size_t)k * ld + row)
+                            : make_uint4(0u, 0u, 0u, 0u);
+            }
+            // word j of in[i] holds rows (2j, 2j+1) at k = i; word i of out[m]
+            // must hold k = (2i, 2i+1) at row m
+            unsigned o[8][4];
+            const unsigned *w = reinterpret_cast<const unsigned *>(in);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned a = w[(2 * i) * 4 + j], c = w[(2 * i + 1) * 4 + j];
+                    o[2 * j][i] = __byte_perm(a, c, 0x5410);
+                    o[2 * j + 1][i] = __byte_perm(a, c, 0x7632);
+                }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                *reinterpret_cast<uint4 *>(dst + (kb >> 4) * (R * 32) + canon_off(rb + m, kb & 15)) =
+                    make_uint4(o[m][0], o[m][1], o[m][2], o[m][3]);
+        }
+    } else {
+        for (int e = tid; e < R * TKC; e += blockDim.x) {
+            int r, kk;
+            if (kmajor) { r = e / TKC; kk = e % TKC; } else { kk = e / R; r = e % R; }
+            const int row = r0 + r, k = k0 + kk;
+            __nv_bfloat16 v = zero;
+            if (row < M && k < K) v = kmajor ? src[(size_t)row * ld + k] : src[(size_t)k * ld + row];
+            *reinterpret_cast<__nv_bfloat16 *>(dst + (kk >> 4) * (R * 32) + canon_off(r, kk & 15)) = v;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128)
-gemm_tc_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda, int a_mk,
-               const __nv_bfloat16 *__restrict__ B, int ldb, int b_nk, const float *__restrict__ bias,
-               int relu, float *Cf, int ldc, __nv_bfloat16 *Cb, int ldcb, int NT, int *err)
+gemm_tc_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda, int a_mk, int a_vec,
+               const __nv_bfloat16 *__restrict__ B, int ldb, int b_nk, int b_vec,
+               const float *__restrict__ bias, int relu, float *Cf, int ldc, __nv_bfloat16 *Cb,
+               int ldcb, int NT, int *err)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ unsigned tmem_base;
     __shared__ int s_fail;
-    unsigned char *As = tsm;                                   // TKC/16 slices of 128 x 16
-    unsigned char *Bs = tsm + (TKC / 16) * TM * 16 * 2;        // TKC/16 slices of NT x 16
+    const int stage_bytes = (TKC / 16) * (TM + NT) * 32;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * NT;
+    const unsigned ncols = NT <= 32 ? 32u : 64u;        // tensor-memory columns (power of 2)
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_fail = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_base)),
-                     "r"(TNMAX)
+                     "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -191,26 +280,15 @@ gemm_tc_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const unsigned tmem = tmem_base;
     const unsigned idesc = umma_idesc(TM, NT);
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    unsigned phase = 0;
-    for (int k0 = 0; k0 < K; k0 += TKC) {
-        // stage A (128 x TKC) and B (NT x TKC) into the canonical layout
-        for (int e = tid; e < TM * TKC; e += 128) {
-            int mm, kk;
-            if (a_mk) { mm = e / TKC; kk = e % TKC; } else { kk = e / TM; mm = e % TM; }
-            const int m = m0 + mm, k = k0 + kk;
-            __nv_bfloat16 v = zero;
-            if (m < M && k < K) v = a_mk ? A[(size_t)m * lda + k] : A[(size_t)k * lda + m];
-            *reinterpret_cast<__nv_bfloat16 *>(As + (kk >> 4) * (TM * 32) + canon_off(mm, kk & 15)) = v;
-        }
-        for (int e = tid; e < NT * TKC; e += 128) {
-            int nn, kk;
-            if (b_nk) { nn = e / TKC; kk = e % TKC; } else { kk = e / NT; nn = e % NT; }
-            const int n = n0 + nn, k = k0 + kk;
-            __nv_bfloat16 v = zero;
-            if (n < N && k < K) v = b_nk ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
-            *reinterpret_cast<__nv_bfloat16 *>(Bs + (kk >> 4) * (NT * 32) + canon_off(nn, kk & 15)) = v;
-        }
+    const int nchunks = (K + TKC - 1) / TKC;
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        unsigned char *As = tsm + buf * stage_bytes;
+        unsigned char *Bs = As + (TKC / 16) * TM * 32;
+        // the MMAs that read this buffer two chunks ago are done before it is restaged
+        if (c >= 2 && !mbar_wait_tc(smem_u32(&mbar[buf]), ((c - 2) >> 1) & 1)) s_fail = 1;
+        stage_operand(As, A, lda, a_mk, a_vec != 0, m0, TM, M, c * TKC, K);
+        stage_operand(Bs, B, ldb, b_nk, b_vec != 0, n0, NT, N, c * TKC, K);
         // thread-written shared memory -> visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -219,27 +297,27 @@ gemm_tc_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda
             for (int s = 0; s < TKC / 16; ++s) {
                 const unsigned long long ad = umma_desc(As + s * (TM * 32), 128, 256);
                 const unsigned long long bd = umma_desc(Bs + s * (NT * 32), 128, 256);
-                const unsigned acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                const unsigned acc = (c > 0 || s > 0) ? 1u : 0u;
                 asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                              : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_u32(&mbar))
+                             smem_u32(&mbar[buf]))
                          : "memory");
         }
-        // the MMAs of this chunk are done before the tiles are restaged (bounded wait)
-        bool done = mbar_try(smem_u32(&mbar), phase);
-        const unsigned long long t0 = global_ns();
-        while (!done && global_ns() - t0 <= WAIT_LIMIT_NS) done = mbar_try(smem_u32(&mbar), phase);
-        if (!done) s_fail = 1;
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        __syncthreads();
     }
+    // the last commit covers every MMA issued before it
+    {
+        const int c = nchunks - 1;
+        if (!mbar_wait_tc(smem_u32(&mbar[c & 1]), (c >> 1) & 1)) s_fail = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    __syncthreads();
     // epilogue: warp w reads accumulator rows 32 w .. 32 w + 31 (TMEM lanes)
     const int row = m0 + 32 * warp + (tid & 31);
+    const bool fail = s_fail != 0;
     for (int c0 = 0; c0 < NT; c0 += 16) {
         unsigned r[16];
         const unsigned taddr = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0;
@@ -250,23 +328,52 @@ gemm_tc_kernel(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda
                      : "r"(taddr)
                      : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (row < M && !s_fail) {
+        if (row >= M || fail) continue;
+        const int nb = n0 + c0;
+        float v[16];
 #pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float t = __uint_as_float(r[j]);
+            if (bias && nb + j < N) t += bias[nb + j];
+            if (relu) t = fmaxf(t, 0.f);
+            v[j] = t;
+        }
+        if (nb + 16 <= N && c0 + 16 <= NT) {
+            if (Cf) {
+                float *o = Cf + (size_t)row * ldc + nb;
+                if ((ldc & 3) == 0 && ((size_t)Cf & 15) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        reinterpret_cast<float4 *>(o)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                } else {
+                    for (int j = 0; j < 16; ++j) o[j] = v[j];
+                }
+            }
+            if (Cb) {
+                __nv_bfloat16 *o = Cb + (size_t)row * ldcb + nb;
+                if ((ldcb & 7) == 0 && ((size_t)Cb & 15) == 0) {
+                    __nv_bfloat162 h[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    reinterpret_cast<uint4 *>(o)[0] = *reinterpret_cast<uint4 *>(&h[0]);
+                    reinterpret_cast<uint4 *>(o)[1] = *reinterpret_cast<uint4 *>(&h[4]);
+                } else {
+                    for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(v[j]);
+                }
+            }
+        } else {
             for (int j = 0; j < 16; ++j) {
-                const int n = n0 + c0 + j;
-                if (n >= N || c0 + j >= NT) continue;
-                float v = __uint_as_float(r[j]);
-                if (bias) v += bias[n];
-                if (relu) v = fmaxf(v, 0.f);
-                if (Cf) Cf[(size_t)row * ldc + n] = v;
-                if (Cb) Cb[(size_t)row * ldcb + n] = __float2bfloat16(v);
+                const int n = nb + j;
+                if (n >= N || c0 + j >= NT) break;
+                if (Cf) Cf[(size_t)row * ldc + n] = v[j];
+                if (Cb) Cb[(size_t)row * ldcb + n] = __float2bfloat16(v[j]);
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TNMAX) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
     if (tid == 0 && s_fail) atomicExch(err, EMPSO_TIMEOUT);
 }
 
@@ -274,12 +381,14 @@ cudaError_t gemm(const SurDev &s, cudaStream_t st, int M, int N, int K, const __
                  const __nv_bfloat16 *B, int ldb, int b_nk, const float *bias, int relu, float *Cf,
                  int ldc, __nv_bfloat16 *Cb, int ldcb)
 {
-    if (s.tc && s.err) {
-        const int NT = N >= TNMAX ? TNMAX : ((N + 15) / 16) * 16;
+    if (s.tc && s.err && M > 0 && N > 0 && K > 0) {
+        const int NT = N >= TNT ? TNT : ((N + 15) / 16) * 16;
         dim3 grid((N + NT - 1) / NT, (M + TM - 1) / TM);
-        const size_t smem = (size_t)(TKC / 16) * (TM + NT) * 32;
-        gemm_tc_kernel<<<grid, 128, smem, st>>>(M, N, K, A, lda, a_mk, B, ldb, b_nk, bias, relu, Cf,
-                                                ldc, Cb, ldcb, NT, s.err);
+        const size_t smem = (size_t)2 * (TKC / 16) * (TM + NT) * 32;
+        const int a_vec = (lda % 8 == 0) && (((size_t)A & 15) == 0);
+        const int b_vec = (ldb % 8 == 0) && (((size_t)B & 15) == 0);
+        gemm_tc_kernel<<<grid, 128, smem, st>>>(M, N, K, A, lda, a_mk, a_vec, B, ldb, b_nk, b_vec, bias,
+                                                relu, Cf, ldc, Cb, ldcb, NT, s.err);
         return cudaGetLastError();
     }
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
@@ -617,8 +726,7 @@ inline int blocks_for(long long n, int per = 256)
 // opt the tcgen05 GEMM into its 48 KiB of dynamic shared memory (current device)
 cudaError_t sur_prepare_tc()
 {
-    return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (TKC / 16) * (TM + TNMAX) * 32);
+    return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
 }
 
 cudaError_t sur_forward(const SurDev &s, const __nv_bfloat16 *Xb, int n, float *y, cudaStream_t st)

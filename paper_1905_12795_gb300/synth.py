@@ -18,11 +18,13 @@ import numpy as np
 
 
 def layered_faulted_model(nx: int, nz: int, hx: float, hz: float, seed: int = 1905,
-                          vmin: float = 1500.0, vmax: float = 4700.0) -> np.ndarray:
+                          vmin: float = 1500.0, vmax: float = 4700.0,
+                          water_depth: float = 0.0) -> np.ndarray:
     """Velocity [nz][nx] in m/s: 4-7 layers with dipping interfaces (dip <= 15
     degrees), velocity increasing with depth from `vmin` (top layer) to at
     most `vmax`, a +-5 % lateral gradient and one 60-degree normal fault with
-    100-300 m throw offsetting the interfaces below its tip."""
+    100-300 m throw offsetting the interfaces below its tip; with
+    water_depth > 0 a 1500 m/s water layer covers depths <= water_depth."""
     rng = np.random.default_rng(seed)
     Lx, Lz = (nx - 1) * hx, (nz - 1) * hz
     nl = int(rng.integers(4, 8))
@@ -47,7 +49,10 @@ def layered_faulted_model(nx: int, nz: int, hx: float, hz: float, seed: int = 19
         layer += (Zs > zb).astype(np.int64)
     v = vel_layers[layer] * (1.0 + grad * (X / max(Lx, 1.0) - 0.5))
     v[layer == 0] = vmin
-    return np.clip(v, vmin, vmax)
+    v = np.clip(v, vmin, vmax)
+    if water_depth > 0:
+        v[z <= water_depth, :] = 1500.0
+    return v
 
 
 def two_layer_model(nx: int, nz: int, hz: float, v_top: float = 1500.0,
@@ -146,6 +151,7 @@ def workloads() -> dict:
     """The five workloads the framework is measured on, by name."""
     single = GridSpec(101, 101, 10.0, 10.0, 20, 4, 0.5, 10.0, 2625.0, 1500.0)
     plain = GridSpec(461, 151, 20.0, 20.0, 40, 8, 3.0, 6.0, 4700.0)
+    plain_bl = GridSpec(461, 151, 20.0, 20.0, 40, 8, 3.0, 6.0, 4700.0, mode=1)
     coarse = GridSpec(231, 76, 40.0, 40.0, 20, 8, 4.0, 3.0, 4700.0)
     hires = GridSpec(921, 301, 10.0, 10.0, 60, 8, 4.0, 12.0, 4700.0, kx=24, kz=8)
     surr = GridSpec(101, 101, 10.0, 10.0, 20, 4, 0.5, 10.0, 3200.0, 1200.0)
@@ -160,4 +166,12 @@ def workloads() -> dict:
                                             100, 20.0, 20.0, xmin=1200.0, xmax=3200.0),
         "hires-921x301-P512-S64": Workload("hires-921x301-P512-S64", [hires], [64], 512, 1,
                                            20.0, 20.0),
+        # the plain workload's grid and geometry under the paper's own
+        # parameterisation: level-wise irregular control grid below a 200 m
+        # water layer, bilinear, depth-dependent ranges around a linear prior
+        "compare-461x151-P32-S16": Workload("compare-461x151-P32-S16", [plain_bl], [16], 32, 60,
+                                            20.0, 20.0,
+                                            extra=dict(water=200.0, v_prior=(1500.0, 4500.0),
+                                                       ranges=(0.3, 0.6, 0.25, 0.25),
+                                                       frac=0.75)),
     }

@@ -28,7 +28,8 @@ def B():
 
 
 def _ctx(B, P=64, K=32, H=256, lo=1500.0, hi=4700.0, seed=5):
-    grid = B.make_grid(41, 31, 10.0, 10.0, 5, 4, 0.2, 10.0, 1500.0, 4700.0, kx=8, kz=K // 8)
+    kx, kz = (8, K // 8) if K % 8 == 0 else (K // 4, 4)
+    grid = B.make_grid(41, 31, 10.0, 10.0, 5, 4, 0.2, 10.0, 1500.0, 4700.0, kx=kx, kz=kz)
     pso = B.EmpsoPso(P, K, 1.2, 2.9, 0.5, 0.3, 0.25, 2, 1, seed)
     ctx = B.Context([grid], synth.receiver_line(41, 10.0, 0.0), pso, lo, hi)
     ctx.surrogate_init(hidden=H, capacity=4096, lr=1e-3, seed=seed)
@@ -67,7 +68,7 @@ def test_forward_matches_oracle(B):
     ctx.close()
 
 
-@pytest.mark.parametrize("K,n", [(32, 300), (192, 64), (32, 1024)])
+@pytest.mark.parametrize("K,n", [(32, 300), (192, 64), (32, 1024), (36, 257)])
 def test_tcgen05_equals_mma_sync(B, K, n):
     """The tcgen05 (TMEM accumulator) and mma.sync paths compute the same BF16
     products with FP32 accumulation: predictions and gradients agree to FP32
