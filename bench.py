@@ -64,6 +64,8 @@ def _args():
                     help="skip the surrogate-vs-plain wall-clock comparison")
     ap.add_argument("--surrogate-seeds", type=int, default=5)
     ap.add_argument("--trials", type=int, default=5, help="PSO vs EMPSO comparison trials")
+    ap.add_argument("--surrogate-case", type=int, default=0,
+                    help="time the surrogate kernels alone for this many particles")
     ap.add_argument("--generations", type=int, default=0,
                     help="PSO vs EMPSO comparison generations (0: the workload's)")
     ap.add_argument("--particles", type=int, default=0,
@@ -97,21 +99,23 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-_KERNEL_SOURCES = {"wave_kernel": "wave.cu", "wave_resident_kernel": "wave_resident.cu"}
+_KERNEL_SOURCES = {"wave_kernel": "wave.cu", "wave_resident_kernel": "wave_resident.cu",
+                   "wave_stream_kernel": "wave_stream.cu"}
 
 
 def _wave_source_hash(kernel):
-    h = hashlib.sha256()
-    for f in (_KERNEL_SOURCES[kernel], "internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1905_12795_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    """First 16 hex digits of the SHA-256 of the kernel's source file."""
+    with open(os.path.join(ROOT, "paper_1905_12795_gb300", "csrc", _KERNEL_SOURCES[kernel]),
+              "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def _traffic_from_profile(kernel):
+def _traffic_from_profile(kernel, grid="empso-461x151"):
     """DRAM bytes per launch of the modelling kernel from its committed ncu
     summary, or None when absent or taken on another version of the kernel."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_empso-461x151.md")
+    if kernel not in _KERNEL_SOURCES:
+        return None
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{grid}.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -332,7 +336,7 @@ def run_ours(a):
     wave_mean = float(np.mean(wave_ms))
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_UPDATE * upd_step / (wave_mean / 1e3) / 1e9
-    kname = "wave_resident_kernel" if launch[0] == 2 else "wave_kernel"
+    kname = ctx.last_kernel_name()
     traffic = _traffic_from_profile(kname)
 
     cpu = None
@@ -532,7 +536,7 @@ def run_uneven(a):
             "fitness_evals_per_s": wl.P * a.steps / (total / 1e3),
             "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
                        "cluster_ctas": launch[1], "autotuned": list(tuned)},
-            "roofline": {"kernel": "wave_resident_kernel" if launch[0] == 2 else "wave_kernel",
+            "roofline": {"kernel": ctx.last_kernel_name(),
                          "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "kernel_ms": float(np.mean(wave))},
@@ -597,9 +601,10 @@ def run_hires(a):
             "fitness_evals_per_s": P * a.steps / (total / 1e3),
             "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
                        "cluster_ctas": launch[1]},
-            "roofline": {"kernel": "wave_resident_kernel" if launch[0] == 2 else "wave_kernel",
+            "roofline": {"kernel": ctx.last_kernel_name(),
                          "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": _traffic_from_profile(ctx.last_kernel_name(), "hires-921x301"),
                          "kernel_ms": float(np.mean(wave))},
             "gpu_launches": 3 * a.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -714,7 +719,46 @@ def run_case(a):
         torch.cuda.synchronize()
         ms = ctx.read_timing()[1]
         print(f"rep {r}: modelling kernel {ms:.3f} ms, {upd / ms / 1e6:.1f} G updates/s, "
-              f"launch {ctx.last_launch()}", flush=True)
+              f"launch {ctx.last_launch()} {ctx.last_kernel_name()}", flush=True)
+    ctx.close()
+
+
+def run_surrogate_case(a):
+    """Surrogate network kernels alone: predictions for P particles and
+    20-step training rounds (batch 256, hidden 256, K = 32) with each
+    dense-layer backend; prints milliseconds per call (used for profiler
+    captures of the dense-layer kernels)."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    P, K = a.surrogate_case, 32
+    grid = B.make_grid(101, 101, 10.0, 10.0, 20, 4, 0.5, 10.0, 1200.0, 3200.0)
+    pso = B.EmpsoPso(P, K, 1.2, 2.9, 0.5, 0.3, 0.25, 10, 1, 5)
+    ctx = B.Context([grid], synth.receiver_line(101, 10.0, 20.0), pso, 1200.0, 3200.0)
+    ctx.surrogate_init(hidden=256, capacity=50000, lr=1e-3, seed=1)
+    x = torch.tensor(synth.random_particles(P, K, 1200.0, 3200.0, 3), dtype=torch.float32,
+                     device="cuda")
+    f = torch.rand(P, dtype=torch.float64, device="cuda") + 0.1
+    for _ in range(max(1, 2048 // P)):
+        ctx.surrogate_add(x, f)
+    y = torch.zeros(P, device="cuda")
+    for kind, name in ((0, "mma.sync"), (1, "tcgen05")):
+        ctx.surrogate_set_backend(kind)
+        for _ in range(a.reps):
+            ctx.surrogate_train(20, 256)
+            ctx.surrogate_predict(x, y)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            ctx.surrogate_train(20, 256)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(50):
+            ctx.surrogate_predict(x, y)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        print(f"{name}: train 20 steps {(t1 - t0) / 10 * 1e3:.3f} ms, predict {P} "
+              f"{(t2 - t1) / 50 * 1e3:.4f} ms", flush=True)
+    assert ctx.device_error() == 0
     ctx.close()
 
 
@@ -722,6 +766,8 @@ def main():
     a = _args()
     if a.case:
         run_case(a)
+    elif a.surrogate_case:
+        run_surrogate_case(a)
     elif a.impl != "reference" and a.workload.startswith("uneven"):
         run_uneven(a)
     elif a.impl != "reference" and a.workload.startswith("hires"):

@@ -298,6 +298,13 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas);
  * instance.  Either pointer may be NULL (host ints). */
 empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *cluster);
 
+/* Device-function name of the last modelling launch's kernel
+ * ("wave_resident_kernel", "wave_stream_kernel" for the streaming kernel
+ * with bulk asynchronous row copies, "wave_kernel" for the plain streaming
+ * kernel; "" before any launch): what a profiler's kernel filter matches.
+ * The string is static. */
+const char *empso_last_kernel_name(const empso_ctx *ctx);
+
 /* Device-side status of the launches since the last call: a bounded wait
  * inside a kernel that gave up (EMPSO_TIMEOUT) - the instance concerned then
  * reports misfit +inf.  Synchronises `stream`, then clears the word.

@@ -32,7 +32,7 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "pso_step_ranked", "surrogate_init", "surrogate_set_backend", "surrogate_predict", "surrogate_add",
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
            "empso_nonfinite_count", "empso_set_strict", "empso_save", "empso_load",
-           "empso_set_levels", "empso_set_water", "empso_level_bounds",
+           "empso_set_levels", "empso_set_water", "empso_level_bounds", "empso_last_kernel_name",
            "empso_status_string", "empso_last_error"]
 
 
@@ -118,6 +118,8 @@ def load():
     L.empso_nonfinite_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _i32, _vp]
     L.empso_set_strict.argtypes = [_vp, _i32]
     L.empso_set_levels.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
+    L.empso_last_kernel_name.argtypes = [_vp]
+    L.empso_last_kernel_name.restype = ctypes.c_char_p
     L.empso_set_water.argtypes = [_vp, _i32, _f32, _f32]
     L.empso_level_bounds.argtypes = [_i32, _vp, _vp, _f64, _f64, _f64, _f64, _f64, _f64, _vp, _vp]
     L.empso_save.argtypes = [_vp, ctypes.c_char_p]
@@ -136,7 +138,8 @@ def load():
     L.empso_last_error.argtypes = [_vp]
     L.empso_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("empso_destroy", "empso_status_string", "empso_last_error"):
+        if name not in ("empso_destroy", "empso_status_string", "empso_last_error",
+                        "empso_last_kernel_name"):
             getattr(L, name).restype = _i32
     _lib = L
     return L
@@ -296,6 +299,10 @@ class Context:
     def load(self, path):
         """Restore a checkpoint written by save() into a context of the same shape."""
         self._check(self._L.empso_load(self._h, os.fsencode(path)))
+
+    def last_kernel_name(self):
+        """Device-function name of the last modelling launch's kernel."""
+        return self._L.empso_last_kernel_name(self._h).decode()
 
     def set_timing(self, enable=True):
         self._check(self._L.empso_set_timing(self._h, 1 if enable else 0))

@@ -56,7 +56,7 @@ struct empso_ctx {
     int wave_ctas_per_sm = 1;
     size_t smem_optin = 0;          // max dynamic shared memory per block
     int forced_C = 0;               // 0: choose the cluster size, else use this one
-    int last_path = 0;              // 1 streaming, 2 resident (last modelling launch)
+    int last_path = 0;              // 1 streaming, 2 resident, 3 bulk-copy streaming (last launch)
     int last_C = 0;
     int *dev_err = nullptr;         // device status word set by bounded waits that give up
     unsigned long long *nonfinite = nullptr;  // non-finite misfits: {running, this call}
@@ -539,7 +539,7 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
         CK(ctx, launch_wave_stream(p.st_R, ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter,
                                    ctx->slots, 2 * p.maxfield, p.n_ctas, p.st_threads, p.st_smem,
                                    p.rec_max, ctx->dev_err, ctx->partial, st));
-        ctx->last_path = 1;
+        ctx->last_path = 3;
         ctx->last_C = 1;
     } else {
         CK(ctx, launch_wave(ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter, ctx->slots,
@@ -1262,9 +1262,20 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas)
 empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *cluster)
 {
     if (!ctx) return EMPSO_INVALID_ARG;
-    if (kind) *kind = ctx->last_path;
+    if (kind) *kind = ctx->last_path == 3 ? EMPSO_KERNEL_STREAMING : ctx->last_path;
     if (cluster) *cluster = ctx->last_C;
     return EMPSO_OK;
+}
+
+const char *empso_last_kernel_name(const empso_ctx *ctx)
+{
+    if (!ctx) return "";
+    switch (ctx->last_path) {
+    case 1: return "wave_kernel";
+    case 2: return "wave_resident_kernel";
+    case 3: return "wave_stream_kernel";
+    default: return "";
+    }
 }
 
 empso_status empso_device_error(empso_ctx *ctx, int32_t *status, void *stream)

@@ -71,3 +71,21 @@ def test_missing_library_raises(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "lib_path", lambda: str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         B.load()
+
+
+def test_host_functions_through_the_binding(lib):
+    """The two entry points that touch no device run here: the depth-dependent
+    ranges equal the oracle's, and the kernel-name query is safe on NULL."""
+    import numpy as np
+    from paper_1905_12795_gb300 import binding as B
+    import oracle
+    level_z = np.array([50.0, 150.0, 300.0, 500.0])
+    counts = [5, 3, 2, 1]
+    lo, hi = B.level_bounds(level_z, counts, 1600.0, 3400.0, 0.2, 0.3, 0.25, 0.15)
+    lo_r, hi_r = oracle.level_bounds(level_z, counts, 1600.0, 3400.0, 0.2, 0.3, 0.25, 0.15)
+    assert np.allclose(lo, lo_r, rtol=1e-15) and np.allclose(hi, hi_r, rtol=1e-15)
+    with pytest.raises(B.EmpsoError):
+        B.level_bounds(level_z, [5, 0, 2, 1], 1600.0, 3400.0, 0.2, 0.3, 0.25, 0.15)
+    assert B.load().empso_last_kernel_name(None) == b""
+    lib.empso_status_string.restype = ctypes.c_char_p
+    assert lib.empso_status_string(8) == b"file error"
