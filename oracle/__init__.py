@@ -26,6 +26,9 @@ itself lives in ``tests/test_oracle_*.py``):
   water layer, depth-dependent ranges) - pinned: ``numpy.interp`` along each
   level and between levels, the tensor-product bilinear mode on a regular
   layout, node reproduction, constant extension, straight-line ranges.
+* ``lowpass`` (band-limited resampling with a Blackman-windowed sinc) -
+  pinned: pass-band and stop-band amplitudes of sampled sinusoids, exact
+  phase at the new sample times, unit DC gain, symmetry of a symmetric pulse.
 * ``philox`` - pinned: published known-answer vectors of Philox4x32-10.
 * ``log`` / ``cos2pi`` / ``normal`` - pinned: ``math.log`` / ``math.cos``
   within 2 ulp, normality (KS test).
@@ -105,6 +108,7 @@ def lib():
         L.eo_interp_levels.argtypes = [_i, _pd, _pi, _pd, _pd, _i, _i, _d, _d, _d, _d, _d, _d,
                                        _pd]
         L.eo_level_bounds.argtypes = [_i, _pd, _pi, _d, _d, _d, _d, _d, _d, _pd, _pd]
+        L.eo_lowpass.argtypes = [_pd, _i, _i, _i, _d, _pd, _i, _d, _d, _d]
         L.eo_philox.argtypes = [_pu32, _pu32, _pu32]
         L.eo_uniform.argtypes = [_u64, _u32, _u32, _u32, _u32]
         L.eo_uniform.restype = _d
@@ -298,6 +302,17 @@ def level_bounds(level_z, level_n, v_first, v_last, lo_first, hi_first, lo_last,
     lib().eo_level_bounds(len(lz), _p(lz), _p(ln, _pi), v_first, v_last, lo_first, hi_first,
                           lo_last, hi_last, _p(lo), _p(hi))
     return lo, hi
+
+
+def lowpass(traces, dt_in: float, nt_out: int, dt_out: float, fc: float, W: float) -> np.ndarray:
+    """Band-limited resampling / low-pass of traces [S][nt_in][nrec] with the
+    Blackman-windowed sinc (cut-off fc Hz, half-width W s) onto the time axis
+    m dt_out, m < nt_out.  Returns [S][nt_out][nrec]."""
+    x = _f64(traces)
+    S, nt_in, nrec = x.shape
+    out = np.zeros((S, nt_out, nrec))
+    lib().eo_lowpass(_p(x), S, nt_in, nrec, dt_in, _p(out), nt_out, dt_out, fc, W)
+    return out
 
 
 def philox(ctr, key) -> np.ndarray:

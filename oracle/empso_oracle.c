@@ -502,6 +502,39 @@ void eo_level_bounds(int L, const double *level_z, const int *level_n, double v_
     }
 }
 
+/* Observed-data preprocessing ("Testing approach": the recorded data are
+ * low-pass filtered below the modelling band before the inversion): a
+ * band-limited resampling of traces with the Blackman-windowed sinc kernel
+ *   h(tau) = 2 fc sinc(2 fc tau) w(tau / W),  sinc(x) = sin(pi x) / (pi x),
+ *   w(u) = 0.42 + 0.5 cos(pi u) + 0.08 cos(2 pi u) for |u| < 1, else 0,
+ * evaluated at the output times:
+ *   out[s][m][r] = dt_in sum_n in[s][n][r] h(m dt_out - n dt_in)
+ * (records start at t = 0; samples outside the record count as zero).  With
+ * dt_out = dt_in this is a zero-phase low-pass; otherwise it also moves the
+ * traces to another time axis. */
+static double eo_bsinc(double tau, double fc, double W)
+{
+    double u = tau / W;
+    if (u <= -1.0 || u >= 1.0) return 0.0;
+    double w = 0.42 + 0.5 * cos(M_PI * u) + 0.08 * cos(2.0 * M_PI * u);
+    double x = 2.0 * fc * tau;
+    double sinc = (x == 0.0) ? 1.0 : sin(M_PI * x) / (M_PI * x);
+    return 2.0 * fc * sinc * w;
+}
+
+void eo_lowpass(const double *in, int S, int nt_in, int nrec, double dt_in, double *out,
+                int nt_out, double dt_out, double fc, double W)
+{
+    for (int s = 0; s < S; ++s)
+        for (int m = 0; m < nt_out; ++m)
+            for (int r = 0; r < nrec; ++r) {
+                double t = m * dt_out, acc = 0.0;
+                for (int n = 0; n < nt_in; ++n)
+                    acc += in[((size_t)s * nt_in + n) * nrec + r] * eo_bsinc(t - n * dt_in, fc, W);
+                out[((size_t)s * nt_out + m) * nrec + r] = dt_in * acc;
+            }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Counter-based random numbers                                              */
 /* ------------------------------------------------------------------------ */
