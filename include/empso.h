@@ -393,6 +393,22 @@ empso_status empso_level_bounds(int32_t n_levels, const float *level_z,
                                 double lo_first, double hi_first, double lo_last,
                                 double hi_last, double *xmin, double *xmax);
 
+/* ---- observed-data preprocessing ("Testing approach") ------------------
+ * Band-limited resampling of traces: in device [S][nt_in][nrec] sampled at
+ * n dt_in (n = 0 .. nt_in - 1, zero outside), out device [S][nt_out][nrec]
+ * at m dt_out, out[s][m][r] = dt_in sum_n in[s][n][r] h(m dt_out - n dt_in)
+ * with the Blackman-windowed sinc h(tau) = 2 f_cut sinc(2 f_cut tau)
+ * w(tau / half_width), w(u) = 0.42 + 0.5 cos(pi u) + 0.08 cos(2 pi u) for
+ * |u| < 1.  With dt_out = dt_in it is a zero-phase low-pass below f_cut; with
+ * another dt_out it also moves the traces onto that time axis (e.g. data
+ * recorded on a fine grid onto the inversion grid's steps).  The transition
+ * band is about 3 / half_width Hz wide.  in and out must not overlap.
+ * Errors: INVALID_ARG, UNSUPPORTED (window of more than the shared memory
+ * holds: half_width / dt_in too large). */
+empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t nt_in,
+                           int32_t nrec, double dt_in, float *out, int32_t nt_out,
+                           double dt_out, double f_cut, double half_width, void *stream);
+
 /* ---- non-finite misfits ------------------------------------------------
  * A particle whose misfit sum is NaN or infinite (a diverging or
  * non-finite model) gets misfit +inf, so it never becomes a personal or

@@ -33,6 +33,7 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
            "empso_nonfinite_count", "empso_set_strict", "empso_save", "empso_load",
            "empso_set_levels", "empso_set_water", "empso_level_bounds", "empso_last_kernel_name",
+           "empso_lowpass",
            "empso_status_string", "empso_last_error"]
 
 
@@ -121,6 +122,7 @@ def load():
     L.empso_last_kernel_name.argtypes = [_vp]
     L.empso_last_kernel_name.restype = ctypes.c_char_p
     L.empso_set_water.argtypes = [_vp, _i32, _f32, _f32]
+    L.empso_lowpass.argtypes = [_vp, _vp, _i32, _i32, _i32, _f64, _vp, _i32, _f64, _f64, _f64, _vp]
     L.empso_level_bounds.argtypes = [_i32, _vp, _vp, _f64, _f64, _f64, _f64, _f64, _f64, _vp, _vp]
     L.empso_save.argtypes = [_vp, ctypes.c_char_p]
     L.empso_load.argtypes = [_vp, ctypes.c_char_p]
@@ -280,6 +282,15 @@ class Context:
     def set_water(self, grid_id, water_depth, v_water=1500.0):
         self._check(self._L.empso_set_water(self._h, int(grid_id), float(water_depth),
                                             float(v_water)))
+
+    def lowpass(self, traces, dt_in, out, dt_out, f_cut, half_width):
+        """Band-limited resampling of traces [S][nt_in][nrec] onto out [S][nt_out][nrec]."""
+        S, nt_in, nrec = traces.shape
+        So, nt_out, nro = out.shape
+        assert So == S and nro == nrec
+        self._check(self._L.empso_lowpass(self._h, _ptr(traces), S, nt_in, nrec, float(dt_in),
+                                          _ptr(out), nt_out, float(dt_out), float(f_cut),
+                                          float(half_width), _stream()))
 
     def nonfinite_count(self, reset=False):
         """Non-finite misfits (returned as +inf) since creation or the last reset."""

@@ -864,6 +864,31 @@ empso_status empso_set_levels(empso_ctx *ctx, int32_t grid_id, int32_t n_levels,
     return grid_changed(ctx, grid_id);
 }
 
+empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t nt_in, int32_t nrec,
+                           double dt_in, float *out, int32_t nt_out, double dt_out, double f_cut,
+                           double half_width, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (S < 1 || nt_in < 1 || nrec < 1 || nt_out < 1 || !in || !out || in == out ||
+        !(dt_in > 0) || !(dt_out > 0) || !(f_cut > 0) || !(half_width > 0) ||
+        !std::isfinite(dt_in) || !std::isfinite(dt_out) || !std::isfinite(f_cut) ||
+        !std::isfinite(half_width))
+        return fail(ctx, EMPSO_INVALID_ARG,
+                    "need positive sizes, finite dt_in, dt_out, f_cut, half_width > 0, in != out");
+    if (((double)nt_out * dt_out + half_width) / dt_in > 1e9)
+        return fail(ctx, EMPSO_INVALID_ARG, "output times beyond 1e9 input samples");
+    const long long span = lowpass_span(dt_in, dt_out, half_width);
+    const size_t smem = lowpass_smem_bytes(span);
+    if (smem > ctx->smem_optin)
+        return fail(ctx, EMPSO_UNSUPPORTED, "filter window too long for shared memory "
+                                            "(half_width / dt_in too large)");
+    CK(ctx, lowpass_configure(smem));
+    CK(ctx, launch_lowpass(in, S, nt_in, nrec, dt_in, out, nt_out, dt_out, f_cut, half_width, smem,
+                           (cudaStream_t)stream));
+    return EMPSO_OK;
+}
+
 empso_status empso_set_water(empso_ctx *ctx, int32_t grid_id, float water_depth, float v_water)
 {
     if (!ctx) return EMPSO_INVALID_ARG;

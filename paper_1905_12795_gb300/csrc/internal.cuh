@@ -76,6 +76,14 @@ struct Inst {
 cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wavelet,
                                float *Wx, float *Wz, double vmax_damp, double f0,
                                cudaStream_t st);
+// Band-limited resampling of traces (filter.cu).
+long long lowpass_span(double dt_in, double dt_out, double W);
+size_t lowpass_smem_bytes(long long span);
+cudaError_t lowpass_configure(size_t smem);
+cudaError_t launch_lowpass(const float *in, int S, int nt_in, int nrec, double dt_in, float *out,
+                           int nt_out, double dt_out, double fc, double W, size_t smem,
+                           cudaStream_t st);
+
 cudaError_t launch_level_taps(const GridDev &g, int L, const float *level_z, const int *level_off,
                               const float *node_x, int4 *lidx, float4 *lw, cudaStream_t st);
 cudaError_t launch_interp(const GridDev &g, const float *particles, int P, float *a_fields,
