@@ -409,6 +409,40 @@ empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t n
                            int32_t nrec, double dt_in, float *out, int32_t nt_out,
                            double dt_out, double f_cut, double half_width, void *stream);
 
+/* ---- local FWI ("Testing approach": the EMPSO model starts a descent-based
+ * full-waveform inversion) ---------------------------------------------
+ * empso_gradient: misfit phi_m = sum_s w_s / 2 |R u_s - d_obs,s|^2 and its
+ * gradient dphi_m/dv at every physical node of M gridded models vel device
+ * [M][nz][nx] (m/s), all shots on one grid.  Computed by the exact discrete
+ * adjoint of the modelling scheme: a forward pass that keeps the whole
+ * wavefield history u^0 .. u^nt of every (model, shot) in device memory
+ * ((nt + 1) x padded-grid floats each, e.g. 0.78 GB per shot of a 461 x 151
+ * grid with 40 damping cells and 1414 steps), then the adjoint pass backward
+ * in time accumulating sum_k mu^k f (L u^{k-1} + s^{k-1}), folded from the
+ * damping pad onto the edge nodes and chained through a = v^2 dt^2.
+ * misfit: device [M] doubles or NULL; grad: device [M][nz][nx].  d_obs as
+ * for eval_models.  Synchronises `stream` once (instance table upload).
+ * Errors: INVALID_ARG, OOM (history does not fit), CUDA_ERROR. */
+empso_status empso_gradient(empso_ctx *ctx, const float *vel, int32_t M,
+                            const empso_shot *shots, int32_t S, const float *d_obs,
+                            double *misfit, float *grad, void *stream);
+
+/* Steepest-descent FWI of one model vel device [nz][nx] (in place), the
+ * paper's local inversion: iteration k moves v <- clip(v - alpha g, vmin,
+ * vmax) along the adjoint gradient g.  The first step length makes the
+ * largest change 1 % of the mean velocity; later ones are the
+ * Barzilai-Borwein length s.s / s.y (s = model change, y = gradient change;
+ * kept when s.y <= 0); a step is accepted when the misfit decreases by at
+ * least 1e-4 g.(v - v_new) (Armijo), else halved, at most 10 times, after
+ * which the inversion stops.  history: host [iters + 1] misfits (initial
+ * and after each accepted iteration) or NULL; *done: accepted iterations.
+ * A multiscale inversion calls this once per frequency band, with that
+ * band's grid (Ricker f0) and low-passed d_obs (empso_lowpass).
+ * Synchronises `stream` every iteration. */
+empso_status empso_fwi(empso_ctx *ctx, float *vel, const empso_shot *shots, int32_t S,
+                       const float *d_obs, int32_t iters, float vmin, float vmax,
+                       double *history, int32_t *done, void *stream);
+
 /* ---- non-finite misfits ------------------------------------------------
  * A particle whose misfit sum is NaN or infinite (a diverging or
  * non-finite model) gets misfit +inf, so it never becomes a personal or

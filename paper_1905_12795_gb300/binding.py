@@ -33,7 +33,7 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
            "empso_nonfinite_count", "empso_set_strict", "empso_save", "empso_load",
            "empso_set_levels", "empso_set_water", "empso_level_bounds", "empso_last_kernel_name",
-           "empso_lowpass",
+           "empso_lowpass", "empso_gradient", "empso_fwi",
            "empso_status_string", "empso_last_error"]
 
 
@@ -122,6 +122,9 @@ def load():
     L.empso_last_kernel_name.argtypes = [_vp]
     L.empso_last_kernel_name.restype = ctypes.c_char_p
     L.empso_set_water.argtypes = [_vp, _i32, _f32, _f32]
+    L.empso_gradient.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp, _vp, _vp]
+    L.empso_fwi.argtypes = [_vp, _vp, P(EmpsoShot), _i32, _vp, _i32, _f32, _f32, P(_f64), P(_i32),
+                            _vp]
     L.empso_lowpass.argtypes = [_vp, _vp, _i32, _i32, _i32, _f64, _vp, _i32, _f64, _f64, _f64, _vp]
     L.empso_level_bounds.argtypes = [_i32, _vp, _vp, _f64, _f64, _f64, _f64, _f64, _f64, _vp, _vp]
     L.empso_save.argtypes = [_vp, ctypes.c_char_p]
@@ -291,6 +294,19 @@ class Context:
         self._check(self._L.empso_lowpass(self._h, _ptr(traces), S, nt_in, nrec, float(dt_in),
                                           _ptr(out), nt_out, float(dt_out), float(f_cut),
                                           float(half_width), _stream()))
+
+    def gradient(self, vel, shots, d_obs, grad, misfit=None):
+        """Misfit (optional device [M] doubles) and dphi/dv [M][nz][nx] of gridded models."""
+        self._check(self._L.empso_gradient(self._h, _ptr(vel), vel.shape[0], shots, len(shots),
+                                           _ptr(d_obs), _ptr(misfit), _ptr(grad), _stream()))
+
+    def fwi(self, vel, shots, d_obs, iters, vmin, vmax):
+        """Steepest-descent FWI of vel [nz][nx] in place; returns the misfit history."""
+        hist = (_f64 * (iters + 1))()
+        done = _i32()
+        self._check(self._L.empso_fwi(self._h, _ptr(vel), shots, len(shots), _ptr(d_obs), int(iters),
+                                      float(vmin), float(vmax), hist, ctypes.byref(done), _stream()))
+        return list(hist)[:done.value + 1]
 
     def nonfinite_count(self, reset=False):
         """Non-finite misfits (returned as +inf) since creation or the last reset."""

@@ -1,0 +1,354 @@
+// Adjoint-state gradient of the l2 misfit with respect to the velocity model
+// (the local full-waveform inversion of section "Testing approach": steepest
+// descent on the misfit's gradient, started from the EMPSO model).
+//
+// Forward scheme (the modelling kernels' scheme, written per point):
+//   u^{n+1} = 2 f u^n - g u^{n-1} + f a (L u^n + s^n),
+//   f = 1 / (1 + t), g = (1 - t) f, t = (eta_x + eta_z) dt / 2, a = v^2 dt^2,
+// with L the order-2R Laplacian (zero outside the padded grid, so L is
+// symmetric), u^0 = u^{-1} = 0, residual e_n = R u^{n+1} - d_obs,n (R the
+// bilinear receiver sampling) and phi = w/2 sum_n |e_n|^2 per shot of weight
+// w.  Its exact discrete adjoint, for k = nt .. 1 with mu^{nt+1} = mu^{nt+2} = 0:
+//   mu^k = w R^T e_{k-1} + 2 f mu^{k+1} + L (f a mu^{k+1}) - g mu^{k+2},
+//   dphi/da = sum_{k=1..nt} mu^k f (L u^{k-1} + s^{k-1}).
+// The forward pass keeps the whole history u^0 .. u^nt in HBM (no
+// checkpointing: a shot of the 461 x 151 grid takes 0.78 GB).  Then
+// dphi/da of the padded grid is folded back onto the physical nodes (the
+// transpose of the edge extension into the damping pad) and chained to the
+// velocity: dphi/dv = 2 v dt^2 dphi/da.
+//
+// Every kernel runs over all instances at once (blockIdx.y = instance), one
+// launch per time step and stage; the receiver transpose adds the four corner
+// contributions in four ordered passes.
+#include "internal.cuh"
+
+namespace empso {
+
+namespace {
+
+__device__ __forceinline__ float lap_at(const float *u, const GridDev &g, long long k)
+{
+    float s = g.cxm[0] * u[k];
+#pragma unroll
+    for (int m = 1; m <= MAX_R; ++m) {
+        if (m > g.R) break;
+        s = fmaf(g.cxm[m], u[k - m] + u[k + m], s);
+        s = fmaf(g.czm[m], u[k - (long long)m * g.pitch] + u[k + (long long)m * g.pitch], s);
+    }
+    return s;
+}
+
+struct SrcCorner {
+    int I0, J0;
+    float w[4];
+};
+
+__device__ __forceinline__ SrcCorner src_corner(float x, float z, const GridDev &g)
+{
+    SrcCorner c;
+    const float fx = x / g.hx + (float)g.pad, fz = z / g.hz + (float)g.pad;
+    c.I0 = min(max((int)floorf(fx), 0), g.NX - 2);
+    c.J0 = min(max((int)floorf(fz), 0), g.NZ - 2);
+    const float ax = fx - (float)c.I0, az = fz - (float)c.J0;
+    c.w[0] = (1.f - ax) * (1.f - az);
+    c.w[1] = ax * (1.f - az);
+    c.w[2] = (1.f - ax) * az;
+    c.w[3] = ax * az;
+    return c;
+}
+
+// bilinear source weight of padded node (I, J)
+__device__ __forceinline__ float src_weight(const SrcCorner &c, int I, int J)
+{
+    if (J == c.J0) return I == c.I0 ? c.w[0] : (I == c.I0 + 1 ? c.w[1] : 0.f);
+    if (J == c.J0 + 1) return I == c.I0 ? c.w[2] : (I == c.I0 + 1 ? c.w[3] : 0.f);
+    return 0.f;
+}
+
+// B = f a per model (m = blockIdx.y)
+__global__ void adj_prep_kernel(GridDev g, const float *a, float *B)
+{
+    const long long off = (long long)blockIdx.y * g.field;
+    const long long pts = (long long)g.NX * g.NZ;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pts;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / g.NX), I = (int)(e % g.NX);
+        const long long k = (long long)(J + HALO) * g.pitch + I + HALO;
+        const float t = g.ex[I + HALO] + g.ez[J + HALO];
+        B[off + k] = a[off + k] / (1.f + t);
+    }
+}
+
+// u^{n+1} of every instance into H[n+1]
+__global__ void adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
+{
+    const AdjInst in = insts[blockIdx.y];
+    const long long pts = (long long)g.NX * g.NZ;
+    const float *u = in.H + (long long)n * g.field;
+    const float *um = in.H + (long long)(n > 0 ? n - 1 : 0) * g.field;   // u^{-1} = u^0 = 0
+    float *u1 = in.H + (long long)(n + 1) * g.field;
+    const SrcCorner sc = src_corner(in.sx, in.sz, g);
+    const float rn = g.wavelet[n] / (g.hx * g.hz);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pts;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / g.NX), I = (int)(e % g.NX);
+        const long long k = (long long)(J + HALO) * g.pitch + I + HALO;
+        const float t = g.ex[I + HALO] + g.ez[J + HALO];
+        const float lap = fmaf(src_weight(sc, I, J), rn, lap_at(u, g, k));
+        u1[k] = (2.f * u[k] - (1.f - t) * um[k] + in.a[k] * lap) / (1.f + t);
+    }
+}
+
+// residual e_n = R u^{n+1} - d_obs,n (one block per instance)
+__global__ void adj_record_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
+{
+    const AdjInst in = insts[blockIdx.x];
+    const float *u = in.H + (long long)(n + 1) * g.field;
+    for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
+        const float2 p = in.rec[r];
+        const SrcCorner c = src_corner(p.x, p.y, g);
+        const long long k = (long long)(c.J0 + HALO) * g.pitch + c.I0 + HALO;
+        const float d = c.w[0] * u[k] + c.w[1] * u[k + 1] + c.w[2] * u[k + g.pitch] +
+                        c.w[3] * u[k + g.pitch + 1];
+        in.E[(long long)n * in.nrec + r] = d - in.dobs[(long long)n * in.nrec + r];
+    }
+}
+
+// mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} (before the receiver term)
+__global__ void adj_back_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
+{
+    const AdjInst in = insts[blockIdx.y];
+    const long long pts = (long long)g.NX * g.NZ;
+    float *mk = in.mu + (long long)(k % 3) * g.field;
+    const float *m1 = in.mu + (long long)((k + 1) % 3) * g.field;
+    const float *m2 = in.mu + (long long)((k + 2) % 3) * g.field;
+    const float *q1 = in.Q + (long long)((k + 1) % 2) * g.field;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pts;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / g.NX), I = (int)(e % g.NX);
+        const long long kk = (long long)(J + HALO) * g.pitch + I + HALO;
+        const float t = g.ex[I + HALO] + g.ez[J + HALO];
+        const float f = 1.f / (1.f + t);
+        mk[kk] = 2.f * f * m1[kk] + lap_at(q1, g, kk) - (1.f - t) * f * m2[kk];
+    }
+}
+
+// mu^k += w R^T e_{k-1}: corner c of every receiver in pass c (one block per
+// instance); receivers sharing a cell meet in an atomic add
+__global__ void adj_inject_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
+{
+    const AdjInst in = insts[blockIdx.x];
+    float *mk = in.mu + (long long)(k % 3) * g.field;
+    for (int c = 0; c < 4; ++c) {
+        for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
+            const float2 p = in.rec[r];
+            const SrcCorner sc = src_corner(p.x, p.y, g);
+            const long long kk = (long long)(sc.J0 + (c >> 1) + HALO) * g.pitch + sc.I0 + (c & 1) + HALO;
+            atomicAdd(mk + kk, in.w * sc.w[c] * in.E[(long long)(k - 1) * in.nrec + r]);
+        }
+        __syncthreads();
+    }
+}
+
+// G += mu^k f (L u^{k-1} + s^{k-1}); Q^k = f a mu^k
+__global__ void adj_grad_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
+{
+    const AdjInst in = insts[blockIdx.y];
+    const long long pts = (long long)g.NX * g.NZ;
+    const float *mk = in.mu + (long long)(k % 3) * g.field;
+    float *qk = in.Q + (long long)(k % 2) * g.field;
+    const float *u = in.H + (long long)(k - 1) * g.field;
+    const SrcCorner sc = src_corner(in.sx, in.sz, g);
+    const float rn = g.wavelet[k - 1] / (g.hx * g.hz);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pts;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / g.NX), I = (int)(e % g.NX);
+        const long long kk = (long long)(J + HALO) * g.pitch + I + HALO;
+        const float t = g.ex[I + HALO] + g.ez[J + HALO];
+        const float m = mk[kk];
+        qk[kk] = in.B[kk] * m;
+        const float lap = fmaf(src_weight(sc, I, J), rn, lap_at(u, g, kk));
+        in.G[kk] = fmaf(m / (1.f + t), lap, in.G[kk]);
+    }
+}
+
+// phi of every instance: w/2 sum e^2, fixed reduction order (one block each)
+__global__ void adj_misfit_kernel(const AdjInst *__restrict__ insts, int nt, double *phi)
+{
+    const AdjInst in = insts[blockIdx.x];
+    __shared__ double red[32];
+    double s = 0.0;
+    const long long n = (long long)nt * in.nrec;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double e = in.E[i];
+        s += e * e;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) v += red[w];
+        phi[blockIdx.x] = 0.5 * (double)in.w * v;
+    }
+}
+
+// per model m: misfit = sum over shots (shot order); dphi/dv at physical node
+// (i, j) = 2 v dt^2 sum_shots sum of G over the padded nodes whose edge
+// extension reads (i, j)
+__global__ void adj_fold_kernel(GridDev g, const AdjInst *__restrict__ insts, int S,
+                                const float *__restrict__ vel, const double *phi, double *misfit,
+                                float *grad)
+{
+    const int m = blockIdx.y;
+    const int np = g.nx * g.nz;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && misfit) {
+        double v = 0.0;
+        for (int s = 0; s < S; ++s) v += phi[m * S + s];
+        misfit[m] = isfinite(v) ? v : __longlong_as_double(0x7ff0000000000000LL);
+    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np; e += gridDim.x * blockDim.x) {
+        const int j = e / g.nx, i = e % g.nx;
+        const int I0 = i == 0 ? 0 : i + g.pad, I1 = i == g.nx - 1 ? g.NX - 1 : i + g.pad;
+        const int J0 = j == 0 ? 0 : j + g.pad, J1 = j == g.nz - 1 ? g.NZ - 1 : j + g.pad;
+        float acc = 0.f;
+        for (int s = 0; s < S; ++s) {
+            const float *G = insts[m * S + s].G;
+            for (int J = J0; J <= J1; ++J)
+                for (int I = I0; I <= I1; ++I) acc += G[(long long)(J + HALO) * g.pitch + I + HALO];
+        }
+        const float v = vel[(long long)m * np + e];
+        grad[(long long)m * np + e] = 2.f * v * g.dt * g.dt * acc;
+    }
+}
+
+int grid_blocks(const GridDev &g)
+{
+    const long long pts = (long long)g.NX * g.NZ;
+    long long b = (pts + 255) / 256;
+    return (int)(b > 4096 ? 4096 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, cudaStream_t st)
+{
+    adj_prep_kernel<<<dim3(grid_blocks(g), M), 256, 0, st>>>(g, a, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
+                               cudaStream_t st)
+{
+    const dim3 grid(grid_blocks(g), n_inst);
+    for (int n = 0; n < g.nt; ++n) {
+        adj_fwd_kernel<<<grid, 256, 0, st>>>(g, insts, n);
+        adj_record_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
+                                cudaStream_t st)
+{
+    const dim3 grid(grid_blocks(g), n_inst);
+    for (int k = g.nt; k >= 1; --k) {
+        adj_back_kernel<<<grid, 256, 0, st>>>(g, insts, k);
+        adj_inject_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, k);
+        adj_grad_kernel<<<grid, 256, 0, st>>>(g, insts, k);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
+                              double *phi, double *misfit, float *grad, cudaStream_t st)
+{
+    adj_misfit_kernel<<<M * S, 256, 0, st>>>(insts, g.nt, phi);
+    const int np = g.nx * g.nz;
+    adj_fold_kernel<<<dim3((np + 255) / 256, M), 256, 0, st>>>(g, insts, S, vel, phi, misfit, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace empso
+
+// ---------------------------------------------------------------------------
+// vector kernels of the local FWI driver (one model field [nz][nx])
+// ---------------------------------------------------------------------------
+namespace empso {
+
+namespace {
+
+// out = clip(v - alpha g, vmin, vmax)
+__global__ void fwi_step_kernel(const float *v, const float *g, float alpha, float vmin, float vmax,
+                                float *out, int n)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        out[e] = fminf(fmaxf(v[e] - alpha * g[e], vmin), vmax);
+}
+
+// r[0] = sum (a - b) c, r[1] = sum (a - b)^2, r[2] = sum (a - b)(c - d),
+// r[3] = max |c|, r[4] = sum a; one block, fixed reduction order
+__global__ void fwi_dots_kernel(const float *a, const float *b, const float *c, const float *d, int n,
+                                double *r)
+{
+    __shared__ double red[5][32];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, mx = 0.0, sa = 0.0;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const double ab = b ? (double)a[e] - (double)b[e] : (double)a[e];
+        const double cc = c[e];
+        const double cd = d ? cc - (double)d[e] : cc;
+        s0 += ab * cc;
+        s1 += ab * ab;
+        s2 += ab * cd;
+        mx = fmax(mx, fabs(cc));
+        sa += a[e];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = s0;
+        red[1][w] = s1;
+        red[2][w] = s2;
+        red[3][w] = mx;
+        red[4][w] = sa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < (int)blockDim.x / 32; ++i) {
+            t[0] += red[0][i];
+            t[1] += red[1][i];
+            t[2] += red[2][i];
+            t[3] = fmax(t[3], red[3][i]);
+            t[4] += red[4][i];
+        }
+        for (int i = 0; i < 5; ++i) r[i] = t[i];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fwi_step(const float *v, const float *g, float alpha, float vmin, float vmax,
+                            float *out, int n, cudaStream_t st)
+{
+    fwi_step_kernel<<<(n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256, 256, 0, st>>>(v, g, alpha, vmin,
+                                                                                    vmax, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwi_dots(const float *a, const float *b, const float *c, const float *d, int n,
+                            double *r, cudaStream_t st)
+{
+    fwi_dots_kernel<<<1, 1024, 0, st>>>(a, b, c, d, n, r);
+    return cudaGetLastError();
+}
+
+}  // namespace empso

@@ -95,6 +95,21 @@ struct empso_ctx {
     double *rank_full = nullptr;    // [P] EM sort keys
     float *logphi = nullptr;        // [P] predictions
 
+    // adjoint-state gradient workspace (grown on demand)
+    struct AdjWork {
+        float *a = nullptr, *B = nullptr, *H = nullptr, *mu = nullptr, *Q = nullptr, *G = nullptr,
+              *E = nullptr;
+        size_t a_cap = 0, H_cap = 0, mu_cap = 0, E_cap = 0;   // floats
+        AdjInst *insts = nullptr;
+        size_t inst_cap = 0;
+        double *phi = nullptr;
+        size_t phi_cap = 0;
+        std::string layout;       // grid and instance count the history was zeroed for
+        float *fv = nullptr;      // FWI vectors: trial model, gradients [3][np]
+        size_t fv_cap = 0;
+        double *fd = nullptr;     // FWI reductions [8] and misfit [1]
+    } adj;
+
     // kernel timing
     bool timing = false;
     bool timed = false;
@@ -627,6 +642,14 @@ void free_ctx(empso_ctx *c)
     cudaFree(c->counter);
     cudaFree(c->dev_err);
     cudaFree(c->nonfinite);
+    cudaFree(c->adj.a);       // B lies inside a; Q and G inside mu
+    cudaFree(c->adj.H);
+    cudaFree(c->adj.mu);
+    cudaFree(c->adj.E);
+    cudaFree(c->adj.insts);
+    cudaFree(c->adj.phi);
+    cudaFree(c->adj.fv);
+    cudaFree(c->adj.fd);
     cudaFree(c->pso_mem);
     cudaFree(c->pso_int);
     cudaFree(c->xf);
@@ -886,6 +909,178 @@ empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t n
     CK(ctx, lowpass_configure(smem));
     CK(ctx, launch_lowpass(in, S, nt_in, nrec, dt_in, out, nt_out, dt_out, f_cut, half_width, smem,
                            (cudaStream_t)stream));
+    return EMPSO_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// grow a device array to at least `need` elements (contents not kept)
+template <class T> empso_status adj_grow(empso_ctx *ctx, T **p, size_t *cap, size_t need, bool *grew)
+{
+    if (*cap >= need) return EMPSO_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, sizeof(T) * std::max<size_t>(need, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, EMPSO_OOM, "gradient workspace: " + std::to_string(sizeof(T) * need) + " bytes");
+    }
+    *cap = need;
+    if (grew) *grew = true;
+    return EMPSO_OK;
+}
+
+// misfit and dphi/dv of M gridded models (all shots on one grid)
+empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_shot *shots, int S,
+                           const float *d_obs, double *misfit, float *grad, cudaStream_t st)
+{
+    const int gid = shots[0].grid_id;
+    for (int s = 1; s < S; ++s)
+        if (shots[s].grid_id != gid) return fail(ctx, EMPSO_INVALID_ARG, "gradient: all shots on one grid");
+    const GridDev &g = ctx->grids[gid].dev;
+    const long long I = (long long)M * S;
+    const size_t F = (size_t)g.field;
+    int rec_max = 0;
+    for (int s = 0; s < S; ++s) rec_max = std::max(rec_max, (int)shots[s].nrec);
+    auto &W = ctx->adj;
+    bool grewH = false;
+    empso_status rc;
+    if ((rc = adj_grow(ctx, &W.a, &W.a_cap, 2 * F * M, nullptr))) return rc;
+    W.B = W.a + F * M;
+    if ((rc = adj_grow(ctx, &W.H, &W.H_cap, F * (size_t)(g.nt + 1) * I, &grewH))) return rc;
+    if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 6 * I, nullptr))) return rc;
+    W.Q = W.mu + F * 3 * I;
+    W.G = W.mu + F * 5 * I;
+    if ((rc = adj_grow(ctx, &W.E, &W.E_cap, (size_t)g.nt * rec_max * I, nullptr))) return rc;
+    if ((rc = adj_grow(ctx, &W.insts, &W.inst_cap, (size_t)I, nullptr))) return rc;
+    if ((rc = adj_grow(ctx, &W.phi, &W.phi_cap, (size_t)I, nullptr))) return rc;
+    // zero halo rows and u^0 of the history whenever its layout changes
+    std::ostringstream lay;
+    lay << gid << "|" << I << "|" << (const void *)W.H;
+    if (grewH || W.layout != lay.str()) {
+        CK(ctx, cudaMemsetAsync(W.H, 0, sizeof(float) * F * (size_t)(g.nt + 1) * I, st));
+        W.layout = lay.str();
+    }
+    CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 6 * I, st));
+    // instance table (the previous call's kernels may still read the old one)
+    std::vector<long long> doff(S + 1, 0);
+    for (int s = 0; s < S; ++s) doff[s + 1] = doff[s] + (long long)g.nt * shots[s].nrec;
+    std::vector<AdjInst> hi((size_t)I);
+    for (int m = 0; m < M; ++m)
+        for (int s = 0; s < S; ++s) {
+            const long long q = (long long)m * S + s;
+            AdjInst &in = hi[(size_t)q];
+            in.a = W.a + F * m;
+            in.B = W.B + F * m;
+            in.H = W.H + F * (size_t)(g.nt + 1) * q;
+            in.mu = W.mu + F * 3 * q;
+            in.Q = W.Q + F * 2 * q;
+            in.G = W.G + F * q;
+            in.E = W.E + (size_t)g.nt * rec_max * q;
+            in.dobs = d_obs + doff[s];
+            in.rec = ctx->rec_dev + shots[s].rec_begin;
+            in.nrec = shots[s].nrec;
+            in.sx = shots[s].sx;
+            in.sz = shots[s].sz;
+            in.w = shots[s].weight;
+        }
+    CK(ctx, cudaStreamSynchronize(st));
+    CK(ctx, cudaMemcpy(W.insts, hi.data(), sizeof(AdjInst) * hi.size(), cudaMemcpyHostToDevice));
+    const int rec_threads = std::min(1024, std::max(32, (rec_max + 31) / 32 * 32));
+    CK(ctx, launch_vel_to_field(g, vel, M, W.a, g.field, st));
+    CK(ctx, launch_adj_prep(g, W.a, W.B, M, st));
+    CK(ctx, launch_adj_forward(g, W.insts, (int)I, rec_threads, st));
+    CK(ctx, launch_adj_backward(g, W.insts, (int)I, rec_threads, st));
+    CK(ctx, launch_adj_finish(g, W.insts, M, S, vel, W.phi, misfit, grad, st));
+    return EMPSO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+empso_status empso_gradient(empso_ctx *ctx, const float *vel, int32_t M, const empso_shot *shots,
+                            int32_t S, const float *d_obs, double *misfit, float *grad, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (M < 1 || !vel || !d_obs || !grad) return fail(ctx, EMPSO_INVALID_ARG, "bad vel/d_obs/grad");
+    empso_status rc = check_shots(ctx, shots, S, shots && S > 0 ? shots[0].grid_id : -1);
+    if (rc) return rc;
+    return gradient_impl(ctx, vel, M, shots, S, d_obs, misfit, grad, (cudaStream_t)stream);
+}
+
+empso_status empso_fwi(empso_ctx *ctx, float *vel, const empso_shot *shots, int32_t S,
+                       const float *d_obs, int32_t iters, float vmin, float vmax, double *history,
+                       int32_t *done, void *stream)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (!vel || !d_obs || iters < 0 || !(vmin > 0) || !(vmin <= vmax))
+        return fail(ctx, EMPSO_INVALID_ARG, "bad vel/d_obs/iters/bounds");
+    empso_status rc = check_shots(ctx, shots, S, shots && S > 0 ? shots[0].grid_id : -1);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const GridDev &g = ctx->grids[shots[0].grid_id].dev;
+    const int np = g.nx * g.nz;
+    auto &W = ctx->adj;
+    if ((rc = adj_grow(ctx, &W.fv, &W.fv_cap, (size_t)3 * np, nullptr))) return rc;
+    if (!W.fd) CK(ctx, cudaMalloc(&W.fd, sizeof(double) * 16));
+    float *vt = W.fv, *gcur = W.fv + np, *gnew = W.fv + 2 * (size_t)np;
+    double *dots = W.fd, *phi_dev = W.fd + 8;
+    double r[5];
+    auto misfit_of = [&](const float *v, double *out) -> empso_status {
+        Models mod;
+        mod.vel = v;
+        mod.M = 1;
+        empso_status e = run_batch(ctx, mod, shots, S, d_obs, nullptr, phi_dev, st);
+        if (e) return e;
+        CK(ctx, cudaMemcpyAsync(out, phi_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaStreamSynchronize(st));
+        return EMPSO_OK;
+    };
+    auto reduce = [&](const float *a, const float *b, const float *c, const float *d) -> empso_status {
+        CK(ctx, launch_fwi_dots(a, b, c, d, np, dots, st));
+        CK(ctx, cudaMemcpyAsync(r, dots, sizeof r, cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaStreamSynchronize(st));
+        return EMPSO_OK;
+    };
+    double phi;
+    if ((rc = misfit_of(vel, &phi))) return rc;
+    if (history) history[0] = phi;
+    if ((rc = gradient_impl(ctx, vel, 1, shots, S, d_obs, nullptr, gcur, st))) return rc;
+    // first step: the largest model change is 1 % of the mean velocity
+    if ((rc = reduce(vel, nullptr, gcur, nullptr))) return rc;
+    double alpha = r[3] > 0 ? 0.01 * (r[4] / np) / r[3] : 0.0;
+    int it = 0;
+    for (; it < iters && alpha > 0; ++it) {
+        bool ok = false;
+        double phi_t = phi;
+        for (int tries = 0; tries < 10 && !ok; ++tries) {
+            CK(ctx, launch_fwi_step(vel, gcur, (float)alpha, vmin, vmax, vt, np, st));
+            if ((rc = misfit_of(vt, &phi_t))) return rc;
+            // Armijo on the step actually taken (after the clip): g . (v - v_t)
+            if ((rc = reduce(vel, vt, gcur, nullptr))) return rc;
+            const double decrease = r[0];
+            if (decrease > 0 && std::isfinite(phi_t) && phi_t <= phi - 1e-4 * decrease) ok = true;
+            else alpha *= 0.5;
+        }
+        if (!ok) break;
+        if ((rc = gradient_impl(ctx, vt, 1, shots, S, d_obs, nullptr, gnew, st))) return rc;
+        // Barzilai-Borwein step: s = v_t - v, y = g_new - g; alpha = s.s / s.y
+        if ((rc = reduce(vt, vel, gnew, gcur))) return rc;
+        const double ss = r[1], sy = r[2];
+        if (sy > 0) alpha = ss / sy;
+        CK(ctx, cudaMemcpyAsync(vel, vt, sizeof(float) * np, cudaMemcpyDeviceToDevice, st));
+        CK(ctx, cudaMemcpyAsync(gcur, gnew, sizeof(float) * np, cudaMemcpyDeviceToDevice, st));
+        phi = phi_t;
+        if (history) history[it + 1] = phi;
+    }
+    CK(ctx, cudaStreamSynchronize(st));
+    if (done) *done = it;
     return EMPSO_OK;
 }
 

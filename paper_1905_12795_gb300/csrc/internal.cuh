@@ -76,6 +76,32 @@ struct Inst {
 cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wavelet,
                                float *Wx, float *Wz, double vmax_damp, double f0,
                                cudaStream_t st);
+// Adjoint-state gradient (adjoint.cu): one (model, shot) instance.
+struct AdjInst {
+    const float *a;      // model field a = v^2 dt^2 (buffer layout)
+    const float *B;      // f a, f = 1 / (1 + t)
+    float *H;            // wavefield history [nt + 1][field], H[n] = u^n
+    float *mu;           // adjoint fields, 3 rolling buffers [3][field]
+    float *Q;            // f a mu, 2 rolling buffers [2][field]
+    float *G;            // dphi/da of this shot [field]
+    float *E;            // residuals [nt][nrec]
+    const float *dobs;   // [nt][nrec]
+    const float2 *rec;   // receiver positions
+    int nrec;
+    float sx, sz, w;     // source position, shot weight
+};
+cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, cudaStream_t st);
+cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
+                               cudaStream_t st);
+cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
+                                cudaStream_t st);
+cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
+                              double *phi, double *misfit, float *grad, cudaStream_t st);
+cudaError_t launch_fwi_step(const float *v, const float *g, float alpha, float vmin, float vmax,
+                            float *out, int n, cudaStream_t st);
+cudaError_t launch_fwi_dots(const float *a, const float *b, const float *c, const float *d, int n,
+                            double *r, cudaStream_t st);
+
 // Band-limited resampling of traces (filter.cu).
 long long lowpass_span(double dt_in, double dt_out, double W);
 size_t lowpass_smem_bytes(long long span);

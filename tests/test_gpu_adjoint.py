@@ -1,0 +1,126 @@
+"""The adjoint-state gradient against the definition of a gradient, and the
+local FWI that uses it.
+
+The oracle of dphi/dv is the derivative of the FP64 oracle misfit itself:
+central differences (phi(v + eps d) - phi(v - eps d)) / (2 eps) along a
+direction d, compared with <grad, d> from the GPU (FP32 forward and adjoint
+passes over a few hundred steps: 2e-3 relative for a dense direction, 1e-2
+for a single node).  One node on the model's edge checks the fold of the
+damping pad (the edge extension's transpose).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_12795_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1905_12795_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_gradient_matches_oracle_directional_derivatives(B, order):
+    nx, nz, h, pad, T, f0, vmax = 41, 31, 10.0, 8, 0.25, 15.0, 3000.0
+    og = oracle.Grid(nx, nz, h, h, pad, order, T, f0, vmax)
+    v = synth.layered_faulted_model(nx, nz, h, h, seed=5, vmin=1500.0, vmax=2800.0)
+    v_true = synth.layered_faulted_model(nx, nz, h, h, seed=6, vmin=1500.0, vmax=2800.0)
+    shots = np.array([[105.0, 23.0], [297.0, 41.0]])
+    rec = synth.receiver_line(nx, h, 27.0)[:-1] + np.array([3.7, 0.0])
+    nrec = len(rec)
+    rb, rc = [0, 0], [nrec, nrec]
+    w = [1.0, 0.5]
+    _, obs = oracle.shot_batch(og, v_true, shots, rec, rb, rc, want_traces=True)
+
+    def phi(vel):
+        p, _ = oracle.shot_batch(og, vel, shots, rec, rb, rc, dobs=obs)
+        return float(np.dot(w, p[0]))
+
+    grid = B.make_grid(nx, nz, h, h, pad, order, T, f0, 1500.0, vmax)
+    ctx = B.Context([grid], rec)
+    sh = B.make_shots(shots, rb, rc, weights=w)
+    dobs = _dev(np.concatenate([o.ravel() for o in obs]))
+    g = torch.zeros(1, nz, nx, device="cuda")
+    mis = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.gradient(_dev(v[None]), sh, dobs, g, mis)
+    G = g[0].cpu().numpy().astype(np.float64)
+    phi0 = phi(v)
+    assert mis.item() == pytest.approx(phi0, rel=1e-4)
+    # the same misfit as the modelling kernels give
+    m2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.eval_models(_dev(v[None]), sh, dobs, m2)
+    assert m2.item() == pytest.approx(mis.item(), rel=1e-5)
+    rng = np.random.default_rng(order)
+    cases = [(rng.normal(size=(nz, nx)), 1.0, 2e-3)]
+    for (j, i) in ((4, 14), (20, 0)):        # near the sources; on the left edge (pad fold)
+        d = np.zeros((nz, nx))
+        d[j, i] = 1.0
+        cases.append((d, 5.0, 1e-2))
+    for d, eps, tol in cases:
+        fd = (phi(v + eps * d) - phi(v - eps * d)) / (2 * eps)
+        ad = float(np.sum(G * d))
+        assert abs(ad - fd) <= tol * abs(fd), (ad, fd)
+    ctx.close()
+
+
+def test_gradient_batch_of_models_equals_single_calls(B):
+    nx, nz, h = 37, 29, 10.0
+    grid = B.make_grid(nx, nz, h, h, 6, 4, 0.2, 15.0, 1500.0, 3000.0)
+    rec = synth.receiver_line(nx, h, 20.0)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    sh = B.make_shots([(120.0, 20.0), (240.0, 20.0)], [0, 0], [nx, nx])
+    dobs = torch.randn(2 * nt * nx, device="cuda") * 1e-3
+    vs = np.stack([synth.layered_faulted_model(nx, nz, h, h, seed=s, vmin=1500.0, vmax=2800.0)
+                   for s in (1, 2, 3)])
+    g3 = torch.zeros(3, nz, nx, device="cuda")
+    m3 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx.gradient(_dev(vs), sh, dobs, g3, m3)
+    for k in range(3):
+        g1 = torch.zeros(1, nz, nx, device="cuda")
+        m1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.gradient(_dev(vs[k:k + 1]), sh, dobs, g1, m1)
+        assert torch.equal(g1[0], g3[k]) and m1.item() == m3[k].item()
+    ctx.close()
+
+
+def test_fwi_descends_and_improves_the_model(B):
+    nx, nz, h, pad = 61, 41, 10.0, 10
+    grid = B.make_grid(nx, nz, h, h, pad, 4, 0.45, 12.0, 1400.0, 3000.0)
+    rec = synth.receiver_line(nx, h, 20.0)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    shots = synth.shot_line(3, (nx - 1) * h, 20.0)
+    sh = B.make_shots(shots, [0] * 3, [nx] * 3)
+    true = synth.layered_faulted_model(nx, nz, h, h, seed=11, vmin=1500.0, vmax=2600.0)
+    dobs = torch.zeros(3 * nt * nx, device="cuda")
+    ctx.forward_traces(_dev(true[None]), sh, dobs)
+    # start: the true model smoothed by a 9 x 9 box (a background model)
+    k = 4
+    pad_t = np.pad(true, k, mode="edge")
+    start = np.zeros_like(true)
+    for dj in range(-k, k + 1):
+        for di in range(-k, k + 1):
+            start += pad_t[k + dj:k + dj + nz, k + di:k + di + nx]
+    start /= (2 * k + 1) ** 2
+    vel = _dev(start)
+    hist = ctx.fwi(vel, sh, dobs, 8, 1400.0, 3000.0)
+    assert len(hist) >= 5
+    assert all(b < a for a, b in zip(hist, hist[1:]))
+    assert hist[-1] < 0.5 * hist[0]
+    err0 = np.linalg.norm(start - true)
+    err1 = np.linalg.norm(vel.cpu().numpy() - true)
+    assert err1 < err0
+    assert float(vel.min()) >= 1400.0 and float(vel.max()) <= 3000.0
+    ctx.close()
