@@ -362,7 +362,7 @@ def run_ours(a):
                     "h2d_bytes_per_step": int(dobs.numel() * 4),
                     "d2h_bytes_per_step": int(mis.numel() * 8),
                     "fitness_evals_per_s": world * wl.P * a.steps / (e2e_total / 1e3)},
-            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
+            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster", 3: "L2 cluster"}.get(launch[0], "?"),
                        "cluster_ctas": launch[1], "autotuned": list(tuned),
                        "step": "CUDA graph: interpolation, persistent modelling launch, "
                                "misfit reduction, EMPSO step"},
@@ -534,7 +534,7 @@ def run_uneven(a):
                        "instances_per_step": wl.P * sum(wl.shots_per_grid),
                        "updates_per_step": upd, "l2": "flushed between timed steps"},
             "fitness_evals_per_s": wl.P * a.steps / (total / 1e3),
-            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
+            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster", 3: "L2 cluster"}.get(launch[0], "?"),
                        "cluster_ctas": launch[1], "autotuned": list(tuned)},
             "roofline": {"kernel": ctx.last_kernel_name(),
                          "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
@@ -599,7 +599,7 @@ def run_hires(a):
                                            "generation (bounded sample)",
                        "updates_per_step": upd, "l2": "inputs larger than L2"},
             "fitness_evals_per_s": P * a.steps / (total / 1e3),
-            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster"}.get(launch[0], "?"),
+            "kernel": {"kind": {1: "streaming", 2: "on-chip cluster", 3: "L2 cluster"}.get(launch[0], "?"),
                        "cluster_ctas": launch[1]},
             "roofline": {"kernel": ctx.last_kernel_name(),
                          "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,

@@ -276,16 +276,24 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
                                   int32_t *n_modelled, void *stream);
 
 /* Modelling kernel selection for the persistent launch:
- *   EMPSO_KERNEL_AUTO      on-chip variant when every grid of the batch fits a
- *                          cluster of <= 8 CTAs, else the streaming variant;
- *   EMPSO_KERNEL_STREAMING wavefields in global memory, one CTA per instance;
- *   EMPSO_KERNEL_RESIDENT  wavefields in distributed shared memory, one
- *                          thread-block cluster per instance (calls return
- *                          UNSUPPORTED when a grid does not fit).
- * Both compute the same scheme; results agree to FP32 rounding. */
+ *   EMPSO_KERNEL_AUTO       the tuned choice for this batch (empso_autotune),
+ *                           else the on-chip variant when every grid fits a
+ *                           cluster of <= 16 CTAs, else the L2 cluster
+ *                           variant, else the streaming variant;
+ *   EMPSO_KERNEL_STREAMING  wavefields in global memory, one CTA per
+ *                           instance;
+ *   EMPSO_KERNEL_RESIDENT   wavefields in distributed shared memory, one
+ *                           thread-block cluster per instance (calls return
+ *                           UNSUPPORTED when a grid does not fit);
+ *   EMPSO_KERNEL_CLUSTER_L2 wavefields in a per-cluster global buffer, one
+ *                           thread-block cluster per instance, with few
+ *                           enough instances in flight to stay in L2 (for
+ *                           grids too large for the on-chip variant).
+ * All compute the same scheme; results agree to FP32 rounding. */
 #define EMPSO_KERNEL_AUTO      0
 #define EMPSO_KERNEL_STREAMING 1
 #define EMPSO_KERNEL_RESIDENT  2
+#define EMPSO_KERNEL_CLUSTER_L2 3
 empso_status empso_set_kernel(empso_ctx *ctx, int32_t kind);
 
 /* Cluster size (CTAs per instance) of the on-chip kernel: 0 lets the library

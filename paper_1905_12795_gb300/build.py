@@ -21,7 +21,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libempso.so")
 
 SOURCES = ["api.cu", "tables.cu", "wave.cu", "wave_resident.cu", "wave_stream.cu", "pso.cu", "noalloc.cu",
-           "surrogate.cu", "filter.cu", "adjoint.cu"]
+           "surrogate.cu", "filter.cu", "adjoint.cu",
+           "wave_l2.cu"]
 EXTRA = {"pso.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -316,6 +316,10 @@ struct Models {
 };
 
 // Everything the host decides about one persistent modelling launch.
+// Instances of the L2-resident cluster kernel in flight are capped so that
+// their time levels and model fields fit this share of the 129 MB L2.
+constexpr long long L2_BUDGET_BYTES = 96LL << 20;
+
 struct Plan {
     int M = 0, S = 0;
     long long n_inst = 0, maxfield = 0;
@@ -324,6 +328,10 @@ struct Plan {
     int resR = 0, resC = 0, res_threads = 0, res_clusters = 0, ring_pitch = 0;
     size_t res_smem = 0;
     int n_ctas = 0;
+    bool l2 = false;                   // L2-resident cluster kernel
+    int l2C = 0, l2_clusters = 0, l2_threads = 0;
+    long long l2_slot_f4 = 0;
+    size_t l2_smem = 0;
     bool stream_tma = false;           // streaming path: row-pipelined bulk-copy kernel
     int st_threads = 0, st_R = 0, rec_max = 0;
     size_t st_smem = 0;
@@ -393,7 +401,7 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
         resR = (resR < 0 || resR == R) ? R : 0;
     }
     p.resident = false;
-    if (kind != EMPSO_KERNEL_STREAMING && resR > 0) {
+    if ((kind == EMPSO_KERNEL_AUTO || kind == EMPSO_KERNEL_RESIDENT) && resR > 0) {
         long long best_sms = 0;
         int nrec_max = 0;
         for (int s = 0; s < S; ++s) nrec_max = std::max(nrec_max, (int)shots[s].nrec);
@@ -431,8 +439,56 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
     if (kind == EMPSO_KERNEL_RESIDENT && !p.resident)
         return fail(ctx, EMPSO_UNSUPPORTED,
                     "the batch does not fit the on-chip kernel (grid too large or mixed orders)");
+    // L2-resident cluster kernel for grids the on-chip kernel cannot hold:
+    // the cluster size that keeps the most SMs busy while every instance in
+    // flight (two time levels and the model field) stays within the L2 budget
+    p.l2 = false;
+    if (!p.resident && resR > 0 && (kind == EMPSO_KERNEL_AUTO || kind == EMPSO_KERNEL_CLUSTER_L2)) {
+        int nrec_max = 0;
+        for (int s = 0; s < S; ++s) nrec_max = std::max(nrec_max, (int)shots[s].nrec);
+        const size_t sm = l2_smem_bytes(nrec_max);
+        long long best_sms = 0;
+        for (int C : {16, 12, 10, 8, 6, 4, 3, 2, 1}) {
+            if (forcedC > 0 && C != forcedC) continue;
+            bool ok = sm <= ctx->smem_optin;
+            long long slot = 0, inst_bytes = 0, items = 32;
+            for (int gid = 0; gid < ng && ok; ++gid) {
+                if (p.fbase[gid] < 0) continue;
+                const GridDev &g = ctx->grids[gid].dev;
+                ok = l2_fits(g, C);
+                slot = std::max(slot, l2_slot_f4(g, C));
+                inst_bytes = std::max(inst_bytes, 32 * l2_slot_f4(g, C) + 4 * g.field);
+                const int rows_c = (g.NZ + C - 1) / C;
+                items = std::max<long long>(items, (long long)g.NQ * ((rows_c + 7) / 8));
+            }
+            if (!ok) continue;
+            const int threads = (int)std::min<long long>(l2_max_threads(), (items + 31) / 32 * 32);
+            CK(ctx, l2_configure(resR, sm, C));
+            const long long by_l2 = std::max<long long>(1, L2_BUDGET_BYTES / std::max<long long>(inst_bytes, 1));
+            const int occ = l2_max_clusters(resR, C, threads, sm);
+            if (occ < 0)
+                return fail(ctx, EMPSO_CUDA_ERROR,
+                            std::string("L2 cluster kernel occupancy (C = ") + std::to_string(C) +
+                                "): " + cudaGetErrorString((cudaError_t)(-occ)));
+            const int nc = (int)std::min<long long>(std::min<long long>(occ, p.n_inst), by_l2);
+            const long long sms = (long long)nc * C;
+            if (nc > 0 && sms > best_sms) {
+                best_sms = sms;
+                p.l2 = true;
+                p.resR = resR;
+                p.l2C = C;
+                p.l2_clusters = nc;
+                p.l2_threads = threads;
+                p.l2_slot_f4 = slot;
+                p.l2_smem = sm;
+                p.ring_pitch = nrec_max;
+            }
+        }
+    }
+    if (kind == EMPSO_KERNEL_CLUSTER_L2 && !p.l2)
+        return fail(ctx, EMPSO_UNSUPPORTED, "the batch does not fit the L2 cluster kernel");
     int max_ctas = ctx->sm_count * ctx->wave_ctas_per_sm;
-    if (!p.resident && resR > 0) {
+    if (!p.resident && !p.l2 && resR > 0) {
         // row-pipelined streaming kernel: one thread per float4 column group
         int nq = 0, pitch = 0, nrec_max = 0;
         for (int gid = 0; gid < ng; ++gid) {
@@ -457,7 +513,11 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
     if ((rc = grow(ctx, (void **)&ctx->fields, &ctx->fields_cap, sizeof(float) * ftotal,
                    sizeof(float))) != EMPSO_OK)
         return rc;
-    if (!p.resident &&
+    if (p.l2 &&
+        (rc = grow(ctx, (void **)&ctx->slots, &ctx->slots_cap,
+                   sizeof(float4) * 2 * (size_t)p.l2_slot_f4 * p.l2_clusters, sizeof(float))) != EMPSO_OK)
+        return rc;
+    if (!p.resident && !p.l2 &&
         (rc = grow(ctx, (void **)&ctx->slots, &ctx->slots_cap,
                    sizeof(float) * 2 * p.maxfield * p.n_ctas, sizeof(float))) != EMPSO_OK)
         return rc;
@@ -550,6 +610,13 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
                                      ctx->partial, st));
         ctx->last_path = 2;
         ctx->last_C = p.resC;
+    } else if (p.l2) {
+        CK(ctx, launch_wave_l2(p.resR, ctx->grids_dev, p.insts,
+                               (int)p.n_inst, ctx->counter, p.l2C, p.l2_clusters, p.l2_threads,
+                               reinterpret_cast<float4 *>(ctx->slots), p.l2_slot_f4, p.ring_pitch,
+                               p.l2_smem, ctx->partial, st));
+        ctx->last_path = 4;
+        ctx->last_C = p.l2C;
     } else if (p.stream_tma) {
         CK(ctx, launch_wave_stream(p.st_R, ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter,
                                    ctx->slots, 2 * p.maxfield, p.n_ctas, p.st_threads, p.st_smem,
@@ -1416,6 +1483,7 @@ empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
     // candidates: the streaming kernel and every cluster size of the on-chip one
     std::vector<std::pair<int, int>> cand = {{EMPSO_KERNEL_STREAMING, 0}};
     for (int C = 1; C <= 16; ++C) cand.push_back({EMPSO_KERNEL_RESIDENT, C});
+    for (int C : {4, 8, 16}) cand.push_back({EMPSO_KERNEL_CLUSTER_L2, C});
     float best = 1e30f;
     std::pair<int, int> choice = {EMPSO_KERNEL_AUTO, 0};
     for (auto &c : cand) {
@@ -1438,7 +1506,7 @@ empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            choice = {c.first, p.resident ? p.resC : 0};
+            choice = {c.first, p.resident ? p.resC : (p.l2 ? p.l2C : 0)};
         }
     }
     ctx->err.clear();
@@ -1464,7 +1532,8 @@ empso_status empso_set_kernel(empso_ctx *ctx, int32_t kind)
 {
     if (!ctx) return EMPSO_INVALID_ARG;
     ctx->err.clear();
-    if (kind != EMPSO_KERNEL_AUTO && kind != EMPSO_KERNEL_STREAMING && kind != EMPSO_KERNEL_RESIDENT)
+    if (kind != EMPSO_KERNEL_AUTO && kind != EMPSO_KERNEL_STREAMING && kind != EMPSO_KERNEL_RESIDENT &&
+        kind != EMPSO_KERNEL_CLUSTER_L2)
         return fail(ctx, EMPSO_INVALID_ARG, "unknown kernel kind");
     ctx->kernel_kind = kind;
     return EMPSO_OK;
@@ -1482,7 +1551,9 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas)
 empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *cluster)
 {
     if (!ctx) return EMPSO_INVALID_ARG;
-    if (kind) *kind = ctx->last_path == 3 ? EMPSO_KERNEL_STREAMING : ctx->last_path;
+    if (kind)
+        *kind = ctx->last_path == 3 ? EMPSO_KERNEL_STREAMING
+                                    : (ctx->last_path == 4 ? EMPSO_KERNEL_CLUSTER_L2 : ctx->last_path);
     if (cluster) *cluster = ctx->last_C;
     return EMPSO_OK;
 }
@@ -1494,6 +1565,7 @@ const char *empso_last_kernel_name(const empso_ctx *ctx)
     case 1: return "wave_kernel";
     case 2: return "wave_resident_kernel";
     case 3: return "wave_stream_kernel";
+    case 4: return "wave_l2_kernel";
     default: return "";
     }
 }

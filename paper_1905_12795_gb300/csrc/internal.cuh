@@ -102,6 +102,18 @@ cudaError_t launch_fwi_step(const float *v, const float *g, float alpha, float v
 cudaError_t launch_fwi_dots(const float *a, const float *b, const float *c, const float *d, int n,
                             double *r, cudaStream_t st);
 
+// L2-resident cluster variant (wave_l2.cu): time levels in a per-cluster
+// global buffer of l2_slot_f4 float4 each.
+int l2_max_threads();
+size_t l2_smem_bytes(int ring_pitch);
+long long l2_slot_f4(const GridDev &g, int C);
+bool l2_fits(const GridDev &g, int C);
+cudaError_t l2_configure(int R, size_t smem, int C);
+int l2_max_clusters(int R, int C, int threads, size_t smem);
+cudaError_t launch_wave_l2(int R, const GridDev *grids_dev, const Inst *insts, int n_inst, int *counter,
+                           int C, int n_clusters, int threads, float4 *slots, long long slot_f4,
+                           int ring_pitch, size_t smem, double *partial, cudaStream_t st);
+
 // Band-limited resampling of traces (filter.cu).
 long long lowpass_span(double dt_in, double dt_out, double W);
 size_t lowpass_smem_bytes(long long span);

@@ -1,0 +1,380 @@
+// L2-resident cluster variant of the persistent modelling launch, for grids
+// whose two time levels do not fit the shared memory of a cluster (e.g. the
+// 921 x 301 grid at 10 m with a 60-cell damping layer).  Same scheme and
+// fused source/receiver/misfit work as the other variants (section "Testing
+// approach": 2nd order in time, 4th/8th order in space, damping layer, Ricker
+// source, l2 misfit).
+//
+// A thread-block cluster of C CTAs owns one instance at a time (global
+// queue) and splits its rows into C slabs, as the on-chip variant does, but
+// both time levels live in a per-cluster buffer in global memory laid out as
+// (C rows_c + 2R) rows of NQ + 2 float4 (one zero group each side, R zero rows
+// above): a CTA addresses its slab as that buffer plus z0 rows, so the halo
+// rows of its neighbours are read in place and nothing is exchanged.  With few
+// enough clusters in flight the working set (two levels and the model field,
+// ~5 MB per instance of the grid above) stays in the 129 MB L2, so each step
+// streams through L2 rather than HBM.  Wavefield loads use ld.global.cg (L2,
+// the point of coherence between the SMs of a cluster); one release/acquire
+// cluster barrier per step orders a step's stores before the next step's
+// loads.  Threads loop over work items (float4 column group x run of ROWS
+// rows), each with its z-stencil in a register window and packed FP32x2
+// arithmetic.
+#include <cooperative_groups.h>
+
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace empso {
+
+namespace {
+
+constexpr int L2_ROWS = 8;
+constexpr int L2_NT = 512;
+constexpr int L2_DEPTH = 2;
+
+__device__ __forceinline__ void set_lane(float4 &v, int l, float x)
+{
+    if (l == 0) v.x = x;
+    else if (l == 1) v.y = x;
+    else if (l == 2) v.z = x;
+    else v.w = x;
+}
+
+__device__ __forceinline__ void cp4(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void bilinear_corner(float x, float z, const GridDev &g, int &i0, int &j0,
+                                                float w[4])
+{
+    const float fx = x / g.hx + (float)g.pad;
+    const float fz = z / g.hz + (float)g.pad;
+    i0 = min(max((int)floorf(fx), 0), g.NX - 2);
+    j0 = min(max((int)floorf(fz), 0), g.NZ - 2);
+    const float ax = fx - (float)i0, az = fz - (float)j0;
+    w[0] = (1.f - ax) * (1.f - az);
+    w[1] = ax * (1.f - az);
+    w[2] = (1.f - ax) * az;
+    w[3] = ax * az;
+}
+
+template <int R>
+__device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float4 *U1, float *wring,
+                            float *dring, float4 *rec_w, int *rec_k, int C, int crank,
+                            cg::cluster_group &cluster, double *cred, double *wred, double *partial)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int NQ = gs.NQ, NZ = gs.NZ, nt = gs.nt, pitch = gs.pitch;
+    const float *__restrict__ gex = gs.ex;
+    const float *__restrict__ gez = gs.ez;
+    const float *__restrict__ gwav = gs.wavelet;
+    const int sp4 = NQ + 2;
+    const int rows_c = (NZ + C - 1) / C;
+    const int z0 = crank * rows_c;
+    const int my_rows = max(0, min(NZ, z0 + rows_c) - z0);
+    const int brows = C * rows_c + 2 * R;             // rows of each time-level buffer
+
+    // zero this CTA's rows of both levels; rank 0 also the R rows above the
+    // grid, the last rank every row below its slab
+    {
+        const int b0 = crank == 0 ? 0 : R + z0;
+        const int b1 = crank == C - 1 ? brows : R + z0 + rows_c;
+        const long long n4 = (long long)(b1 - b0) * sp4;
+        float4 *p0 = U0 + (long long)b0 * sp4, *p1 = U1 + (long long)b0 * sp4;
+        for (long long e = tid; e < n4; e += nth) {
+            p0[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            p1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    float cx[R + 1], cz[R + 1];
+#pragma unroll
+    for (int m = 0; m <= R; ++m) {
+        cx[m] = gs.cxm[m];
+        cz[m] = gs.czm[m];
+    }
+    int s_i0, s_j0;
+    float sw[4];
+    bilinear_corner(in.sx, in.sz, gs, s_i0, s_j0, sw);
+    const float inv_cell = 1.f / (gs.hx * gs.hz);
+    const int nrec = in.nrec;
+    const float *__restrict__ dobs = in.dobs;
+    for (int r = tid; r < nrec; r += nth) {
+        const float2 pr = in.rec[r];
+        int i0, j0;
+        float w4[4];
+        bilinear_corner(pr.x, pr.y, gs, i0, j0, w4);
+        const bool mine = j0 >= z0 && j0 < z0 + my_rows;
+        rec_k[r] = mine ? (j0 - z0 + R) * (4 * sp4) + 4 + i0 : -1;
+        rec_w[r] = make_float4(w4[0], w4[1], w4[2], w4[3]);
+    }
+    if (tid == 0 && nt > 0) cp4(wring, gwav);
+    cp_commit();
+    cp_wait_all();
+    float accf = 0.f;
+    double acc = 0.0;
+    const int nseg = (my_rows + L2_ROWS - 1) / L2_ROWS;
+    const int items = NQ * nseg;
+    const float4 *__restrict__ arow = reinterpret_cast<const float4 *>(in.a + (size_t)HALO * pitch + HALO);
+    const int ap4 = pitch / 4;
+
+    cluster.sync();                          // zeroed before any CTA reads a neighbour's rows
+
+    float4 *cur = U0 + (long long)z0 * sp4, *nxt = U1 + (long long)z0 * sp4;
+    for (int n = 0; n <= nt; ++n) {
+        {
+            const int iw = n + 1, ir = n;
+            if (tid == 0 && iw < nt) cp4(wring + iw % L2_DEPTH, gwav + iw);
+            if (dobs && ir < nt)
+                for (int r = tid; r < nrec; r += nth)
+                    if (rec_k[r] >= 0) cp4(dring + (ir % L2_DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
+            cp_commit();
+        }
+        if (n < nt) {
+            const float rn = wring[n % L2_DEPTH];
+            for (int it = tid; it < items; it += nth) {
+                const int q = it % NQ, seg = it / NQ;
+                const int r0 = max(0, min(seg * L2_ROWS, my_rows - L2_ROWS));
+                const int kfirst = seg * L2_ROWS - r0, klast = my_rows - r0;
+                const float4 ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
+                const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));
+                const float2 gx23 = make_float2(2.f / (1.f + ex.z), 2.f / (1.f + ex.w));
+                const int ks = s_j0 - (z0 + r0);
+                const bool src_here = s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3 && ks + 1 >= 0 && ks < L2_ROWS;
+                float4 sb0 = make_float4(0.f, 0.f, 0.f, 0.f), sb1 = sb0;
+                if (src_here) {
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const int I = 4 * q + l;
+                        const float bx0 = (I == s_i0 ? 1.f : 0.f), bx1 = (I == s_i0 + 1 ? 1.f : 0.f);
+                        set_lane(sb0, l, (bx0 * sw[0] + bx1 * sw[1]) * inv_cell);
+                        set_lane(sb1, l, (bx0 * sw[2] + bx1 * sw[3]) * inv_cell);
+                    }
+                }
+                float4 w[2 * R + 1];
+#pragma unroll
+                for (int m = 0; m < 2 * R; ++m) w[m] = __ldcg(cur + (r0 + m) * sp4 + 1 + q);
+#pragma unroll
+                for (int k = 0; k < L2_ROWS; ++k) {
+                    const int lr = R + r0 + k;
+                    w[2 * R] = __ldcg(cur + (lr + R) * sp4 + 1 + q);
+                    const float4 lft = __ldcg(cur + lr * sp4 + q);
+                    const float4 rgt = __ldcg(cur + lr * sp4 + 2 + q);
+                    const float4 um = __ldcg(nxt + lr * sp4 + 1 + q);
+                    const int zr = z0 + r0 + k;                   // padded row of the output
+                    const float4 av = __ldg(arow + (size_t)min(zr, NZ - 1) * ap4 + q);
+                    const float2 c01 = make_float2(w[R].x, w[R].y), c23 = make_float2(w[R].z, w[R].w);
+                    const float s[12] = {lft.x, lft.y, lft.z, lft.w, w[R].x, w[R].y, w[R].z,
+                                         w[R].w, rgt.x, rgt.y, rgt.z, rgt.w};
+                    float2 lx01 = __fmul2_rn(make_float2(cx[0], cx[0]), c01);
+                    float2 lx23 = __fmul2_rn(make_float2(cx[0], cx[0]), c23);
+                    float2 lz01 = make_float2(0.f, 0.f), lz23 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int m = 1; m <= R; ++m) {
+                        const float2 czm = make_float2(cz[m], cz[m]);
+                        const float2 cxm = make_float2(cx[m], cx[m]);
+                        lz01 = __ffma2_rn(czm, __fadd2_rn(make_float2(w[R - m].x, w[R - m].y),
+                                                          make_float2(w[R + m].x, w[R + m].y)), lz01);
+                        lz23 = __ffma2_rn(czm, __fadd2_rn(make_float2(w[R - m].z, w[R - m].w),
+                                                          make_float2(w[R + m].z, w[R + m].w)), lz23);
+                        const float2 sx01 = make_float2(s[4 - m] + s[4 + m], s[5 - m] + s[5 + m]);
+                        const float2 sx23 = make_float2(s[6 - m] + s[6 + m], s[7 - m] + s[7 + m]);
+                        lx01 = __ffma2_rn(cxm, sx01, lx01);
+                        lx23 = __ffma2_rn(cxm, sx23, lx23);
+                    }
+                    float2 lap01 = __fadd2_rn(lx01, lz01), lap23 = __fadd2_rn(lx23, lz23);
+                    if (src_here && (k == ks || k == ks + 1)) {
+                        const float4 sb = (k == ks) ? sb0 : sb1;
+                        lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);
+                        lap23 = __ffma2_rn(make_float2(sb.z, sb.w), make_float2(rn, rn), lap23);
+                    }
+                    // u^{n+1} = g (u^n - u^{n-1}) + u^{n-1} + (a f) lap, g = 2 f, f = 1 / (1 + t)
+                    const float ezk = zr < NZ ? __ldg(gez + zr + HALO) : 0.f;
+                    float2 g01 = gx01, g23 = gx23;
+                    if (ezk != 0.f) {
+                        g01 = make_float2(__fdividef(2.f, 1.f + (ex.x + ezk)), __fdividef(2.f, 1.f + (ex.y + ezk)));
+                        g23 = make_float2(__fdividef(2.f, 1.f + (ex.z + ezk)), __fdividef(2.f, 1.f + (ex.w + ezk)));
+                    }
+                    const float2 af01 = __fmul2_rn(make_float2(av.x, av.y), __fmul2_rn(g01, make_float2(0.5f, 0.5f)));
+                    const float2 af23 = __fmul2_rn(make_float2(av.z, av.w), __fmul2_rn(g23, make_float2(0.5f, 0.5f)));
+                    const float2 um01 = make_float2(um.x, um.y), um23 = make_float2(um.z, um.w);
+                    const float2 o01 = __ffma2_rn(g01, __fadd2_rn(c01, make_float2(-um.x, -um.y)),
+                                                  __ffma2_rn(af01, lap01, um01));
+                    const float2 o23 = __ffma2_rn(g23, __fadd2_rn(c23, make_float2(-um.z, -um.w)),
+                                                  __ffma2_rn(af23, lap23, um23));
+                    if (k >= kfirst && k < klast) nxt[lr * sp4 + 1 + q] = make_float4(o01.x, o01.y, o23.x, o23.y);
+#pragma unroll
+                    for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
+                }
+            }
+        }
+        if (n >= 1) {
+            const float *cf = reinterpret_cast<const float *>(cur);
+            const int sp = 4 * sp4;
+            for (int r = tid; r < nrec; r += nth) {
+                const int k0 = rec_k[r];
+                if (k0 < 0) continue;
+                const float4 w4 = rec_w[r];
+                const float d = w4.x * __ldcg(cf + k0) + w4.y * __ldcg(cf + k0 + 1) +
+                                w4.z * __ldcg(cf + k0 + sp) + w4.w * __ldcg(cf + k0 + sp + 1);
+                if (in.traces) in.traces[(size_t)(n - 1) * nrec + r] = d;
+                if (dobs) {
+                    const float e = d - dring[((n - 1) % L2_DEPTH) * nrec + r];
+                    accf = fmaf(e, e, accf);
+                }
+            }
+            if ((n & 31) == 0) {
+                acc += (double)accf;
+                accf = 0.f;
+            }
+        }
+        cp_wait_all();
+        cluster.sync();
+        float4 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (!dobs) accf = 0.f, acc = 0.0;
+    acc += (double)accf;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) wred[tid >> 5] = acc;
+    __syncthreads();
+    if (tid < 32) {
+        double v = (tid < nth / 32) ? wred[tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (tid == 0) *cluster.map_shared_rank(cred + crank, 0) = v;
+    }
+    cluster.sync();
+    if (crank == 0 && tid == 0) {
+        double sum = 0.0;
+        for (int c = 0; c < C; ++c) sum += cred[c];
+        partial[in.out] = 0.5 * sum;
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(L2_NT, 1)
+wave_l2_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts, int n_inst,
+               int *counter, float4 *slots, long long slot_f4, int ring_pitch, double *partial)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ int s_q;
+    __shared__ double cred[16];
+    __shared__ double wred[L2_NT / 32];
+    __shared__ GridDev sg;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    float4 *U0 = slots + (long long)(blockIdx.x / C) * 2 * slot_f4;
+    float4 *U1 = U0 + slot_f4;
+    float *wring = reinterpret_cast<float *>(smem4);
+    float *dring = wring + 4;
+    float4 *rec_w = reinterpret_cast<float4 *>(dring + ((L2_DEPTH * ring_pitch + 3) / 4) * 4);
+    int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
+    for (;;) {
+        if (crank == 0 && threadIdx.x == 0) {
+            const int q = atomicAdd(counter, 1);
+            for (int c = 0; c < C; ++c) *cluster.map_shared_rank(&s_q, c) = q;
+        }
+        cluster.sync();
+        const int q = s_q;
+        if (q >= n_inst) break;
+        const Inst in = insts[q];
+        if (threadIdx.x == 0) sg = grids[in.grid];
+        __syncthreads();
+        l2_instance<R>(sg, in, U0, U1, wring, dring, rec_w, rec_k, C, crank, cluster, cred, wred, partial);
+    }
+}
+
+using L2Fn = void (*)(const GridDev *, const Inst *, int, int *, float4 *, long long, int, double *);
+
+L2Fn l2_fn(int R)
+{
+    if (R == 4) return wave_l2_kernel<4>;
+    if (R == 2) return wave_l2_kernel<2>;
+    return wave_l2_kernel<1>;
+}
+
+}  // namespace
+
+int l2_max_threads() { return L2_NT; }
+
+size_t l2_smem_bytes(int ring_pitch)
+{
+    return sizeof(float) * (4 + ((size_t)L2_DEPTH * ring_pitch + 3) / 4 * 4) +
+           (sizeof(float4) + sizeof(int)) * (size_t)ring_pitch;
+}
+
+// float4 per time-level buffer of grid g on a cluster of C CTAs
+long long l2_slot_f4(const GridDev &g, int C)
+{
+    const int rows_c = (g.NZ + C - 1) / C;
+    return (long long)(C * rows_c + 2 * g.R) * (g.NQ + 2);
+}
+
+// a cluster of C CTAs runs grid g when no CTA is left without rows and every
+// slab holds at least one full run of rows (a work item's reads then stay
+// inside the C rows_c + 2R rows of the buffer)
+bool l2_fits(const GridDev &g, int C)
+{
+    const int rows_c = (g.NZ + C - 1) / C;
+    return C >= 1 && C <= 16 && rows_c >= L2_ROWS && (C - 1) * rows_c < g.NZ;
+}
+
+cudaError_t l2_configure(int R, size_t smem, int C)
+{
+    cudaError_t e = cudaFuncSetAttribute(l2_fn(R), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(l2_fn(R), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+int l2_max_clusters(int R, int C, int threads, size_t smem)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * 64, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, l2_fn(R), &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return -(int)e;        // the query's error, negated
+    }
+    return n;
+}
+
+cudaError_t launch_wave_l2(int R, const GridDev *grids_dev, const Inst *insts, int n_inst, int *counter,
+                           int C, int n_clusters, int threads, float4 *slots, long long slot_f4,
+                           int ring_pitch, size_t smem, double *partial, cudaStream_t st)
+{
+    if (n_inst <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * n_clusters, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, l2_fn(R), grids_dev, insts, n_inst, counter, slots, slot_f4,
+                              ring_pitch, partial);
+}
+
+}  // namespace empso

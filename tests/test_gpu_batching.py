@@ -47,7 +47,7 @@ def _state(ctx, P, D):
     return [t.cpu().numpy() for t in (x, v, p, pf, gk)]
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 def test_graph_generation_equals_eager(B, kind):
     grid, rec, sh, dobs, pso = _problem(B)
     P = pso.P

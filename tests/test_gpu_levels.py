@@ -68,7 +68,7 @@ def test_level_bounds_match_oracle(B):
         B.level_bounds(lz[::-1].copy(), lc, 1500.0, 3000.0, 0.1, 0.1, 0.1, 0.1)
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 def test_level_fitness_and_generation_match_oracle(B, kind):
     nx, nz, h, pad = 77, 35, 20.0, 12
     vmin, vmax, water = 1500.0, 4700.0, 40.0

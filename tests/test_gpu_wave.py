@@ -52,7 +52,7 @@ def _geometry(nx, nz, h, S, src_z, rec_z, off_grid=False):
     return shots, rec
 
 
-KINDS = [1, 2]   # streaming, resident (on-chip cluster) variants of the persistent launch
+KINDS = [1, 2, 3]   # streaming, on-chip cluster and L2 cluster variants of the persistent launch
 
 
 def _use(ctx, kind):
@@ -281,7 +281,7 @@ def _full_size_reference():
     return _FULL
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
 def test_full_size_sampled(B, kind):
     """The 461 x 151 / 20 m / order 8 / 3 s / 6 Hz grid of the plain EMPSO
     workload with 32 particles x 16 shots in one launch (the benchmarked launch
@@ -345,4 +345,38 @@ def test_nonfinite_model_gives_inf_misfit(B, kind):
     gk = torch.zeros(2, dtype=torch.int32, device="cuda")
     ctx.pso_get_state(pf=pf, gk=gk)
     assert np.isinf(pf.cpu().numpy()[1]) and gk.cpu().numpy()[0] == 0
+    ctx.close()
+
+
+def test_grid_too_large_for_chip_runs_on_l2_cluster_kernel(B):
+    """The 921 x 301 / 10 m grid with a 60-cell damping layer (the
+    high-resolution workload's grid, record shortened to 0.3 s for the
+    oracle) does not fit the on-chip kernel: the default picks the L2 cluster
+    kernel, which matches the oracle and the streaming kernel."""
+    nx, nz, h, pad = 921, 301, 10.0, 60
+    vmin, vmax = 1500.0, 4700.0
+    og = oracle.Grid(nx, nz, h, h, pad, 8, 0.3, 12.0, vmax)
+    true = synth.layered_faulted_model(nx, nz, h, h, seed=1905, vmin=vmin, vmax=vmax)
+    shots = synth.shot_line(2, (nx - 1) * h, 20.0)
+    rec = synth.receiver_line(nx, h, 20.0)[::2]
+    nrec = len(rec)
+    _, obs = oracle.shot_batch(og, true, shots, rec, [0, 0], [nrec, nrec], want_traces=True)
+    parts = synth.random_particles(2, 8 * 24, vmin, vmax, seed=4)
+    ref = _oracle_fitness(og, parts, 8, 24, 0, vmin, vmax, shots, rec, [0, 0], [nrec, nrec], obs)
+    grid = B.make_grid(nx, nz, h, h, pad, 8, 0.3, 12.0, vmin, vmax, kx=24, kz=8)
+    ctx = B.Context([grid], rec)
+    sh = B.make_shots(shots, [0, 0], [nrec, nrec])
+    dobs = _dev(np.concatenate([o.ravel() for o in obs]))
+    e = 0.5 * sum(np.sum(o ** 2) for o in obs)
+    got = {}
+    for kind in (0, 1):
+        ctx.set_kernel(kind)
+        mis = torch.zeros(2, dtype=torch.float64, device="cuda")
+        ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+        if kind == 0:
+            assert ctx.last_launch()[0] == 3 and ctx.last_kernel_name() == "wave_l2_kernel"
+        got[kind] = mis.cpu().numpy()
+        _check_misfit(got[kind], ref, [e] * 2)
+    assert np.allclose(got[0], got[1], rtol=1e-5)
+    assert ctx.device_error() == 0
     ctx.close()
