@@ -62,7 +62,7 @@ def _args():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-vs-plain wall-clock comparison")
-    ap.add_argument("--surrogate-seeds", type=int, default=5)
+    ap.add_argument("--surrogate-seeds", type=int, default=9)
     ap.add_argument("--trials", type=int, default=5, help="PSO vs EMPSO comparison trials")
     ap.add_argument("--surrogate-case", type=int, default=0,
                     help="time the surrogate kernels alone for this many particles")
@@ -383,7 +383,7 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=20, batch=256):
+def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch=512, overlap=True):
     """Wall-clock to a target misfit, surrogate-assisted vs plain EMPSO.
 
     Problem: the 101 x 101 / 10 m / order-4 / 0.5 s / 10 Hz grid with a
@@ -392,9 +392,11 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=20, batch
     with +5 % velocity; particles of 4 x 8 nodes in [1200, 3200] m/s, swarm
     1024.  The plain run does `gens` generations (graph replays); its final
     best misfit is the target.  The surrogate run models the predicted-best
-    quarter each generation (after a one-generation warm-up) and stops when
-    it reaches the target.  Both times include a host read of the best
-    misfit every generation."""
+    quarter each generation (after a one-generation warm-up), training the
+    network beside the modelling (`overlap`), and stops when it reaches the
+    target.  Both times include a host read of the best misfit every
+    generation.  One untimed run of each comes first (module loading, first
+    launches)."""
     import torch
     from paper_1905_12795_gb300 import binding as B
     wl = synth.workloads()["surrogate-101x101-P1024"]
@@ -406,10 +408,9 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=20, batch
     sh = B.make_shots(shots, [0], [len(rec)])
     true = synth.two_layer_model(gs.nx, gs.nz, gs.hz) * 1.05
     K = gs.kx * gs.kz
-    runs = []
-    for seed in range(seeds):
+
+    def one(seed, n_gens):
         pso = B.EmpsoPso(P, K, 1.2, 2.9, 0.5, 0.3, 0.25, max(1, gens // 10), 1, 12795 + seed)
-        # plain
         ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
         _, nt = ctx.grid_info(0)
         dobs = torch.zeros(nt * len(rec), device="cuda")
@@ -421,21 +422,21 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=20, batch
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         best, hist = float("inf"), []
-        for g in range(gens):
+        for _ in range(n_gens):
             ctx.generation(sh, dobs, mis)
             best = min(best, mis.min().item())
             hist.append((time.perf_counter() - t0, best))
         ctx.close()
         target = best
         t_plain = next(t for t, b in hist if b <= target)
-        # surrogate-assisted
         ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
         ctx.surrogate_init(hidden=256, capacity=50000, lr=1e-3, seed=seed + 1)
+        ctx.surrogate_set_overlap(overlap)
         ctx.pso_init()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         best_s, modelled, g, t_sur = float("inf"), 0, 0, None
-        while g < 4 * gens:
+        while g < 4 * n_gens:
             modelled += ctx.surrogate_generation(sh, dobs, keep, warm=P, train_steps=train_steps,
                                                  batch=batch, misfit_out=mis)
             g += 1
@@ -443,17 +444,42 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=20, batch
             if best_s <= target:
                 t_sur = time.perf_counter() - t0
                 break
+        # surrogate error against the true misfit on the final swarm
+        x = torch.zeros(P, K, dtype=torch.float64, device="cuda")
+        ctx.pso_get_state(x=x)
+        xf = x.float().contiguous()
+        pred = torch.zeros(P, device="cuda")
+        ctx.surrogate_predict(xf, pred)
+        true_m = torch.zeros(P, dtype=torch.float64, device="cuda")
+        ctx.eval_fitness(xf, sh, dobs, true_m)
+        lt = torch.log(true_m).cpu().numpy()
+        lp = pred.double().cpu().numpy()
+        rank = lambda v: np.argsort(np.argsort(v))  # noqa: E731
+        err = {"median_abs_log_error": float(np.median(np.abs(lp - lt))),
+               "spearman": float(np.corrcoef(rank(lp), rank(lt))[0, 1])}
         ctx.close()
-        runs.append({"seed": seed, "target_misfit": target, "plain_s": t_plain,
-                     "plain_models": P * gens, "surrogate_s": t_sur, "surrogate_generations": g,
-                     "surrogate_models": modelled, "surrogate_best": best_s})
+        return {"seed": seed, "target_misfit": target, "plain_s": t_plain, "plain_models": P * n_gens,
+                "surrogate_s": t_sur, "surrogate_generations": g, "surrogate_models": modelled,
+                "surrogate_best": best_s, "surrogate_error": err}
+
+    one(-1, 5)                                   # untimed
+    runs = [one(seed, gens) for seed in range(seeds)]
     reached = [r for r in runs if r["surrogate_s"] is not None]
     med = lambda v: float(np.median(v)) if v else None  # noqa: E731
+    mean = lambda v: float(np.mean(v)) if v else None  # noqa: E731
     return {"problem": "101x101 order 4, 1 shot, swarm 1024, 100 plain generations, keep 25 %",
+            "training": {"steps_per_generation": train_steps, "batch": batch,
+                         "beside_modelling": overlap},
             "seeds": seeds, "reached": len(reached),
             "median_plain_s": med([r["plain_s"] for r in runs]),
             "median_surrogate_s": med([r["surrogate_s"] for r in reached]),
             "median_speedup": med([r["plain_s"] / r["surrogate_s"] for r in reached]),
+            "mean_plain_s": mean([r["plain_s"] for r in runs]),
+            "mean_surrogate_s": mean([r["surrogate_s"] for r in reached]),
+            "speedup_of_means": (mean([r["plain_s"] for r in runs]) / mean([r["surrogate_s"] for r in reached])
+                                 if reached else None),
+            "median_surrogate_abs_log_error": med([r["surrogate_error"]["median_abs_log_error"] for r in runs]),
+            "median_surrogate_spearman": med([r["surrogate_error"]["spearman"] for r in runs]),
             "runs": runs}
 
 

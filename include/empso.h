@@ -232,6 +232,13 @@ empso_status pso_step_ranked(empso_ctx *ctx, const double *misfit, const double 
 empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, float lr,
                             uint64_t seed);
 
+/* Training in pre-screening generations of surrogate_generation: with
+ * enable = 0 (default) the network trains after the generation's modelling
+ * on the pairs of all generations so far; with enable = 1 it trains on the
+ * pairs of the earlier generations on a second stream while the selected
+ * particles are modelled (one generation of lag, shorter generations). */
+empso_status surrogate_set_overlap(empso_ctx *ctx, int32_t enable);
+
 /* Tensor-core path of this context's dense layers: 1 = tcgen05.mma with
  * the accumulator in tensor memory (default), 0 = mma.sync.  Both compute
  * BF16 products with FP32 accumulation. */

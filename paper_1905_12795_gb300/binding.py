@@ -29,7 +29,7 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
            "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_device_error", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
            "empso_generation", "empso_autotune", "empso_set_tuning_cache",
-           "pso_step_ranked", "surrogate_init", "surrogate_set_backend", "surrogate_predict", "surrogate_add",
+           "pso_step_ranked", "surrogate_init", "surrogate_set_backend", "surrogate_set_overlap", "surrogate_predict", "surrogate_add",
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
            "empso_nonfinite_count", "empso_set_strict", "empso_save", "empso_load",
            "empso_set_levels", "empso_set_water", "empso_level_bounds", "empso_last_kernel_name",
@@ -116,6 +116,7 @@ def load():
     L.pso_step_ranked.argtypes = [_vp, _vp, _vp, _vp, P(_i32), _vp]
     L.surrogate_init.argtypes = [_vp, _i32, _i32, _f32, ctypes.c_uint64]
     L.surrogate_set_backend.argtypes = [_vp, _i32]
+    L.surrogate_set_overlap.argtypes = [_vp, _i32]
     L.empso_nonfinite_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _i32, _vp]
     L.empso_set_strict.argtypes = [_vp, _i32]
     L.empso_set_levels.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
@@ -365,6 +366,10 @@ class Context:
     # surrogate pre-screening
     def surrogate_init(self, hidden=256, capacity=50000, lr=1e-3, seed=1):
         self._check(self._L.surrogate_init(self._h, hidden, capacity, lr, seed))
+
+    def surrogate_set_overlap(self, enable=True):
+        """Train pre-screening generations beside their modelling (one generation of lag)."""
+        self._check(self._L.surrogate_set_overlap(self._h, 1 if enable else 0))
 
     def surrogate_set_backend(self, kind):
         """1: tcgen05 tensor cores (default), 0: mma.sync."""

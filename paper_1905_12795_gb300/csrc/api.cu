@@ -88,6 +88,10 @@ struct empso_ctx {
     bool has_sur = false;
     SurDev sur;
     std::vector<void *> sur_mem;
+    cudaStream_t sur_stream = nullptr;   // training of prescreen generations, beside the modelling
+    cudaEvent_t sur_fork = nullptr, sur_done = nullptr;
+    bool sur_done_rec = false;
+    bool sur_overlap = false;            // train prescreen generations beside their modelling
     int *sel_rows = nullptr;        // [P] indices of the modelled particles
     float *xk = nullptr;            // [P][D] their positions
     double *fk = nullptr;           // [P] their misfits
@@ -727,6 +731,9 @@ void free_ctx(empso_ctx *c)
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void *p : c->sur_mem) cudaFree(p);
+    if (c->sur_stream) cudaStreamDestroy(c->sur_stream);
+    if (c->sur_fork) cudaEventDestroy(c->sur_fork);
+    if (c->sur_done) cudaEventDestroy(c->sur_done);
     if (c->stage_host) cudaFreeHost(c->stage_host);
     if (c->stage_free) cudaEventDestroy(c->stage_free);
     for (auto &e : c->tev)
@@ -1702,6 +1709,9 @@ empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, fl
     CK(ctx, sur_prepare_tc());
     s.tc = 1;
     s.err = ctx->dev_err;
+    CK(ctx, cudaStreamCreateWithFlags(&ctx->sur_stream, cudaStreamNonBlocking));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->sur_fork, cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->sur_done, cudaEventDisableTiming));
     CK(ctx, cudaDeviceSynchronize());
     ctx->has_sur = true;
     return EMPSO_OK;
@@ -1713,6 +1723,20 @@ empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, fl
         ctx->err.clear();                                                               \
         if (!ctx->has_sur) return fail(ctx, EMPSO_NOT_INITIALIZED, "no surrogate");      \
     } while (0)
+
+// Every use of the network waits for training still running beside the
+// modelling of the last prescreen generation.
+#define JOIN_SUR(ctx, st)                                                               \
+    do {                                                                                \
+        if ((ctx)->sur_done_rec) CK(ctx, cudaStreamWaitEvent((st), (ctx)->sur_done, 0));  \
+    } while (0)
+
+empso_status surrogate_set_overlap(empso_ctx *ctx, int32_t enable)
+{
+    NEED_SUR(ctx);
+    ctx->sur_overlap = enable != 0;
+    return EMPSO_OK;
+}
 
 empso_status surrogate_set_backend(empso_ctx *ctx, int32_t kind)
 {
@@ -1726,6 +1750,7 @@ empso_status surrogate_predict(empso_ctx *ctx, const float *particles, int32_t P
                                void *stream)
 {
     NEED_SUR(ctx);
+    JOIN_SUR(ctx, (cudaStream_t)stream);
     if (P < 0 || P > ctx->sur.rows_max || (P > 0 && (!particles || !logphi)))
         return fail(ctx, EMPSO_INVALID_ARG, "bad particles/logphi or too many rows");
     if (P == 0) return EMPSO_OK;
@@ -1737,6 +1762,7 @@ empso_status surrogate_add(empso_ctx *ctx, const float *particles, const double 
                            void *stream)
 {
     NEED_SUR(ctx);
+    JOIN_SUR(ctx, (cudaStream_t)stream);
     if (n < 0 || (n > 0 && (!particles || !misfit))) return fail(ctx, EMPSO_INVALID_ARG, "bad particles/misfit");
     if (n == 0) return EMPSO_OK;
     CK(ctx, sur_append(ctx->sur, particles, misfit, nullptr, n, (cudaStream_t)stream));
@@ -1746,6 +1772,7 @@ empso_status surrogate_add(empso_ctx *ctx, const float *particles, const double 
 empso_status surrogate_train(empso_ctx *ctx, int32_t steps, int32_t batch, void *stream)
 {
     NEED_SUR(ctx);
+    JOIN_SUR(ctx, (cudaStream_t)stream);
     if (steps < 0 || batch < 1 || batch > ctx->sur.rows_max)
         return fail(ctx, EMPSO_INVALID_ARG, "need steps >= 0 and 1 <= batch <= max rows");
     CK(ctx, sur_train(ctx->sur, steps, batch, (cudaStream_t)stream));
@@ -1756,6 +1783,7 @@ empso_status surrogate_params(empso_ctx *ctx, float *get, const float *set, int3
                               void *stream)
 {
     NEED_SUR(ctx);
+    JOIN_SUR(ctx, (cudaStream_t)stream);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = 4 * (size_t)ctx->sur.n_params;
     if (n_params) *n_params = (int32_t)ctx->sur.n_params;
@@ -1771,6 +1799,7 @@ empso_status surrogate_grad(empso_ctx *ctx, const float *particles, const float 
                             float *grad, float *loss, void *stream)
 {
     NEED_SUR(ctx);
+    JOIN_SUR(ctx, (cudaStream_t)stream);
     if (n < 1 || n > ctx->sur.rows_max || !particles || !target || !grad)
         return fail(ctx, EMPSO_INVALID_ARG, "bad particles/target/grad");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1799,6 +1828,7 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
         if (ctx->grids[shots[i].grid_id].dev.K != K)
             return fail(ctx, EMPSO_INVALID_ARG, "swarm dimension differs from the grids' control nodes");
     }
+    JOIN_SUR(ctx, st);
     // how many pairs the replay buffer holds (host read: decides the branch)
     int have = 0;
     CK(ctx, cudaMemcpyAsync(&have, s.count, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1807,7 +1837,7 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
     Models mod;
     int k;
     if (have < warm) {
-        // warm-up: model every particle
+        // warm-up: model every particle, then train on everything so far
         k = P;
         mod.particles = ctx->xf;
         mod.M = P;
@@ -1821,12 +1851,28 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
         CK(ctx, sur_predict(s, ctx->xf, P, ctx->logphi, st));
         CK(ctx, sur_select(ctx->logphi, P, k, ctx->sel_rows, st));
         CK(ctx, sur_gather(ctx->xf, ctx->sel_rows, k, K, ctx->xk, st));
+        // overlap mode: training on the pairs of the earlier generations (the
+        // first `have` rows) runs on a second stream beside this generation's
+        // modelling, which appends only behind those rows; when the append
+        // would wrap the ring onto them it runs first instead (same data,
+        // same result).  Default: train after the append, on every pair.
+        if (train_steps > 0 && ctx->sur_overlap) {
+            if ((long long)have + k <= s.cap) {
+                CK(ctx, cudaEventRecord(ctx->sur_fork, st));
+                CK(ctx, cudaStreamWaitEvent(ctx->sur_stream, ctx->sur_fork, 0));
+                CK(ctx, sur_train(s, train_steps, batch, ctx->sur_stream, have));
+                CK(ctx, cudaEventRecord(ctx->sur_done, ctx->sur_stream));
+                ctx->sur_done_rec = true;
+            } else {
+                CK(ctx, sur_train(s, train_steps, batch, st, have));
+            }
+        }
         mod.particles = ctx->xk;
         mod.M = k;
         if ((rc = run_batch(ctx, mod, shots, S, d_obs, nullptr, ctx->fk, st))) return rc;
         CK(ctx, sur_append(s, ctx->xf, ctx->fk, ctx->sel_rows, k, st));
         CK(ctx, sur_scatter(ctx->sel_rows, ctx->fk, k, ctx->logphi, P, ctx->fit_full, ctx->rank_full, st));
-        CK(ctx, sur_train(s, train_steps, batch, st));
+        if (train_steps > 0 && !ctx->sur_overlap) CK(ctx, sur_train(s, train_steps, batch, st));
         CK(ctx, launch_pso_step(ctx->pso, ctx->fit_full, nullptr, st, ctx->rank_full));
     }
     if (misfit_out)

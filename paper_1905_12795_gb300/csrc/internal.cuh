@@ -205,7 +205,9 @@ cudaError_t sur_normalize(const SurDev &s, const float *x, const int *rows, int 
 cudaError_t sur_predict(const SurDev &s, const float *x, int n, float *logphi, cudaStream_t st);
 cudaError_t sur_append(const SurDev &s, const float *x, const double *misfit, const int *rows, int n,
                        cudaStream_t st);
-cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st);
+// have >= 0: train on the first min(have, cap) replay rows (a host snapshot);
+// have < 0: on the rows the device count says are filled
+cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st, int have = -1);
 cudaError_t sur_select(const float *key, int P, int k, int *rows, cudaStream_t st);
 cudaError_t sur_prepare_tc();
 cudaError_t sur_gather(const float *x, const int *rows, int k, int K, float *out, cudaStream_t st);

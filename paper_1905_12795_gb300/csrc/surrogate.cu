@@ -546,12 +546,14 @@ __device__ __forceinline__ uint4 philox_s(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
-// batch rows drawn uniformly from the filled part of the replay buffer
-__global__ void sample_kernel(int *rows, int B, const int *count, int cap, uint64_t seed, int step)
+// batch rows drawn uniformly from the filled part of the replay buffer (its
+// first min(have_host, cap) rows when have_host >= 0, else the device count's)
+__global__ void sample_kernel(int *rows, int B, const int *count, int have_host, int cap, uint64_t seed,
+                              int step)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const int have = min(*count, cap);
+    const int have = min(have_host >= 0 ? have_host : *count, cap);
     const uint4 w = philox_s(make_uint4((uint32_t)step, (uint32_t)b, 0x5u, 0x7u), (uint32_t)seed,
                              (uint32_t)(seed >> 32));
     rows[b] = have > 0 ? (int)(((unsigned long long)w.x * (unsigned long long)have) >> 32) : 0;
@@ -566,10 +568,11 @@ __global__ void targets_kernel(const float *__restrict__ ybuf, const int *__rest
 }
 
 // mean and standard deviation of the filled replay targets (one block)
-__global__ void stats_kernel(const float *__restrict__ ybuf, const int *count, int cap, float *stats)
+__global__ void stats_kernel(const float *__restrict__ ybuf, const int *count, int have_host, int cap,
+                             float *stats)
 {
     __shared__ double s1[32], s2[32];
-    const int n = min(*count, cap);
+    const int n = min(have_host >= 0 ? have_host : *count, cap);
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         a += ybuf[i];
@@ -818,12 +821,13 @@ cudaError_t sur_append(const SurDev &s, const float *x, const double *misfit, co
     return cudaGetLastError();
 }
 
-cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st)
+cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st, int have)
 {
     cudaError_t e;
-    stats_kernel<<<1, 256, 0, st>>>(s.ybuf, s.count, s.cap, s.stats);
+    stats_kernel<<<1, 256, 0, st>>>(s.ybuf, s.count, have, s.cap, s.stats);
     for (int i = 0; i < steps; ++i) {
-        sample_kernel<<<(B + 255) / 256, 256, 0, st>>>(s.rows, B, s.count, s.cap, s.seed, s.sample_step++);
+        sample_kernel<<<(B + 255) / 256, 256, 0, st>>>(s.rows, B, s.count, have, s.cap, s.seed,
+                                                       s.sample_step++);
         targets_kernel<<<(B + 255) / 256, 256, 0, st>>>(s.ybuf, s.rows, B, s.stats, s.tb);
         // the buffer holds raw positions: scale the batch rows to [-1, 1] in BF16
         if ((e = sur_normalize(s, s.xbuf, s.rows, B, s.Xb, st))) return e;

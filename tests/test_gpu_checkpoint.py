@@ -89,11 +89,15 @@ def test_resume_plain_generations_bit_exact(B, tmp_path):
     b.close()
 
 
-def test_resume_surrogate_generations_bit_exact(B, tmp_path):
+@pytest.mark.parametrize("overlap", [False, True])
+def test_resume_surrogate_generations_bit_exact(B, tmp_path, overlap):
+    """Also with training beside the modelling (second stream): the result
+    does not depend on how the two streams interleave."""
     P = 48
     path = str(tmp_path / "sur.ck")
     kw = dict(keep_frac=0.25, warm=P, train_steps=8, batch=32)
     a, sh, dobs = _problem(B, P, seed=4, surrogate=True)
+    a.surrogate_set_overlap(overlap)
     a.pso_init()
     mis = torch.zeros(P, dtype=torch.float64, device="cuda")
     for _ in range(2):
@@ -108,6 +112,7 @@ def test_resume_surrogate_generations_bit_exact(B, tmp_path):
     a.close()
 
     b, sh, dobs = _problem(B, P, seed=4, surrogate=True)
+    b.surrogate_set_overlap(overlap)
     b.load(path)
     for _ in range(3):
         b.surrogate_generation(sh, dobs, misfit_out=mis, **kw)
