@@ -100,7 +100,7 @@ def _peaks():
 
 
 _KERNEL_SOURCES = {"wave_kernel": "wave.cu", "wave_resident_kernel": "wave_resident.cu",
-                   "wave_stream_kernel": "wave_stream.cu"}
+                   "wave_stream_kernel": "wave_stream.cu", "wave_l2_kernel": "wave_l2.cu"}
 
 
 def _wave_source_hash(kernel):
