@@ -112,6 +112,9 @@ struct empso_ctx {
         float *fv = nullptr;      // FWI vectors: trial model, gradients [3][np]
         size_t fv_cap = 0;
         double *fd = nullptr;     // FWI reductions [8] and misfit [1]
+        // forward + adjoint time loops captured once per grid, instance count
+        // and instance table (their kernels read everything else from it)
+        std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
     } adj;
 
     // kernel timing
@@ -685,6 +688,9 @@ empso_status grid_changed(empso_ctx *ctx, int gid)
         cudaFree(e.table);
     }
     ctx->graphs.clear();
+    for (auto &e : ctx->adj.graphs)
+        if (e.second) cudaGraphExecDestroy(e.second);
+    ctx->adj.graphs.clear();
     return EMPSO_OK;
 }
 
@@ -720,6 +726,8 @@ void free_ctx(empso_ctx *c)
     cudaFree(c->adj.insts);
     cudaFree(c->adj.phi);
     cudaFree(c->adj.fv);
+    for (auto &e : c->adj.graphs)
+        if (e.second) cudaGraphExecDestroy(e.second);
     cudaFree(c->adj.fd);
     cudaFree(c->pso_mem);
     cudaFree(c->pso_int);
@@ -1066,8 +1074,26 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     const int rec_threads = std::min(1024, std::max(32, (rec_max + 31) / 32 * 32));
     CK(ctx, launch_vel_to_field(g, vel, M, W.a, g.field, st));
     CK(ctx, launch_adj_prep(g, W.a, W.B, M, st));
-    CK(ctx, launch_adj_forward(g, W.insts, (int)I, rec_threads, st));
-    CK(ctx, launch_adj_backward(g, W.insts, (int)I, rec_threads, st));
+    // the 5 nt launches of the two time loops replay as one graph
+    std::ostringstream key;
+    key << gid << "|" << I << "|" << rec_threads << "|" << (const void *)W.insts;
+    cudaGraphExec_t exec = nullptr;
+    for (auto &e : W.graphs)
+        if (e.first == key.str()) exec = e.second;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        CK(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = launch_adj_forward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
+        if (ce == cudaSuccess) ce = launch_adj_backward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
+        const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (ce == cudaSuccess) ce = ee;
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (ce != cudaSuccess)
+            return fail(ctx, EMPSO_CUDA_ERROR, std::string("gradient graph: ") + cudaGetErrorString(ce));
+        W.graphs.push_back({key.str(), exec});
+    }
+    CK(ctx, cudaGraphLaunch(exec, st));
     CK(ctx, launch_adj_finish(g, W.insts, M, S, vel, W.phi, misfit, grad, st));
     return EMPSO_OK;
 }
