@@ -18,25 +18,15 @@
 // velocity: dphi/dv = 2 v dt^2 dphi/da.
 //
 // Every kernel runs over all instances at once (blockIdx.y = instance), one
-// launch per time step and stage; the receiver transpose adds the four corner
-// contributions in four ordered passes.
+// launch per time step and stage (the two time loops replay as one CUDA
+// graph); the per-point kernels take one float4 group of a row per thread;
+// the receiver transpose adds the four corner contributions in four ordered
+// passes.
 #include "internal.cuh"
 
 namespace empso {
 
 namespace {
-
-__device__ __forceinline__ float lap_at(const float *u, const GridDev &g, long long k)
-{
-    float s = g.cxm[0] * u[k];
-#pragma unroll
-    for (int m = 1; m <= MAX_R; ++m) {
-        if (m > g.R) break;
-        s = fmaf(g.cxm[m], u[k - m] + u[k + m], s);
-        s = fmaf(g.czm[m], u[k - (long long)m * g.pitch] + u[k + (long long)m * g.pitch], s);
-    }
-    return s;
-}
 
 struct SrcCorner {
     int I0, J0;
@@ -79,23 +69,135 @@ __global__ void adj_prep_kernel(GridDev g, const float *a, float *B)
     }
 }
 
+// Laplacian of the four points of float4 group k4 (row pitch p4 float4s):
+// z-neighbours as whole float4s, x-neighbours from the groups left and right
+template <int R>
+__device__ __forceinline__ float4 lap4(const float4 *__restrict__ U, long long k4, int p4, const GridDev &g)
+{
+    const float4 c = U[k4], l = U[k4 - 1], r = U[k4 + 1];
+    const float s[12] = {l.x, l.y, l.z, l.w, c.x, c.y, c.z, c.w, r.x, r.y, r.z, r.w};
+    float o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = g.cxm[0] * s[4 + i];
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+        const float4 zm = U[k4 - (long long)m * p4], zp = U[k4 + (long long)m * p4];
+        const float zs[4] = {zm.x + zp.x, zm.y + zp.y, zm.z + zp.z, zm.w + zp.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            o[i] = fmaf(g.czm[m], zs[i], fmaf(g.cxm[m], s[4 + i - m] + s[4 + i + m], o[i]));
+    }
+    return make_float4(o[0], o[1], o[2], o[3]);
+}
+
+__device__ __forceinline__ float lane_of(const float4 &v, int i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// The per-point kernels take one float4 group (4 points of a row) per
+// thread; lanes past the last column (I >= NX) stay zero.
+
 // u^{n+1} of every instance into H[n+1]
+template <int R>
 __global__ void adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
 {
     const AdjInst in = insts[blockIdx.y];
-    const long long pts = (long long)g.NX * g.NZ;
-    const float *u = in.H + (long long)n * g.field;
-    const float *um = in.H + (long long)(n > 0 ? n - 1 : 0) * g.field;   // u^{-1} = u^0 = 0
-    float *u1 = in.H + (long long)(n + 1) * g.field;
+    const long long items = (long long)g.NQ * g.NZ;
+    const int p4 = g.pitch / 4;
+    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)n * g.field);
+    const float4 *um = reinterpret_cast<const float4 *>(in.H + (long long)(n > 0 ? n - 1 : 0) * g.field);
+    float4 *u1 = reinterpret_cast<float4 *>(in.H + (long long)(n + 1) * g.field);
+    const float4 *a4 = reinterpret_cast<const float4 *>(in.a);
+    const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
     const SrcCorner sc = src_corner(in.sx, in.sz, g);
     const float rn = g.wavelet[n] / (g.hx * g.hz);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pts;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
          e += (long long)gridDim.x * blockDim.x) {
-        const int J = (int)(e / g.NX), I = (int)(e % g.NX);
-        const long long k = (long long)(J + HALO) * g.pitch + I + HALO;
-        const float t = g.ex[I + HALO] + g.ez[J + HALO];
-        const float lap = fmaf(src_weight(sc, I, J), rn, lap_at(u, g, k));
-        u1[k] = (2.f * u[k] - (1.f - t) * um[k] + in.a[k] * lap) / (1.f + t);
+        const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
+        const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
+        const float4 lap = lap4<R>(u, k4, p4, g);
+        const float4 c = u[k4], m = um[k4], av = a4[k4], ex = ex4[q];
+        const float ez = g.ez[J + HALO];
+        float o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int I = 4 * q + i;
+            const float t = lane_of(ex, i) + ez;
+            const float li = fmaf(src_weight(sc, I, J), rn, lane_of(lap, i));
+            o[i] = I < g.NX ? (2.f * lane_of(c, i) - (1.f - t) * lane_of(m, i) + lane_of(av, i) * li) / (1.f + t)
+                            : 0.f;
+        }
+        u1[k4] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} (before the receiver term)
+template <int R>
+__global__ void adj_back_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
+{
+    const AdjInst in = insts[blockIdx.y];
+    const long long items = (long long)g.NQ * g.NZ;
+    const int p4 = g.pitch / 4;
+    float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 3) * g.field);
+    const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 3) * g.field);
+    const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 3) * g.field);
+    const float4 *q1 = reinterpret_cast<const float4 *>(in.Q + (long long)((k + 1) % 2) * g.field);
+    const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
+        const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
+        const float4 lq = lap4<R>(q1, k4, p4, g);
+        const float4 a1 = m1[k4], a2 = m2[k4], ex = ex4[q];
+        const float ez = g.ez[J + HALO];
+        float o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float t = lane_of(ex, i) + ez;
+            const float f = 1.f / (1.f + t);
+            o[i] = 4 * q + i < g.NX ? 2.f * f * lane_of(a1, i) + lane_of(lq, i) - (1.f - t) * f * lane_of(a2, i)
+                                    : 0.f;
+        }
+        mk[k4] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// G += mu^k f (L u^{k-1} + s^{k-1}); Q^k = f a mu^k
+template <int R>
+__global__ void adj_grad_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
+{
+    const AdjInst in = insts[blockIdx.y];
+    const long long items = (long long)g.NQ * g.NZ;
+    const int p4 = g.pitch / 4;
+    const float4 *mk = reinterpret_cast<const float4 *>(in.mu + (long long)(k % 3) * g.field);
+    float4 *qk = reinterpret_cast<float4 *>(in.Q + (long long)(k % 2) * g.field);
+    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(k - 1) * g.field);
+    const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
+    float4 *G4 = reinterpret_cast<float4 *>(in.G);
+    const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
+    const SrcCorner sc = src_corner(in.sx, in.sz, g);
+    const float rn = g.wavelet[k - 1] / (g.hx * g.hz);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
+        const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
+        const float4 lap = lap4<R>(u, k4, p4, g);
+        const float4 m = mk[k4], b = B4[k4], ex = ex4[q];
+        float4 gg = G4[k4];
+        const float ez = g.ez[J + HALO];
+        float qo[4], go[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int I = 4 * q + i;
+            const float t = lane_of(ex, i) + ez;
+            const float mi = I < g.NX ? lane_of(m, i) : 0.f;
+            qo[i] = lane_of(b, i) * mi;
+            const float li = fmaf(src_weight(sc, I, J), rn, lane_of(lap, i));
+            go[i] = fmaf(mi / (1.f + t), li, lane_of(gg, i));
+        }
+        qk[k4] = make_float4(qo[0], qo[1], qo[2], qo[3]);
+        G4[k4] = make_float4(go[0], go[1], go[2], go[3]);
     }
 }
 
@@ -114,25 +216,6 @@ __global__ void adj_record_kernel(GridDev g, const AdjInst *__restrict__ insts, 
     }
 }
 
-// mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} (before the receiver term)
-__global__ void adj_back_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
-{
-    const AdjInst in = insts[blockIdx.y];
-    const long long pts = (long long)g.NX * g.NZ;
-    float *mk = in.mu + (long long)(k % 3) * g.field;
-    const float *m1 = in.mu + (long long)((k + 1) % 3) * g.field;
-    const float *m2 = in.mu + (long long)((k + 2) % 3) * g.field;
-    const float *q1 = in.Q + (long long)((k + 1) % 2) * g.field;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pts;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int J = (int)(e / g.NX), I = (int)(e % g.NX);
-        const long long kk = (long long)(J + HALO) * g.pitch + I + HALO;
-        const float t = g.ex[I + HALO] + g.ez[J + HALO];
-        const float f = 1.f / (1.f + t);
-        mk[kk] = 2.f * f * m1[kk] + lap_at(q1, g, kk) - (1.f - t) * f * m2[kk];
-    }
-}
-
 // mu^k += w R^T e_{k-1}: corner c of every receiver in pass c (one block per
 // instance); receivers sharing a cell meet in an atomic add
 __global__ void adj_inject_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
@@ -147,28 +230,6 @@ __global__ void adj_inject_kernel(GridDev g, const AdjInst *__restrict__ insts, 
             atomicAdd(mk + kk, in.w * sc.w[c] * in.E[(long long)(k - 1) * in.nrec + r]);
         }
         __syncthreads();
-    }
-}
-
-// G += mu^k f (L u^{k-1} + s^{k-1}); Q^k = f a mu^k
-__global__ void adj_grad_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
-{
-    const AdjInst in = insts[blockIdx.y];
-    const long long pts = (long long)g.NX * g.NZ;
-    const float *mk = in.mu + (long long)(k % 3) * g.field;
-    float *qk = in.Q + (long long)(k % 2) * g.field;
-    const float *u = in.H + (long long)(k - 1) * g.field;
-    const SrcCorner sc = src_corner(in.sx, in.sz, g);
-    const float rn = g.wavelet[k - 1] / (g.hx * g.hz);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pts;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int J = (int)(e / g.NX), I = (int)(e % g.NX);
-        const long long kk = (long long)(J + HALO) * g.pitch + I + HALO;
-        const float t = g.ex[I + HALO] + g.ez[J + HALO];
-        const float m = mk[kk];
-        qk[kk] = in.B[kk] * m;
-        const float lap = fmaf(src_weight(sc, I, J), rn, lap_at(u, g, kk));
-        in.G[kk] = fmaf(m / (1.f + t), lap, in.G[kk]);
     }
 }
 
@@ -225,10 +286,15 @@ __global__ void adj_fold_kernel(GridDev g, const AdjInst *__restrict__ insts, in
 
 int grid_blocks(const GridDev &g)
 {
-    const long long pts = (long long)g.NX * g.NZ;
-    long long b = (pts + 255) / 256;
+    const long long items = (long long)g.NQ * g.NZ;
+    long long b = (items + 255) / 256;
     return (int)(b > 4096 ? 4096 : b);
 }
+
+using StepFn = void (*)(GridDev, const AdjInst *, int);
+StepFn fwd_fn(int R) { return R == 4 ? adj_fwd_kernel<4> : (R == 2 ? adj_fwd_kernel<2> : adj_fwd_kernel<1>); }
+StepFn back_fn(int R) { return R == 4 ? adj_back_kernel<4> : (R == 2 ? adj_back_kernel<2> : adj_back_kernel<1>); }
+StepFn grad_fn(int R) { return R == 4 ? adj_grad_kernel<4> : (R == 2 ? adj_grad_kernel<2> : adj_grad_kernel<1>); }
 
 }  // namespace
 
@@ -243,7 +309,7 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
 {
     const dim3 grid(grid_blocks(g), n_inst);
     for (int n = 0; n < g.nt; ++n) {
-        adj_fwd_kernel<<<grid, 256, 0, st>>>(g, insts, n);
+        fwd_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, n);
         adj_record_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, n);
     }
     return cudaGetLastError();
@@ -254,9 +320,9 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
 {
     const dim3 grid(grid_blocks(g), n_inst);
     for (int k = g.nt; k >= 1; --k) {
-        adj_back_kernel<<<grid, 256, 0, st>>>(g, insts, k);
+        back_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, k);
         adj_inject_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, k);
-        adj_grad_kernel<<<grid, 256, 0, st>>>(g, insts, k);
+        grad_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, k);
     }
     return cudaGetLastError();
 }
