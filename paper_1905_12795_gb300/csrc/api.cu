@@ -1516,7 +1516,7 @@ empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
     // candidates: the streaming kernel and every cluster size of the on-chip one
     std::vector<std::pair<int, int>> cand = {{EMPSO_KERNEL_STREAMING, 0}};
     for (int C = 1; C <= 16; ++C) cand.push_back({EMPSO_KERNEL_RESIDENT, C});
-    for (int C : {4, 8, 16}) cand.push_back({EMPSO_KERNEL_CLUSTER_L2, C});
+    for (int C : {4, 8, 10, 12, 16}) cand.push_back({EMPSO_KERNEL_CLUSTER_L2, C});
     float best = 1e30f;
     std::pair<int, int> choice = {EMPSO_KERNEL_AUTO, 0};
     for (auto &c : cand) {
