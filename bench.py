@@ -64,6 +64,8 @@ def _args():
                     help="skip the surrogate-vs-plain wall-clock comparison")
     ap.add_argument("--surrogate-seeds", type=int, default=9)
     ap.add_argument("--trials", type=int, default=5, help="PSO vs EMPSO comparison trials")
+    ap.add_argument("--gradient-case", type=int, default=0,
+                    help="time one adjoint gradient of this many shots")
     ap.add_argument("--surrogate-case", type=int, default=0,
                     help="time the surrogate kernels alone for this many particles")
     ap.add_argument("--generations", type=int, default=0,
@@ -930,6 +932,38 @@ def run_case(a):
     ctx.close()
 
 
+def run_gradient_case(a):
+    """One adjoint gradient of S shots of the plain workload's grid for the
+    layered/faulted model against observed data of the model +5 %, after one
+    untimed call (workspace and graph); prints the device time per call and
+    the traffic rate at 56 B per point-step (used for profiler captures)."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    S = a.gradient_case
+    wl, gs, _, _, rec, true = _setup("empso-461x151-P32-S16")
+    shots = synth.shot_line(S, (gs.nx - 1) * gs.hx, wl.src_z)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin, gs.vmax)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    sh = B.make_shots(shots, [0] * S, [len(rec)] * S)
+    v = torch.tensor(true, dtype=torch.float32, device="cuda")[None].contiguous()
+    dobs = torch.zeros(S * nt * len(rec), device="cuda")
+    ctx.forward_traces(v * 1.05, sh, dobs)
+    g = torch.zeros_like(v)
+    ctx.gradient(v, sh, dobs, g)
+    for r in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.gradient(v, sh, dobs, g)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        upd = S * _updates_per_instance(gs, nt)
+        print(f"rep {r}: gradient of {S} shots {ms:.3f} ms, "
+              f"{ADJ_BYTES_PER_UPDATE * upd / (ms / 1e3) / 1e9:.0f} GB/s at 56 B/point-step", flush=True)
+    ctx.close()
+
+
 def run_surrogate_case(a):
     """Surrogate network kernels alone: predictions for P particles and
     20-step training rounds (batch 256, hidden 256, K = 32) with each
@@ -975,6 +1009,8 @@ def main():
         run_case(a)
     elif a.surrogate_case:
         run_surrogate_case(a)
+    elif a.gradient_case:
+        run_gradient_case(a)
     elif a.impl != "reference" and a.workload.startswith("uneven"):
         run_uneven(a)
     elif a.impl != "reference" and a.workload.startswith("hires"):

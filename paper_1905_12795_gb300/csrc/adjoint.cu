@@ -17,11 +17,12 @@
 // transpose of the edge extension into the damping pad) and chained to the
 // velocity: dphi/dv = 2 v dt^2 dphi/da.
 //
-// Every kernel runs over all instances at once (blockIdx.y = instance), one
-// launch per time step and stage (the two time loops replay as one CUDA
+// Every kernel runs over all instances at once (blockIdx.y = instance): one
+// forward launch per time step (which also records the previous step's
+// residuals) and two per adjoint step (the two time loops replay as one CUDA
 // graph); the per-point kernels take one float4 group of a row per thread;
 // the receiver transpose adds the four corner contributions in four ordered
-// passes.
+// passes into a separate field that the gradient pass folds into mu.
 #include "internal.cuh"
 
 namespace empso {
@@ -112,8 +113,23 @@ __global__ void adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int
     const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
     const SrcCorner sc = src_corner(in.sx, in.sz, g);
     const float rn = g.wavelet[n] / (g.hx * g.hz);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
-         e += (long long)gridDim.x * blockDim.x) {
+    // block 0 only records e_{n-1} = R u^n - d_obs,n-1 (u^n is complete),
+    // beside the other blocks' stencil work
+    if (blockIdx.x == 0) {
+        if (n < 1) return;
+        const float *uf = in.H + (long long)n * g.field;
+        for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
+            const float2 p = in.rec[r];
+            const SrcCorner c = src_corner(p.x, p.y, g);
+            const long long kk = (long long)(c.J0 + HALO) * g.pitch + c.I0 + HALO;
+            const float d = c.w[0] * uf[kk] + c.w[1] * uf[kk + 1] + c.w[2] * uf[kk + g.pitch] +
+                            c.w[3] * uf[kk + g.pitch + 1];
+            in.E[(long long)(n - 1) * in.nrec + r] = d - in.dobs[(long long)(n - 1) * in.nrec + r];
+        }
+        return;
+    }
+    for (long long e = (blockIdx.x - 1) * (long long)blockDim.x + threadIdx.x; e < items;
+         e += (long long)(gridDim.x - 1) * blockDim.x) {
         const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
         const float4 lap = lap4<R>(u, k4, p4, g);
@@ -144,8 +160,25 @@ __global__ void adj_back_kernel(GridDev g, const AdjInst *__restrict__ insts, in
     const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 3) * g.field);
     const float4 *q1 = reinterpret_cast<const float4 *>(in.Q + (long long)((k + 1) % 2) * g.field);
     const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
-         e += (long long)gridDim.x * blockDim.x) {
+    // block 0 only scatters the receiver term w R^T e_{k-1} into J (zero
+    // before, cleared again by adj_grad_kernel), corner c of every receiver
+    // in pass c (receivers sharing a cell meet in an atomic add), beside the
+    // other blocks' stencil work
+    if (blockIdx.x == 0) {
+        for (int c = 0; c < 4; ++c) {
+            for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
+                const float2 p = in.rec[r];
+                const SrcCorner sc = src_corner(p.x, p.y, g);
+                const long long kk =
+                    (long long)(sc.J0 + (c >> 1) + HALO) * g.pitch + sc.I0 + (c & 1) + HALO;
+                atomicAdd(in.J + kk, in.w * sc.w[c] * in.E[(long long)(k - 1) * in.nrec + r]);
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    for (long long e = (blockIdx.x - 1) * (long long)blockDim.x + threadIdx.x; e < items;
+         e += (long long)(gridDim.x - 1) * blockDim.x) {
         const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
         const float4 lq = lap4<R>(q1, k4, p4, g);
@@ -170,7 +203,8 @@ __global__ void adj_grad_kernel(GridDev g, const AdjInst *__restrict__ insts, in
     const AdjInst in = insts[blockIdx.y];
     const long long items = (long long)g.NQ * g.NZ;
     const int p4 = g.pitch / 4;
-    const float4 *mk = reinterpret_cast<const float4 *>(in.mu + (long long)(k % 3) * g.field);
+    float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 3) * g.field);
+    float4 *J4 = reinterpret_cast<float4 *>(in.J);
     float4 *qk = reinterpret_cast<float4 *>(in.Q + (long long)(k % 2) * g.field);
     const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(k - 1) * g.field);
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
@@ -183,7 +217,15 @@ __global__ void adj_grad_kernel(GridDev g, const AdjInst *__restrict__ insts, in
         const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
         const float4 lap = lap4<R>(u, k4, p4, g);
-        const float4 m = mk[k4], b = B4[k4], ex = ex4[q];
+        float4 m = mk[k4];
+        const float4 jj = J4[k4];
+        if (jj.x != 0.f || jj.y != 0.f || jj.z != 0.f || jj.w != 0.f) {
+            // the receiver term completes mu^k here (the next step reads it)
+            m = make_float4(m.x + jj.x, m.y + jj.y, m.z + jj.z, m.w + jj.w);
+            mk[k4] = m;
+            J4[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float4 b = B4[k4], ex = ex4[q];
         float4 gg = G4[k4];
         const float ez = g.ez[J + HALO];
         float qo[4], go[4];
@@ -213,23 +255,6 @@ __global__ void adj_record_kernel(GridDev g, const AdjInst *__restrict__ insts, 
         const float d = c.w[0] * u[k] + c.w[1] * u[k + 1] + c.w[2] * u[k + g.pitch] +
                         c.w[3] * u[k + g.pitch + 1];
         in.E[(long long)n * in.nrec + r] = d - in.dobs[(long long)n * in.nrec + r];
-    }
-}
-
-// mu^k += w R^T e_{k-1}: corner c of every receiver in pass c (one block per
-// instance); receivers sharing a cell meet in an atomic add
-__global__ void adj_inject_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
-{
-    const AdjInst in = insts[blockIdx.x];
-    float *mk = in.mu + (long long)(k % 3) * g.field;
-    for (int c = 0; c < 4; ++c) {
-        for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
-            const float2 p = in.rec[r];
-            const SrcCorner sc = src_corner(p.x, p.y, g);
-            const long long kk = (long long)(sc.J0 + (c >> 1) + HALO) * g.pitch + sc.I0 + (c & 1) + HALO;
-            atomicAdd(mk + kk, in.w * sc.w[c] * in.E[(long long)(k - 1) * in.nrec + r]);
-        }
-        __syncthreads();
     }
 }
 
@@ -308,20 +333,21 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
                                cudaStream_t st)
 {
     const dim3 grid(grid_blocks(g), n_inst);
-    for (int n = 0; n < g.nt; ++n) {
-        fwd_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, n);
-        adj_record_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, n);
-    }
+    // step n also records e_{n-1} (in an extra block); the last record
+    // follows the loop
+    const dim3 grid1(grid.x + 1, n_inst);
+    for (int n = 0; n < g.nt; ++n) fwd_fn(g.R)<<<grid1, 256, 0, st>>>(g, insts, n);
+    adj_record_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt - 1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                 cudaStream_t st)
 {
+    (void)rec_threads;   // the receiver term is scattered by block 0 of each stencil launch
     const dim3 grid(grid_blocks(g), n_inst);
     for (int k = g.nt; k >= 1; --k) {
-        back_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, k);
-        adj_inject_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, k);
+        back_fn(g.R)<<<dim3(grid.x + 1, n_inst), 256, 0, st>>>(g, insts, k);
         grad_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, k);
     }
     return cudaGetLastError();
