@@ -573,6 +573,40 @@ def run_uneven(a):
     ctx.close()
 
 
+def _hires_prescreen(ctx_model, B, gs, rec, sh, dobs, P=32, shots=4, gens=3):
+    """Surrogate pre-screening on the high-resolution grid, bounded: a swarm of
+    P particles of 24 x 8 nodes on `shots` of the shots; one warm-up
+    generation models everyone, then `gens` pre-screening generations model
+    the predicted-best quarter.  Returns the device-synchronised wall time of
+    each kind of generation."""
+    import torch
+    del ctx_model
+    K = gs.kx * gs.kz
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin,
+                       gs.vmax, kx=gs.kx, kz=gs.kz)
+    pso = B.EmpsoPso(P, K, 1.2, 2.9, 0.5, 0.3, 0.25, 2, 1, 12795)
+    ctx = B.Context([grid], rec, pso, 1500.0, 4700.0)
+    ctx.surrogate_init(hidden=256, capacity=4096, lr=1e-3, seed=1)
+    ctx.surrogate_set_overlap(True)
+    _, nt = ctx.grid_info(0)
+    sub = (B.EmpsoShot * shots)(*sh[:shots])
+    d = dobs[: shots * nt * len(rec)]
+    mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+    ctx.pso_init()
+    times = []
+    for g in range(1 + gens):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = ctx.surrogate_generation(sub, d, 0.25, warm=P, train_steps=10, batch=64, misfit_out=mis)
+        torch.cuda.synchronize()
+        times.append((n, time.perf_counter() - t0))
+    ctx.close()
+    return {"swarm": P, "shots": shots, "nodes": K,
+            "warm_generation": {"modelled": times[0][0], "s": times[0][1]},
+            "prescreen_generations": [{"modelled": n, "s": t} for n, t in times[1:]],
+            "speedup_per_generation": times[0][1] / float(np.median([t for _, t in times[1:]]))}
+
+
 def run_hires(a):
     """High-resolution grid (921 x 301 at 10 m + 60 damping cells, order 8,
     12 Hz, 4 s): a bounded sample of the generation, `--particles` x 64 shots
@@ -638,6 +672,7 @@ def run_hires(a):
                          "traffic": _traffic_from_profile(ctx.last_kernel_name(), "hires-921x301"),
                          "kernel_ms": float(np.mean(wave))},
             "gpu_launches": 3 * a.steps, "clocks": clk}
+    line["surrogate_prescreen"] = _hires_prescreen(ctx, B, gs, rec, sh, dobs)
     print(json.dumps(line), flush=True)
     ctx.close()
 
