@@ -847,7 +847,7 @@ def run_noncrime(a):
     print(json.dumps(line), flush=True)
 
 
-ADJ_BYTES_PER_UPDATE = 56   # forward 16 B + adjoint stencil 16 B + gradient/Q pass 24 B per point-step
+ADJ_BYTES_PER_UPDATE = 56   # forward 16 B + adjoint step 40 B per point-step (algorithmic)
 
 
 def run_fwi(a):
@@ -915,7 +915,7 @@ def run_fwi(a):
             achieved = ADJ_BYTES_PER_UPDATE * upd / t / 1e9
             grad_line = {"gradient_ms": t * 1e3, "point_steps": upd,
                          "forward_plus_adjoint_updates_per_s": 2 * upd / t,
-                         "roofline": {"kernel": "adjoint path (adj_fwd/adj_back/adj_grad)",
+                         "roofline": {"kernel": "adjoint path (adj_fwd_kernel / adj_step_kernel)",
                                       "bound": "hbm", "achieved": achieved, "peak": peak,
                                       "peak_kind": peak_kind, "unit": "GB/s",
                                       "frac": achieved / peak,

@@ -19,10 +19,11 @@
 //
 // Every kernel runs over all instances at once (blockIdx.y = instance): one
 // forward launch per time step (which also records the previous step's
-// residuals) and two per adjoint step (the two time loops replay as one CUDA
+// residuals) and one per adjoint step (the two time loops replay as one CUDA
 // graph); the per-point kernels take one float4 group of a row per thread;
 // the receiver transpose adds the four corner contributions in four ordered
-// passes into a separate field that the gradient pass folds into mu.
+// passes into one of two separate fields, one step ahead, which the adjoint
+// step folds into mu.
 #include "internal.cuh"
 
 namespace empso {
@@ -148,96 +149,81 @@ __global__ void adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int
     }
 }
 
-// mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} (before the receiver term)
+// Scatter of the receiver term J^kk = w R^T e_{kk-1} into J slot kk % 2 (zero
+// before; the adjoint step kk clears it again): corner c of every receiver in
+// pass c; receivers sharing a cell meet in an atomic add.  Run by one block.
+__device__ __forceinline__ void scatter_receiver_term(const GridDev &g, const AdjInst &in, int kk)
+{
+    float *J = in.J + (long long)(kk % 2) * g.field;
+    for (int c = 0; c < 4; ++c) {
+        for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
+            const float2 p = in.rec[r];
+            const SrcCorner sc = src_corner(p.x, p.y, g);
+            const long long q = (long long)(sc.J0 + (c >> 1) + HALO) * g.pitch + sc.I0 + (c & 1) + HALO;
+            atomicAdd(J + q, in.w * sc.w[c] * in.E[(long long)(kk - 1) * in.nrec + r]);
+        }
+        __syncthreads();
+    }
+}
+
+// the receiver term of the first adjoint step (one block per instance)
+__global__ void adj_scatter_kernel(GridDev g, const AdjInst *__restrict__ insts, int kk)
+{
+    scatter_receiver_term(g, insts[blockIdx.x], kk);
+}
+
+// One adjoint step k, per point:
+//   mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} + J^k   (J^k then cleared)
+//   Q^k  = f a mu^k,   G += mu^k f (L u^{k-1} + s^{k-1})
+// Block 0 meanwhile scatters J^{k-1} into the other J slot for the next step.
 template <int R>
-__global__ void adj_back_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
+__global__ void adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
 {
     const AdjInst in = insts[blockIdx.y];
+    if (blockIdx.x == 0) {
+        if (k >= 2) scatter_receiver_term(g, in, k - 1);
+        return;
+    }
     const long long items = (long long)g.NQ * g.NZ;
     const int p4 = g.pitch / 4;
     float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 3) * g.field);
     const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 3) * g.field);
     const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 3) * g.field);
     const float4 *q1 = reinterpret_cast<const float4 *>(in.Q + (long long)((k + 1) % 2) * g.field);
-    const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
-    // block 0 only scatters the receiver term w R^T e_{k-1} into J (zero
-    // before, cleared again by adj_grad_kernel), corner c of every receiver
-    // in pass c (receivers sharing a cell meet in an atomic add), beside the
-    // other blocks' stencil work
-    if (blockIdx.x == 0) {
-        for (int c = 0; c < 4; ++c) {
-            for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
-                const float2 p = in.rec[r];
-                const SrcCorner sc = src_corner(p.x, p.y, g);
-                const long long kk =
-                    (long long)(sc.J0 + (c >> 1) + HALO) * g.pitch + sc.I0 + (c & 1) + HALO;
-                atomicAdd(in.J + kk, in.w * sc.w[c] * in.E[(long long)(k - 1) * in.nrec + r]);
-            }
-            __syncthreads();
-        }
-        return;
-    }
-    for (long long e = (blockIdx.x - 1) * (long long)blockDim.x + threadIdx.x; e < items;
-         e += (long long)(gridDim.x - 1) * blockDim.x) {
-        const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
-        const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
-        const float4 lq = lap4<R>(q1, k4, p4, g);
-        const float4 a1 = m1[k4], a2 = m2[k4], ex = ex4[q];
-        const float ez = g.ez[J + HALO];
-        float o[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float t = lane_of(ex, i) + ez;
-            const float f = 1.f / (1.f + t);
-            o[i] = 4 * q + i < g.NX ? 2.f * f * lane_of(a1, i) + lane_of(lq, i) - (1.f - t) * f * lane_of(a2, i)
-                                    : 0.f;
-        }
-        mk[k4] = make_float4(o[0], o[1], o[2], o[3]);
-    }
-}
-
-// G += mu^k f (L u^{k-1} + s^{k-1}); Q^k = f a mu^k
-template <int R>
-__global__ void adj_grad_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
-{
-    const AdjInst in = insts[blockIdx.y];
-    const long long items = (long long)g.NQ * g.NZ;
-    const int p4 = g.pitch / 4;
-    float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 3) * g.field);
-    float4 *J4 = reinterpret_cast<float4 *>(in.J);
     float4 *qk = reinterpret_cast<float4 *>(in.Q + (long long)(k % 2) * g.field);
+    float4 *J4 = reinterpret_cast<float4 *>(in.J + (long long)(k % 2) * g.field);
     const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(k - 1) * g.field);
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
     float4 *G4 = reinterpret_cast<float4 *>(in.G);
     const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
     const SrcCorner sc = src_corner(in.sx, in.sz, g);
     const float rn = g.wavelet[k - 1] / (g.hx * g.hz);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
-         e += (long long)gridDim.x * blockDim.x) {
+    for (long long e = (blockIdx.x - 1) * (long long)blockDim.x + threadIdx.x; e < items;
+         e += (long long)(gridDim.x - 1) * blockDim.x) {
         const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
-        const float4 lap = lap4<R>(u, k4, p4, g);
-        float4 m = mk[k4];
+        const float4 lq = lap4<R>(q1, k4, p4, g);
+        const float4 lu = lap4<R>(u, k4, p4, g);
+        const float4 a1 = m1[k4], a2 = m2[k4], ex = ex4[q], b = B4[k4];
         const float4 jj = J4[k4];
-        if (jj.x != 0.f || jj.y != 0.f || jj.z != 0.f || jj.w != 0.f) {
-            // the receiver term completes mu^k here (the next step reads it)
-            m = make_float4(m.x + jj.x, m.y + jj.y, m.z + jj.z, m.w + jj.w);
-            mk[k4] = m;
-            J4[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const float4 b = B4[k4], ex = ex4[q];
-        float4 gg = G4[k4];
+        if (jj.x != 0.f || jj.y != 0.f || jj.z != 0.f || jj.w != 0.f) J4[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 gg = G4[k4];
         const float ez = g.ez[J + HALO];
-        float qo[4], go[4];
+        float mo[4], qo[4], go[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int I = 4 * q + i;
             const float t = lane_of(ex, i) + ez;
-            const float mi = I < g.NX ? lane_of(m, i) : 0.f;
-            qo[i] = lane_of(b, i) * mi;
-            const float li = fmaf(src_weight(sc, I, J), rn, lane_of(lap, i));
-            go[i] = fmaf(mi / (1.f + t), li, lane_of(gg, i));
+            const float f = 1.f / (1.f + t);
+            const float m = I < g.NX ? 2.f * f * lane_of(a1, i) + lane_of(lq, i) - (1.f - t) * f * lane_of(a2, i) +
+                                           lane_of(jj, i)
+                                     : 0.f;
+            mo[i] = m;
+            qo[i] = lane_of(b, i) * m;
+            const float li = fmaf(src_weight(sc, I, J), rn, lane_of(lu, i));
+            go[i] = fmaf(m / (1.f + t), li, lane_of(gg, i));
         }
+        mk[k4] = make_float4(mo[0], mo[1], mo[2], mo[3]);
         qk[k4] = make_float4(qo[0], qo[1], qo[2], qo[3]);
         G4[k4] = make_float4(go[0], go[1], go[2], go[3]);
     }
@@ -318,8 +304,7 @@ int grid_blocks(const GridDev &g)
 
 using StepFn = void (*)(GridDev, const AdjInst *, int);
 StepFn fwd_fn(int R) { return R == 4 ? adj_fwd_kernel<4> : (R == 2 ? adj_fwd_kernel<2> : adj_fwd_kernel<1>); }
-StepFn back_fn(int R) { return R == 4 ? adj_back_kernel<4> : (R == 2 ? adj_back_kernel<2> : adj_back_kernel<1>); }
-StepFn grad_fn(int R) { return R == 4 ? adj_grad_kernel<4> : (R == 2 ? adj_grad_kernel<2> : adj_grad_kernel<1>); }
+StepFn step_fn(int R) { return R == 4 ? adj_step_kernel<4> : (R == 2 ? adj_step_kernel<2> : adj_step_kernel<1>); }
 
 }  // namespace
 
@@ -344,12 +329,11 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                 cudaStream_t st)
 {
-    (void)rec_threads;   // the receiver term is scattered by block 0 of each stencil launch
-    const dim3 grid(grid_blocks(g), n_inst);
-    for (int k = g.nt; k >= 1; --k) {
-        back_fn(g.R)<<<dim3(grid.x + 1, n_inst), 256, 0, st>>>(g, insts, k);
-        grad_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, k);
-    }
+    // the receiver term of step nt first; each step's extra block then
+    // scatters the next step's
+    const dim3 grid(grid_blocks(g) + 1, n_inst);
+    adj_scatter_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
+    for (int k = g.nt; k >= 1; --k) step_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, k);
     return cudaGetLastError();
 }
 

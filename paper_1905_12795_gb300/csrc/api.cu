@@ -1033,7 +1033,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     if ((rc = adj_grow(ctx, &W.a, &W.a_cap, 2 * F * M, nullptr))) return rc;
     W.B = W.a + F * M;
     if ((rc = adj_grow(ctx, &W.H, &W.H_cap, F * (size_t)(g.nt + 1) * I, &grewH))) return rc;
-    if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 7 * I, nullptr))) return rc;
+    if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 8 * I, nullptr))) return rc;
     W.Q = W.mu + F * 3 * I;
     W.G = W.mu + F * 5 * I;
     if ((rc = adj_grow(ctx, &W.E, &W.E_cap, (size_t)g.nt * rec_max * I, nullptr))) return rc;
@@ -1046,7 +1046,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         CK(ctx, cudaMemsetAsync(W.H, 0, sizeof(float) * F * (size_t)(g.nt + 1) * I, st));
         W.layout = lay.str();
     }
-    CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 7 * I, st));
+    CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 8 * I, st));
     // instance table (the previous call's kernels may still read the old one)
     std::vector<long long> doff(S + 1, 0);
     for (int s = 0; s < S; ++s) doff[s + 1] = doff[s] + (long long)g.nt * shots[s].nrec;
@@ -1061,7 +1061,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             in.mu = W.mu + F * 3 * q;
             in.Q = W.Q + F * 2 * q;
             in.G = W.G + F * q;
-            in.J = W.mu + F * 6 * I + F * q;
+            in.J = W.mu + F * 6 * I + F * 2 * q;
             in.E = W.E + (size_t)g.nt * rec_max * q;
             in.dobs = d_obs + doff[s];
             in.rec = ctx->rec_dev + shots[s].rec_begin;

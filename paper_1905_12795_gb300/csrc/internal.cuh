@@ -84,7 +84,7 @@ struct AdjInst {
     float *mu;           // adjoint fields, 3 rolling buffers [3][field]
     float *Q;            // f a mu, 2 rolling buffers [2][field]
     float *G;            // dphi/da of this shot [field]
-    float *J;            // receiver term w R^T e of the current adjoint step [field], zero elsewhere
+    float *J;            // receiver terms w R^T e of two adjoint steps [2][field], zero elsewhere
     float *E;            // residuals [nt][nrec]
     const float *dobs;   // [nt][nrec]
     const float2 *rec;   // receiver positions
