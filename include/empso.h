@@ -313,6 +313,12 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas);
  * instance.  Either pointer may be NULL (host ints). */
 empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *cluster);
 
+/* Work units of the last on-chip launch that ran two instances at once, one
+ * on each half of the cluster (instances of a grid that fits half the
+ * cluster without raising the launch's shared memory or threads, e.g. the
+ * coarse grid of a mixed-resolution batch); 0 for other kernels. */
+empso_status empso_last_paired_units(const empso_ctx *ctx, int32_t *paired);
+
 /* Device-function name of the last modelling launch's kernel
  * ("wave_resident_kernel", "wave_stream_kernel" for the streaming kernel
  * with bulk asynchronous row copies, "wave_kernel" for the plain streaming

@@ -33,7 +33,7 @@ EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
            "empso_nonfinite_count", "empso_set_strict", "empso_save", "empso_load",
            "empso_set_levels", "empso_set_water", "empso_level_bounds", "empso_last_kernel_name",
-           "empso_lowpass", "empso_gradient", "empso_fwi",
+           "empso_lowpass", "empso_gradient", "empso_fwi", "empso_last_paired_units",
            "empso_status_string", "empso_last_error"]
 
 
@@ -121,6 +121,7 @@ def load():
     L.empso_set_strict.argtypes = [_vp, _i32]
     L.empso_set_levels.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
     L.empso_last_kernel_name.argtypes = [_vp]
+    L.empso_last_paired_units.argtypes = [_vp, P(_i32)]
     L.empso_last_kernel_name.restype = ctypes.c_char_p
     L.empso_set_water.argtypes = [_vp, _i32, _f32, _f32]
     L.empso_gradient.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp, _vp, _vp]
@@ -327,6 +328,12 @@ class Context:
     def load(self, path):
         """Restore a checkpoint written by save() into a context of the same shape."""
         self._check(self._L.empso_load(self._h, os.fsencode(path)))
+
+    def last_paired_units(self):
+        """Work units of the last on-chip launch that ran two instances (one per half cluster)."""
+        n = _i32()
+        self._check(self._L.empso_last_paired_units(self._h, ctypes.byref(n)))
+        return n.value
 
     def last_kernel_name(self):
         """Device-function name of the last modelling launch's kernel."""

@@ -58,6 +58,7 @@ struct empso_ctx {
     int forced_C = 0;               // 0: choose the cluster size, else use this one
     int last_path = 0;              // 1 streaming, 2 resident, 3 bulk-copy streaming (last launch)
     int last_C = 0;
+    int last_paired = 0;            // on-chip launch: units running two instances
     int *dev_err = nullptr;         // device status word set by bounded waits that give up
     unsigned long long *nonfinite = nullptr;  // non-finite misfits: {running, this call}
     bool strict = false;            // report non-finite misfits as EMPSO_NONFINITE
@@ -334,6 +335,9 @@ struct Plan {
     bool resident = false;
     int resR = 0, resC = 0, res_threads = 0, res_clusters = 0, ring_pitch = 0;
     size_t res_smem = 0;
+    std::vector<char> res_pair;        // per grid: two instances share a cluster (half each)
+    const int4 *units = nullptr;       // device work units of the on-chip kernel
+    int n_units = 0, n_paired = 0;
     int n_ctas = 0;
     bool l2 = false;                   // L2-resident cluster kernel
     int l2C = 0, l2_clusters = 0, l2_threads = 0;
@@ -429,11 +433,25 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
             }
             if (!ok) continue;
             const int threads = (items + 31) / 32 * 32;
+            // a grid runs two instances per cluster, one on each half, when it
+            // fits C / 2 CTAs without raising the launch's shared memory or threads
+            std::vector<char> pair(ng, 0);
+            if (C % 2 == 0)
+                for (int gid = 0; gid < ng; ++gid) {
+                    if (p.fbase[gid] < 0) continue;
+                    const GridDev &g = ctx->grids[gid].dev;
+                    const int rows_h = (g.NZ + C / 2 - 1) / (C / 2);
+                    const int rpt = resident_rows_per_thread();
+                    pair[gid] = resident_fits(g, C / 2, ring_pitch, ctx->smem_optin) &&
+                                resident_smem_bytes(g, C / 2, ring_pitch) <= sm &&
+                                g.NQ * ((rows_h + rpt - 1) / rpt) <= threads;
+                }
             const int nc = (int)std::min<long long>(resident_max_clusters(resR, C, threads, sm), p.n_inst);
             const long long sms = (long long)nc * C;
             if (nc > 0 && sms > best_sms) {
                 best_sms = sms;
                 p.resident = true;
+                p.res_pair = pair;
                 p.resR = resR;
                 p.resC = C;
                 p.res_smem = sm;
@@ -533,7 +551,9 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
         return rc;
     const size_t inst_bytes = sizeof(Inst) * p.n_inst;
     const size_t wofs = (inst_bytes + 255) / 256 * 256;
-    if ((rc = grow_stage(ctx, wofs + sizeof(float) * S)) != EMPSO_OK) return rc;
+    const size_t uofs = wofs + (sizeof(float) * S + 15) / 16 * 16;
+    const size_t tbytes = uofs + sizeof(int4) * p.n_inst;
+    if ((rc = grow_stage(ctx, tbytes)) != EMPSO_OK) return rc;
 
     // instance table, longest work first so the dynamic queue balances
     std::vector<long long> order(p.n_inst);
@@ -566,22 +586,39 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
     }
     float *wh = reinterpret_cast<float *>(ctx->stage_host + wofs);
     for (int s = 0; s < S; ++s) wh[s] = shots[s].weight;
+    // work units of the on-chip kernel: consecutive instances of a paired grid
+    // (the sort keeps a grid's instances together) share a cluster
+    int4 *uh = reinterpret_cast<int4 *>(ctx->stage_host + uofs);
+    p.n_units = 0;
+    p.n_paired = 0;
+    for (long long k = 0; k < p.n_inst;) {
+        const int gid = shots[order[k] % S].grid_id;
+        if (p.resident && p.res_pair[gid] && k + 1 < p.n_inst && shots[order[k + 1] % S].grid_id == gid) {
+            uh[p.n_units++] = make_int4((int)k, (int)k + 1, 1, 0);
+            ++p.n_paired;
+            k += 2;
+        } else {
+            uh[p.n_units++] = make_int4((int)k, -1, 0, 0);
+            k += 1;
+        }
+    }
     unsigned char *dst = table ? table : ctx->stage_dev;
     if (table) {
-        CK(ctx, cudaMemcpy(table, ctx->stage_host, wofs + sizeof(float) * S, cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(table, ctx->stage_host, tbytes, cudaMemcpyHostToDevice));
     } else {
-        CK(ctx, cudaMemcpyAsync(ctx->stage_dev, ctx->stage_host, wofs + sizeof(float) * S,
-                                cudaMemcpyHostToDevice, st));
+        CK(ctx, cudaMemcpyAsync(ctx->stage_dev, ctx->stage_host, tbytes, cudaMemcpyHostToDevice, st));
         CK(ctx, cudaEventRecord(ctx->stage_free, st));
     }
     p.insts = reinterpret_cast<const Inst *>(dst);
     p.weights = reinterpret_cast<const float *>(dst + wofs);
+    p.units = reinterpret_cast<const int4 *>(dst + uofs);
     return EMPSO_OK;
 }
 
 size_t table_bytes(long long n_inst, int S)
 {
-    return (sizeof(Inst) * n_inst + 255) / 256 * 256 + sizeof(float) * S;
+    return (sizeof(Inst) * n_inst + 255) / 256 * 256 + (sizeof(float) * S + 15) / 16 * 16 +
+           sizeof(int4) * n_inst;
 }
 
 // Timing event on `st`; inside a stream capture it becomes an event-record
@@ -612,11 +649,13 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
     CK(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int), st));
     if (ctx->timing) CK(ctx, mark(ctx->tev[1], st));
     if (p.resident) {
-        CK(ctx, launch_wave_resident(p.resR, ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter,
+        CK(ctx, launch_wave_resident(p.resR, ctx->grids_dev, p.insts, p.units, p.n_units, p.n_paired > 0,
+                                     ctx->counter,
                                      p.resC, p.res_clusters, p.res_threads, p.ring_pitch, p.res_smem,
                                      ctx->partial, st));
         ctx->last_path = 2;
         ctx->last_C = p.resC;
+        ctx->last_paired = p.n_paired;
     } else if (p.l2) {
         CK(ctx, launch_wave_l2(p.resR, ctx->grids_dev, p.insts,
                                (int)p.n_inst, ctx->counter, p.l2C, p.l2_clusters, p.l2_threads,
@@ -1589,6 +1628,13 @@ empso_status empso_last_launch(const empso_ctx *ctx, int32_t *kind, int32_t *clu
         *kind = ctx->last_path == 3 ? EMPSO_KERNEL_STREAMING
                                     : (ctx->last_path == 4 ? EMPSO_KERNEL_CLUSTER_L2 : ctx->last_path);
     if (cluster) *cluster = ctx->last_C;
+    return EMPSO_OK;
+}
+
+empso_status empso_last_paired_units(const empso_ctx *ctx, int32_t *paired)
+{
+    if (!ctx || !paired) return EMPSO_INVALID_ARG;
+    *paired = ctx->last_path == 2 ? ctx->last_paired : 0;
     return EMPSO_OK;
 }
 

@@ -143,7 +143,8 @@ size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch);
 bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit);
 cudaError_t resident_configure(int R, size_t smem_bytes, int C);
 int resident_max_clusters(int R, int C, int threads, size_t smem_bytes);
-cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, int n_inst,
+cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, const int4 *units,
+                                 int n_units, bool pairs,
                                  int *counter, int C, int n_clusters, int threads, int ring_pitch,
                                  size_t smem_bytes, double *partial, cudaStream_t st);
 

@@ -67,11 +67,13 @@ __device__ __forceinline__ void corners(float x, float z, const GridDev &g, int 
     w[3] = ax * az;
 }
 
+// C CTAs (ranks base .. base + C - 1 of the cluster; crank is the rank among
+// them) run instance `in`
 template <int R>
 __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
                                   float4 *M4, float *ezs, float *wring, float *dring, float4 *rec_w,
                                   int *rec_k, int ring_pitch,
-                                  int C, int crank, cg::cluster_group &cluster, double *cred,
+                                  int C, int crank, int base, cg::cluster_group &cluster, double *cred,
                                   double *wred, double *partial)
 {
     const int tid = threadIdx.x;
@@ -177,12 +179,12 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     // neighbours' views of both time-level buffers
     float4 *prev_A = nullptr, *prev_B = nullptr, *next_A = nullptr, *next_B = nullptr;
     if (crank > 0) {
-        prev_A = cluster.map_shared_rank(A4, crank - 1);
-        prev_B = cluster.map_shared_rank(B4, crank - 1);
+        prev_A = cluster.map_shared_rank(A4, base + crank - 1);
+        prev_B = cluster.map_shared_rank(B4, base + crank - 1);
     }
     if (crank < C - 1) {
-        next_A = cluster.map_shared_rank(A4, crank + 1);
-        next_B = cluster.map_shared_rank(B4, crank + 1);
+        next_A = cluster.map_shared_rank(A4, base + crank + 1);
+        next_B = cluster.map_shared_rank(B4, base + crank + 1);
     }
     const bool top_item = r0 < R;                        // may hold halo rows of the CTA above
     const bool bot_item = r0 + ROWS > rows_c - R;        // ... of the CTA below
@@ -319,7 +321,7 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         double v = (tid < nth / 32) ? wred[tid] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (tid == 0) *cluster.map_shared_rank(cred + crank, 0) = v;
+        if (tid == 0) *cluster.map_shared_rank(cred + crank, base) = v;
     }
     cluster.sync();
     if (crank == 0 && tid == 0) {
@@ -329,10 +331,16 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     }
 }
 
-template <int R, int NT>
+// Work unit u of the queue: units[u] = {a, b, halves}.  halves = 0: the whole
+// cluster runs instance a; halves = 1: ranks 0 .. C/2 - 1 run instance a and
+// ranks C/2 .. C - 1 instance b, both of the same grid (so both halves pass
+// the same number of cluster barriers).  Launches with no halved unit use the
+// PAIRS = false instantiation, where the whole-cluster layout is constant.
+template <int R, int NT, bool PAIRS>
 __global__ void __launch_bounds__(NT, 1)
 wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts,
-                     int n_inst, int *counter, int ring_pitch, double *partial)
+                     const int4 *__restrict__ units, int n_units, int *counter, int ring_pitch,
+                     double *partial)
 {
     extern __shared__ float4 smem4[];
     __shared__ int s_q;
@@ -348,12 +356,17 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
             for (int c = 0; c < C; ++c) *cluster.map_shared_rank(&s_q, c) = q;
         }
         cluster.sync();
-        const int q = s_q;
-        if (q >= n_inst) break;
-        const Inst in = insts[q];
+        const int u = s_q;
+        if (u >= n_units) break;
+        const int4 un = units[u];
+        const bool halves = PAIRS && un.z != 0;
+        const int Ce = halves ? C / 2 : C;
+        const int sub = halves ? (crank >= C / 2 ? 1 : 0) : 0;
+        const int ce = crank - sub * Ce;
+        const Inst in = insts[sub ? un.y : un.x];
         if (threadIdx.x == 0) sg = grids[in.grid];
         __syncthreads();
-        const int rows_c = (sg.NZ + C - 1) / C;
+        const int rows_c = (sg.NZ + Ce - 1) / Ce;
         float4 *A4 = smem4;
         float4 *B4 = A4 + (size_t)(rows_c + 2 * R) * (sg.NQ + 2);
         float4 *M4 = B4 + (size_t)(rows_c + 2 * R) * (sg.NQ + 2);
@@ -362,8 +375,8 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float *dring = wring + 4 * ((DEPTH + 3) / 4);
         float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
         int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
-        resident_instance<R>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, ring_pitch, C,
-                             crank, cluster, cred, wred, partial);
+        resident_instance<R>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, ring_pitch, Ce,
+                             ce, sub * Ce, cluster, cred, wred, partial);
     }
 }
 
@@ -401,26 +414,38 @@ bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit)
 }
 
 namespace {
-template <int R>
-cudaError_t configure_r(size_t smem_bytes, int C)
+template <int R, bool PAIRS>
+cudaError_t configure_rp(size_t smem_bytes, int C)
 {
-    cudaError_t e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT>,
+    cudaError_t e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes);
     if (e != cudaSuccess) return e;
     if (C > 8)
-        e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT>,
+        e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
-using ResidentFn = void (*)(const GridDev *, const Inst *, int, int *, int, double *);
-
-ResidentFn resident_fn(int R)
+template <int R>
+cudaError_t configure_r(size_t smem_bytes, int C)
 {
-    if (R == 4) return wave_resident_kernel<4, RES_NT>;
-    if (R == 2) return wave_resident_kernel<2, RES_NT>;
-    return wave_resident_kernel<1, RES_NT>;
+    cudaError_t e = configure_rp<R, false>(smem_bytes, C);
+    return e != cudaSuccess ? e : configure_rp<R, true>(smem_bytes, C);
+}
+
+using ResidentFn = void (*)(const GridDev *, const Inst *, const int4 *, int, int *, int, double *);
+
+ResidentFn resident_fn(int R, bool pairs)
+{
+    if (pairs) {
+        if (R == 4) return wave_resident_kernel<4, RES_NT, true>;
+        if (R == 2) return wave_resident_kernel<2, RES_NT, true>;
+        return wave_resident_kernel<1, RES_NT, true>;
+    }
+    if (R == 4) return wave_resident_kernel<4, RES_NT, false>;
+    if (R == 2) return wave_resident_kernel<2, RES_NT, false>;
+    return wave_resident_kernel<1, RES_NT, false>;
 }
 }  // namespace
 
@@ -445,18 +470,18 @@ int resident_max_clusters(int R, int C, int threads, size_t smem_bytes)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, resident_fn(R), &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, resident_fn(R, false), &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
-cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, int n_inst,
-                                 int *counter, int C, int n_clusters, int threads, int ring_pitch,
-                                 size_t smem_bytes, double *partial, cudaStream_t st)
+cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, const int4 *units,
+                                 int n_units, bool pairs, int *counter, int C, int n_clusters, int threads,
+                                 int ring_pitch, size_t smem_bytes, double *partial, cudaStream_t st)
 {
-    if (n_inst <= 0) return cudaSuccess;
+    if (n_units <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -469,8 +494,8 @@ cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *in
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, resident_fn(R), grids_dev, insts, n_inst, counter, ring_pitch,
-                              partial);
+    return cudaLaunchKernelEx(&cfg, resident_fn(R, pairs), grids_dev, insts, units, n_units, counter,
+                              ring_pitch, partial);
 }
 
 }  // namespace empso

@@ -176,16 +176,14 @@ def test_eval_fitness_particles(B, kind):
     ctx.close()
 
 
-@pytest.mark.parametrize("kind", KINDS)
-def test_uneven_batch_two_grids(B, kind):
-    """One launch over instances of two grid classes (coarse 40 m / 3 Hz / long
-    record, fine 20 m / 6 Hz), weighted misfit sum in fixed shot order."""
+def _uneven_problem(B):
+    """Two grid classes (coarse 40 m / 3 Hz / long record, fine 20 m / 6 Hz),
+    2 shots each, 5 particles, weighted misfit sum in fixed shot order."""
     vmin, vmax = 1500.0, 4700.0
     coarse = dict(nx=39, nz=17, h=40.0, pad=6, T=1.2, f0=3.0)
     fine = dict(nx=77, nz=33, h=20.0, pad=10, T=0.9, f0=6.0)
     ogs, grids, recs, shots_all, obs_all = [], [], [], [], []
-    rec_table = []
-    for gi, c in enumerate((coarse, fine)):
+    for c in (coarse, fine):
         og = oracle.Grid(c["nx"], c["nz"], c["h"], c["h"], c["pad"], 8, c["T"], c["f0"], vmax)
         ogs.append(og)
         grids.append(B.make_grid(c["nx"], c["nz"], c["h"], c["h"], c["pad"], 8, c["T"], c["f0"],
@@ -197,27 +195,57 @@ def test_uneven_batch_two_grids(B, kind):
         recs.append(rec)
         shots_all.append(sh)
         obs_all.append(obs)
-        rec_table.append(rec)
     parts = synth.random_particles(5, 32, vmin, vmax, seed=11)
     w = [0.7, 0.7, 1.3, 1.3]
     ref = np.zeros(5)
     for gi in range(2):
-        og = ogs[gi]
         nrec = len(recs[gi])
-        ref += _oracle_fitness(og, parts, 4, 8, 0, vmin, vmax, shots_all[gi], recs[gi], [0, 0],
+        ref += _oracle_fitness(ogs[gi], parts, 4, 8, 0, vmin, vmax, shots_all[gi], recs[gi], [0, 0],
                                [nrec] * 2, obs_all[gi], weights=w[2 * gi:2 * gi + 2])
-    ctx = B.Context(grids, np.concatenate(rec_table))
-    _use(ctx, kind)
     n0 = len(recs[0])
-    xz = np.concatenate(shots_all)
-    sh = B.make_shots(xz, [0, 0, n0, n0], [n0, n0, len(recs[1]), len(recs[1])],
+    sh = B.make_shots(np.concatenate(shots_all), [0, 0, n0, n0], [n0, n0, len(recs[1]), len(recs[1])],
                       grid_ids=[0, 0, 1, 1], weights=w)
     dobs = _dev(np.concatenate([o.ravel() for ob in obs_all for o in ob]))
+    e = sum(wi * 0.5 * np.sum(o ** 2) for wi, o in zip(w, [o for ob in obs_all for o in ob]))
+    return grids, np.concatenate(recs), sh, dobs, parts, ref, e
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_uneven_batch_two_grids(B, kind):
+    """One launch over instances of two grid classes."""
+    grids, rec, sh, dobs, parts, ref, e = _uneven_problem(B)
+    ctx = B.Context(grids, rec)
+    _use(ctx, kind)
     mis = torch.zeros(5, dtype=torch.float64, device="cuda")
     ctx.eval_fitness(_dev(parts), sh, dobs, mis)
     _ran(ctx, kind)
-    e = sum(wi * 0.5 * np.sum(o ** 2) for wi, o in zip(w, [o for ob in obs_all for o in ob]))
     _check_misfit(mis.cpu().numpy(), ref, [e] * 5)
+    ctx.close()
+
+
+def test_uneven_batch_pairs_the_small_grid(B):
+    """On a cluster of 4 CTAs the coarse grid also fits 2 CTAs without needing
+    more shared memory or threads than the fine one: its instances run two per
+    cluster, one on each half, in the same launch as the fine ones.  The result
+    matches the oracle and the unpaired launch (3 CTAs, odd: no halves)."""
+    grids, rec, sh, dobs, parts, ref, e = _uneven_problem(B)
+    ctx = B.Context(grids, rec)
+    ctx.set_kernel(2)
+    got = {}
+    for C in (4, 3):
+        ctx.set_cluster(C)
+        mis = torch.zeros(5, dtype=torch.float64, device="cuda")
+        ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+        assert ctx.last_launch() == (2, C)
+        got[C] = mis.cpu().numpy()
+        _check_misfit(got[C], ref, [e] * 5)
+    ctx.set_cluster(4)
+    ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+    assert ctx.last_paired_units() == 5          # 10 coarse instances in 5 pairs
+    ctx.set_cluster(3)
+    ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+    assert ctx.last_paired_units() == 0
+    assert np.allclose(got[4], got[3], rtol=1e-5)
     ctx.close()
 
 
