@@ -20,7 +20,8 @@
 // Every kernel runs over all instances at once (blockIdx.y = instance): one
 // forward launch per time step (which also records the previous step's
 // residuals) and one per adjoint step (the two time loops replay as one CUDA
-// graph); the per-point kernels take one float4 group of a row per thread;
+// graph); the per-point kernels stage the fields their Laplacians read in
+// shared-memory tiles and give each thread a few rows of one float4 group;
 // the receiver transpose adds the four corner contributions in four ordered
 // passes into one of two separate fields, one step ahead, which the adjoint
 // step folds into mu.
@@ -71,19 +72,48 @@ __global__ void adj_prep_kernel(GridDev g, const float *a, float *B)
     }
 }
 
-// Laplacian of the four points of float4 group k4 (row pitch p4 float4s):
+// The per-point kernels work on tiles of TW float4 groups (4 TW points) by
+// TT = 8 TZ rows; each of the block's TW x 8 threads computes TZ consecutive
+// rows of one group.  The fields that enter a Laplacian are staged first,
+// with R rows and one group of halo on every side, in shared memory.  The
+// forward step takes TZ = 1 (its Laplacian reads one field; more rows per
+// thread cost it registers and occupancy).  The adjoint step takes TZ = 4
+// when that still gives every SM enough blocks (less halo re-read, one wave),
+// else 2 or 1 (more, smaller blocks to fill the GPU).
+constexpr int TW = 16, TILE_THREADS = TW * 8;
+
+__host__ __device__ inline int tiles_x(const GridDev &g) { return (g.NQ + TW - 1) / TW; }
+
+// rows J0 - R .. J0 + TT - 1 + R, groups q0 - 1 .. q0 + TW of buffer U into
+// S[TT + 2R][TW + 2]; cells outside the buffer read as zero
+template <int R, int TT>
+__device__ __forceinline__ void stage_tile(float4 *S, const float4 *__restrict__ U, int J0, int q0,
+                                           const GridDev &g)
+{
+    constexpr int W = TW + 2, H = TT + 2 * R;
+    const int p4 = g.pitch / 4;
+    for (int c = threadIdx.x; c < W * H; c += TILE_THREADS) {
+        const int row = J0 - R + c / W + HALO;  // buffer row
+        const int grp = q0 + c % W;             // buffer group of interior group q0 - 1 + c % W
+        S[c] = (row >= 0 && row < g.rows && grp < p4) ? U[(long long)row * p4 + grp]
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Laplacian of the four points of the staged group at tile row sr, column sc:
 // z-neighbours as whole float4s, x-neighbours from the groups left and right
 template <int R>
-__device__ __forceinline__ float4 lap4(const float4 *__restrict__ U, long long k4, int p4, const GridDev &g)
+__device__ __forceinline__ float4 lap4_tile(const float4 *S, int sr, int sc, const GridDev &g)
 {
-    const float4 c = U[k4], l = U[k4 - 1], r = U[k4 + 1];
+    constexpr int W = TW + 2;
+    const float4 c = S[sr * W + sc], l = S[sr * W + sc - 1], r = S[sr * W + sc + 1];
     const float s[12] = {l.x, l.y, l.z, l.w, c.x, c.y, c.z, c.w, r.x, r.y, r.z, r.w};
     float o[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) o[i] = g.cxm[0] * s[4 + i];
 #pragma unroll
     for (int m = 1; m <= R; ++m) {
-        const float4 zm = U[k4 - (long long)m * p4], zp = U[k4 + (long long)m * p4];
+        const float4 zm = S[(sr - m) * W + sc], zp = S[(sr + m) * W + sc];
         const float zs[4] = {zm.x + zp.x, zm.y + zp.y, zm.z + zp.z, zm.w + zp.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -97,23 +127,15 @@ __device__ __forceinline__ float lane_of(const float4 &v, int i)
     return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// The per-point kernels take one float4 group (4 points of a row) per
-// thread; lanes past the last column (I >= NX) stay zero.
+// Lanes past the last column (I >= NX) stay zero.
 
 // u^{n+1} of every instance into H[n+1]
-template <int R>
-__global__ void adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
+template <int R, int TZ>
+__global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
 {
+    constexpr int W = TW + 2, TT = 8 * TZ;
+    __shared__ float4 S[(TT + 2 * R) * W];
     const AdjInst in = insts[blockIdx.y];
-    const long long items = (long long)g.NQ * g.NZ;
-    const int p4 = g.pitch / 4;
-    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)n * g.field);
-    const float4 *um = reinterpret_cast<const float4 *>(in.H + (long long)(n > 0 ? n - 1 : 0) * g.field);
-    float4 *u1 = reinterpret_cast<float4 *>(in.H + (long long)(n + 1) * g.field);
-    const float4 *a4 = reinterpret_cast<const float4 *>(in.a);
-    const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
-    const SrcCorner sc = src_corner(in.sx, in.sz, g);
-    const float rn = g.wavelet[n] / (g.hx * g.hz);
     // block 0 only records e_{n-1} = R u^n - d_obs,n-1 (u^n is complete),
     // beside the other blocks' stencil work
     if (blockIdx.x == 0) {
@@ -129,12 +151,28 @@ __global__ void adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int
         }
         return;
     }
-    for (long long e = (blockIdx.x - 1) * (long long)blockDim.x + threadIdx.x; e < items;
-         e += (long long)(gridDim.x - 1) * blockDim.x) {
-        const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
+    const int t = blockIdx.x - 1, ntx = tiles_x(g);
+    const int q0 = (t % ntx) * TW, J0 = (t / ntx) * TT;
+    const int p4 = g.pitch / 4;
+    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)n * g.field);
+    const float4 *um = reinterpret_cast<const float4 *>(in.H + (long long)(n > 0 ? n - 1 : 0) * g.field);
+    float4 *u1 = reinterpret_cast<float4 *>(in.H + (long long)(n + 1) * g.field);
+    const float4 *a4 = reinterpret_cast<const float4 *>(in.a);
+    stage_tile<R, TT>(S, u, J0, q0, g);
+    __syncthreads();
+    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW, q = q0 + lx;
+    if (q >= g.NQ) return;
+    const SrcCorner sc = src_corner(in.sx, in.sz, g);
+    const float rn = g.wavelet[n] / (g.hx * g.hz);
+    const float4 ex = reinterpret_cast<const float4 *>(g.ex + HALO)[q];
+#pragma unroll
+    for (int r = 0; r < TZ; ++r) {
+        const int J = J0 + ly * TZ + r;
+        if (J >= g.NZ) break;
+        const int sr = ly * TZ + r + R;
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
-        const float4 lap = lap4<R>(u, k4, p4, g);
-        const float4 c = u[k4], m = um[k4], av = a4[k4], ex = ex4[q];
+        const float4 lap = lap4_tile<R>(S, sr, lx + 1, g);
+        const float4 c = S[sr * W + lx + 1], m = um[k4], av = a4[k4];
         const float ez = g.ez[J + HALO];
         float o[4];
 #pragma unroll
@@ -176,15 +214,19 @@ __global__ void adj_scatter_kernel(GridDev g, const AdjInst *__restrict__ insts,
 //   mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} + J^k   (J^k then cleared)
 //   Q^k  = f a mu^k,   G += mu^k f (L u^{k-1} + s^{k-1})
 // Block 0 meanwhile scatters J^{k-1} into the other J slot for the next step.
-template <int R>
-__global__ void adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts, int k)
+template <int R, int TZ>
+__global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts,
+                                                                   int k)
 {
+    constexpr int W = TW + 2, TT = 8 * TZ;
+    __shared__ float4 SQ[(TT + 2 * R) * W], SU[(TT + 2 * R) * W];
     const AdjInst in = insts[blockIdx.y];
     if (blockIdx.x == 0) {
         if (k >= 2) scatter_receiver_term(g, in, k - 1);
         return;
     }
-    const long long items = (long long)g.NQ * g.NZ;
+    const int t = blockIdx.x - 1, ntx = tiles_x(g);
+    const int q0 = (t % ntx) * TW, J0 = (t / ntx) * TT;
     const int p4 = g.pitch / 4;
     float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 3) * g.field);
     const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 3) * g.field);
@@ -195,16 +237,23 @@ __global__ void adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts, in
     const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(k - 1) * g.field);
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
     float4 *G4 = reinterpret_cast<float4 *>(in.G);
-    const float4 *ex4 = reinterpret_cast<const float4 *>(g.ex + HALO);
+    stage_tile<R, TT>(SQ, q1, J0, q0, g);
+    stage_tile<R, TT>(SU, u, J0, q0, g);
+    __syncthreads();
+    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW, q = q0 + lx;
+    if (q >= g.NQ) return;
     const SrcCorner sc = src_corner(in.sx, in.sz, g);
     const float rn = g.wavelet[k - 1] / (g.hx * g.hz);
-    for (long long e = (blockIdx.x - 1) * (long long)blockDim.x + threadIdx.x; e < items;
-         e += (long long)(gridDim.x - 1) * blockDim.x) {
-        const int J = (int)(e / g.NQ), q = (int)(e % g.NQ);
+    const float4 ex = reinterpret_cast<const float4 *>(g.ex + HALO)[q];
+#pragma unroll
+    for (int r = 0; r < TZ; ++r) {
+        const int J = J0 + ly * TZ + r;
+        if (J >= g.NZ) break;
+        const int sr = ly * TZ + r + R;
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
-        const float4 lq = lap4<R>(q1, k4, p4, g);
-        const float4 lu = lap4<R>(u, k4, p4, g);
-        const float4 a1 = m1[k4], a2 = m2[k4], ex = ex4[q], b = B4[k4];
+        const float4 lq = lap4_tile<R>(SQ, sr, lx + 1, g);
+        const float4 lu = lap4_tile<R>(SU, sr, lx + 1, g);
+        const float4 a1 = m1[k4], a2 = m2[k4], b = B4[k4];
         const float4 jj = J4[k4];
         if (jj.x != 0.f || jj.y != 0.f || jj.z != 0.f || jj.w != 0.f) J4[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 gg = G4[k4];
@@ -302,9 +351,31 @@ int grid_blocks(const GridDev &g)
     return (int)(b > 4096 ? 4096 : b);
 }
 
+int tile_count(const GridDev &g, int TT) { return tiles_x(g) * ((g.NZ + TT - 1) / TT); }
+
 using StepFn = void (*)(GridDev, const AdjInst *, int);
-StepFn fwd_fn(int R) { return R == 4 ? adj_fwd_kernel<4> : (R == 2 ? adj_fwd_kernel<2> : adj_fwd_kernel<1>); }
-StepFn step_fn(int R) { return R == 4 ? adj_step_kernel<4> : (R == 2 ? adj_step_kernel<2> : adj_step_kernel<1>); }
+
+StepFn fwd_fn(int R) { return R == 4 ? adj_fwd_kernel<4, 1> : (R == 2 ? adj_fwd_kernel<2, 1> : adj_fwd_kernel<1, 1>); }
+template <int TZ>
+StepFn step_fn_z(int R)
+{
+    return R == 4 ? adj_step_kernel<4, TZ> : (R == 2 ? adj_step_kernel<2, TZ> : adj_step_kernel<1, TZ>);
+}
+StepFn step_fn(int R, int TZ) { return TZ == 4 ? step_fn_z<4>(R) : (TZ == 2 ? step_fn_z<2>(R) : step_fn_z<1>(R)); }
+
+// rows per thread of an adjoint-step launch over n_inst instances: 4 while
+// that gives every SM 7 tile blocks (one wave at 8 resident), else 2 while
+// that gives 3, else 1 (measured on the 461 x 151 grid: 16 shots run fastest
+// at 4, 4 shots at 2)
+int adj_rows_per_thread(const GridDev &g, int n_inst)
+{
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    if ((long long)tile_count(g, 32) * n_inst >= 7LL * sms) return 4;
+    if ((long long)tile_count(g, 16) * n_inst >= 3LL * sms) return 2;
+    return 1;
+}
 
 }  // namespace
 
@@ -317,11 +388,11 @@ cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, c
 cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                cudaStream_t st)
 {
-    const dim3 grid(grid_blocks(g), n_inst);
     // step n also records e_{n-1} (in an extra block); the last record
     // follows the loop
-    const dim3 grid1(grid.x + 1, n_inst);
-    for (int n = 0; n < g.nt; ++n) fwd_fn(g.R)<<<grid1, 256, 0, st>>>(g, insts, n);
+    const dim3 grid(tile_count(g, 8) + 1, n_inst);
+    const StepFn fn = fwd_fn(g.R);
+    for (int n = 0; n < g.nt; ++n) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, n);
     adj_record_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt - 1);
     return cudaGetLastError();
 }
@@ -331,9 +402,11 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
 {
     // the receiver term of step nt first; each step's extra block then
     // scatters the next step's
-    const dim3 grid(grid_blocks(g) + 1, n_inst);
+    const int tz = adj_rows_per_thread(g, n_inst);
+    const dim3 grid(tile_count(g, 8 * tz) + 1, n_inst);
+    const StepFn fn = step_fn(g.R, tz);
     adj_scatter_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
-    for (int k = g.nt; k >= 1; --k) step_fn(g.R)<<<grid, 256, 0, st>>>(g, insts, k);
+    for (int k = g.nt; k >= 1; --k) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, k);
     return cudaGetLastError();
 }
 
