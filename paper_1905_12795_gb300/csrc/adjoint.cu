@@ -25,6 +25,8 @@
 // the receiver transpose adds the four corner contributions in four ordered
 // passes into one of two separate fields, one step ahead, which the adjoint
 // step folds into mu.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace empso {
@@ -293,6 +295,16 @@ __global__ void adj_record_kernel(GridDev g, const AdjInst *__restrict__ insts, 
     }
 }
 
+// e_n = d_n - d_obs,n of every instance in place, where the on-chip forward
+// pass left its traces d_n = R u^{n+1} in E (blockIdx.y = instance)
+__global__ void adj_residual_kernel(const AdjInst *__restrict__ insts, int nt)
+{
+    const AdjInst in = insts[blockIdx.y];
+    const long long n = (long long)nt * in.nrec;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        in.E[i] -= in.dobs[i];
+}
+
 // phi of every instance: w/2 sum e^2, fixed reduction order (one block each)
 __global__ void adj_misfit_kernel(const AdjInst *__restrict__ insts, int nt, double *phi)
 {
@@ -394,6 +406,14 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
     const StepFn fn = fwd_fn(g.R);
     for (int n = 0; n < g.nt; ++n) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, n);
     adj_record_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt - 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_inst, int rec_max,
+                                cudaStream_t st)
+{
+    const long long n = (long long)g.nt * rec_max;
+    adj_residual_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 64), n_inst), 256, 0, st>>>(insts, g.nt);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,10 @@ struct empso_ctx {
         float *fv = nullptr;      // FWI vectors: trial model, gradients [3][np]
         size_t fv_cap = 0;
         double *fd = nullptr;     // FWI reductions [8] and misfit [1]
+        unsigned char *rtab = nullptr;   // on-chip forward pass: Inst [I], then work units [I]
+        size_t rtab_cap = 0;
+        int *counter = nullptr;          // its work queue
+        size_t counter_cap = 0;
         // forward + adjoint time loops captured once per grid, instance count
         // and instance table (their kernels read everything else from it)
         std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
@@ -768,6 +772,8 @@ void free_ctx(empso_ctx *c)
     for (auto &e : c->adj.graphs)
         if (e.second) cudaGraphExecDestroy(e.second);
     cudaFree(c->adj.fd);
+    cudaFree(c->adj.rtab);
+    cudaFree(c->adj.counter);
     cudaFree(c->pso_mem);
     cudaFree(c->pso_int);
     cudaFree(c->xf);
@@ -1075,7 +1081,10 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 8 * I, nullptr))) return rc;
     W.Q = W.mu + F * 3 * I;
     W.G = W.mu + F * 5 * I;
-    if ((rc = adj_grow(ctx, &W.E, &W.E_cap, (size_t)g.nt * rec_max * I, nullptr))) return rc;
+    // residuals in the modelling trace layout [model][shot][nt][nrec]
+    std::vector<long long> doff(S + 1, 0);
+    for (int s = 0; s < S; ++s) doff[s + 1] = doff[s] + (long long)g.nt * shots[s].nrec;
+    if ((rc = adj_grow(ctx, &W.E, &W.E_cap, (size_t)doff[S] * M, nullptr))) return rc;
     if ((rc = adj_grow(ctx, &W.insts, &W.inst_cap, (size_t)I, nullptr))) return rc;
     if ((rc = adj_grow(ctx, &W.phi, &W.phi_cap, (size_t)I, nullptr))) return rc;
     // zero halo rows and u^0 of the history whenever its layout changes
@@ -1086,10 +1095,39 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         W.layout = lay.str();
     }
     CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 8 * I, st));
-    // instance table (the previous call's kernels may still read the old one)
-    std::vector<long long> doff(S + 1, 0);
-    for (int s = 0; s < S; ++s) doff[s + 1] = doff[s] + (long long)g.nt * shots[s].nrec;
+    // The forward pass runs on the on-chip cluster kernel, which streams the
+    // history out beside its usual work, when the grid fits a cluster's shared
+    // memory (the cluster size that keeps the most SMs busy); else one
+    // tiled launch per step.
+    int rC = 0, r_threads = 0, r_nc = 0;
+    size_t r_smem = 0;
+    {
+        long long best = 0;
+        const int rpt = resident_rows_per_thread();
+        for (int C = 1; C <= 16; ++C) {
+            if (!resident_fits(g, C, rec_max, ctx->smem_optin)) continue;
+            const size_t sm = resident_smem_bytes(g, C, rec_max);
+            const int rows_c = (g.NZ + C - 1) / C;
+            const int items = std::max(32, g.NQ * ((rows_c + rpt - 1) / rpt));
+            const int threads = (items + 31) / 32 * 32;
+            const int nc = (int)std::min<long long>(resident_max_clusters(g.R, C, threads, sm), I);
+            if (nc > 0 && (long long)nc * C > best) {
+                best = (long long)nc * C;
+                rC = C;
+                r_threads = threads;
+                r_nc = nc;
+                r_smem = sm;
+            }
+        }
+    }
+    const size_t r_ofs = ((size_t)I * sizeof(Inst) + 255) / 256 * 256;
+    if (rC) {
+        if ((rc = adj_grow(ctx, &W.rtab, &W.rtab_cap, r_ofs + sizeof(int4) * (size_t)I, nullptr))) return rc;
+        if ((rc = adj_grow(ctx, &W.counter, &W.counter_cap, 1, nullptr))) return rc;
+    }
+    // instance tables (the previous call's kernels may still read the old ones)
     std::vector<AdjInst> hi((size_t)I);
+    std::vector<unsigned char> rh(rC ? r_ofs + sizeof(int4) * (size_t)I : 0);
     for (int m = 0; m < M; ++m)
         for (int s = 0; s < S; ++s) {
             const long long q = (long long)m * S + s;
@@ -1101,29 +1139,57 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             in.Q = W.Q + F * 2 * q;
             in.G = W.G + F * q;
             in.J = W.mu + F * 6 * I + F * 2 * q;
-            in.E = W.E + (size_t)g.nt * rec_max * q;
+            in.E = W.E + (size_t)doff[S] * m + doff[s];
             in.dobs = d_obs + doff[s];
             in.rec = ctx->rec_dev + shots[s].rec_begin;
             in.nrec = shots[s].nrec;
             in.sx = shots[s].sx;
             in.sz = shots[s].sz;
             in.w = shots[s].weight;
+            if (rC) {
+                Inst ri{};
+                ri.a = in.a;
+                ri.dobs = nullptr;        // traces only; the residual kernel subtracts d_obs
+                ri.traces = in.E;
+                ri.rec = in.rec;
+                ri.grid = gid;
+                ri.nrec = in.nrec;
+                ri.sx = in.sx;
+                ri.sz = in.sz;
+                ri.out = (int)q;
+                ri.hist = in.H;
+                reinterpret_cast<Inst *>(rh.data())[q] = ri;
+                reinterpret_cast<int4 *>(rh.data() + r_ofs)[q] = make_int4((int)q, -1, 0, 0);
+            }
         }
     CK(ctx, cudaStreamSynchronize(st));
     CK(ctx, cudaMemcpy(W.insts, hi.data(), sizeof(AdjInst) * hi.size(), cudaMemcpyHostToDevice));
+    if (rC) CK(ctx, cudaMemcpy(W.rtab, rh.data(), rh.size(), cudaMemcpyHostToDevice));
     const int rec_threads = std::min(1024, std::max(32, (rec_max + 31) / 32 * 32));
     CK(ctx, launch_vel_to_field(g, vel, M, W.a, g.field, st));
     CK(ctx, launch_adj_prep(g, W.a, W.B, M, st));
-    // the 5 nt launches of the two time loops replay as one graph
+    // the two time loops replay as one graph
     std::ostringstream key;
-    key << gid << "|" << I << "|" << rec_threads << "|" << (const void *)W.insts;
+    key << gid << "|" << I << "|" << rec_threads << "|" << (const void *)W.insts << "|" << rC << "|"
+        << (const void *)W.rtab;
     cudaGraphExec_t exec = nullptr;
     for (auto &e : W.graphs)
         if (e.first == key.str()) exec = e.second;
     if (!exec) {
         cudaGraph_t graph = nullptr;
         CK(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = launch_adj_forward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
+        cudaError_t ce;
+        if (rC) {
+            ce = cudaMemsetAsync(W.counter, 0, sizeof(int), ctx->cap_stream);
+            if (ce == cudaSuccess)
+                ce = launch_wave_resident(g.R, ctx->grids_dev, reinterpret_cast<const Inst *>(W.rtab),
+                                          reinterpret_cast<const int4 *>(W.rtab + r_ofs), (int)I, false,
+                                          W.counter, rC, r_nc, r_threads, rec_max, r_smem, W.phi,
+                                          ctx->cap_stream, true);
+            if (ce == cudaSuccess) ce = launch_adj_residual(g, W.insts, (int)I, rec_max, ctx->cap_stream);
+        } else {
+            ce = launch_adj_forward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
+        }
         if (ce == cudaSuccess) ce = launch_adj_backward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
         const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
         if (ce == cudaSuccess) ce = ee;

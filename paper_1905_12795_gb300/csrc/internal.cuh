@@ -69,6 +69,8 @@ struct Inst {
     float sx, sz;            // source position (m)
     int out;                 // slot of the partial misfit
     int pad_;
+    float *hist;             // [nt + 1][field] wavefield history (u^{n+1} into slot n + 1,
+                             // buffer layout), or null; the on-chip kernel's HIST variant only
 };
 
 // Host-side launchers (each enqueues on `st`).  Return cudaSuccess or the
@@ -94,6 +96,10 @@ struct AdjInst {
 cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, cudaStream_t st);
 cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                cudaStream_t st);
+// e = d - d_obs in place in every instance's E (after an on-chip forward pass
+// that wrote its traces there)
+cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_inst, int rec_max,
+                                cudaStream_t st);
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                 cudaStream_t st);
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
@@ -143,10 +149,12 @@ size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch);
 bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit);
 cudaError_t resident_configure(int R, size_t smem_bytes, int C);
 int resident_max_clusters(int R, int C, int threads, size_t smem_bytes);
+// `hist`: the variant that also streams every u^{n+1} into Inst::hist (no
+// halved units)
 cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, const int4 *units,
                                  int n_units, bool pairs,
                                  int *counter, int C, int n_clusters, int threads, int ring_pitch,
-                                 size_t smem_bytes, double *partial, cudaStream_t st);
+                                 size_t smem_bytes, double *partial, cudaStream_t st, bool hist = false);
 
 // TMA-pipelined streaming variant (wave_stream.cu).
 int stream_max_threads();

@@ -68,8 +68,8 @@ __device__ __forceinline__ void corners(float x, float z, const GridDev &g, int 
 }
 
 // C CTAs (ranks base .. base + C - 1 of the cluster; crank is the rank among
-// them) run instance `in`
-template <int R>
+// them) run instance `in`; with HIST every u^{n+1} also goes to in.hist
+template <int R, bool HIST>
 __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
                                   float4 *M4, float *ezs, float *wring, float *dring, float4 *rec_w,
                                   int *rec_k, int ring_pitch,
@@ -189,8 +189,13 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     const bool top_item = r0 < R;                        // may hold halo rows of the CTA above
     const bool bot_item = r0 + ROWS > rows_c - R;        // ... of the CTA below
 
+    // history: this item's first row in slot n + 1 (advanced one field per step)
+    float4 *hrow = nullptr;
+    if (HIST && active)
+        hrow = reinterpret_cast<float4 *>(in.hist) + (size_t)(z0 + r0 + HALO) * (pitch / 4) + 1 + q;
     float4 *cur = A4, *nxt = B4;
     for (int n = 0; n <= nt; ++n) {
+        if (HIST) hrow += gs.field / 4;
         // stage wavelet sample n + 1 and record n (sampled in step n + 1); their
         // slots were last read in step n - 1, which the previous barrier closed
         {
@@ -270,6 +275,7 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
                     const float4 out = make_float4(o01.x, o01.y, o23.x, o23.y);
                     if (k >= kfirst && k < klast) {
                         nxt[lr * sp4 + 1 + q] = out;
+                        if (HIST) __stcs(hrow + k * (pitch / 4), out);   // written once: evict first
                         // halo rows of the neighbours
                         const int rr = r0 + k;
                         if (top_item && prevA && rr < R) prevA[(rr + rows_c + R) * sp4 + 1 + q] = out;
@@ -336,7 +342,8 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
 // ranks C/2 .. C - 1 instance b, both of the same grid (so both halves pass
 // the same number of cluster barriers).  Launches with no halved unit use the
 // PAIRS = false instantiation, where the whole-cluster layout is constant.
-template <int R, int NT, bool PAIRS>
+// HIST (never with PAIRS) also writes the wavefield history.
+template <int R, int NT, bool PAIRS, bool HIST>
 __global__ void __launch_bounds__(NT, 1)
 wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts,
                      const int4 *__restrict__ units, int n_units, int *counter, int ring_pitch,
@@ -375,7 +382,7 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float *dring = wring + 4 * ((DEPTH + 3) / 4);
         float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
         int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
-        resident_instance<R>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, ring_pitch, Ce,
+        resident_instance<R, HIST>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, ring_pitch, Ce,
                              ce, sub * Ce, cluster, cred, wred, partial);
     }
 }
@@ -414,15 +421,15 @@ bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit)
 }
 
 namespace {
-template <int R, bool PAIRS>
+template <int R, bool PAIRS, bool HIST>
 cudaError_t configure_rp(size_t smem_bytes, int C)
 {
-    cudaError_t e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS>,
+    cudaError_t e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS, HIST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes);
     if (e != cudaSuccess) return e;
     if (C > 8)
-        e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS>,
+        e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS, HIST>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
@@ -430,22 +437,28 @@ cudaError_t configure_rp(size_t smem_bytes, int C)
 template <int R>
 cudaError_t configure_r(size_t smem_bytes, int C)
 {
-    cudaError_t e = configure_rp<R, false>(smem_bytes, C);
-    return e != cudaSuccess ? e : configure_rp<R, true>(smem_bytes, C);
+    cudaError_t e = configure_rp<R, false, false>(smem_bytes, C);
+    if (e == cudaSuccess) e = configure_rp<R, true, false>(smem_bytes, C);
+    return e != cudaSuccess ? e : configure_rp<R, false, true>(smem_bytes, C);
 }
 
 using ResidentFn = void (*)(const GridDev *, const Inst *, const int4 *, int, int *, int, double *);
 
-ResidentFn resident_fn(int R, bool pairs)
+ResidentFn resident_fn(int R, bool pairs, bool hist = false)
 {
-    if (pairs) {
-        if (R == 4) return wave_resident_kernel<4, RES_NT, true>;
-        if (R == 2) return wave_resident_kernel<2, RES_NT, true>;
-        return wave_resident_kernel<1, RES_NT, true>;
+    if (hist) {
+        if (R == 4) return wave_resident_kernel<4, RES_NT, false, true>;
+        if (R == 2) return wave_resident_kernel<2, RES_NT, false, true>;
+        return wave_resident_kernel<1, RES_NT, false, true>;
     }
-    if (R == 4) return wave_resident_kernel<4, RES_NT, false>;
-    if (R == 2) return wave_resident_kernel<2, RES_NT, false>;
-    return wave_resident_kernel<1, RES_NT, false>;
+    if (pairs) {
+        if (R == 4) return wave_resident_kernel<4, RES_NT, true, false>;
+        if (R == 2) return wave_resident_kernel<2, RES_NT, true, false>;
+        return wave_resident_kernel<1, RES_NT, true, false>;
+    }
+    if (R == 4) return wave_resident_kernel<4, RES_NT, false, false>;
+    if (R == 2) return wave_resident_kernel<2, RES_NT, false, false>;
+    return wave_resident_kernel<1, RES_NT, false, false>;
 }
 }  // namespace
 
@@ -479,7 +492,8 @@ int resident_max_clusters(int R, int C, int threads, size_t smem_bytes)
 
 cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, const int4 *units,
                                  int n_units, bool pairs, int *counter, int C, int n_clusters, int threads,
-                                 int ring_pitch, size_t smem_bytes, double *partial, cudaStream_t st)
+                                 int ring_pitch, size_t smem_bytes, double *partial, cudaStream_t st,
+                                 bool hist)
 {
     if (n_units <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
@@ -494,7 +508,7 @@ cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *in
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, resident_fn(R, pairs), grids_dev, insts, units, n_units, counter,
+    return cudaLaunchKernelEx(&cfg, resident_fn(R, pairs && !hist, hist), grids_dev, insts, units, n_units, counter,
                               ring_pitch, partial);
 }
 
