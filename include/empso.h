@@ -440,10 +440,14 @@ empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t n
  * ((nt + 1) x padded-grid floats each, e.g. 0.78 GB per shot of a 461 x 151
  * grid with 40 damping cells and 1414 steps), then the adjoint pass backward
  * in time accumulating sum_k mu^k f (L u^{k-1} + s^{k-1}), folded from the
- * damping pad onto the edge nodes and chained through a = v^2 dt^2.
+ * damping pad onto the edge nodes and chained through a = v^2 dt^2.  The
+ * forward pass runs on the on-chip kernel (history streamed out) when the
+ * kernel selection is EMPSO_KERNEL_AUTO or EMPSO_KERNEL_RESIDENT and the grid
+ * fits a cluster (RESIDENT: else UNSUPPORTED), otherwise as one launch per
+ * time step; the two agree to FP32 rounding.
  * misfit: device [M] doubles or NULL; grad: device [M][nz][nx].  d_obs as
  * for eval_models.  Synchronises `stream` once (instance table upload).
- * Errors: INVALID_ARG, OOM (history does not fit), CUDA_ERROR. */
+ * Errors: INVALID_ARG, OOM (history does not fit), UNSUPPORTED, CUDA_ERROR. */
 empso_status empso_gradient(empso_ctx *ctx, const float *vel, int32_t M,
                             const empso_shot *shots, int32_t S, const float *d_obs,
                             double *misfit, float *grad, void *stream);

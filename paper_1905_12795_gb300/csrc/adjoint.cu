@@ -86,8 +86,19 @@ constexpr int TW = 16, TILE_THREADS = TW * 8;
 
 __host__ __device__ inline int tiles_x(const GridDev &g) { return (g.NQ + TW - 1) / TW; }
 
+// 16-byte asynchronous global -> shared copy; an invalid cell is filled with
+// zeros and reads nothing (the source operand then only names the buffer)
+__device__ __forceinline__ void cp_async16_zfill(void *sdst, const void *gsrc, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // rows J0 - R .. J0 + TT - 1 + R, groups q0 - 1 .. q0 + TW of buffer U into
-// S[TT + 2R][TW + 2]; cells outside the buffer read as zero
+// S[TT + 2R][TW + 2] by asynchronous copies (complete after
+// cp_async_wait_all and a barrier); cells outside the buffer read as zero
 template <int R, int TT>
 __device__ __forceinline__ void stage_tile(float4 *S, const float4 *__restrict__ U, int J0, int q0,
                                            const GridDev &g)
@@ -97,8 +108,31 @@ __device__ __forceinline__ void stage_tile(float4 *S, const float4 *__restrict__
     for (int c = threadIdx.x; c < W * H; c += TILE_THREADS) {
         const int row = J0 - R + c / W + HALO;  // buffer row
         const int grp = q0 + c % W;             // buffer group of interior group q0 - 1 + c % W
-        S[c] = (row >= 0 && row < g.rows && grp < p4) ? U[(long long)row * p4 + grp]
-                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = row >= 0 && row < g.rows && grp < p4;
+        cp_async16_zfill(S + c, ok ? U + (long long)row * p4 + grp : U, ok);
+    }
+}
+
+// the same tile of the pointwise product of buffers X and Y (a fixed trip
+// count, so that every thread's loads can be in flight together)
+template <int R, int TT>
+__device__ __forceinline__ void stage_tile_product(float4 *S, const float4 *__restrict__ X,
+                                                   const float4 *__restrict__ Y, int J0, int q0,
+                                                   const GridDev &g)
+{
+    constexpr int W = TW + 2, H = TT + 2 * R, NIT = (W * H + TILE_THREADS - 1) / TILE_THREADS;
+    const int p4 = g.pitch / 4;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int c = threadIdx.x + it * TILE_THREADS;
+        const int row = J0 - R + c / W + HALO;
+        const int grp = q0 + c % W;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < W * H && row >= 0 && row < g.rows && grp < p4) {
+            const float4 x = X[(long long)row * p4 + grp], y = Y[(long long)row * p4 + grp];
+            v = make_float4(x.x * y.x, x.y * y.y, x.z * y.z, x.w * y.w);
+        }
+        if (c < W * H) S[c] = v;
     }
 }
 
@@ -161,6 +195,7 @@ __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const 
     float4 *u1 = reinterpret_cast<float4 *>(in.H + (long long)(n + 1) * g.field);
     const float4 *a4 = reinterpret_cast<const float4 *>(in.a);
     stage_tile<R, TT>(S, u, J0, q0, g);
+    cp_async_wait_all();
     __syncthreads();
     const int lx = threadIdx.x % TW, ly = threadIdx.x / TW, q = q0 + lx;
     if (q >= g.NQ) return;
@@ -213,9 +248,11 @@ __global__ void adj_scatter_kernel(GridDev g, const AdjInst *__restrict__ insts,
 }
 
 // One adjoint step k, per point:
-//   mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} + J^k   (J^k then cleared)
-//   Q^k  = f a mu^k,   G += mu^k f (L u^{k-1} + s^{k-1})
-// Block 0 meanwhile scatters J^{k-1} into the other J slot for the next step.
+//   mu^k = 2 f mu^{k+1} + L Q^{k+1} - g mu^{k+2} + J^k   (J^k then cleared),
+//   G += mu^k f (L u^{k-1} + s^{k-1}),
+// with Q^{k+1} = f a mu^{k+1} formed as the tile is staged.  J is read only
+// on the instance's receiver rows.  Block 0 meanwhile scatters J^{k-1} into
+// the other J slot for the next step.
 template <int R, int TZ>
 __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts,
                                                                    int k)
@@ -233,14 +270,13 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
     float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 3) * g.field);
     const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 3) * g.field);
     const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 3) * g.field);
-    const float4 *q1 = reinterpret_cast<const float4 *>(in.Q + (long long)((k + 1) % 2) * g.field);
-    float4 *qk = reinterpret_cast<float4 *>(in.Q + (long long)(k % 2) * g.field);
     float4 *J4 = reinterpret_cast<float4 *>(in.J + (long long)(k % 2) * g.field);
     const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(k - 1) * g.field);
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
     float4 *G4 = reinterpret_cast<float4 *>(in.G);
-    stage_tile<R, TT>(SQ, q1, J0, q0, g);
-    stage_tile<R, TT>(SU, u, J0, q0, g);
+    stage_tile<R, TT>(SU, u, J0, q0, g);                  // in flight during the product tile
+    stage_tile_product<R, TT>(SQ, B4, m1, J0, q0, g);
+    cp_async_wait_all();
     __syncthreads();
     const int lx = threadIdx.x % TW, ly = threadIdx.x / TW, q = q0 + lx;
     if (q >= g.NQ) return;
@@ -255,12 +291,13 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
         const float4 lq = lap4_tile<R>(SQ, sr, lx + 1, g);
         const float4 lu = lap4_tile<R>(SU, sr, lx + 1, g);
-        const float4 a1 = m1[k4], a2 = m2[k4], b = B4[k4];
-        const float4 jj = J4[k4];
+        const float4 a1 = m1[k4], a2 = m2[k4];
+        const bool jrow = J >= in.jr0 && J <= in.jr1;
+        const float4 jj = jrow ? J4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
         if (jj.x != 0.f || jj.y != 0.f || jj.z != 0.f || jj.w != 0.f) J4[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 gg = G4[k4];
         const float ez = g.ez[J + HALO];
-        float mo[4], qo[4], go[4];
+        float mo[4], go[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int I = 4 * q + i;
@@ -270,12 +307,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
                                            lane_of(jj, i)
                                      : 0.f;
             mo[i] = m;
-            qo[i] = lane_of(b, i) * m;
             const float li = fmaf(src_weight(sc, I, J), rn, lane_of(lu, i));
             go[i] = fmaf(m / (1.f + t), li, lane_of(gg, i));
         }
         mk[k4] = make_float4(mo[0], mo[1], mo[2], mo[3]);
-        qk[k4] = make_float4(qo[0], qo[1], qo[2], qo[3]);
         G4[k4] = make_float4(go[0], go[1], go[2], go[3]);
     }
 }
@@ -327,12 +362,33 @@ __global__ void adj_misfit_kernel(const AdjInst *__restrict__ insts, int nt, dou
     }
 }
 
-// per model m: misfit = sum over shots (shot order); dphi/dv at physical node
-// (i, j) = 2 v dt^2 sum_shots sum of G over the padded nodes whose edge
-// extension reads (i, j)
-__global__ void adj_fold_kernel(GridDev g, const AdjInst *__restrict__ insts, int S,
-                                const float *__restrict__ vel, const double *phi, double *misfit,
-                                float *grad)
+// The fold of dphi/da from the padded grid onto the physical nodes is the
+// transpose of the edge extension, separable in x and z: pass 1 sums, per
+// padded row J and physical column i, every shot's G over the padded columns
+// whose extension reads column i (one column inside, the pad and the edge
+// column at either side) into T[m][J][i]; pass 2 sums T over the padded rows
+// that read physical row j and chains to v: dphi/dv = 2 v dt^2 dphi/da.
+__global__ void adj_fold_x_kernel(GridDev g, const AdjInst *__restrict__ insts, int S, float *T)
+{
+    const int m = blockIdx.y;
+    const long long n = (long long)g.NZ * g.nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / g.nx), i = (int)(e % g.nx);
+        const int I0 = i == 0 ? 0 : i + g.pad, I1 = i == g.nx - 1 ? g.NX - 1 : i + g.pad;
+        float acc = 0.f;
+        for (int s = 0; s < S; ++s) {
+            const float *G = insts[m * S + s].G + (long long)(J + HALO) * g.pitch + HALO;
+            for (int I = I0; I <= I1; ++I) acc += G[I];
+        }
+        T[(long long)m * n + e] = acc;
+    }
+}
+
+// pass 2, and per model m the misfit = sum over shots (shot order)
+__global__ void adj_fold_z_kernel(GridDev g, int S, const float *__restrict__ T,
+                                  const float *__restrict__ vel, const double *phi, double *misfit,
+                                  float *grad)
 {
     const int m = blockIdx.y;
     const int np = g.nx * g.nz;
@@ -341,16 +397,12 @@ __global__ void adj_fold_kernel(GridDev g, const AdjInst *__restrict__ insts, in
         for (int s = 0; s < S; ++s) v += phi[m * S + s];
         misfit[m] = isfinite(v) ? v : __longlong_as_double(0x7ff0000000000000LL);
     }
+    const float *Tm = T + (long long)m * g.NZ * g.nx;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < np; e += gridDim.x * blockDim.x) {
         const int j = e / g.nx, i = e % g.nx;
-        const int I0 = i == 0 ? 0 : i + g.pad, I1 = i == g.nx - 1 ? g.NX - 1 : i + g.pad;
         const int J0 = j == 0 ? 0 : j + g.pad, J1 = j == g.nz - 1 ? g.NZ - 1 : j + g.pad;
         float acc = 0.f;
-        for (int s = 0; s < S; ++s) {
-            const float *G = insts[m * S + s].G;
-            for (int J = J0; J <= J1; ++J)
-                for (int I = I0; I <= I1; ++I) acc += G[(long long)(J + HALO) * g.pitch + I + HALO];
-        }
+        for (int J = J0; J <= J1; ++J) acc += Tm[(long long)J * g.nx + i];
         const float v = vel[(long long)m * np + e];
         grad[(long long)m * np + e] = 2.f * v * g.dt * g.dt * acc;
     }
@@ -431,11 +483,13 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
 }
 
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
-                              double *phi, double *misfit, float *grad, cudaStream_t st)
+                              double *phi, double *misfit, float *grad, float *T, cudaStream_t st)
 {
     adj_misfit_kernel<<<M * S, 256, 0, st>>>(insts, g.nt, phi);
+    const long long nT = (long long)g.NZ * g.nx;
+    adj_fold_x_kernel<<<dim3((unsigned)((nT + 255) / 256), M), 256, 0, st>>>(g, insts, S, T);
     const int np = g.nx * g.nz;
-    adj_fold_kernel<<<dim3((np + 255) / 256, M), 256, 0, st>>>(g, insts, S, vel, phi, misfit, grad);
+    adj_fold_z_kernel<<<dim3((np + 255) / 256, M), 256, 0, st>>>(g, S, T, vel, phi, misfit, grad);
     return cudaGetLastError();
 }
 

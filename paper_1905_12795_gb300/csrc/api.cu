@@ -102,7 +102,7 @@ struct empso_ctx {
 
     // adjoint-state gradient workspace (grown on demand)
     struct AdjWork {
-        float *a = nullptr, *B = nullptr, *H = nullptr, *mu = nullptr, *Q = nullptr, *G = nullptr,
+        float *a = nullptr, *B = nullptr, *H = nullptr, *mu = nullptr, *G = nullptr,
               *E = nullptr;
         size_t a_cap = 0, H_cap = 0, mu_cap = 0, E_cap = 0;   // floats
         AdjInst *insts = nullptr;
@@ -762,7 +762,7 @@ void free_ctx(empso_ctx *c)
     cudaFree(c->counter);
     cudaFree(c->dev_err);
     cudaFree(c->nonfinite);
-    cudaFree(c->adj.a);       // B lies inside a; Q, G and J inside mu
+    cudaFree(c->adj.a);       // B lies inside a; G and J inside mu
     cudaFree(c->adj.H);
     cudaFree(c->adj.mu);
     cudaFree(c->adj.E);
@@ -1078,9 +1078,9 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     if ((rc = adj_grow(ctx, &W.a, &W.a_cap, 2 * F * M, nullptr))) return rc;
     W.B = W.a + F * M;
     if ((rc = adj_grow(ctx, &W.H, &W.H_cap, F * (size_t)(g.nt + 1) * I, &grewH))) return rc;
-    if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 8 * I, nullptr))) return rc;
-    W.Q = W.mu + F * 3 * I;
-    W.G = W.mu + F * 5 * I;
+    // per instance: mu [3], G, J [2]
+    if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 6 * I, nullptr))) return rc;
+    W.G = W.mu + F * 3 * I;
     // residuals in the modelling trace layout [model][shot][nt][nrec]
     std::vector<long long> doff(S + 1, 0);
     for (int s = 0; s < S; ++s) doff[s + 1] = doff[s] + (long long)g.nt * shots[s].nrec;
@@ -1094,14 +1094,15 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         CK(ctx, cudaMemsetAsync(W.H, 0, sizeof(float) * F * (size_t)(g.nt + 1) * I, st));
         W.layout = lay.str();
     }
-    CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 8 * I, st));
+    CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 6 * I, st));
     // The forward pass runs on the on-chip cluster kernel, which streams the
-    // history out beside its usual work, when the grid fits a cluster's shared
-    // memory (the cluster size that keeps the most SMs busy); else one
-    // tiled launch per step.
+    // history out beside its usual work, when the kernel selection allows it
+    // and the grid fits a cluster's shared memory (the cluster size that
+    // keeps the most SMs busy); else one tiled launch per step.
     int rC = 0, r_threads = 0, r_nc = 0;
     size_t r_smem = 0;
-    {
+    const bool want_res = ctx->kernel_kind == EMPSO_KERNEL_AUTO || ctx->kernel_kind == EMPSO_KERNEL_RESIDENT;
+    if (want_res) {
         long long best = 0;
         const int rpt = resident_rows_per_thread();
         for (int C = 1; C <= 16; ++C) {
@@ -1120,6 +1121,8 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             }
         }
     }
+    if (ctx->kernel_kind == EMPSO_KERNEL_RESIDENT && !rC)
+        return fail(ctx, EMPSO_UNSUPPORTED, "gradient: the grid does not fit the on-chip kernel");
     const size_t r_ofs = ((size_t)I * sizeof(Inst) + 255) / 256 * 256;
     if (rC) {
         if ((rc = adj_grow(ctx, &W.rtab, &W.rtab_cap, r_ofs + sizeof(int4) * (size_t)I, nullptr))) return rc;
@@ -1136,9 +1139,8 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             in.B = W.B + F * m;
             in.H = W.H + F * (size_t)(g.nt + 1) * q;
             in.mu = W.mu + F * 3 * q;
-            in.Q = W.Q + F * 2 * q;
             in.G = W.G + F * q;
-            in.J = W.mu + F * 6 * I + F * 2 * q;
+            in.J = W.mu + F * 4 * I + F * 2 * q;
             in.E = W.E + (size_t)doff[S] * m + doff[s];
             in.dobs = d_obs + doff[s];
             in.rec = ctx->rec_dev + shots[s].rec_begin;
@@ -1146,6 +1148,16 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             in.sx = shots[s].sx;
             in.sz = shots[s].sz;
             in.w = shots[s].weight;
+            // padded rows of the receivers' bilinear corners, one row of margin
+            // either side of the device's rounding
+            in.jr0 = g.NZ;
+            in.jr1 = -1;
+            for (int r = 0; r < shots[s].nrec; ++r) {
+                const float fz = ctx->rec_host[2 * ((size_t)shots[s].rec_begin + r) + 1] / g.hz + (float)g.pad;
+                const int j0 = std::min(std::max((int)std::floor(fz), 0), g.NZ - 2);
+                in.jr0 = std::min(in.jr0, j0 - 1);
+                in.jr1 = std::max(in.jr1, j0 + 2);
+            }
             if (rC) {
                 Inst ri{};
                 ri.a = in.a;
@@ -1200,7 +1212,8 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         W.graphs.push_back({key.str(), exec});
     }
     CK(ctx, cudaGraphLaunch(exec, st));
-    CK(ctx, launch_adj_finish(g, W.insts, M, S, vel, W.phi, misfit, grad, st));
+    // the fold's scratch takes the adjoint fields' slots (free now; G lies past them)
+    CK(ctx, launch_adj_finish(g, W.insts, M, S, vel, W.phi, misfit, grad, W.mu, st));
     return EMPSO_OK;
 }
 

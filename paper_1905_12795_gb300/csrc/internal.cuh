@@ -84,7 +84,6 @@ struct AdjInst {
     const float *B;      // f a, f = 1 / (1 + t)
     float *H;            // wavefield history [nt + 1][field], H[n] = u^n
     float *mu;           // adjoint fields, 3 rolling buffers [3][field]
-    float *Q;            // f a mu, 2 rolling buffers [2][field]
     float *G;            // dphi/da of this shot [field]
     float *J;            // receiver terms w R^T e of two adjoint steps [2][field], zero elsewhere
     float *E;            // residuals [nt][nrec]
@@ -92,6 +91,7 @@ struct AdjInst {
     const float2 *rec;   // receiver positions
     int nrec;
     float sx, sz, w;     // source position, shot weight
+    int jr0, jr1;        // padded rows that may hold a receiver term (J is zero elsewhere)
 };
 cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, cudaStream_t st);
 cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
@@ -102,8 +102,9 @@ cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_in
                                 cudaStream_t st);
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                 cudaStream_t st);
+// T: scratch of M * NZ * nx floats (the x-folded gradient)
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
-                              double *phi, double *misfit, float *grad, cudaStream_t st);
+                              double *phi, double *misfit, float *grad, float *T, cudaStream_t st);
 cudaError_t launch_fwi_step(const float *v, const float *g, float alpha, float vmin, float vmax,
                             float *out, int n, cudaStream_t st);
 cudaError_t launch_fwi_dots(const float *a, const float *b, const float *c, const float *d, int n,

@@ -30,8 +30,9 @@ def _dev(a, dtype=torch.float32):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
+@pytest.mark.parametrize("kernel", [0, 1])   # forward pass: on-chip kernel / one launch per step
 @pytest.mark.parametrize("order", [4, 8])
-def test_gradient_matches_oracle_directional_derivatives(B, order):
+def test_gradient_matches_oracle_directional_derivatives(B, order, kernel):
     nx, nz, h, pad, T, f0, vmax = 41, 31, 10.0, 8, 0.25, 15.0, 3000.0
     og = oracle.Grid(nx, nz, h, h, pad, order, T, f0, vmax)
     v = synth.layered_faulted_model(nx, nz, h, h, seed=5, vmin=1500.0, vmax=2800.0)
@@ -49,6 +50,7 @@ def test_gradient_matches_oracle_directional_derivatives(B, order):
 
     grid = B.make_grid(nx, nz, h, h, pad, order, T, f0, 1500.0, vmax)
     ctx = B.Context([grid], rec)
+    ctx.set_kernel(kernel)
     sh = B.make_shots(shots, rb, rc, weights=w)
     dobs = _dev(np.concatenate([o.ravel() for o in obs]))
     g = torch.zeros(1, nz, nx, device="cuda")
@@ -59,6 +61,7 @@ def test_gradient_matches_oracle_directional_derivatives(B, order):
     assert mis.item() == pytest.approx(phi0, rel=1e-4)
     # the same misfit as the modelling kernels give
     m2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.set_kernel(0)
     ctx.eval_models(_dev(v[None]), sh, dobs, m2)
     assert m2.item() == pytest.approx(mis.item(), rel=1e-5)
     rng = np.random.default_rng(order)
@@ -92,6 +95,14 @@ def test_gradient_batch_of_models_equals_single_calls(B):
         m1 = torch.zeros(1, dtype=torch.float64, device="cuda")
         ctx.gradient(_dev(vs[k:k + 1]), sh, dobs, g1, m1)
         assert torch.equal(g1[0], g3[k]) and m1.item() == m3[k].item()
+    # the per-step forward pass agrees with the on-chip one to FP32 rounding
+    ctx.set_kernel(1)
+    gs = torch.zeros(3, nz, nx, device="cuda")
+    ms = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx.gradient(_dev(vs), sh, dobs, gs, ms)
+    scale = float(g3.abs().max())
+    assert float((gs - g3).abs().max()) <= 1e-4 * scale
+    assert torch.allclose(ms, m3, rtol=1e-5)
     ctx.close()
 
 
