@@ -931,7 +931,6 @@ def run_fwi(a):
                        "misfit_history": hist, "model_rel_l2": err(vel),
                        "wall_s": time.perf_counter() - t0})
         cb.close()
-    grad_line.pop("history_bytes")
     line = {"metric": "EMPSO + multiscale local FWI: model error per stage; adjoint gradient time",
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": "fwi-461x151-S16", "grid": f"{gs.nx}x{gs.nz}@{gs.hx:g}m",

@@ -340,14 +340,20 @@ __global__ void adj_residual_kernel(const AdjInst *__restrict__ insts, int nt)
         in.E[i] -= in.dobs[i];
 }
 
-// phi of every instance: w/2 sum e^2, fixed reduction order (one block each)
-__global__ void adj_misfit_kernel(const AdjInst *__restrict__ insts, int nt, double *phi)
+// phi of every instance: w/2 sum e^2 in a fixed order.  Pass 1: block b of
+// instance q (blockIdx.y) sums chunk b of its residuals into part[q][b];
+// pass 2 adds the MISFIT_PARTS partials in order.
+constexpr int MISFIT_PARTS = 64;
+
+__global__ void adj_misfit_part_kernel(const AdjInst *__restrict__ insts, int nt, double *part)
 {
-    const AdjInst in = insts[blockIdx.x];
+    const AdjInst in = insts[blockIdx.y];
     __shared__ double red[32];
-    double s = 0.0;
     const long long n = (long long)nt * in.nrec;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const long long chunk = (n + MISFIT_PARTS - 1) / MISFIT_PARTS;
+    const long long i0 = blockIdx.x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
+    double s = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const double e = in.E[i];
         s += e * e;
     }
@@ -358,8 +364,18 @@ __global__ void adj_misfit_kernel(const AdjInst *__restrict__ insts, int nt, dou
     if (threadIdx.x == 0) {
         double v = 0.0;
         for (int w = 0; w < (int)blockDim.x / 32; ++w) v += red[w];
-        phi[blockIdx.x] = 0.5 * (double)in.w * v;
+        part[(long long)blockIdx.y * MISFIT_PARTS + blockIdx.x] = v;
     }
+}
+
+__global__ void adj_misfit_sum_kernel(const AdjInst *__restrict__ insts, int n_inst, const double *part,
+                                      double *phi)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_inst) return;
+    double v = 0.0;
+    for (int b = 0; b < MISFIT_PARTS; ++b) v += part[(long long)q * MISFIT_PARTS + b];
+    phi[q] = 0.5 * (double)insts[q].w * v;
 }
 
 // The fold of dphi/da from the padded grid onto the physical nodes is the
@@ -485,7 +501,11 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
                               double *phi, double *misfit, float *grad, float *T, cudaStream_t st)
 {
-    adj_misfit_kernel<<<M * S, 256, 0, st>>>(insts, g.nt, phi);
+    // the misfit partials borrow the fold's scratch, which pass 1 of the fold
+    // overwrites only after they are summed
+    double *part = reinterpret_cast<double *>(T);
+    adj_misfit_part_kernel<<<dim3(MISFIT_PARTS, M * S), 256, 0, st>>>(insts, g.nt, part);
+    adj_misfit_sum_kernel<<<(M * S + 127) / 128, 128, 0, st>>>(insts, M * S, part, phi);
     const long long nT = (long long)g.NZ * g.nx;
     adj_fold_x_kernel<<<dim3((unsigned)((nT + 255) / 256), M), 256, 0, st>>>(g, insts, S, T);
     const int np = g.nx * g.nz;

@@ -102,7 +102,8 @@ cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_in
                                 cudaStream_t st);
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                 cudaStream_t st);
-// T: scratch of M * NZ * nx floats (the x-folded gradient)
+// T: scratch of max(M * NZ * nx floats, M * S * 64 doubles), 8-byte aligned
+// (the misfit partials, then the x-folded gradient)
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
                               double *phi, double *misfit, float *grad, float *T, cudaStream_t st);
 cudaError_t launch_fwi_step(const float *v, const float *g, float alpha, float vmin, float vmax,
