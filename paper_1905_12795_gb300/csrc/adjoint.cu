@@ -17,12 +17,14 @@
 // transpose of the edge extension into the damping pad) and chained to the
 // velocity: dphi/dv = 2 v dt^2 dphi/da.
 //
-// Every kernel runs over all instances at once (blockIdx.y = instance): one
-// forward launch per time step (which also records the previous step's
-// residuals) and one per adjoint step (the two time loops replay as one CUDA
-// graph); the per-point kernels stage the fields their Laplacians read in
-// shared-memory tiles and give each thread a few rows of one float4 group;
-// the receiver transpose adds the four corner contributions in four ordered
+// The forward pass normally runs on the on-chip modelling kernel, which
+// streams the history out (wave_resident.cu) and leaves its traces for
+// adj_residual_kernel; adj_fwd_kernel is the per-step form for grids it
+// cannot hold.  The per-step kernels here run over all instances at once
+// (blockIdx.y = instance), one launch per time step (the time loops replay as
+// one CUDA graph).  They stage the fields their Laplacians read in
+// shared-memory tiles and give each thread a few rows of one float4 group.
+// The receiver transpose adds the four corner contributions in four ordered
 // passes into one of two separate fields, one step ahead, which the adjoint
 // step folds into mu.
 #include <algorithm>
