@@ -106,6 +106,35 @@ def test_gradient_batch_of_models_equals_single_calls(B):
     ctx.close()
 
 
+def test_gradient_edge_cases(B):
+    nx, nz, h = 37, 29, 10.0
+    grid = B.make_grid(nx, nz, h, h, 6, 8, 0.2, 15.0, 1500.0, 3000.0)
+    rec = synth.receiver_line(nx, h, 20.0)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    v = _dev(synth.layered_faulted_model(nx, nz, h, h, seed=4, vmin=1500.0, vmax=2800.0)[None])
+    dobs = torch.randn(nt * nx, device="cuda") * 1e-3
+    g1 = torch.zeros(1, nz, nx, device="cuda")
+    m1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.gradient(v, B.make_shots([(120.0, 20.0)], [0], [nx]), dobs, g1, m1)
+    assert m1.item() > 0.0 and float(g1.abs().max()) > 0.0
+    # a shot without receivers has no residual, no adjoint source and zero
+    # misfit: adding it changes neither the gradient nor the misfit
+    g2 = torch.zeros(1, nz, nx, device="cuda")
+    m2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.gradient(v, B.make_shots([(120.0, 20.0), (250.0, 20.0)], [0, 0], [nx, 0]), dobs, g2, m2)
+    assert torch.equal(g1, g2) and m1.item() == m2.item()
+    # invalid arguments are refused before any launch
+    sh = B.make_shots([(120.0, 20.0)], [0], [nx])
+    with pytest.raises(B.EmpsoError) as e:
+        ctx.gradient(v[:0], sh, dobs, g1)
+    assert e.value.status == 1
+    with pytest.raises(B.EmpsoError) as e:
+        ctx.gradient(v, B.make_shots([(-5.0, 20.0)], [0], [nx]), dobs, g1)
+    assert e.value.status == 1
+    ctx.close()
+
+
 def test_fwi_descends_and_improves_the_model(B):
     nx, nz, h, pad = 61, 41, 10.0, 10
     grid = B.make_grid(nx, nz, h, h, pad, 4, 0.45, 12.0, 1400.0, 3000.0)
