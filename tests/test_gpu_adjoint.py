@@ -77,6 +77,46 @@ def test_gradient_matches_oracle_directional_derivatives(B, order, kernel):
     ctx.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("order", [4, 8])
+def test_gradient_field_matches_oracle_at_every_node(B, order, kernel):
+    """The whole dphi/dv field against FP64 central differences of the oracle
+    misfit at every physical node of a tiny grid, edge and corner nodes
+    (whose sensitivity includes the folded damping pad) included."""
+    nx, nz, h, pad, T, f0, vmax = 14, 11, 10.0, 4, 0.1, 25.0, 3000.0
+    og = oracle.Grid(nx, nz, h, h, pad, order, T, f0, vmax)
+    v = synth.layered_faulted_model(nx, nz, h, h, seed=5, vmin=1500.0, vmax=2800.0)
+    v_true = synth.layered_faulted_model(nx, nz, h, h, seed=6, vmin=1500.0, vmax=2800.0)
+    shots = np.array([[35.0, 23.0], [97.0, 61.0]])
+    rec = synth.receiver_line(nx, h, 15.0)[:-1] + np.array([3.7, 0.0])
+    nrec = len(rec)
+    rb, rc = [0, 0], [nrec, nrec]
+    _, obs = oracle.shot_batch(og, v_true, shots, rec, rb, rc, want_traces=True)
+
+    def phi(vel):
+        p, _ = oracle.shot_batch(og, vel, shots, rec, rb, rc, dobs=obs)
+        return float(np.sum(p[0]))
+
+    ref = np.zeros((nz, nx))
+    for j in range(nz):
+        for i in range(nx):
+            d = np.zeros((nz, nx))
+            d[j, i] = 1.0
+            ref[j, i] = (phi(v + d) - phi(v - d)) / 2.0
+    grid = B.make_grid(nx, nz, h, h, pad, order, T, f0, 1500.0, vmax)
+    ctx = B.Context([grid], rec)
+    ctx.set_kernel(kernel)
+    g = torch.zeros(1, nz, nx, device="cuda")
+    ctx.gradient(_dev(v[None]), B.make_shots(shots, rb, rc),
+                 _dev(np.concatenate([o.ravel() for o in obs])), g)
+    got = g[0].cpu().numpy().astype(np.float64)
+    scale = np.abs(ref).max()
+    assert scale > 0.0
+    assert np.abs(got - ref).max() <= 1e-2 * scale
+    assert np.linalg.norm(got - ref) <= 5e-3 * np.linalg.norm(ref)
+    ctx.close()
+
+
 def test_gradient_batch_of_models_equals_single_calls(B):
     nx, nz, h = 37, 29, 10.0
     grid = B.make_grid(nx, nz, h, h, 6, 4, 0.2, 15.0, 1500.0, 3000.0)
