@@ -443,8 +443,11 @@ empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t n
  * damping pad onto the edge nodes and chained through a = v^2 dt^2.  The
  * forward pass runs on the on-chip kernel (history streamed out) when the
  * kernel selection is EMPSO_KERNEL_AUTO or EMPSO_KERNEL_RESIDENT and the grid
- * fits a cluster (RESIDENT: else UNSUPPORTED), otherwise as one launch per
- * time step; the two agree to FP32 rounding.
+ * fits a cluster (RESIDENT: else UNSUPPORTED); else on the L2 cluster kernel
+ * (also streaming the history out) when the selection is EMPSO_KERNEL_AUTO or
+ * EMPSO_KERNEL_CLUSTER_L2 and the grid fits it (CLUSTER_L2: else
+ * UNSUPPORTED); otherwise (EMPSO_KERNEL_STREAMING) as one launch per time
+ * step.  All agree to FP32 rounding.
  * misfit: device [M] doubles or NULL; grad: device [M][nz][nx].  d_obs as
  * for eval_models.  Synchronises `stream` once (instance table upload).
  * Errors: INVALID_ARG, OOM (history does not fit), UNSUPPORTED, CUDA_ERROR. */

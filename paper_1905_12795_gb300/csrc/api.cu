@@ -117,6 +117,8 @@ struct empso_ctx {
         size_t rtab_cap = 0;
         int *counter = nullptr;          // its work queue
         size_t counter_cap = 0;
+        float4 *slots = nullptr;         // L2 cluster forward pass: two time levels per cluster
+        size_t slots_cap = 0;
         // forward + adjoint time loops captured once per grid, instance count
         // and instance table (their kernels read everything else from it)
         std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
@@ -774,6 +776,7 @@ void free_ctx(empso_ctx *c)
     cudaFree(c->adj.fd);
     cudaFree(c->adj.rtab);
     cudaFree(c->adj.counter);
+    cudaFree(c->adj.slots);
     cudaFree(c->pso_mem);
     cudaFree(c->pso_int);
     cudaFree(c->xf);
@@ -1123,14 +1126,49 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     }
     if (ctx->kernel_kind == EMPSO_KERNEL_RESIDENT && !rC)
         return fail(ctx, EMPSO_UNSUPPORTED, "gradient: the grid does not fit the on-chip kernel");
+    // else the L2 cluster kernel, also streaming the history out, when the
+    // selection allows it and the grid fits: the cluster size that keeps the
+    // most SMs busy with the instances in flight inside the L2 budget
+    int lC = 0, l_threads = 0, l_nc = 0;
+    long long l_slot = 0;
+    size_t l_smem = 0;
+    if (!rC && (ctx->kernel_kind == EMPSO_KERNEL_AUTO || ctx->kernel_kind == EMPSO_KERNEL_CLUSTER_L2)) {
+        const size_t sm = l2_smem_bytes(rec_max);
+        long long best = 0;
+        for (int C : {16, 12, 10, 8, 6, 4, 3, 2, 1}) {
+            if (sm > ctx->smem_optin || !l2_fits(g, C)) continue;
+            const long long slot = l2_slot_f4(g, C);
+            const long long inst_bytes = 32 * slot + 4 * g.field;
+            const int rows_c = (g.NZ + C - 1) / C;
+            const long long items = std::max<long long>(32, (long long)g.NQ * ((rows_c + 7) / 8));
+            const int threads = (int)std::min<long long>(l2_max_threads(), (items + 31) / 32 * 32);
+            CK(ctx, l2_configure(g.R, sm, C));
+            const int occ = l2_max_clusters(g.R, C, threads, sm);
+            if (occ <= 0) continue;
+            const long long by_l2 = std::max<long long>(1, L2_BUDGET_BYTES / inst_bytes);
+            const int nc = (int)std::min<long long>(std::min<long long>(occ, I), by_l2);
+            if ((long long)nc * C > best) {
+                best = (long long)nc * C;
+                lC = C;
+                l_threads = threads;
+                l_nc = nc;
+                l_slot = slot;
+                l_smem = sm;
+            }
+        }
+    }
+    if (ctx->kernel_kind == EMPSO_KERNEL_CLUSTER_L2 && !lC)
+        return fail(ctx, EMPSO_UNSUPPORTED, "gradient: the grid does not fit the L2 cluster kernel");
     const size_t r_ofs = ((size_t)I * sizeof(Inst) + 255) / 256 * 256;
-    if (rC) {
+    const bool table = rC || lC;
+    if (table) {
         if ((rc = adj_grow(ctx, &W.rtab, &W.rtab_cap, r_ofs + sizeof(int4) * (size_t)I, nullptr))) return rc;
         if ((rc = adj_grow(ctx, &W.counter, &W.counter_cap, 1, nullptr))) return rc;
     }
+    if (lC && (rc = adj_grow(ctx, &W.slots, &W.slots_cap, 2 * (size_t)l_slot * l_nc, nullptr))) return rc;
     // instance tables (the previous call's kernels may still read the old ones)
     std::vector<AdjInst> hi((size_t)I);
-    std::vector<unsigned char> rh(rC ? r_ofs + sizeof(int4) * (size_t)I : 0);
+    std::vector<unsigned char> rh(table ? r_ofs + sizeof(int4) * (size_t)I : 0);
     for (int m = 0; m < M; ++m)
         for (int s = 0; s < S; ++s) {
             const long long q = (long long)m * S + s;
@@ -1158,7 +1196,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
                 in.jr0 = std::min(in.jr0, j0 - 1);
                 in.jr1 = std::max(in.jr1, j0 + 2);
             }
-            if (rC) {
+            if (table) {
                 Inst ri{};
                 ri.a = in.a;
                 ri.dobs = nullptr;        // traces only; the residual kernel subtracts d_obs
@@ -1176,14 +1214,14 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         }
     CK(ctx, cudaStreamSynchronize(st));
     CK(ctx, cudaMemcpy(W.insts, hi.data(), sizeof(AdjInst) * hi.size(), cudaMemcpyHostToDevice));
-    if (rC) CK(ctx, cudaMemcpy(W.rtab, rh.data(), rh.size(), cudaMemcpyHostToDevice));
+    if (table) CK(ctx, cudaMemcpy(W.rtab, rh.data(), rh.size(), cudaMemcpyHostToDevice));
     const int rec_threads = std::min(1024, std::max(32, (rec_max + 31) / 32 * 32));
     CK(ctx, launch_vel_to_field(g, vel, M, W.a, g.field, st));
     CK(ctx, launch_adj_prep(g, W.a, W.B, M, st));
     // the two time loops replay as one graph
     std::ostringstream key;
-    key << gid << "|" << I << "|" << rec_threads << "|" << (const void *)W.insts << "|" << rC << "|"
-        << (const void *)W.rtab;
+    key << gid << "|" << I << "|" << rec_threads << "|" << (const void *)W.insts << "|" << rC << "|" << lC
+        << "|" << (const void *)W.rtab << "|" << (const void *)W.slots;
     cudaGraphExec_t exec = nullptr;
     for (auto &e : W.graphs)
         if (e.first == key.str()) exec = e.second;
@@ -1198,6 +1236,13 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
                                           reinterpret_cast<const int4 *>(W.rtab + r_ofs), (int)I, false,
                                           W.counter, rC, r_nc, r_threads, rec_max, r_smem, W.phi,
                                           ctx->cap_stream, true);
+            if (ce == cudaSuccess) ce = launch_adj_residual(g, W.insts, (int)I, rec_max, ctx->cap_stream);
+        } else if (lC) {
+            ce = cudaMemsetAsync(W.counter, 0, sizeof(int), ctx->cap_stream);
+            if (ce == cudaSuccess)
+                ce = launch_wave_l2(g.R, ctx->grids_dev, reinterpret_cast<const Inst *>(W.rtab), (int)I, W.counter,
+                                    lC, l_nc, l_threads, W.slots, l_slot, rec_max, l_smem, W.phi,
+                                    ctx->cap_stream, true);
             if (ce == cudaSuccess) ce = launch_adj_residual(g, W.insts, (int)I, rec_max, ctx->cap_stream);
         } else {
             ce = launch_adj_forward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);

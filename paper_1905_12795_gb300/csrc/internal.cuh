@@ -70,7 +70,8 @@ struct Inst {
     int out;                 // slot of the partial misfit
     int pad_;
     float *hist;             // [nt + 1][field] wavefield history (u^{n+1} into slot n + 1,
-                             // buffer layout), or null; the on-chip kernel's HIST variant only
+                             // buffer layout), or null; the HIST variants of the cluster
+                             // kernels only
 };
 
 // Host-side launchers (each enqueues on `st`).  Return cudaSuccess or the
@@ -121,7 +122,7 @@ cudaError_t l2_configure(int R, size_t smem, int C);
 int l2_max_clusters(int R, int C, int threads, size_t smem);
 cudaError_t launch_wave_l2(int R, const GridDev *grids_dev, const Inst *insts, int n_inst, int *counter,
                            int C, int n_clusters, int threads, float4 *slots, long long slot_f4,
-                           int ring_pitch, size_t smem, double *partial, cudaStream_t st);
+                           int ring_pitch, size_t smem, double *partial, cudaStream_t st, bool hist = false);
 
 // Band-limited resampling of traces (filter.cu).
 long long lowpass_span(double dt_in, double dt_out, double W);

@@ -63,7 +63,8 @@ __device__ __forceinline__ void bilinear_corner(float x, float z, const GridDev 
     w[3] = ax * az;
 }
 
-template <int R>
+// with HIST every u^{n+1} also goes to in.hist (slot n + 1, buffer layout)
+template <int R, bool HIST>
 __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float4 *U1, float *wring,
                             float *dring, float4 *rec_w, int *rec_k, int C, int crank,
                             cg::cluster_group &cluster, double *cred, double *wred, double *partial)
@@ -206,7 +207,14 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
                                                   __ffma2_rn(af01, lap01, um01));
                     const float2 o23 = __ffma2_rn(g23, __fadd2_rn(c23, make_float2(-um.z, -um.w)),
                                                   __ffma2_rn(af23, lap23, um23));
-                    if (k >= kfirst && k < klast) nxt[lr * sp4 + 1 + q] = make_float4(o01.x, o01.y, o23.x, o23.y);
+                    if (k >= kfirst && k < klast) {
+                        const float4 out = make_float4(o01.x, o01.y, o23.x, o23.y);
+                        nxt[lr * sp4 + 1 + q] = out;
+                        if (HIST)   // written once, read back by a later pass: evict first
+                            __stcs(reinterpret_cast<float4 *>(in.hist + (size_t)(n + 1) * gs.field) +
+                                       (size_t)(zr + HALO) * ap4 + 1 + q,
+                                   out);
+                    }
 #pragma unroll
                     for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
                 }
@@ -258,7 +266,7 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
     }
 }
 
-template <int R>
+template <int R, bool HIST>
 __global__ void __launch_bounds__(L2_NT, 1)
 wave_l2_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts, int n_inst,
                int *counter, float4 *slots, long long slot_f4, int ring_pitch, double *partial)
@@ -288,17 +296,22 @@ wave_l2_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts
         const Inst in = insts[q];
         if (threadIdx.x == 0) sg = grids[in.grid];
         __syncthreads();
-        l2_instance<R>(sg, in, U0, U1, wring, dring, rec_w, rec_k, C, crank, cluster, cred, wred, partial);
+        l2_instance<R, HIST>(sg, in, U0, U1, wring, dring, rec_w, rec_k, C, crank, cluster, cred, wred, partial);
     }
 }
 
 using L2Fn = void (*)(const GridDev *, const Inst *, int, int *, float4 *, long long, int, double *);
 
-L2Fn l2_fn(int R)
+L2Fn l2_fn(int R, bool hist = false)
 {
-    if (R == 4) return wave_l2_kernel<4>;
-    if (R == 2) return wave_l2_kernel<2>;
-    return wave_l2_kernel<1>;
+    if (hist) {
+        if (R == 4) return wave_l2_kernel<4, true>;
+        if (R == 2) return wave_l2_kernel<2, true>;
+        return wave_l2_kernel<1, true>;
+    }
+    if (R == 4) return wave_l2_kernel<4, false>;
+    if (R == 2) return wave_l2_kernel<2, false>;
+    return wave_l2_kernel<1, false>;
 }
 
 }  // namespace
@@ -329,8 +342,13 @@ bool l2_fits(const GridDev &g, int C)
 
 cudaError_t l2_configure(int R, size_t smem, int C)
 {
-    cudaError_t e = cudaFuncSetAttribute(l2_fn(R), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(l2_fn(R), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaSuccess;
+    for (const bool hist : {false, true}) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(l2_fn(R, hist), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && C > 8)
+            e = cudaFuncSetAttribute(l2_fn(R, hist), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
     return e;
 }
 
@@ -358,7 +376,7 @@ int l2_max_clusters(int R, int C, int threads, size_t smem)
 
 cudaError_t launch_wave_l2(int R, const GridDev *grids_dev, const Inst *insts, int n_inst, int *counter,
                            int C, int n_clusters, int threads, float4 *slots, long long slot_f4,
-                           int ring_pitch, size_t smem, double *partial, cudaStream_t st)
+                           int ring_pitch, size_t smem, double *partial, cudaStream_t st, bool hist)
 {
     if (n_inst <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
@@ -373,7 +391,7 @@ cudaError_t launch_wave_l2(int R, const GridDev *grids_dev, const Inst *insts, i
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, l2_fn(R), grids_dev, insts, n_inst, counter, slots, slot_f4,
+    return cudaLaunchKernelEx(&cfg, l2_fn(R, hist), grids_dev, insts, n_inst, counter, slots, slot_f4,
                               ring_pitch, partial);
 }
 

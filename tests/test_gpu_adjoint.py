@@ -30,7 +30,7 @@ def _dev(a, dtype=torch.float32):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-@pytest.mark.parametrize("kernel", [0, 1])   # forward pass: on-chip kernel / one launch per step
+@pytest.mark.parametrize("kernel", [0, 1, 3])   # forward pass: on-chip / per step / L2 cluster kernel
 @pytest.mark.parametrize("order", [4, 8])
 def test_gradient_matches_oracle_directional_derivatives(B, order, kernel):
     nx, nz, h, pad, T, f0, vmax = 41, 31, 10.0, 8, 0.25, 15.0, 3000.0
@@ -77,7 +77,7 @@ def test_gradient_matches_oracle_directional_derivatives(B, order, kernel):
     ctx.close()
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 @pytest.mark.parametrize("order", [4, 8])
 def test_gradient_field_matches_oracle_at_every_node(B, order, kernel):
     """The whole dphi/dv field against FP64 central differences of the oracle
