@@ -141,7 +141,7 @@ def _f64(a):
 # --------------------------------------------------------------------------
 
 def fd_coeffs(order: int) -> np.ndarray:
-    c = np.zeros(8)
+    c = np.zeros(9)
     R = lib().eo_fd_coeffs(order, _p(c))
     if R < 0:
         raise ValueError(f"unsupported space order {order}")

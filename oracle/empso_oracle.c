@@ -37,9 +37,9 @@
 
 /* Central second-derivative weights c_0..c_R of accuracy order 2R (Fornberg
  * 1988 tables): f''(x) ~ (1/h^2) [c_0 f(x) + sum_m c_m (f(x+mh) + f(x-mh))].
- * The paper's modelling uses order 8 in space ("Testing approach"); orders 2
- * and 4 are kept for the smaller workloads.  Returns R, or -1 for an
- * unsupported order. */
+ * The paper's modelling uses order 8 in space and its local FWI order 16
+ * ("Testing approach"); orders 2 and 4 are kept for the smaller workloads.
+ * Returns R, or -1 for an unsupported order. */
 int eo_fd_coeffs(int order, double *c)
 {
     if (order == 2) {
@@ -54,6 +54,12 @@ int eo_fd_coeffs(int order, double *c)
         c[0] = -205.0 / 72.0; c[1] = 8.0 / 5.0; c[2] = -1.0 / 5.0;
         c[3] = 8.0 / 315.0; c[4] = -1.0 / 560.0;
         return 4;
+    }
+    if (order == 16) {   /* the local FWI's spatial order ("Testing approach") */
+        c[0] = -1077749.0 / 352800.0; c[1] = 16.0 / 9.0; c[2] = -14.0 / 45.0;
+        c[3] = 112.0 / 1485.0; c[4] = -7.0 / 396.0; c[5] = 112.0 / 32175.0;
+        c[6] = -2.0 / 3861.0; c[7] = 16.0 / 315315.0; c[8] = -1.0 / 411840.0;
+        return 8;
     }
     return -1;
 }
@@ -79,7 +85,7 @@ double eo_ricker(double f0, double t)
 int eo_time_axis(int order, double hx, double hz, double vmax, double T,
                  double cfl, double *dt_out)
 {
-    double c[8];
+    double c[9];
     int R = eo_fd_coeffs(order, c);
     if (R < 0) return -1;
     double rho = c[0];
@@ -120,7 +126,7 @@ void eo_damping_profile(int n, int pad, double h, double vmax, double *eta)
 void eo_laplacian(const double *u, int NX, int NZ, double hx, double hz,
                   int order, double *out)
 {
-    double c[8];
+    double c[9];
     int R = eo_fd_coeffs(order, c);
     for (int J = 0; J < NZ; ++J) {
         for (int I = 0; I < NX; ++I) {
