@@ -115,6 +115,14 @@ void empso_destroy(empso_ctx *ctx);
 empso_status empso_grid_info(const empso_ctx *ctx, int32_t grid_id, float *dt,
                              int32_t *nt);
 
+/* The same without a context: validates `grid` (host) with the rules of
+ * empso_create and returns the time axis it gets (CFL rule of the scheme in
+ * "Testing approach" unless grid->dt > 0).  Host only, no device work.
+ * dt, nt: host, either may be NULL.
+ * Errors: INVALID_ARG (bad sizes/bounds or NULL grid), UNSUPPORTED (space order);
+ * the message is in empso_last_error(NULL). */
+empso_status empso_time_axis(const empso_grid *grid, float *dt, int32_t *nt);
+
 /* Two-grid parameterisation ("Testing approach"): particles device [P][K]
  * (K = kz kx of the grid, m/s) -> vel_out device [P][nz][nx] (m/s), clipped
  * to [vmin, vmax].  Exposed for tests; eval_fitness does this internally. */

@@ -25,7 +25,7 @@ _vp = ctypes.c_void_p
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
           5: "TIMEOUT", 6: "UNSUPPORTED", 7: "NOT_INITIALIZED", 8: "IO_ERROR"}
 
-EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_interp", "forward_traces",
+EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_time_axis", "empso_interp", "forward_traces",
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
            "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_device_error", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
            "empso_generation", "empso_autotune", "empso_set_tuning_cache",
@@ -96,6 +96,7 @@ def load():
     L.empso_destroy.argtypes = [_vp]
     L.empso_destroy.restype = None
     L.empso_grid_info.argtypes = [_vp, _i32, P(_f32), P(_i32)]
+    L.empso_time_axis.argtypes = [P(EmpsoGrid), P(_f32), P(_i32)]
     L.empso_interp.argtypes = [_vp, _i32, _vp, _i32, _vp, _vp]
     L.forward_traces.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp]
     L.eval_models.argtypes = [_vp, _vp, _i32, P(EmpsoShot), _i32, _vp, _vp, _vp]
@@ -170,6 +171,17 @@ def make_grid(nx, nz, hx, hz, pad, order, T, f0, vmin, vmax, kx=8, kz=4, mode=0,
     return EmpsoGrid(nx, nz, pad, order, hx, hz, T, f0, dt, vmin, vmax, kx, kz, mode)
 
 
+def time_axis(grid: EmpsoGrid):
+    """(dt, nt) the library gives `grid`, without a context (host only)."""
+    L = load()
+    dt = _f32()
+    nt = _i32()
+    rc = L.empso_time_axis(ctypes.byref(grid), ctypes.byref(dt), ctypes.byref(nt))
+    if rc != 0:
+        raise EmpsoError(rc, L.empso_last_error(None).decode())
+    return dt.value, nt.value
+
+
 def make_shots(shot_xz, rec_begin, rec_count, grid_ids=None, weights=None):
     S = len(shot_xz)
     arr = (EmpsoShot * S)()
@@ -184,8 +196,20 @@ def eval_models_noalloc(grid: EmpsoGrid, rec_xz, vel, shots, d_obs, misfit):
     """Allocation-free misfit of gridded models (no context; fixed scratch
     inside the library).  vel, d_obs, misfit: CUDA tensors; rec_xz: host
     array [N][2]; shots: ``make_shots`` array on grid 0."""
+    import torch
     L = load()
     rec = np.ascontiguousarray(np.asarray(rec_xz, dtype=np.float32).reshape(-1, 2))
+    # the library sees raw pointers only: sizes and types are checked here
+    if vel.dtype != torch.float32 or vel.dim() != 3 or tuple(vel.shape[1:]) != (grid.nz, grid.nx):
+        raise TypeError(f"vel must be float32 [M][{grid.nz}][{grid.nx}], got "
+                        f"{vel.dtype} {tuple(vel.shape)}")
+    M = vel.shape[0]
+    if misfit.dtype != torch.float64 or misfit.numel() < M:
+        raise TypeError(f"misfit must be float64 with at least {M} elements")
+    if M > 0:
+        need = time_axis(grid)[1] * sum(int(sh.nrec) for sh in shots)
+        if d_obs.dtype != torch.float32 or d_obs.numel() < need:
+            raise ValueError(f"d_obs must be float32 with at least nt * sum(nrec) = {need} elements")
     rc = L.eval_models_noalloc(ctypes.byref(grid), rec.ctypes.data_as(ctypes.POINTER(_f32)),
                                rec.shape[0], _ptr(vel), vel.shape[0], shots, len(shots),
                                _ptr(d_obs), _ptr(misfit), _stream())

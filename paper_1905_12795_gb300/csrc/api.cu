@@ -151,8 +151,10 @@ empso_status fail(empso_ctx *c, empso_status s, const std::string &msg)
                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
     } while (0)
 
+}  // namespace
+
 // Centred second-derivative weights of accuracy order 2R (Fornberg 1988).
-bool fd_weights(int order, double *c, int *R)
+bool empso::fd_weights(int order, double *c, int *R)
 {
     static const double w2[] = {-2.0, 1.0};
     static const double w4[] = {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
@@ -166,24 +168,27 @@ bool fd_weights(int order, double *c, int *R)
     return true;
 }
 
-empso_status setup_grid(empso_ctx *ctx, GridHost &G, int id)
+// Validation of a grid description and everything derived from it on the
+// host: stencil weights, time axis (CFL rule unless dt is given), buffer
+// layout.  Device table pointers stay null.
+empso_status empso::derive_grid(const empso_grid &s, int id, GridDev &g, std::string &err)
 {
-    const empso_grid &s = G.spec;
     char buf[256];
     if (s.nx < 2 || s.nz < 2 || s.pad < 0 || !(s.hx > 0) || !(s.hz > 0) || !(s.t_rec > 0) ||
         !(s.f0 > 0) || !(s.vmax > 0) || !(s.vmin <= s.vmax) || s.kx < 2 || s.kz < 2 ||
         s.kx > 64 || s.kz > 64 || (s.interp_mode != 0 && s.interp_mode != 1)) {
         snprintf(buf, sizeof buf, "grid %d: invalid sizes/spacings/bounds (need nx,nz>=2, "
                  "pad>=0, h>0, T>0, f0>0, vmin<=vmax, 2<=kx,kz<=64, mode 0|1)", id);
-        return fail(ctx, EMPSO_INVALID_ARG, buf);
+        err = buf;
+        return EMPSO_INVALID_ARG;
     }
     double c[MAX_R + 1];
     int R = 0;
     if (!fd_weights(s.space_order, c, &R)) {
         snprintf(buf, sizeof buf, "grid %d: space order %d not in {2,4,8}", id, s.space_order);
-        return fail(ctx, EMPSO_UNSUPPORTED, buf);
+        err = buf;
+        return EMPSO_UNSUPPORTED;
     }
-    GridDev &g = G.dev;
     memset(&g, 0, sizeof g);
     g.nx = s.nx;
     g.nz = s.nz;
@@ -219,7 +224,8 @@ empso_status setup_grid(empso_ctx *ctx, GridHost &G, int id)
     }
     if (nt < 2 || nt > (1 << 24)) {
         snprintf(buf, sizeof buf, "grid %d: %d time steps out of range", id, nt);
-        return fail(ctx, EMPSO_INVALID_ARG, buf);
+        err = buf;
+        return EMPSO_INVALID_ARG;
     }
     g.nt = nt;
     g.dt = (float)dt;
@@ -232,6 +238,19 @@ empso_status setup_grid(empso_ctx *ctx, GridHost &G, int id)
     }
     g.cxm[0] = (float)(c[0] * (ihx2 + ihz2));
     g.czm[0] = 0.f;
+    return EMPSO_OK;
+}
+
+namespace {
+
+empso_status setup_grid(empso_ctx *ctx, GridHost &G, int id)
+{
+    const empso_grid &s = G.spec;
+    GridDev &g = G.dev;
+    std::string err;
+    const empso_status rc = derive_grid(s, id, g, err);
+    if (rc != EMPSO_OK) return fail(ctx, rc, err);
+    const int nt = g.nt;
     CK(ctx, cudaMalloc(&G.ex, sizeof(float) * g.pitch));
     CK(ctx, cudaMalloc(&G.ez, sizeof(float) * g.rows));
     CK(ctx, cudaMalloc(&G.wavelet, sizeof(float) * nt));
@@ -965,6 +984,19 @@ empso_status empso_grid_info(const empso_ctx *ctx, int32_t grid_id, float *dt, i
     return EMPSO_OK;
 }
 
+empso_status empso_time_axis(const empso_grid *grid, float *dt, int32_t *nt)
+{
+    g_create_error.clear();
+    if (!grid) return fail(nullptr, EMPSO_INVALID_ARG, "null grid");
+    GridDev g;
+    std::string err;
+    const empso_status rc = derive_grid(*grid, 0, g, err);
+    if (rc != EMPSO_OK) return fail(nullptr, rc, err);
+    if (dt) *dt = g.dt;
+    if (nt) *nt = g.nt;
+    return EMPSO_OK;
+}
+
 empso_status empso_set_levels(empso_ctx *ctx, int32_t grid_id, int32_t n_levels,
                               const float *level_z, const int32_t *level_count, const float *node_x)
 {
@@ -1143,7 +1175,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             const long long items = std::max<long long>(32, (long long)g.NQ * ((rows_c + 7) / 8));
             const int threads = (int)std::min<long long>(l2_max_threads(), (items + 31) / 32 * 32);
             CK(ctx, l2_configure(g.R, sm, C));
-            const int occ = l2_max_clusters(g.R, C, threads, sm);
+            const int occ = l2_max_clusters(g.R, C, threads, sm, true);
             if (occ <= 0) continue;
             const long long by_l2 = std::max<long long>(1, L2_BUDGET_BYTES / inst_bytes);
             const int nc = (int)std::min<long long>(std::min<long long>(occ, I), by_l2);

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "empso.h"
 
 namespace empso {
@@ -74,6 +76,14 @@ struct Inst {
                              // kernels only
 };
 
+// Centred 2nd-derivative weights c_0..c_R of space order `order` (false when
+// the order is not supported).
+bool fd_weights(int order, double *c, int *R);
+// Validate a grid description and derive its host-side part (stencil
+// weights, time axis, buffer layout); the device table pointers stay null.
+// Returns EMPSO_INVALID_ARG / EMPSO_UNSUPPORTED with a message in `err`.
+empso_status derive_grid(const empso_grid &s, int id, GridDev &g, std::string &err);
+
 // Host-side launchers (each enqueues on `st`).  Return cudaSuccess or the
 // launch error.
 cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wavelet,
@@ -119,7 +129,9 @@ size_t l2_smem_bytes(int ring_pitch);
 long long l2_slot_f4(const GridDev &g, int C);
 bool l2_fits(const GridDev &g, int C);
 cudaError_t l2_configure(int R, size_t smem, int C);
-int l2_max_clusters(int R, int C, int threads, size_t smem);
+// clusters of the modelling (hist = false) or history (hist = true) instantiation
+// that fit the device at once
+int l2_max_clusters(int R, int C, int threads, size_t smem, bool hist = false);
 cudaError_t launch_wave_l2(int R, const GridDev *grids_dev, const Inst *insts, int n_inst, int *counter,
                            int C, int n_clusters, int threads, float4 *slots, long long slot_f4,
                            int ring_pitch, size_t smem, double *partial, cudaStream_t st, bool hist = false);

@@ -111,79 +111,6 @@ empso_status nfail(empso_status s, const std::string &msg)
     return s;
 }
 
-// Grid derivation of the library's contexts (time axis from the CFL rule,
-// stencil weights, buffer layout), restated here so this entry point needs no
-// context.
-bool derive_grid(const empso_grid &s, GridDev &g, std::string &err)
-{
-    if (s.nx < 2 || s.nz < 2 || s.pad < 0 || !(s.hx > 0) || !(s.hz > 0) || !(s.t_rec > 0) ||
-        !(s.f0 > 0) || !(s.vmax > 0) || s.kx < 2 || s.kz < 2 || s.kx > 64 || s.kz > 64) {
-        err = "invalid grid sizes/spacings/bounds";
-        return false;
-    }
-    static const double w2[] = {-2.0, 1.0};
-    static const double w4[] = {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
-    static const double w8[] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
-    const double *c;
-    int R;
-    if (s.space_order == 2) { c = w2; R = 1; }
-    else if (s.space_order == 4) { c = w4; R = 2; }
-    else if (s.space_order == 8) { c = w8; R = 4; }
-    else {
-        err = "space order not in {2,4,8}";
-        return false;
-    }
-    memset(&g, 0, sizeof g);
-    g.nx = s.nx;
-    g.nz = s.nz;
-    g.pad = s.pad;
-    g.R = R;
-    g.NX = s.nx + 2 * s.pad;
-    g.NZ = s.nz + 2 * s.pad;
-    g.NQ = (g.NX + 3) / 4;
-    g.pitch = ((4 * g.NQ + 2 * HALO) + 31) / 32 * 32;
-    g.rows = g.NZ + 2 * HALO;
-    g.field = (long long)g.rows * g.pitch;
-    g.kx = s.kx;
-    g.kz = s.kz;
-    g.K = s.kx * s.kz;
-    g.mode = s.interp_mode;
-    g.hx = s.hx;
-    g.hz = s.hz;
-    g.vmin = s.vmin;
-    g.vmax = s.vmax;
-    double dt = s.dt;
-    const double T = s.t_rec;
-    int nt;
-    if (dt <= 0) {
-        double rho = c[0];
-        for (int m = 1; m <= R; ++m) rho += 2.0 * ((m & 1) ? -c[m] : c[m]);
-        rho = std::fabs(rho);
-        const double hx = s.hx, hz = s.hz;
-        const double dtmax = 2.0 / (s.vmax * std::sqrt(rho * (1.0 / (hx * hx) + 1.0 / (hz * hz))));
-        nt = (int)std::ceil(T / (0.9 * dtmax)) + 1;
-        dt = T / (double)(nt - 1);
-    } else {
-        nt = (int)std::lround(T / dt) + 1;
-    }
-    if (nt < 2 || nt > (1 << 24)) {
-        err = "time steps out of range";
-        return false;
-    }
-    g.nt = nt;
-    g.dt = (float)dt;
-    const double ihx2 = 1.0 / ((double)s.hx * s.hx), ihz2 = 1.0 / ((double)s.hz * s.hz);
-    for (int m = 0; m <= MAX_R; ++m) {
-        const double cm = m <= R ? c[m] : 0.0;
-        g.c[m] = (float)cm;
-        g.cxm[m] = (float)(cm * ihx2);
-        g.czm[m] = (float)(cm * ihz2);
-    }
-    g.cxm[0] = (float)(c[0] * (ihx2 + ihz2));
-    g.czm[0] = 0.f;
-    return true;
-}
-
 }  // namespace
 }  // namespace empso
 
@@ -203,7 +130,8 @@ extern "C" empso_status eval_models_noalloc(const empso_grid *grid, const float 
     SetupParams p;
     memset(&p, 0, sizeof p);
     std::string err;
-    if (!derive_grid(*grid, p.g, err)) return nfail(EMPSO_INVALID_ARG, err);
+    const empso_status grc = derive_grid(*grid, 0, p.g, err);
+    if (grc != EMPSO_OK) return nfail(grc, err);
     const GridDev &g = p.g;
     const float Lx = (grid->nx - 1) * grid->hx, Lz = (grid->nz - 1) * grid->hz;
     long long off = 0;

@@ -352,7 +352,7 @@ cudaError_t l2_configure(int R, size_t smem, int C)
     return e;
 }
 
-int l2_max_clusters(int R, int C, int threads, size_t smem)
+int l2_max_clusters(int R, int C, int threads, size_t smem, bool hist)
 {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -366,7 +366,7 @@ int l2_max_clusters(int R, int C, int threads, size_t smem)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, l2_fn(R), &cfg);
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, l2_fn(R, hist), &cfg);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return -(int)e;        // the query's error, negated

@@ -89,3 +89,25 @@ def test_host_functions_through_the_binding(lib):
     assert B.load().empso_last_kernel_name(None) == b""
     lib.empso_status_string.restype = ctypes.c_char_p
     assert lib.empso_status_string(8) == b"file error"
+
+
+@pytest.mark.parametrize("order,nx,nz,h,T,vmax", [(2, 37, 29, 10.0, 0.3, 3200.0),
+                                                   (4, 101, 101, 10.0, 0.5, 2625.0),
+                                                   (8, 461, 151, 20.0, 3.0, 4700.0),
+                                                   (8, 921, 301, 10.0, 4.0, 4700.0)])
+def test_context_free_time_axis_matches_oracle(lib, order, nx, nz, h, T, vmax):
+    """Host logic only (no device work): the library's CFL time axis for a
+    grid equals the oracle's, and invalid grids are refused with the codes
+    empso_create uses."""
+    import oracle
+    from paper_1905_12795_gb300 import binding as B
+    g = B.make_grid(nx, nz, h, h, 10, order, T, 6.0, 1500.0, vmax)
+    dt, nt = B.time_axis(g)
+    dt_o, nt_o = oracle.time_axis(order, h, h, vmax, T)
+    assert nt == nt_o and dt == pytest.approx(dt_o, rel=1e-6)
+    with pytest.raises(B.EmpsoError) as e:
+        B.time_axis(B.make_grid(nx, nz, h, h, 10, 6, T, 6.0, 1500.0, vmax))
+    assert e.value.status == 6
+    with pytest.raises(B.EmpsoError) as e:
+        B.time_axis(B.make_grid(nx, nz, h, h, 10, order, T, 6.0, 2000.0, 1900.0))
+    assert e.value.status == 1

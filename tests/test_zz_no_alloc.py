@@ -55,7 +55,35 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     sh = B.make_shots([(4600.0, 20.0)], [0], [461])
     M = 64
     vel = torch.full((M, 151, 461), 2000.0, device="cuda")
+    _, nt = B.time_axis(grid)
+    dobs = torch.zeros(nt * 461, device="cuda")
     with pytest.raises(B.EmpsoError) as e:
-        B.eval_models_noalloc(grid, rec, vel, sh, torch.zeros(1, device="cuda"),
+        B.eval_models_noalloc(grid, rec, vel, sh, dobs,
                               torch.zeros(M, dtype=torch.float64, device="cuda"))
     assert e.value.status == 6 and "scratch" in str(e.value)
+
+
+def test_noalloc_binding_checks_what_the_library_cannot_see():
+    """The C entry point receives raw device pointers, so the binding checks
+    the tensors' types and sizes before the call: a float32 misfit buffer
+    or a short d_obs would otherwise be written or read past its end."""
+    from paper_1905_12795_gb300 import binding as B
+    nx = nz = 41
+    grid = B.make_grid(nx, nz, 10.0, 10.0, 5, 4, 0.2, 10.0, 1500.0, 3000.0)
+    rec = synth.receiver_line(nx, 10.0, 20.0)
+    sh = B.make_shots([(200.0, 20.0)], [0], [nx])
+    _, nt = B.time_axis(grid)
+    vel = torch.full((2, nz, nx), 2000.0, device="cuda")
+    dobs = torch.zeros(nt * nx, device="cuda")
+    mis = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        B.eval_models_noalloc(grid, rec, vel, sh, dobs, mis.float())
+    with pytest.raises(TypeError):
+        B.eval_models_noalloc(grid, rec, vel.double(), sh, dobs, mis)
+    with pytest.raises(TypeError):
+        B.eval_models_noalloc(grid, rec, vel[:, :, :-1], sh, dobs, mis)
+    with pytest.raises(ValueError):
+        B.eval_models_noalloc(grid, rec, vel, sh, dobs[:-1], mis)
+    B.eval_models_noalloc(grid, rec, vel, sh, dobs, mis)
+    torch.cuda.synchronize()
+    assert np.all(mis.cpu().numpy() > 0.0)
