@@ -30,6 +30,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "stencil.cuh"
 
 namespace empso {
 
@@ -140,8 +141,26 @@ __device__ __forceinline__ void stage_tile_product(float4 *S, const float4 *__re
 
 // Laplacian of the four points of the staged group at tile row sr, column sc:
 // z-neighbours as whole float4s, x-neighbours from the groups left and right
+// (the modelling kernels' operator, stencil.cuh)
 template <int R>
 __device__ __forceinline__ float4 lap4_tile(const float4 *S, int sr, int sc, const GridDev &g)
+{
+    constexpr int W = TW + 2;
+    float4 w[2 * R + 1];
+#pragma unroll
+    for (int m = 0; m <= 2 * R; ++m) w[m] = S[(sr - R + m) * W + sc];
+    float xs[12];
+    xline1(S[sr * W + sc - 1], w[R], S[sr * W + sc + 1], xs);
+    float2 l01, l23;
+    lap_group<R>(w, xs, g.cxm, g.czm, g.cres, l01, l23);
+    return make_float4(l01.x, l01.y, l23.x, l23.y);
+}
+
+// The same operator summed as written (centre weight c_0, pair sums): the
+// adjoint step's form, where its FP32 rounding only enters the gradient and
+// the differences would cost the step registers it does not have
+template <int R>
+__device__ __forceinline__ float4 lap4_tile_sum(const float4 *S, int sr, int sc, const GridDev &g)
 {
     constexpr int W = TW + 2;
     const float4 c = S[sr * W + sc], l = S[sr * W + sc - 1], r = S[sr * W + sc + 1];
@@ -291,8 +310,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
         if (J >= g.NZ) break;
         const int sr = ly * TZ + r + R;
         const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
-        const float4 lq = lap4_tile<R>(SQ, sr, lx + 1, g);
-        const float4 lu = lap4_tile<R>(SU, sr, lx + 1, g);
+        const float4 lq = lap4_tile_sum<R>(SQ, sr, lx + 1, g);
+        const float4 lu = lap4_tile_sum<R>(SU, sr, lx + 1, g);
         const float4 a1 = m1[k4], a2 = m2[k4];
         const bool jrow = J >= in.jr0 && J <= in.jr1;
         const float4 jj = jrow ? J4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);

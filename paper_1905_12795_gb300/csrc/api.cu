@@ -238,6 +238,9 @@ empso_status empso::derive_grid(const empso_grid &s, int id, GridDev &g, std::st
     }
     g.cxm[0] = (float)(c[0] * (ihx2 + ihz2));
     g.czm[0] = 0.f;
+    double cres = c[0];
+    for (int m = 1; m <= std::min(R, 2); ++m) cres += 2.0 * c[m];
+    g.cres = (float)(cres * (ihx2 + ihz2));
     return EMPSO_OK;
 }
 

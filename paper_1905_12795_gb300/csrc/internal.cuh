@@ -49,7 +49,9 @@ struct GridDev {
     float vmin, vmax;
     float c[MAX_R + 1];      // centred 2nd-derivative weights c_0..c_R
     float cxm[MAX_R + 1];    // c_m / hx^2 (m >= 1), [0] = c_0 (1/hx^2 + 1/hz^2)
-    float czm[MAX_R + 1];    // c_m / hz^2
+    float czm[MAX_R + 1];    // c_m / hz^2 (m >= 1), [0] = 0
+    float cres;              // (c_0 + 2 c_1 + 2 c_2)(1/hx^2 + 1/hz^2): the centre weight left
+                             // once the m = 1, 2 terms are taken as differences (stencil.cuh)
     const float *wavelet;    // [nt]      Ricker r(n dt)
     const float *ex;         // [pitch]   eta_x dt / 2 per buffer column (0 in halo)
     const float *ez;         // [rows]    eta_z dt / 2 per buffer row (0 in halo)

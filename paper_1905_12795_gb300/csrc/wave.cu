@@ -19,6 +19,7 @@
 // x-stencil.  u^{n+1} overwrites u^{n-1} in place.  One CTA barrier per step;
 // the receivers of u^n are sampled during step n (they only read u^n).
 #include "internal.cuh"
+#include "stencil.cuh"
 
 namespace empso {
 
@@ -81,6 +82,7 @@ __device__ void run_instance(const GridDev &g, const Inst &in, float *bufA, floa
         cx[m] = g.cxm[m];
         cz[m] = g.czm[m];
     }
+    const float cres = g.cres;
     double acc = 0.0;
     __syncthreads();
 
@@ -109,17 +111,15 @@ __device__ void run_instance(const GridDev &g, const Inst &in, float *bufA, floa
                     float4 um = *reinterpret_cast<const float4 *>(prev + row + col);
                     const float4 av = *reinterpret_cast<const float4 *>(in.a + row + col);
                     const float ezj = g.ez[j + HALO];
-                    const float s[12] = {lft.x, lft.y, lft.z, lft.w, w[R].x, w[R].y, w[R].z, w[R].w,
-                                         rgt.x, rgt.y, rgt.z, rgt.w};
+                    float s[12];
+                    xline1(lft, w[R], rgt, s);
+                    float2 L01, L23;
+                    lap_group<R>(w, s, cx, cz, cres, L01, L23);
+                    const float lapv[4] = {L01.x, L01.y, L23.x, L23.y};
                     float outv[4];
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
-                        float lap = cx[0] * s[4 + l];
-#pragma unroll
-                        for (int m = 1; m <= R; ++m) {
-                            lap = fmaf(cx[m], s[4 + l - m] + s[4 + l + m], lap);
-                            lap = fmaf(cz[m], lane(w[R - m], l) + lane(w[R + m], l), lap);
-                        }
+                        float lap = lapv[l];
                         if (src_here) {
                             const int I = 4 * q + l;
                             float b = 0.f;

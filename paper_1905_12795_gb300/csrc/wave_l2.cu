@@ -22,6 +22,7 @@
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
+#include "stencil.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -98,6 +99,7 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
         cx[m] = gs.cxm[m];
         cz[m] = gs.czm[m];
     }
+    const float cres = gs.cres;
     int s_i0, s_j0;
     float sw[4];
     bilinear_corner(in.sx, in.sz, gs, s_i0, s_j0, sw);
@@ -168,26 +170,11 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
                     const float4 um = __ldcg(nxt + lr * sp4 + 1 + q);
                     const int zr = z0 + r0 + k;                   // padded row of the output
                     const float4 av = __ldg(arow + (size_t)min(zr, NZ - 1) * ap4 + q);
-                    const float2 c01 = make_float2(w[R].x, w[R].y), c23 = make_float2(w[R].z, w[R].w);
-                    const float s[12] = {lft.x, lft.y, lft.z, lft.w, w[R].x, w[R].y, w[R].z,
-                                         w[R].w, rgt.x, rgt.y, rgt.z, rgt.w};
-                    float2 lx01 = __fmul2_rn(make_float2(cx[0], cx[0]), c01);
-                    float2 lx23 = __fmul2_rn(make_float2(cx[0], cx[0]), c23);
-                    float2 lz01 = make_float2(0.f, 0.f), lz23 = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int m = 1; m <= R; ++m) {
-                        const float2 czm = make_float2(cz[m], cz[m]);
-                        const float2 cxm = make_float2(cx[m], cx[m]);
-                        lz01 = __ffma2_rn(czm, __fadd2_rn(make_float2(w[R - m].x, w[R - m].y),
-                                                          make_float2(w[R + m].x, w[R + m].y)), lz01);
-                        lz23 = __ffma2_rn(czm, __fadd2_rn(make_float2(w[R - m].z, w[R - m].w),
-                                                          make_float2(w[R + m].z, w[R + m].w)), lz23);
-                        const float2 sx01 = make_float2(s[4 - m] + s[4 + m], s[5 - m] + s[5 + m]);
-                        const float2 sx23 = make_float2(s[6 - m] + s[6 + m], s[7 - m] + s[7 + m]);
-                        lx01 = __ffma2_rn(cxm, sx01, lx01);
-                        lx23 = __ffma2_rn(cxm, sx23, lx23);
-                    }
-                    float2 lap01 = __fadd2_rn(lx01, lz01), lap23 = __fadd2_rn(lx23, lz23);
+                    const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
+                    float xs[12];
+                    xline1(lft, w[R], rgt, xs);
+                    float2 lap01, lap23;
+                    lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
                     if (src_here && (k == ks || k == ks + 1)) {
                         const float4 sb = (k == ks) ? sb0 : sb1;
                         lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);

@@ -14,6 +14,7 @@
 // slots; no wait is unbounded (a wait that times out sets an error flag and
 // the instance is abandoned with misfit NaN -> +inf).
 #include "internal.cuh"
+#include "stencil.cuh"
 
 namespace empso {
 
@@ -129,6 +130,7 @@ __device__ void stream_instance(const GridDev &g, const Inst &in, float *bufA, f
         cx[m] = g.cxm[m];
         cz[m] = g.czm[m];
     }
+    const float cres = g.cres;
     float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) ex = __ldg(reinterpret_cast<const float4 *>(g.ex + HALO) + q);
     const Corner sc = corner_of(in.sx, in.sz, g);
@@ -221,17 +223,15 @@ __device__ void stream_instance(const GridDev &g, const Inst &in, float *bufA, f
                     const float4 um = mring[((size_t)ms * RB + b) * sp4 + 1 + q];
                     const float4 av = aring[((size_t)ms * RB + b) * sp4 + 1 + q];
                     const float ezj = live ? __ldg(g.ez + J + HALO) : 0.f;
-                    const float s[12] = {lft.x, lft.y, lft.z, lft.w, w[R].x, w[R].y, w[R].z, w[R].w,
-                                         rgt.x, rgt.y, rgt.z, rgt.w};
+                    float s[12];
+                    xline1(lft, w[R], rgt, s);
+                    float2 L01, L23;
+                    lap_group<R>(w, s, cx, cz, cres, L01, L23);
+                    const float lapv[4] = {L01.x, L01.y, L23.x, L23.y};
                     float o[4];
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
-                        float lap = cx[0] * s[4 + l];
-#pragma unroll
-                        for (int m = 1; m <= R; ++m) {
-                            lap = fmaf(cx[m], s[4 + l - m] + s[4 + l + m], lap);
-                            lap = fmaf(cz[m], lane4(w[R - m], l) + lane4(w[R + m], l), lap);
-                        }
+                        float lap = lapv[l];
                         if (src_cols && (J == sc.j0 || J == sc.j0 + 1)) {
                             const int I = 4 * q + l;
                             float bw = 0.f;

@@ -111,3 +111,27 @@ def test_context_free_time_axis_matches_oracle(lib, order, nx, nz, h, T, vmax):
     with pytest.raises(B.EmpsoError) as e:
         B.time_axis(B.make_grid(nx, nz, h, h, 10, order, T, 6.0, 2000.0, 1900.0))
     assert e.value.status == 1
+
+
+def test_misfit_rule_is_the_trace_bar_propagated():
+    """The misfit parity bar (tests/misfit_rule.py) against its definition:
+    traces perturbed by exactly 1e-4 of their norm, in the worst direction
+    (along the residual), change the misfit by at most the bound, and the
+    bound is 1e-4 relative once the residual reaches 10 % of the data."""
+    import numpy as np
+    from misfit_rule import misfit_bound
+    rng = np.random.default_rng(3)
+    dobs = rng.normal(size=5000)
+    E = 0.5 * float(dobs @ dobs)
+    for frac in (0.0, 1e-3, 1e-2, 0.05, 0.099, 0.2, 1.0, 3.0):
+        r = rng.normal(size=5000)
+        r *= frac * np.linalg.norm(dobs) / max(np.linalg.norm(r), 1e-300)
+        d = dobs + r
+        phi = 0.5 * float(r @ r)
+        u = r / np.linalg.norm(r) if frac > 0 else d / np.linalg.norm(d)
+        dd = d + 1e-4 * np.linalg.norm(d) * u
+        phi2 = 0.5 * float((dd - dobs) @ (dd - dobs))
+        if phi < 1e-2 * E:
+            assert abs(phi2 - phi) <= misfit_bound(phi, E) * (1 + 1e-9)
+        else:
+            assert misfit_bound(phi, E) == pytest.approx(1e-4 * phi)

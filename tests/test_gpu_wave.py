@@ -1,14 +1,16 @@
 """GPU parity of the modelling path against the FP64 CPU oracle.
 
 Bar (from the method's accuracy target): traces within 1e-4 relative L2 of the
-oracle; misfits within 1e-4 relative when the residual is at least 1 % of the
-observed data, else |dphi| <= 1e-4 * 1/2 |d_obs|^2.  All inputs are seeded and
+oracle; misfits within 1e-4 relative when the residual is at least 10 % of the
+observed data, else within the error that traces at 1e-4 can put on them
+(misfit_rule.py).  All inputs are seeded and
 synthetic (layered/faulted or two-layer models, shots and receivers on a line).
 """
 import numpy as np
 import pytest
 
 import oracle
+from misfit_rule import misfit_bound, misfit_ok
 from paper_1905_12795_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -36,10 +38,7 @@ def _rel_l2(a, b):
 
 def _check_misfit(got, ref, dobs_energy):
     for g, r, e in zip(np.atleast_1d(got), np.atleast_1d(ref), np.atleast_1d(dobs_energy)):
-        if r >= 1e-4 * e:      # |r| >= 1 % |d_obs|  <=>  phi >= 1e-4 * 1/2 |d_obs|^2
-            assert abs(g - r) <= MISFIT_TOL * r, (g, r)
-        else:
-            assert abs(g - r) <= MISFIT_TOL * e, (g, r, e)
+        assert misfit_ok(g, r, e), (g, r, e, misfit_bound(r, e))
 
 
 def _geometry(nx, nz, h, S, src_z, rec_z, off_grid=False):
