@@ -58,12 +58,15 @@ def _args():
     ap.add_argument("--cpu-sample-particles", type=int, default=2)
     ap.add_argument("--case", default=None,
                     help="P,S: small profiling case on the workload's grid (no JSON line)")
-    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 streaming, 2 on-chip")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 streaming, 2 on-chip, 3 L2 cluster")
+    ap.add_argument("--cluster", type=int, default=0, help="--case: CTAs per instance (0 automatic)")
+    ap.add_argument("--rows", type=int, default=0, help="--case: on-chip rows per thread (0 automatic)")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-vs-plain wall-clock comparison")
     ap.add_argument("--surrogate-seeds", type=int, default=9)
     ap.add_argument("--trials", type=int, default=5, help="PSO vs EMPSO comparison trials")
+    ap.add_argument("--bands", type=int, default=0, help="fwi workload: number of bands (0: all six)")
     ap.add_argument("--gradient-case", type=int, default=0,
                     help="time one adjoint gradient of this many shots")
     ap.add_argument("--surrogate-case", type=int, default=0,
@@ -853,25 +856,30 @@ def run_noncrime(a):
 ADJ_BYTES_PER_UPDATE = 44
 
 
+FWI_BANDS = (4.6, 11.5, 18.4, 25.3, 32.2, 39.0)   # maximum frequencies of the paper's bands (Hz)
+
+
 def run_fwi(a):
-    """The paper's full workflow on the plain workload: EMPSO (32 particles,
-    30 generations) gives the starting model, then a multiscale local FWI
-    (steepest descent, Barzilai-Borwein step, backtracking) over the bands
-    with maximum frequencies 4.6 and 11.5 Hz (the paper's first two; the
-    20 m grid resolves no higher), each band modelled with a Ricker of peak
-    f_max / 2.5 and its own observed data.  Reports the model error after
-    each stage, the misfit histories, and the device time of one adjoint
-    gradient of all 16 shots (forward pass with the wavefield history in HBM
-    plus the adjoint pass) with its algorithmic traffic against the HBM
-    peak."""
+    """The paper's full workflow ("Testing approach", local FWI paragraph):
+    EMPSO (32 particles of 4 x 8 control nodes, 30 generations, on the plain
+    workload's 461 x 151 / 20 m grid) gives the starting model, then a
+    multiscale local FWI (steepest descent, Barzilai-Borwein initial step,
+    backtracking) runs 30 iterations in each of the six bands with maximum
+    frequencies 4.6, 11.5, 18.4, 25.3, 32.2 and 39 Hz, with the 16th-order
+    operator in space, on a grid that resolves 39 Hz (the same 9.2 km x 3 km
+    area at 10 m, 60 damping cells, the same 3 s record, 16 shots and one
+    receiver per horizontal node).  Each band is modelled with a Ricker of
+    peak f_max / 2.5 and has its own observed data from the true model.
+    Reports the model error after each stage, the misfit histories, and the
+    device time of one adjoint gradient of all 16 shots with its algorithmic
+    traffic against the HBM peak."""
     import torch
     from paper_1905_12795_gb300 import binding as B
     wl, gs, S, shots, rec, true = _setup("empso-461x151-P32-S16")
     nrec = len(rec)
     sh = B.make_shots(shots, [0] * S, [nrec] * S)
     tt = torch.tensor(true, dtype=torch.float32, device="cuda")
-    err = lambda v: float(torch.linalg.norm(v - tt) / torch.linalg.norm(tt))  # noqa: E731
-    # 1. EMPSO starting model
+    # 1. EMPSO starting model on the plain grid
     grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin, gs.vmax,
                        kx=gs.kx, kz=gs.kz, mode=gs.mode)
     K = gs.kx * gs.kz
@@ -883,58 +891,80 @@ def run_fwi(a):
     mis = torch.zeros(wl.P, dtype=torch.float64, device="cuda")
     ctx.pso_init()
     gens = a.generations or 30
+    t0 = time.perf_counter()
     for _ in range(gens):
         ctx.generation(sh, dobs, mis)
+    torch.cuda.synchronize()
+    empso_s = time.perf_counter() - t0
     p = torch.zeros(wl.P, K, dtype=torch.float64, device="cuda")
     gk = torch.zeros(2, dtype=torch.int32, device="cuda")
     ctx.pso_get_state(p=p, gk=gk)
-    vel = torch.zeros(1, gs.nz, gs.nx, device="cuda")
-    ctx.interp(0, p[int(gk[0].item())][None].float().contiguous(), vel)
+    best = p[int(gk[0].item())][None].float().contiguous()
     ctx.close()
+    # 2. the FWI grid: the same area at 10 m, the control nodes' model on it
+    h = 10.0
+    fx, fz = int(round((gs.nx - 1) * gs.hx / h)) + 1, int(round((gs.nz - 1) * gs.hz / h)) + 1
+    pad = 60
+    true_f = torch.tensor(synth.layered_faulted_model(fx, fz, h, h, seed=wl.seed_model, vmin=gs.vmin,
+                                                      vmax=gs.vmax), dtype=torch.float32, device="cuda")
+    rec_f = synth.receiver_line(fx, h, wl.rec_z)
+    nrec_f = len(rec_f)
+    sh_f = B.make_shots(shots, [0] * S, [nrec_f] * S)
+    gstart = B.make_grid(fx, fz, h, h, pad, 16, gs.T, gs.f0, gs.vmin, gs.vmax, kx=gs.kx, kz=gs.kz)
+    cs = B.Context([gstart], rec_f)
+    vel = torch.zeros(1, fz, fx, device="cuda")
+    cs.interp(0, best, vel)
+    cs.close()
     vel = vel[0].contiguous()
-    stages = [{"stage": f"EMPSO {gens} generations", "model_rel_l2": err(vel)}]
+    err = lambda v: float(torch.linalg.norm(v - true_f) / torch.linalg.norm(true_f))  # noqa: E731
+    stages = [{"stage": f"EMPSO {gens} generations ({gs.nx}x{gs.nz} @ {gs.hx:g} m)",
+               "model_rel_l2": err(vel), "wall_s": empso_s}]
     grad_line = None
-    iters = a.trials if a.trials != 5 else 10
-    for fmax in (4.6, 11.5):
+    iters = a.trials if a.trials != 5 else 30
+    bands = FWI_BANDS[:a.bands] if a.bands else FWI_BANDS
+    nt_f = 0
+    for fmax in bands:
         f0 = fmax / 2.5
-        gb = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, f0, gs.vmin, gs.vmax)
-        cb = B.Context([gb], rec)
-        d_b = torch.zeros(S * nt * nrec, device="cuda")
-        cb.forward_traces(tt[None], sh, d_b)
+        gb = B.make_grid(fx, fz, h, h, pad, 16, gs.T, f0, gs.vmin, gs.vmax)
+        cb = B.Context([gb], rec_f)
+        _, nt_f = cb.grid_info(0)
+        d_b = torch.zeros(S * nt_f * nrec_f, device="cuda")
+        cb.forward_traces(true_f[None], sh_f, d_b)
         if grad_line is None:
-            g = torch.zeros(1, gs.nz, gs.nx, device="cuda")
-            cb.gradient(vel[None], sh, d_b, g)           # warm-up (workspace allocation)
+            g = torch.zeros(1, fz, fx, device="cuda")
+            cb.gradient(vel[None], sh_f, d_b, g)           # warm-up (workspace allocation)
             ms = []
             for _ in range(3):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
-                cb.gradient(vel[None], sh, d_b, g)
+                cb.gradient(vel[None], sh_f, d_b, g)
                 e1.record()
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
-            upd = S * _updates_per_instance(gs, nt)
+            upd = S * (fx + 2 * pad) * (fz + 2 * pad) * nt_f
             t = float(np.median(ms)) / 1e3
             peak, peak_kind = _peaks()
             achieved = ADJ_BYTES_PER_UPDATE * upd / t / 1e9
-            grad_line = {"gradient_ms": t * 1e3, "point_steps": upd,
+            grad_line = {"gradient_ms": t * 1e3, "point_steps": upd, "space_order": 16,
                          "forward_plus_adjoint_updates_per_s": 2 * upd / t,
-                         "roofline": {"kernel": "adjoint path (wave_resident_kernel with history / adj_step_kernel)",
+                         "roofline": {"kernel": "adjoint path (adj_fwd_kernel / adj_step_kernel, radius 8)",
                                       "bound": "hbm", "achieved": achieved, "peak": peak,
                                       "peak_kind": peak_kind, "unit": "GB/s",
                                       "frac": achieved / peak,
                                       "bytes_per_point_step": ADJ_BYTES_PER_UPDATE}}
         t0 = time.perf_counter()
-        hist = cb.fwi(vel, sh, d_b, iters, gs.vmin, gs.vmax)
+        hist = cb.fwi(vel, sh_f, d_b, iters, gs.vmin, gs.vmax)
         torch.cuda.synchronize()
         stages.append({"stage": f"FWI band f_max {fmax} Hz (Ricker {f0:.2f} Hz)",
                        "iterations": len(hist) - 1, "misfit_first": hist[0], "misfit_last": hist[-1],
                        "misfit_history": hist, "model_rel_l2": err(vel),
                        "wall_s": time.perf_counter() - t0})
         cb.close()
-    line = {"metric": "EMPSO + multiscale local FWI: model error per stage; adjoint gradient time",
+    line = {"metric": "EMPSO + multiscale local FWI (16th order): model error per stage; adjoint gradient time",
             "data": "synthetic", "dtype": "f32",
-            "config": {"workload": "fwi-461x151-S16", "grid": f"{gs.nx}x{gs.nz}@{gs.hx:g}m",
-                       "shots": S, "nt": nt, "iterations_per_band": iters},
+            "config": {"workload": f"fwi-{fx}x{fz}-S16", "grid": f"{fx}x{fz}@{h:g}m (+{pad} damping)",
+                       "space_order": 16, "shots": S, "nt": nt_f, "bands_hz": list(bands),
+                       "iterations_per_band": iters},
             "stages": stages, "gradient": grad_line}
     print(json.dumps(line), flush=True)
 
@@ -951,6 +981,8 @@ def run_case(a):
                        gs.vmax, kx=gs.kx, kz=gs.kz, mode=gs.mode)
     ctx = B.Context([grid], rec)
     ctx.set_kernel(a.kernel)
+    ctx.set_cluster(a.cluster)
+    ctx.set_tile_rows(a.rows)
     _, nt = ctx.grid_info(0)
     sh = B.make_shots(shots, [0] * S, [len(rec)] * S)
     dobs = torch.zeros(S * nt * len(rec), device="cuda")
@@ -964,7 +996,8 @@ def run_case(a):
         torch.cuda.synchronize()
         ms = ctx.read_timing()[1]
         print(f"rep {r}: modelling kernel {ms:.3f} ms, {upd / ms / 1e6:.1f} G updates/s, "
-              f"launch {ctx.last_launch()} {ctx.last_kernel_name()}", flush=True)
+              f"launch {ctx.last_launch()} rows {ctx.last_tile_rows()} {ctx.last_kernel_name()}",
+              flush=True)
     ctx.close()
 
 

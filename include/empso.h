@@ -316,6 +316,18 @@ empso_status empso_set_kernel(empso_ctx *ctx, int32_t kind);
  * UNSUPPORTED when the batch does not fit that size). */
 empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas);
 
+/* Rows per thread of the on-chip kernel (EMPSO_KERNEL_RESIDENT): each thread
+ * updates a run of at most `rows` consecutive rows of one 4-point column
+ * group per step.  0 (default): the planner's or the autotuner's choice;
+ * 8 (up to 512 threads per CTA) or 13 (up to 384 threads, more registers per
+ * thread).  An engineering choice of this library (the paper has no such
+ * parameter).  Errors: INVALID_ARG for any other value. */
+empso_status empso_set_tile_rows(empso_ctx *ctx, int32_t rows);
+
+/* Rows per thread of the last on-chip launch (0 if the last launch used
+ * another kernel).  rows: host. */
+empso_status empso_last_tile_rows(const empso_ctx *ctx, int32_t *rows);
+
 /* Which modelling kernel the last launch used: *kind = EMPSO_KERNEL_STREAMING
  * or EMPSO_KERNEL_RESIDENT (0 before any launch), *cluster = CTAs per
  * instance.  Either pointer may be NULL (host ints). */

@@ -27,7 +27,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
 
 EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_time_axis", "empso_interp", "forward_traces",
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
-           "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_last_launch", "empso_device_error", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
+           "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_set_tile_rows",
+           "empso_last_tile_rows", "empso_last_launch", "empso_device_error", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
            "empso_generation", "empso_autotune", "empso_set_tuning_cache",
            "pso_step_ranked", "surrogate_init", "surrogate_set_backend", "surrogate_set_overlap", "surrogate_predict", "surrogate_add",
            "surrogate_train", "surrogate_params", "surrogate_grad", "surrogate_generation",
@@ -107,6 +108,8 @@ def load():
     L.pso_set_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp]
     L.empso_set_kernel.argtypes = [_vp, _i32]
     L.empso_set_cluster.argtypes = [_vp, _i32]
+    L.empso_set_tile_rows.argtypes = [_vp, _i32]
+    L.empso_last_tile_rows.argtypes = [_vp, P(_i32)]
     L.empso_device_error.argtypes = [_vp, P(_i32), _vp]
     L.empso_last_launch.argtypes = [_vp, P(_i32), P(_i32)]
     L.empso_set_timing.argtypes = [_vp, _i32]
@@ -293,6 +296,15 @@ class Context:
 
     def set_cluster(self, ctas: int):
         self._check(self._L.empso_set_cluster(self._h, int(ctas)))
+
+    def set_tile_rows(self, rows: int):
+        """Rows per thread of the on-chip kernel: 0 automatic, 8 or 13."""
+        self._check(self._L.empso_set_tile_rows(self._h, int(rows)))
+
+    def last_tile_rows(self) -> int:
+        r = _i32()
+        self._check(self._L.empso_last_tile_rows(self._h, ctypes.byref(r)))
+        return r.value
 
     def last_launch(self):
         """(kernel kind, CTAs per instance) of the last modelling launch."""

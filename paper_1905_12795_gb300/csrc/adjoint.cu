@@ -80,12 +80,17 @@ __global__ void adj_prep_kernel(GridDev g, const float *a, float *B)
 // The per-point kernels work on tiles of TW float4 groups (4 TW points) by
 // TT = 8 TZ rows; each of the block's TW x 8 threads computes TZ consecutive
 // rows of one group.  The fields that enter a Laplacian are staged first,
-// with R rows and one group of halo on every side, in shared memory.  The
-// forward step takes TZ = 1 (its Laplacian reads one field; more rows per
-// thread cost it registers and occupancy).  The adjoint step takes TZ = 4
-// when that still gives every SM enough blocks (less halo re-read, one wave),
-// else 2 or 1 (more, smaller blocks to fill the GPU).
+// with R rows and XG = ceil(R / 4) groups of halo on every side, in shared
+// memory.  The forward step takes TZ = 1 (its Laplacian reads one field; more
+// rows per thread cost it registers and occupancy).  The adjoint step takes
+// TZ = 4 when that still gives every SM enough blocks (less halo re-read, one
+// wave), else 2 or 1 (more, smaller blocks to fill the GPU).
 constexpr int TW = 16, TILE_THREADS = TW * 8;
+
+template <int R> struct Tile {
+    static constexpr int XG = (R + 3) / 4;     // halo groups each side
+    static constexpr int W = TW + 2 * XG;      // staged groups per row
+};
 
 __host__ __device__ inline int tiles_x(const GridDev &g) { return (g.NQ + TW - 1) / TW; }
 
@@ -99,19 +104,19 @@ __device__ __forceinline__ void cp_async16_zfill(void *sdst, const void *gsrc, b
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// rows J0 - R .. J0 + TT - 1 + R, groups q0 - 1 .. q0 + TW of buffer U into
-// S[TT + 2R][TW + 2] by asynchronous copies (complete after
+// rows J0 - R .. J0 + TT - 1 + R, groups q0 - XG .. q0 + TW - 1 + XG of buffer
+// U into S[TT + 2R][W] by asynchronous copies (complete after
 // cp_async_wait_all and a barrier); cells outside the buffer read as zero
 template <int R, int TT>
 __device__ __forceinline__ void stage_tile(float4 *S, const float4 *__restrict__ U, int J0, int q0,
                                            const GridDev &g)
 {
-    constexpr int W = TW + 2, H = TT + 2 * R;
+    constexpr int XG = Tile<R>::XG, W = Tile<R>::W, H = TT + 2 * R;
     const int p4 = g.pitch / 4;
     for (int c = threadIdx.x; c < W * H; c += TILE_THREADS) {
-        const int row = J0 - R + c / W + HALO;  // buffer row
-        const int grp = q0 + c % W;             // buffer group of interior group q0 - 1 + c % W
-        const bool ok = row >= 0 && row < g.rows && grp < p4;
+        const int row = J0 - R + c / W + HALO;      // buffer row
+        const int grp = q0 - XG + HALO4 + c % W;    // buffer group of interior group q0 - XG + c % W
+        const bool ok = row >= 0 && row < g.rows && grp >= 0 && grp < p4;
         cp_async16_zfill(S + c, ok ? U + (long long)row * p4 + grp : U, ok);
     }
 }
@@ -123,20 +128,33 @@ __device__ __forceinline__ void stage_tile_product(float4 *S, const float4 *__re
                                                    const float4 *__restrict__ Y, int J0, int q0,
                                                    const GridDev &g)
 {
-    constexpr int W = TW + 2, H = TT + 2 * R, NIT = (W * H + TILE_THREADS - 1) / TILE_THREADS;
+    constexpr int XG = Tile<R>::XG, W = Tile<R>::W, H = TT + 2 * R;
+    constexpr int NIT = (W * H + TILE_THREADS - 1) / TILE_THREADS;
     const int p4 = g.pitch / 4;
 #pragma unroll
     for (int it = 0; it < NIT; ++it) {
         const int c = threadIdx.x + it * TILE_THREADS;
         const int row = J0 - R + c / W + HALO;
-        const int grp = q0 + c % W;
+        const int grp = q0 - XG + HALO4 + c % W;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c < W * H && row >= 0 && row < g.rows && grp < p4) {
+        if (c < W * H && row >= 0 && row < g.rows && grp >= 0 && grp < p4) {
             const float4 x = X[(long long)row * p4 + grp], y = Y[(long long)row * p4 + grp];
             v = make_float4(x.x * y.x, x.y * y.y, x.z * y.z, x.w * y.w);
         }
         if (c < W * H) S[c] = v;
     }
+}
+
+// the staged x-line of the group at tile row sr, column sc (XG groups each side)
+template <int R>
+__device__ __forceinline__ void tile_xline(const float4 *S, int sr, int sc, float *xs)
+{
+    constexpr int W = Tile<R>::W;
+    if (Tile<R>::XG == 1)
+        xline1(S[sr * W + sc - 1], S[sr * W + sc], S[sr * W + sc + 1], xs);
+    else
+        xline2(S[sr * W + sc - 2], S[sr * W + sc - 1], S[sr * W + sc], S[sr * W + sc + 1], S[sr * W + sc + 2],
+               xs);
 }
 
 // Laplacian of the four points of the staged group at tile row sr, column sc:
@@ -145,12 +163,12 @@ __device__ __forceinline__ void stage_tile_product(float4 *S, const float4 *__re
 template <int R>
 __device__ __forceinline__ float4 lap4_tile(const float4 *S, int sr, int sc, const GridDev &g)
 {
-    constexpr int W = TW + 2;
+    constexpr int W = Tile<R>::W;
     float4 w[2 * R + 1];
 #pragma unroll
     for (int m = 0; m <= 2 * R; ++m) w[m] = S[(sr - R + m) * W + sc];
-    float xs[12];
-    xline1(S[sr * W + sc - 1], w[R], S[sr * W + sc + 1], xs);
+    float xs[4 * (2 * Tile<R>::XG + 1)];
+    tile_xline<R>(S, sr, sc, xs);
     float2 l01, l23;
     lap_group<R>(w, xs, g.cxm, g.czm, g.cres, l01, l23);
     return make_float4(l01.x, l01.y, l23.x, l23.y);
@@ -162,19 +180,19 @@ __device__ __forceinline__ float4 lap4_tile(const float4 *S, int sr, int sc, con
 template <int R>
 __device__ __forceinline__ float4 lap4_tile_sum(const float4 *S, int sr, int sc, const GridDev &g)
 {
-    constexpr int W = TW + 2;
-    const float4 c = S[sr * W + sc], l = S[sr * W + sc - 1], r = S[sr * W + sc + 1];
-    const float s[12] = {l.x, l.y, l.z, l.w, c.x, c.y, c.z, c.w, r.x, r.y, r.z, r.w};
+    constexpr int XG = Tile<R>::XG, O = 4 * XG, W = Tile<R>::W;
+    float s[4 * (2 * XG + 1)];
+    tile_xline<R>(S, sr, sc, s);
     float o[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) o[i] = g.cxm[0] * s[4 + i];
+    for (int i = 0; i < 4; ++i) o[i] = g.cxm[0] * s[O + i];
 #pragma unroll
     for (int m = 1; m <= R; ++m) {
         const float4 zm = S[(sr - m) * W + sc], zp = S[(sr + m) * W + sc];
         const float zs[4] = {zm.x + zp.x, zm.y + zp.y, zm.z + zp.z, zm.w + zp.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            o[i] = fmaf(g.czm[m], zs[i], fmaf(g.cxm[m], s[4 + i - m] + s[4 + i + m], o[i]));
+            o[i] = fmaf(g.czm[m], zs[i], fmaf(g.cxm[m], s[O + i - m] + s[O + i + m], o[i]));
     }
     return make_float4(o[0], o[1], o[2], o[3]);
 }
@@ -190,7 +208,7 @@ __device__ __forceinline__ float lane_of(const float4 &v, int i)
 template <int R, int TZ>
 __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
 {
-    constexpr int W = TW + 2, TT = 8 * TZ;
+    constexpr int W = Tile<R>::W, XG = Tile<R>::XG, TT = 8 * TZ;
     __shared__ float4 S[(TT + 2 * R) * W];
     const AdjInst in = insts[blockIdx.y];
     // block 0 only records e_{n-1} = R u^n - d_obs,n-1 (u^n is complete),
@@ -228,9 +246,9 @@ __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const 
         const int J = J0 + ly * TZ + r;
         if (J >= g.NZ) break;
         const int sr = ly * TZ + r + R;
-        const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
-        const float4 lap = lap4_tile<R>(S, sr, lx + 1, g);
-        const float4 c = S[sr * W + lx + 1], m = um[k4], av = a4[k4];
+        const long long k4 = (long long)(J + HALO) * p4 + HALO4 + q;
+        const float4 lap = lap4_tile<R>(S, sr, lx + XG, g);
+        const float4 c = S[sr * W + lx + XG], m = um[k4], av = a4[k4];
         const float ez = g.ez[J + HALO];
         float o[4];
 #pragma unroll
@@ -278,7 +296,7 @@ template <int R, int TZ>
 __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts,
                                                                    int k)
 {
-    constexpr int W = TW + 2, TT = 8 * TZ;
+    constexpr int W = Tile<R>::W, XG = Tile<R>::XG, TT = 8 * TZ;
     __shared__ float4 SQ[(TT + 2 * R) * W], SU[(TT + 2 * R) * W];
     const AdjInst in = insts[blockIdx.y];
     if (blockIdx.x == 0) {
@@ -309,9 +327,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
         const int J = J0 + ly * TZ + r;
         if (J >= g.NZ) break;
         const int sr = ly * TZ + r + R;
-        const long long k4 = (long long)(J + HALO) * p4 + 1 + q;
-        const float4 lq = lap4_tile_sum<R>(SQ, sr, lx + 1, g);
-        const float4 lu = lap4_tile_sum<R>(SU, sr, lx + 1, g);
+        const long long k4 = (long long)(J + HALO) * p4 + HALO4 + q;
+        const float4 lq = lap4_tile_sum<R>(SQ, sr, lx + XG, g);
+        const float4 lu = lap4_tile_sum<R>(SU, sr, lx + XG, g);
         const float4 a1 = m1[k4], a2 = m2[k4];
         const bool jrow = J >= in.jr0 && J <= in.jr1;
         const float4 jj = jrow ? J4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -456,11 +474,18 @@ int tile_count(const GridDev &g, int TT) { return tiles_x(g) * ((g.NZ + TT - 1) 
 
 using StepFn = void (*)(GridDev, const AdjInst *, int);
 
-StepFn fwd_fn(int R) { return R == 4 ? adj_fwd_kernel<4, 1> : (R == 2 ? adj_fwd_kernel<2, 1> : adj_fwd_kernel<1, 1>); }
+StepFn fwd_fn(int R)
+{
+    if (R == 8) return adj_fwd_kernel<8, 1>;
+    if (R == 4) return adj_fwd_kernel<4, 1>;
+    return R == 2 ? adj_fwd_kernel<2, 1> : adj_fwd_kernel<1, 1>;
+}
 template <int TZ>
 StepFn step_fn_z(int R)
 {
-    return R == 4 ? adj_step_kernel<4, TZ> : (R == 2 ? adj_step_kernel<2, TZ> : adj_step_kernel<1, TZ>);
+    if (R == 8) return adj_step_kernel<8, TZ>;
+    if (R == 4) return adj_step_kernel<4, TZ>;
+    return R == 2 ? adj_step_kernel<2, TZ> : adj_step_kernel<1, TZ>;
 }
 StepFn step_fn(int R, int TZ) { return TZ == 4 ? step_fn_z<4>(R) : (TZ == 2 ? step_fn_z<2>(R) : step_fn_z<1>(R)); }
 
@@ -516,6 +541,25 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
     const StepFn fn = step_fn(g.R, tz);
     adj_scatter_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
     for (int k = g.nt; k >= 1; --k) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, k);
+    return cudaGetLastError();
+}
+
+// misfit[m] = sum over shots of phi (shot order), +inf when not finite
+__global__ void adj_model_misfit_kernel(int M, int S, const double *phi, double *misfit)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += phi[m * S + s];
+    misfit[m] = isfinite(v) ? v : __longlong_as_double(0x7ff0000000000000LL);
+}
+
+cudaError_t launch_adj_misfit(const GridDev &g, const AdjInst *insts, int M, int S, double *phi,
+                              double *misfit, double *part, cudaStream_t st)
+{
+    adj_misfit_part_kernel<<<dim3(MISFIT_PARTS, M * S), 256, 0, st>>>(insts, g.nt, part);
+    adj_misfit_sum_kernel<<<(M * S + 127) / 128, 128, 0, st>>>(insts, M * S, part, phi);
+    adj_model_misfit_kernel<<<(M + 127) / 128, 128, 0, st>>>(M, S, phi, misfit);
     return cudaGetLastError();
 }
 

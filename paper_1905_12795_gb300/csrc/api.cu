@@ -56,8 +56,10 @@ struct empso_ctx {
     int wave_ctas_per_sm = 1;
     size_t smem_optin = 0;          // max dynamic shared memory per block
     int forced_C = 0;               // 0: choose the cluster size, else use this one
+    int forced_rows = 0;            // on-chip kernel: 0 choose the rows per thread, else use this many
     int last_path = 0;              // 1 streaming, 2 resident, 3 bulk-copy streaming (last launch)
     int last_C = 0;
+    int last_rows = 0;              // on-chip launch: rows per thread
     int last_paired = 0;            // on-chip launch: units running two instances
     int *dev_err = nullptr;         // device status word set by bounded waits that give up
     unsigned long long *nonfinite = nullptr;  // non-finite misfits: {running, this call}
@@ -70,8 +72,11 @@ struct empso_ctx {
     double *pso_mem = nullptr;
     int *pso_int = nullptr;
 
-    // tuned (kind, cluster) choices by batch signature, and the cache file
-    std::map<std::string, std::pair<int, int>> tuned;
+    // tuned (kind, cluster, rows per thread) choices by batch signature, and the cache file
+    struct Tuned {
+        int kind = 0, C = 0, rows = 0;
+    };
+    std::map<std::string, Tuned> tuned;
     std::string tune_cache;
 
     // captured generations (eval + EMPSO step), one per shape and buffers
@@ -159,10 +164,14 @@ bool empso::fd_weights(int order, double *c, int *R)
     static const double w2[] = {-2.0, 1.0};
     static const double w4[] = {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
     static const double w8[] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+    static const double w16[] = {-1077749.0 / 352800.0, 16.0 / 9.0, -14.0 / 45.0, 112.0 / 1485.0,
+                                 -7.0 / 396.0, 112.0 / 32175.0, -2.0 / 3861.0, 16.0 / 315315.0,
+                                 -1.0 / 411840.0};
     const double *w = nullptr;
     if (order == 2) { w = w2; *R = 1; }
     else if (order == 4) { w = w4; *R = 2; }
     else if (order == 8) { w = w8; *R = 4; }
+    else if (order == 16) { w = w16; *R = 8; }
     else return false;
     for (int m = 0; m <= *R; ++m) c[m] = w[m];
     return true;
@@ -185,7 +194,7 @@ empso_status empso::derive_grid(const empso_grid &s, int id, GridDev &g, std::st
     double c[MAX_R + 1];
     int R = 0;
     if (!fd_weights(s.space_order, c, &R)) {
-        snprintf(buf, sizeof buf, "grid %d: space order %d not in {2,4,8}", id, s.space_order);
+        snprintf(buf, sizeof buf, "grid %d: space order %d not in {2,4,8,16}", id, s.space_order);
         err = buf;
         return EMPSO_UNSUPPORTED;
     }
@@ -361,7 +370,7 @@ struct Plan {
     long long n_inst = 0, maxfield = 0;
     std::vector<long long> fbase;      // per grid: offset of its M model fields, -1 if unused
     bool resident = false;
-    int resR = 0, resC = 0, res_threads = 0, res_clusters = 0, ring_pitch = 0;
+    int resR = 0, resC = 0, res_threads = 0, res_clusters = 0, res_rows = 0, ring_pitch = 0;
     size_t res_smem = 0;
     std::vector<char> res_pair;        // per grid: two instances share a cluster (half each)
     const int4 *units = nullptr;       // device work units of the on-chip kernel
@@ -425,12 +434,13 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
 
     // kernel and cluster size: explicit settings, else the tuned choice, else
     // the on-chip kernel with the cluster size that keeps the most SMs busy
-    int kind = ctx->kernel_kind, forcedC = ctx->forced_C;
-    if (kind == EMPSO_KERNEL_AUTO && forcedC == 0) {
+    int kind = ctx->kernel_kind, forcedC = ctx->forced_C, forcedRows = ctx->forced_rows;
+    if (kind == EMPSO_KERNEL_AUTO && forcedC == 0 && forcedRows == 0) {
         auto it = ctx->tuned.find(batch_key(ctx, shots, S, M));
         if (it != ctx->tuned.end()) {
-            kind = it->second.first;
-            forcedC = it->second.second;
+            kind = it->second.kind;
+            forcedC = it->second.C;
+            forcedRows = it->second.rows;
         }
     }
     int resR = -1;
@@ -439,28 +449,32 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
         const int R = ctx->grids[gid].dev.R;
         resR = (resR < 0 || resR == R) ? R : 0;
     }
+    // the cluster and bulk-copy kernels hold stencils up to radius 4; order
+    // 16 (and mixed orders) run on the plain streaming kernel
+    if (resR > MAX_R_FAST) resR = 0;
     p.resident = false;
     if ((kind == EMPSO_KERNEL_AUTO || kind == EMPSO_KERNEL_RESIDENT) && resR > 0) {
         long long best_sms = 0;
         int nrec_max = 0;
         for (int s = 0; s < S; ++s) nrec_max = std::max(nrec_max, (int)shots[s].nrec);
         const int ring_pitch = nrec_max;
-        for (int C = 1; C <= 16; ++C) {
+        // every cluster size and rows-per-thread shape; the most SMs busy wins,
+        // the longer runs (fewer, fatter threads) on a tie
+        for (int C = 1; C <= 16; ++C)
+            for (const int rows : {13, 8}) {
             if (forcedC > 0 && C != forcedC) continue;
+            if (forcedRows > 0 && rows != forcedRows) continue;
             bool ok = true;
             size_t sm = 0;
-            int items = 32;
+            int threads = 32;
             for (int gid = 0; gid < ng && ok; ++gid) {
                 if (p.fbase[gid] < 0) continue;
                 const GridDev &g = ctx->grids[gid].dev;
-                ok = resident_fits(g, C, ring_pitch, ctx->smem_optin);
+                ok = resident_fits(g, C, ring_pitch, ctx->smem_optin, rows);
                 sm = std::max(sm, resident_smem_bytes(g, C, ring_pitch));
-                const int rows_c = (g.NZ + C - 1) / C;
-                const int rpt = resident_rows_per_thread();
-                items = std::max(items, g.NQ * ((rows_c + rpt - 1) / rpt));
+                threads = std::max(threads, resident_threads(g, C, rows));
             }
             if (!ok) continue;
-            const int threads = (items + 31) / 32 * 32;
             // a grid runs two instances per cluster, one on each half, when it
             // fits C / 2 CTAs without raising the launch's shared memory or threads
             std::vector<char> pair(ng, 0);
@@ -468,13 +482,11 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
                 for (int gid = 0; gid < ng; ++gid) {
                     if (p.fbase[gid] < 0) continue;
                     const GridDev &g = ctx->grids[gid].dev;
-                    const int rows_h = (g.NZ + C / 2 - 1) / (C / 2);
-                    const int rpt = resident_rows_per_thread();
-                    pair[gid] = resident_fits(g, C / 2, ring_pitch, ctx->smem_optin) &&
+                    pair[gid] = resident_fits(g, C / 2, ring_pitch, ctx->smem_optin, rows) &&
                                 resident_smem_bytes(g, C / 2, ring_pitch) <= sm &&
-                                g.NQ * ((rows_h + rpt - 1) / rpt) <= threads;
+                                resident_threads(g, C / 2, rows) <= threads;
                 }
-            const int nc = (int)std::min<long long>(resident_max_clusters(resR, C, threads, sm), p.n_inst);
+            const int nc = (int)std::min<long long>(resident_max_clusters(resR, C, threads, sm, rows), p.n_inst);
             const long long sms = (long long)nc * C;
             if (nc > 0 && sms > best_sms) {
                 best_sms = sms;
@@ -482,6 +494,7 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
                 p.res_pair = pair;
                 p.resR = resR;
                 p.resC = C;
+                p.res_rows = rows;
                 p.res_smem = sm;
                 p.res_threads = threads;
                 p.res_clusters = nc;
@@ -678,11 +691,11 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
     if (ctx->timing) CK(ctx, mark(ctx->tev[1], st));
     if (p.resident) {
         CK(ctx, launch_wave_resident(p.resR, ctx->grids_dev, p.insts, p.units, p.n_units, p.n_paired > 0,
-                                     ctx->counter,
-                                     p.resC, p.res_clusters, p.res_threads, p.ring_pitch, p.res_smem,
-                                     ctx->partial, st));
+                                     ctx->counter, p.resC, p.res_clusters, p.res_threads, p.res_rows,
+                                     p.ring_pitch, p.res_smem, ctx->partial, st));
         ctx->last_path = 2;
         ctx->last_C = p.resC;
+        ctx->last_rows = p.res_rows;
         ctx->last_paired = p.n_paired;
     } else if (p.l2) {
         CK(ctx, launch_wave_l2(p.resR, ctx->grids_dev, p.insts,
@@ -1099,8 +1112,12 @@ template <class T> empso_status adj_grow(empso_ctx *ctx, T **p, size_t *cap, siz
 }
 
 // misfit and dphi/dv of M gridded models (all shots on one grid)
+// The adjoint-state gradient of M models (and their misfits); with
+// forward_only just the misfits, from the gradient's forward pass (the local
+// FWI's line search on grids the cluster kernels do not hold).
 empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_shot *shots, int S,
-                           const float *d_obs, double *misfit, float *grad, cudaStream_t st)
+                           const float *d_obs, double *misfit, float *grad, cudaStream_t st,
+                           bool forward_only = false)
 {
     const int gid = shots[0].grid_id;
     for (int s = 1; s < S; ++s)
@@ -1137,27 +1154,30 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     // history out beside its usual work, when the kernel selection allows it
     // and the grid fits a cluster's shared memory (the cluster size that
     // keeps the most SMs busy); else one tiled launch per step.
-    int rC = 0, r_threads = 0, r_nc = 0;
+    int rC = 0, r_threads = 0, r_nc = 0, r_rows = 0;
     size_t r_smem = 0;
-    const bool want_res = ctx->kernel_kind == EMPSO_KERNEL_AUTO || ctx->kernel_kind == EMPSO_KERNEL_RESIDENT;
+    // (the cluster kernels hold stencils up to radius 4: order 16 takes the
+    // per-step launches)
+    const bool want_res = g.R <= MAX_R_FAST &&
+                          (ctx->kernel_kind == EMPSO_KERNEL_AUTO || ctx->kernel_kind == EMPSO_KERNEL_RESIDENT);
     if (want_res) {
         long long best = 0;
-        const int rpt = resident_rows_per_thread();
-        for (int C = 1; C <= 16; ++C) {
-            if (!resident_fits(g, C, rec_max, ctx->smem_optin)) continue;
-            const size_t sm = resident_smem_bytes(g, C, rec_max);
-            const int rows_c = (g.NZ + C - 1) / C;
-            const int items = std::max(32, g.NQ * ((rows_c + rpt - 1) / rpt));
-            const int threads = (items + 31) / 32 * 32;
-            const int nc = (int)std::min<long long>(resident_max_clusters(g.R, C, threads, sm), I);
-            if (nc > 0 && (long long)nc * C > best) {
-                best = (long long)nc * C;
-                rC = C;
-                r_threads = threads;
-                r_nc = nc;
-                r_smem = sm;
+        for (int C = 1; C <= 16; ++C)
+            for (const int rows : {13, 8}) {
+                if (ctx->forced_rows > 0 && rows != ctx->forced_rows) continue;
+                if (!resident_fits(g, C, rec_max, ctx->smem_optin, rows)) continue;
+                const size_t sm = resident_smem_bytes(g, C, rec_max);
+                const int threads = resident_threads(g, C, rows);
+                const int nc = (int)std::min<long long>(resident_max_clusters(g.R, C, threads, sm, rows, true), I);
+                if (nc > 0 && (long long)nc * C > best) {
+                    best = (long long)nc * C;
+                    rC = C;
+                    r_rows = rows;
+                    r_threads = threads;
+                    r_nc = nc;
+                    r_smem = sm;
+                }
             }
-        }
     }
     if (ctx->kernel_kind == EMPSO_KERNEL_RESIDENT && !rC)
         return fail(ctx, EMPSO_UNSUPPORTED, "gradient: the grid does not fit the on-chip kernel");
@@ -1167,7 +1187,8 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     int lC = 0, l_threads = 0, l_nc = 0;
     long long l_slot = 0;
     size_t l_smem = 0;
-    if (!rC && (ctx->kernel_kind == EMPSO_KERNEL_AUTO || ctx->kernel_kind == EMPSO_KERNEL_CLUSTER_L2)) {
+    if (!rC && g.R <= MAX_R_FAST &&
+        (ctx->kernel_kind == EMPSO_KERNEL_AUTO || ctx->kernel_kind == EMPSO_KERNEL_CLUSTER_L2)) {
         const size_t sm = l2_smem_bytes(rec_max);
         long long best = 0;
         for (int C : {16, 12, 10, 8, 6, 4, 3, 2, 1}) {
@@ -1256,7 +1277,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     // the two time loops replay as one graph
     std::ostringstream key;
     key << gid << "|" << I << "|" << rec_threads << "|" << (const void *)W.insts << "|" << rC << "|" << lC
-        << "|" << (const void *)W.rtab << "|" << (const void *)W.slots;
+        << "|" << (const void *)W.rtab << "|" << (const void *)W.slots << "|" << forward_only;
     cudaGraphExec_t exec = nullptr;
     for (auto &e : W.graphs)
         if (e.first == key.str()) exec = e.second;
@@ -1269,7 +1290,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             if (ce == cudaSuccess)
                 ce = launch_wave_resident(g.R, ctx->grids_dev, reinterpret_cast<const Inst *>(W.rtab),
                                           reinterpret_cast<const int4 *>(W.rtab + r_ofs), (int)I, false,
-                                          W.counter, rC, r_nc, r_threads, rec_max, r_smem, W.phi,
+                                          W.counter, rC, r_nc, r_threads, r_rows, rec_max, r_smem, W.phi,
                                           ctx->cap_stream, true);
             if (ce == cudaSuccess) ce = launch_adj_residual(g, W.insts, (int)I, rec_max, ctx->cap_stream);
         } else if (lC) {
@@ -1282,7 +1303,8 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         } else {
             ce = launch_adj_forward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
         }
-        if (ce == cudaSuccess) ce = launch_adj_backward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
+        if (ce == cudaSuccess && !forward_only)
+            ce = launch_adj_backward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
         const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
         if (ce == cudaSuccess) ce = ee;
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -1292,6 +1314,10 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         W.graphs.push_back({key.str(), exec});
     }
     CK(ctx, cudaGraphLaunch(exec, st));
+    if (forward_only) {
+        CK(ctx, launch_adj_misfit(g, W.insts, M, S, W.phi, misfit, reinterpret_cast<double *>(W.mu), st));
+        return EMPSO_OK;
+    }
     // the fold's scratch takes the adjoint fields' slots (free now; G lies past them)
     CK(ctx, launch_adj_finish(g, W.insts, M, S, vel, W.phi, misfit, grad, W.mu, st));
     return EMPSO_OK;
@@ -1331,11 +1357,15 @@ empso_status empso_fwi(empso_ctx *ctx, float *vel, const empso_shot *shots, int3
     float *vt = W.fv, *gcur = W.fv + np, *gnew = W.fv + 2 * (size_t)np;
     double *dots = W.fd, *phi_dev = W.fd + 8;
     double r[5];
+    // misfits on the modelling kernels, or, for stencils the cluster kernels do
+    // not hold (order 16), on the gradient's tiled forward pass over every SM
+    const bool fwd_misfit = g.R > MAX_R_FAST;
     auto misfit_of = [&](const float *v, double *out) -> empso_status {
         Models mod;
         mod.vel = v;
         mod.M = 1;
-        empso_status e = run_batch(ctx, mod, shots, S, d_obs, nullptr, phi_dev, st);
+        empso_status e = fwd_misfit ? gradient_impl(ctx, v, 1, shots, S, d_obs, phi_dev, nullptr, st, true)
+                                    : run_batch(ctx, mod, shots, S, d_obs, nullptr, phi_dev, st);
         if (e) return e;
         CK(ctx, cudaMemcpyAsync(out, phi_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(ctx, cudaStreamSynchronize(st));
@@ -1585,7 +1615,10 @@ empso_status empso_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S
     {
         std::ostringstream os;
         os << "|" << (const void *)d_obs << "|" << (const void *)misfit_out << "|k" << ctx->kernel_kind
-           << "c" << ctx->forced_C << "t" << ctx->timing;
+           << "c" << ctx->forced_C << "r" << ctx->forced_rows << "t" << ctx->timing;
+        auto tu = ctx->tuned.find(key);
+        if (tu != ctx->tuned.end())
+            os << "|tuned" << tu->second.kind << "," << tu->second.C << "," << tu->second.rows;
         for (int s = 0; s < S; ++s)
             os << "|" << shots[s].sx << "," << shots[s].sz << "," << shots[s].rec_begin << ","
                << shots[s].nrec << "," << shots[s].grid_id << "," << shots[s].weight;
@@ -1677,7 +1710,11 @@ void load_tune_cache(empso_ctx *ctx)
         if (json_str(line, "gpu") != gpu) continue;
         const std::string key = json_str(line, "key");
         if (key.empty()) continue;
-        ctx->tuned[key] = {(int)json_int(line, "kind", 0), (int)json_int(line, "cluster", 0)};
+        empso_ctx::Tuned t;
+        t.kind = (int)json_int(line, "kind", 0);
+        t.C = (int)json_int(line, "cluster", 0);
+        t.rows = (int)json_int(line, "rows", 0);
+        ctx->tuned[key] = t;
     }
 }
 
@@ -1705,22 +1742,26 @@ empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
     cudaStream_t st = (cudaStream_t)stream;
     const std::string key = batch_key(ctx, shots, S, P);
     ctx->tuned.erase(key);
-    const int save_kind = ctx->kernel_kind, save_C = ctx->forced_C;
+    const int save_kind = ctx->kernel_kind, save_C = ctx->forced_C, save_rows = ctx->forced_rows;
     Models mod;
     mod.particles = particles;
     mod.M = P;
     cudaEvent_t e0, e1;
     CK(ctx, cudaEventCreate(&e0));
     CK(ctx, cudaEventCreate(&e1));
-    // candidates: the streaming kernel and every cluster size of the on-chip one
-    std::vector<std::pair<int, int>> cand = {{EMPSO_KERNEL_STREAMING, 0}};
-    for (int C = 1; C <= 16; ++C) cand.push_back({EMPSO_KERNEL_RESIDENT, C});
-    for (int C : {4, 8, 10, 12, 16}) cand.push_back({EMPSO_KERNEL_CLUSTER_L2, C});
+    // candidates: the streaming kernel, every cluster size and rows-per-thread
+    // shape of the on-chip one, and the usual cluster sizes of the L2 one
+    std::vector<empso_ctx::Tuned> cand = {{EMPSO_KERNEL_STREAMING, 0, 0}};
+    for (int C = 1; C <= 16; ++C)
+        for (const int rows : {13, 8}) cand.push_back({EMPSO_KERNEL_RESIDENT, C, rows});
+    for (int C : {4, 8, 10, 12, 16}) cand.push_back({EMPSO_KERNEL_CLUSTER_L2, C, 0});
     float best = 1e30f;
-    std::pair<int, int> choice = {EMPSO_KERNEL_AUTO, 0};
+    empso_ctx::Tuned choice;
+    choice.kind = EMPSO_KERNEL_AUTO;
     for (auto &c : cand) {
-        ctx->kernel_kind = c.first;
-        ctx->forced_C = c.second;
+        ctx->kernel_kind = c.kind;
+        ctx->forced_C = c.C;
+        ctx->forced_rows = c.rows;
         Plan p;
         rc = plan_batch(ctx, mod, shots, S, d_obs, nullptr, p, nullptr, st);
         if (rc == EMPSO_UNSUPPORTED) continue;   // this size does not fit the batch
@@ -1738,24 +1779,27 @@ empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            choice = {c.first, p.resident ? p.resC : (p.l2 ? p.l2C : 0)};
+            choice.kind = c.kind;
+            choice.C = p.resident ? p.resC : (p.l2 ? p.l2C : 0);
+            choice.rows = p.resident ? p.res_rows : 0;
         }
     }
     ctx->err.clear();
     ctx->kernel_kind = save_kind;
     ctx->forced_C = save_C;
+    ctx->forced_rows = save_rows;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc && rc != EMPSO_UNSUPPORTED) return rc;
-    if (choice.first == EMPSO_KERNEL_AUTO) return fail(ctx, EMPSO_UNSUPPORTED, "no kernel fits the batch");
+    if (choice.kind == EMPSO_KERNEL_AUTO) return fail(ctx, EMPSO_UNSUPPORTED, "no kernel fits the batch");
     ctx->tuned[key] = choice;
-    if (kind_out) *kind_out = choice.first;
-    if (cluster_out) *cluster_out = choice.second;
+    if (kind_out) *kind_out = choice.kind;
+    if (cluster_out) *cluster_out = choice.C;
     if (!ctx->tune_cache.empty()) {
         std::ofstream out(ctx->tune_cache, std::ios::app);
         out << "{\"gpu\": \"" << gpu_name(ctx->device) << "\", \"key\": \"" << key
-            << "\", \"kind\": " << choice.first << ", \"cluster\": " << choice.second
-            << ", \"ms\": " << best << "}\n";
+            << "\", \"kind\": " << choice.kind << ", \"cluster\": " << choice.C
+            << ", \"rows\": " << choice.rows << ", \"ms\": " << best << "}\n";
     }
     return EMPSO_OK;
 }
@@ -1777,6 +1821,23 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas)
     ctx->err.clear();
     if (ctas < 0 || ctas > 16) return fail(ctx, EMPSO_INVALID_ARG, "cluster size must be 0..16");
     ctx->forced_C = ctas;
+    return EMPSO_OK;
+}
+
+empso_status empso_set_tile_rows(empso_ctx *ctx, int32_t rows)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (rows != 0 && !resident_rows_supported(rows))
+        return fail(ctx, EMPSO_INVALID_ARG, "rows per thread must be 0 (automatic), 8 or 13");
+    ctx->forced_rows = rows;
+    return EMPSO_OK;
+}
+
+empso_status empso_last_tile_rows(const empso_ctx *ctx, int32_t *rows)
+{
+    if (!ctx || !rows) return EMPSO_INVALID_ARG;
+    *rows = ctx->last_path == 2 ? ctx->last_rows : 0;
     return EMPSO_OK;
 }
 

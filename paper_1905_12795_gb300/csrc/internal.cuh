@@ -13,12 +13,18 @@
 namespace empso {
 
 // Every wavefield / model buffer carries HALO zero cells around the padded
-// grid on all sides, enough for the widest stencil (space order 8, radius 4),
+// grid on all sides, enough for the widest stencil (space order 16, radius 8),
 // so the stencil never tests bounds.  Padded node (I, J) lives at
-// buf[(J + HALO) * pitch + I + HALO]; the interior starts 16 bytes into a row,
-// so float4 group q (nodes 4q .. 4q+3) is 16-byte aligned.
-constexpr int HALO = 4;
-constexpr int MAX_R = 4;
+// buf[(J + HALO) * pitch + I + HALO]; the interior starts 32 bytes into a row,
+// so float4 group q (nodes 4q .. 4q+3) is 16-byte aligned and sits at float4
+// index HALO4 + q of its row.
+constexpr int HALO = 8;
+constexpr int HALO4 = HALO / 4;
+constexpr int MAX_R = 8;
+// radius of the widest stencil of the cluster and streaming modelling kernels
+// (orders 2, 4, 8); order 16 runs on the plain streaming kernel and the
+// per-step adjoint kernels
+constexpr int MAX_R_FAST = 4;
 constexpr int MAX_PSO_P = 2048;
 constexpr int MAX_PSO_D = 1024;
 
@@ -119,6 +125,10 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
 // (the misfit partials, then the x-folded gradient)
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
                               double *phi, double *misfit, float *grad, float *T, cudaStream_t st);
+// the misfit of every model from the residuals of a forward pass (part:
+// scratch of M * S * 64 doubles)
+cudaError_t launch_adj_misfit(const GridDev &g, const AdjInst *insts, int M, int S, double *phi,
+                              double *misfit, double *part, cudaStream_t st);
 cudaError_t launch_fwi_step(const float *v, const float *g, float alpha, float vmin, float vmax,
                             float *out, int n, cudaStream_t st);
 cudaError_t launch_fwi_dots(const float *a, const float *b, const float *c, const float *d, int n,
@@ -160,18 +170,22 @@ cudaError_t launch_finalize(const double *partial, const float *weights, int P, 
 int wave_max_ctas_per_sm(int threads);
 
 // On-chip variant (wave_resident.cu): one thread-block cluster per instance.
-int resident_max_threads();
-int resident_rows_per_thread();
+// `rows`: the rows-per-thread shape (8 or 13).
+int resident_max_threads(int rows);
+int resident_default_rows();
+bool resident_rows_supported(int rows);
+int resident_threads(const GridDev &g, int C, int rows);
 size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch);
-bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit);
+bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit, int rows);
 cudaError_t resident_configure(int R, size_t smem_bytes, int C);
-int resident_max_clusters(int R, int C, int threads, size_t smem_bytes);
+// clusters of the modelling (hist = false) or history instantiation that fit at once
+int resident_max_clusters(int R, int C, int threads, size_t smem_bytes, int rows, bool hist = false);
 // `hist`: the variant that also streams every u^{n+1} into Inst::hist (no
 // halved units)
 cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, const int4 *units,
-                                 int n_units, bool pairs,
-                                 int *counter, int C, int n_clusters, int threads, int ring_pitch,
-                                 size_t smem_bytes, double *partial, cudaStream_t st, bool hist = false);
+                                 int n_units, bool pairs, int *counter, int C, int n_clusters, int threads,
+                                 int rows, int ring_pitch, size_t smem_bytes, double *partial,
+                                 cudaStream_t st, bool hist = false);
 
 // TMA-pipelined streaming variant (wave_stream.cu).
 int stream_max_threads();

@@ -43,17 +43,15 @@ __device__ __forceinline__ void lap_group(const float4 *w, const float *xs, cons
 {
     constexpr int O = 4 * XGroups<R>::G;
     const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
-    const float2 n01 = neg2(c01), n23 = neg2(c23);
+    const float2 m1 = splat2(-1.f);
+    // v - c as one fused operation (-c + v, rounded once): no separate negation
+    auto dif = [&](const float2 &v, const float2 &c) { return __ffma2_rn(c, m1, v); };
     // z: m = 1 (and 2) as differences from the centre, then plain pair sums
-    float2 z01 = __fmul2_rn(splat2(cz[1]), __fadd2_rn(__fadd2_rn(lo2(w[R - 1]), n01),
-                                                      __fadd2_rn(lo2(w[R + 1]), n01)));
-    float2 z23 = __fmul2_rn(splat2(cz[1]), __fadd2_rn(__fadd2_rn(hi2(w[R - 1]), n23),
-                                                      __fadd2_rn(hi2(w[R + 1]), n23)));
+    float2 z01 = __fmul2_rn(splat2(cz[1]), __fadd2_rn(dif(lo2(w[R - 1]), c01), dif(lo2(w[R + 1]), c01)));
+    float2 z23 = __fmul2_rn(splat2(cz[1]), __fadd2_rn(dif(hi2(w[R - 1]), c23), dif(hi2(w[R + 1]), c23)));
     if (R >= 2) {
-        z01 = __ffma2_rn(splat2(cz[2]), __fadd2_rn(__fadd2_rn(lo2(w[R - 2]), n01),
-                                                   __fadd2_rn(lo2(w[R + 2]), n01)), z01);
-        z23 = __ffma2_rn(splat2(cz[2]), __fadd2_rn(__fadd2_rn(hi2(w[R - 2]), n23),
-                                                   __fadd2_rn(hi2(w[R + 2]), n23)), z23);
+        z01 = __ffma2_rn(splat2(cz[2]), __fadd2_rn(dif(lo2(w[R - 2]), c01), dif(lo2(w[R + 2]), c01)), z01);
+        z23 = __ffma2_rn(splat2(cz[2]), __fadd2_rn(dif(hi2(w[R - 2]), c23), dif(hi2(w[R + 2]), c23)), z23);
     }
 #pragma unroll
     for (int m = 3; m <= R; ++m) {
@@ -67,10 +65,10 @@ __device__ __forceinline__ void lap_group(const float4 *w, const float *xs, cons
     float2 x01 = __fmul2_rn(splat2(cx[1]), f2(e[1] - e[0], e[2] - e[1]));
     float2 x23 = __fmul2_rn(splat2(cx[1]), f2(e[3] - e[2], e[4] - e[3]));
     if (R >= 2) {   // m = 2: the pairs line up with the register pairs
-        x01 = __ffma2_rn(splat2(cx[2]), __fadd2_rn(__fadd2_rn(f2(xs[O + 2], xs[O + 3]), n01),
-                                                   __fadd2_rn(f2(xs[O - 2], xs[O - 1]), n01)), x01);
-        x23 = __ffma2_rn(splat2(cx[2]), __fadd2_rn(__fadd2_rn(f2(xs[O + 4], xs[O + 5]), n23),
-                                                   __fadd2_rn(f2(xs[O + 0], xs[O + 1]), n23)), x23);
+        x01 = __ffma2_rn(splat2(cx[2]), __fadd2_rn(dif(f2(xs[O + 2], xs[O + 3]), c01),
+                                                   dif(f2(xs[O - 2], xs[O - 1]), c01)), x01);
+        x23 = __ffma2_rn(splat2(cx[2]), __fadd2_rn(dif(f2(xs[O + 4], xs[O + 5]), c23),
+                                                   dif(f2(xs[O + 0], xs[O + 1]), c23)), x23);
     }
 #pragma unroll
     for (int m = 3; m <= R; ++m) {
@@ -88,6 +86,17 @@ __device__ __forceinline__ void lap_group(const float4 *w, const float *xs, cons
     }
     l01 = __fadd2_rn(x01, z01);
     l23 = __fadd2_rn(x23, z23);
+}
+
+// The x-line of a group for R <= 8 from its float4 neighbours l2, l, r, r2.
+__device__ __forceinline__ void xline2(const float4 &l2, const float4 &l, const float4 &c, const float4 &r,
+                                       const float4 &r2, float *xs)
+{
+    xs[0] = l2.x; xs[1] = l2.y; xs[2] = l2.z; xs[3] = l2.w;
+    xs[4] = l.x; xs[5] = l.y; xs[6] = l.z; xs[7] = l.w;
+    xs[8] = c.x; xs[9] = c.y; xs[10] = c.z; xs[11] = c.w;
+    xs[12] = r.x; xs[13] = r.y; xs[14] = r.z; xs[15] = r.w;
+    xs[16] = r2.x; xs[17] = r2.y; xs[18] = r2.z; xs[19] = r2.w;
 }
 
 // The x-line of a group for R <= 4 from its float4 neighbours l and r.

@@ -111,8 +111,14 @@ __device__ void run_instance(const GridDev &g, const Inst &in, float *bufA, floa
                     float4 um = *reinterpret_cast<const float4 *>(prev + row + col);
                     const float4 av = *reinterpret_cast<const float4 *>(in.a + row + col);
                     const float ezj = g.ez[j + HALO];
-                    float s[12];
-                    xline1(lft, w[R], rgt, s);
+                    float s[4 * (2 * XGroups<R>::G + 1)];
+                    if (XGroups<R>::G == 1) {
+                        xline1(lft, w[R], rgt, s);
+                    } else {
+                        const float4 l2 = *reinterpret_cast<const float4 *>(cur + row + col - 8);
+                        const float4 r2 = *reinterpret_cast<const float4 *>(cur + row + col + 8);
+                        xline2(l2, lft, w[R], rgt, r2, s);
+                    }
                     float2 L01, L23;
                     lap_group<R>(w, s, cx, cz, cres, L01, L23);
                     const float lapv[4] = {L01.x, L01.y, L23.x, L23.y};
@@ -128,7 +134,7 @@ __device__ void run_instance(const GridDev &g, const Inst &in, float *bufA, floa
                             lap = fmaf(b, rn, lap);
                         }
                         const float t = lane(exq, l) + ezj;
-                        const float u0 = s[4 + l];
+                        const float u0 = s[4 * XGroups<R>::G + l];
                         const float num = fmaf(lane(av, l), lap, fmaf(2.f, u0, -(1.f - t) * lane(um, l)));
                         outv[l] = num / (1.f + t);
                     }
@@ -192,7 +198,8 @@ wave_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts, i
         __syncthreads();
         const GridDev g = sg;
         float *bufB = bufA + g.field;
-        if (g.R == 4) run_instance<4, THREADS>(g, in, bufA, bufB, red, partial);
+        if (g.R == 8) run_instance<8, THREADS>(g, in, bufA, bufB, red, partial);
+        else if (g.R == 4) run_instance<4, THREADS>(g, in, bufA, bufB, red, partial);
         else if (g.R == 2) run_instance<2, THREADS>(g, in, bufA, bufB, red, partial);
         else run_instance<1, THREADS>(g, in, bufA, bufB, red, partial);
     }

@@ -199,7 +199,7 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
                         nxt[lr * sp4 + 1 + q] = out;
                         if (HIST)   // written once, read back by a later pass: evict first
                             __stcs(reinterpret_cast<float4 *>(in.hist + (size_t)(n + 1) * gs.field) +
-                                       (size_t)(zr + HALO) * ap4 + 1 + q,
+                                       (size_t)(zr + HALO) * ap4 + HALO4 + q,
                                    out);
                     }
 #pragma unroll
@@ -294,11 +294,11 @@ L2Fn l2_fn(int R, bool hist = false)
     if (hist) {
         if (R == 4) return wave_l2_kernel<4, true>;
         if (R == 2) return wave_l2_kernel<2, true>;
-        return wave_l2_kernel<1, true>;
+        return R == 1 ? wave_l2_kernel<1, true> : nullptr;
     }
     if (R == 4) return wave_l2_kernel<4, false>;
     if (R == 2) return wave_l2_kernel<2, false>;
-    return wave_l2_kernel<1, false>;
+    return R == 1 ? wave_l2_kernel<1, false> : nullptr;
 }
 
 }  // namespace

@@ -6,14 +6,20 @@
 // A thread-block cluster of C CTAs owns one instance at a time (taken from a
 // global queue by cluster rank 0).  The padded grid is split by rows: CTA c
 // holds rows [c*rows_c, (c+1)*rows_c) of u^n and u^{n-1}/u^{n+1} in its shared
-// memory with R halo rows above and below, and keeps its share of the model
-// field a = v^2 dt^2 in registers.  Every step each thread updates ROWS rows
-// of one float4 column group (z-stencil from a register window, x-stencil from
-// the neighbouring float4s in shared memory), writes u^{n+1} in place of
-// u^{n-1}, and stores its slab's first/last R rows straight into the halo rows
-// of the neighbouring CTAs (distributed shared memory).  One cluster barrier
-// (release/acquire) per step orders it all.  Global memory is touched only for
-// the model field (once per instance), the observed traces and the output.
+// memory with R halo rows above and below, and its slab of the model field
+// a = v^2 dt^2 (pre-scaled by the damping).  Every step each thread updates a
+// run of at most RW consecutive rows of one float4 column group (z-stencil
+// from a register window, x-stencil from the neighbouring float4s in shared
+// memory, the next row's inputs read while the current one is computed),
+// writes u^{n+1} in place of u^{n-1}, and then copies its slab's first/last R
+// rows straight into the halo rows of the neighbouring CTAs (distributed
+// shared memory).  One cluster barrier (release/acquire) per step orders it
+// all.  Global memory is touched only for the model field (once per
+// instance), the observed traces and the output.
+//
+// Two shapes of the same code: RW = 8 rows per thread with up to 512 threads
+// (128 registers), and RW = 13 with up to 384 threads (168 registers, fewer
+// and longer runs); the planner and the autotuner choose per batch.
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
@@ -24,8 +30,6 @@ namespace cg = cooperative_groups;
 namespace empso {
 
 namespace {
-
-constexpr int ROWS = 8;
 
 __device__ __forceinline__ void set_comp(float4 &v, int l, float x)
 {
@@ -68,19 +72,114 @@ __device__ __forceinline__ void corners(float x, float z, const GridDev &g, int 
     w[3] = ax * az;
 }
 
+// 1 / x to the hardware reciprocal's accuracy (one MUFU operation)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Source position of the instance, shared by the CTA: bilinear corner (padded
+// indices) and the four weights b / (hx hz)
+struct SrcInfo {
+    int i0, j0;
+    float w[4];
+};
+
+// One step of a work item: rows r0 .. r0 + nrows - 1 (nrows <= RW) of column
+// group q (cq / nq / mq point at group q of row 0 of u^n, u^{n-1} -> u^{n+1}
+// and the pre-scaled model slab).  ZPAD (the same for a whole CTA): some row
+// of the slab lies in the z-damping layer, so g = 1 / (hx + hz) per row;
+// otherwise g is the per-lane constant gx.  The rows are swept downwards
+// (D = 1) or upwards (D = -1, the window mirrored; the stencil is symmetric
+// in z), one instruction stream for both.  The first R rows swept are also
+// halo rows of a neighbouring CTA when `peer` is set: they go to its buffer
+// (shared-row offset peer_off) as soon as they are computed, so the remote
+// stores complete under the rest of the sweep.
+template <int R, int RW, bool ZPAD, bool HIST>
+__device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const float4 *mq, const float *ezs,
+                                           int sp4, int NQ, int r0, int nrows, int D, const float *cx,
+                                           const float *cz, float cres, float2 gx01, float2 gx23,
+                                           float2 hx01, float2 hx23, float4 *hrow, int hp4, float4 *peer,
+                                           int peer_off)
+{
+    const float2 m1 = splat2(-1.f);
+    const int rs = D > 0 ? r0 : r0 + nrows - 1; // first slab row swept
+    const int ds = D * sp4, dm = D * NQ, dh = D * hp4;
+    const float4 *cp = cq + (R + rs) * sp4;      // u^n group of the current row
+    float4 *np = nq + (R + rs) * sp4;            // its u^{n-1} -> u^{n+1}
+    const float4 *ap = mq + rs * NQ;             // its model value
+    float4 *hp = HIST ? hrow + (rs - r0) * hp4 : nullptr;
+    float4 *pp = peer ? peer + (R + rs + peer_off) * sp4 : nullptr;
+    float4 w[2 * R + 1];
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) w[m] = cp[(m - R) * ds];
+    // the inputs of the next row are read before this row is stored
+    // (software pipelined: the loads need not wait behind the store)
+    float4 p_w = cp[R * ds], p_l = cp[-1], p_r = cp[1], p_um = *np, p_av = *ap;
+    float p_hz = ZPAD ? ezs[rs] : 0.f;
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {
+        if (k >= nrows) break;
+        w[2 * R] = p_w;
+        const float4 lft = p_l, rgt = p_r, um = p_um, av = p_av;
+        const float hz = p_hz;
+        if (k + 1 < RW) {
+            p_w = cp[(R + 1) * ds];
+            p_l = cp[ds - 1];
+            p_r = cp[ds + 1];
+            p_um = np[ds];
+            p_av = ap[dm];
+            if (ZPAD) p_hz = ezs[rs + D * (k + 1)];
+        }
+        const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
+        float xs[12];
+        xline1(lft, w[R], rgt, xs);
+        float2 lap01, lap23;
+        lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
+        // u^{n+1} = [2 u^n - (1 - t) u^{n-1} + a lap] / (1 + t)
+        //         = g (u^n - u^{n-1}) + u^{n-1} + (a f) lap,  g = 2 f, f = 1 / (1 + t)
+        // (a f is the pre-scaled model slab)
+        float2 g01 = gx01, g23 = gx23;
+        if (ZPAD) {
+            const float2 d01 = __fadd2_rn(hx01, splat2(hz)), d23 = __fadd2_rn(hx23, splat2(hz));
+            g01 = make_float2(rcp_approx(d01.x), rcp_approx(d01.y));
+            g23 = make_float2(rcp_approx(d23.x), rcp_approx(d23.y));
+        }
+        const float2 um01 = lo2(um), um23 = hi2(um);
+        const float2 o01 = __ffma2_rn(g01, __ffma2_rn(um01, m1, c01), __ffma2_rn(lo2(av), lap01, um01));
+        const float2 o23 = __ffma2_rn(g23, __ffma2_rn(um23, m1, c23), __ffma2_rn(hi2(av), lap23, um23));
+        const float4 out = make_float4(o01.x, o01.y, o23.x, o23.y);
+        *np = out;
+        if (k < R && pp) {
+            *pp = out;
+            pp += ds;
+        }
+        if (HIST) {
+            __stcs(hp, out);                         // written once: evict first
+            hp += dh;
+        }
+        cp += ds;
+        np += ds;
+        ap += dm;
+#pragma unroll
+        for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
+    }
+}
+
 // C CTAs (ranks base .. base + C - 1 of the cluster; crank is the rank among
 // them) run instance `in`; with HIST every u^{n+1} also goes to in.hist
-template <int R, bool HIST>
+template <int R, int RW, bool HIST>
 __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
                                   float4 *M4, float *ezs, float *wring, float *dring, float4 *rec_w,
-                                  int *rec_k, int ring_pitch,
-                                  int C, int crank, int base, cg::cluster_group &cluster, double *cred,
-                                  double *wred, double *partial)
+                                  int *rec_k, SrcInfo &src, int C, int crank, int base,
+                                  cg::cluster_group &cluster, double *cred, double *wred, double *partial)
 {
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
     // scalars of the grid in registers (the descriptor lives in shared memory)
-    const int NQ = gs.NQ, NZ = gs.NZ, NX = gs.NX, nt = gs.nt, pitch = gs.pitch;
+    const int NQ = gs.NQ, NZ = gs.NZ, nt = gs.nt, pitch = gs.pitch;
     const float *__restrict__ gex = gs.ex;
     const float *__restrict__ gez = gs.ez;
     const float *__restrict__ gwav = gs.wavelet;
@@ -103,28 +202,37 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         M4[r * NQ + qq] = make_float4(av.x / (1.f + (exq.x + ez)), av.y / (1.f + (exq.y + ez)),
                                       av.z / (1.f + (exq.z + ez)), av.w / (1.f + (exq.w + ez)));
     }
-    for (int r = tid; r < my_rows; r += nth) ezs[r] = __ldg(gez + z0 + r + HALO);
+    // half the z-damping of each slab row: g = 2 / (1 + t) = 1 / (hx + hz) with
+    // hx = (1 + t_x) / 2 per lane and hz = t_z / 2 per row
+    for (int r = tid; r < my_rows; r += nth) ezs[r] = 0.5f * __ldg(gez + z0 + r + HALO);
+    if (tid == 0) {
+        int i0, j0;
+        float sw[4];
+        corners(in.sx, in.sz, gs, i0, j0, sw);
+        const float inv_cell = 1.f / (gs.hx * gs.hz);
+        src.i0 = i0;
+        src.j0 = j0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) src.w[c] = sw[c] * inv_cell;
+    }
 
-    // work item: column group q and ROWS consecutive slab rows from r0.  Every
-    // item computes exactly ROWS rows (no per-row conditions): the last item of
-    // a column starts at my_rows - ROWS, overlapping its predecessor, and stores
-    // only rows >= seg * ROWS.  rows_c >= ROWS keeps every read inside the slab
-    // buffers even on a short last CTA.
-    const int nseg = (my_rows + ROWS - 1) / ROWS;
+    // work item: column group q and rows [r0, r1) of the slab, the slab's rows
+    // split into nseg runs of at most RW rows each (lengths differ by one at most)
+    const int nseg = (my_rows + RW - 1) / RW;
     const bool active = tid < NQ * nseg;
     const int q = active ? tid % NQ : 0;
     const int seg = active ? tid / NQ : 0;
-    const int r0 = active ? max(0, min(seg * ROWS, my_rows - ROWS)) : 0;
-    const int kfirst = seg * ROWS - r0;          // first row this item stores
-    const int klast = my_rows - r0;              // one past the last row it stores
-    const int rc = ROWS;
+    const int r0 = active ? seg * my_rows / nseg : 0;
+    const int r1 = active ? (seg + 1) * my_rows / nseg : 0;
 
     float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
     // update weight g = 2 / (1 + t) of rows without z-damping: per lane,
-    // constant over the instance (g = 2 in the interior)
+    // constant over the instance (g = 2 in the interior); hx for the others
     const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));
     const float2 gx23 = make_float2(2.f / (1.f + ex.z), 2.f / (1.f + ex.w));
+    const float2 hx01 = make_float2(0.5f * (1.f + ex.x), 0.5f * (1.f + ex.y));
+    const float2 hx23 = make_float2(0.5f * (1.f + ex.z), 0.5f * (1.f + ex.w));
     float cx[R + 1], cz[R + 1];
 #pragma unroll
     for (int m = 0; m <= R; ++m) {
@@ -133,50 +241,62 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     }
     const float cres = gs.cres;
 
-    // source: weights b / (hx hz) of the (up to) two rows and four lanes of
-    // this item that hold one of its bilinear corners
-    int s_i0, s_j0;
-    float sw[4];
-    corners(in.sx, in.sz, gs, s_i0, s_j0, sw);
-    const float inv_cell = 1.f / (gs.hx * gs.hz);
-    const int ks = s_j0 - (z0 + r0);             // item row of the upper corner row
-    float4 sb0 = make_float4(0.f, 0.f, 0.f, 0.f), sb1 = sb0;
-    bool src_here = false;
-    if (active && s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3 && ks + 1 >= 0 && ks < rc) {
-        src_here = true;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const int I = 4 * q + l;
-            const float bx0 = (I == s_i0 ? 1.f : 0.f), bx1 = (I == s_i0 + 1 ? 1.f : 0.f);
-            set_comp(sb0, l, (bx0 * sw[0] + bx1 * sw[1]) * inv_cell);
-            set_comp(sb1, l, (bx0 * sw[2] + bx1 * sw[3]) * inv_cell);
-        }
-    }
-
     // receivers: bilinear corners and weights of every receiver, computed once
     // per instance; rec_k = float index of the lower-left corner in this CTA's
     // slab, or -1 when another CTA holds the receiver's lower corner row
     const int nrec = in.nrec;
     const float *__restrict__ dobs = in.dobs;
+    int owns = 0;
     for (int r = tid; r < nrec; r += nth) {
         const float2 pr = in.rec[r];
         int i0, j0;
         float w4[4];
         corners(pr.x, pr.y, gs, i0, j0, w4);
         const bool mine = j0 >= z0 && j0 < z0 + my_rows;
+        owns |= mine;
         rec_k[r] = mine ? (j0 - z0 + R) * (4 * sp4) + 4 + i0 : -1;
         rec_w[r] = make_float4(w4[0], w4[1], w4[2], w4[3]);
     }
+    // CTAs that hold no receiver skip the per-step receiver loops
+    const bool has_rec = __syncthreads_or(owns) != 0;
     // staging prologue: the wavelet sample of step 0
     if (tid == 0 && nt > 0) cp_async4(wring, gwav);
     cp_async_commit();
     cp_async_wait<0>();
     float accf = 0.f;
     double acc = 0.0;
-    (void)NX;
-    (void)ring_pitch;
 
     cluster.sync();                                      // zeroed everywhere before halo stores
+
+    // some row of the slab in the z-damping layer (rows of the layer are the
+    // first and last of the grid, so the slab's end rows tell); the same path
+    // for every thread of the CTA
+    const bool zpad = my_rows > 0 && (ezs[0] != 0.f || ezs[my_rows - 1] != 0.f);
+    // The source: the items holding a row of its corners add (a f) b r(t_n) to
+    // those points after their rows (u^{n+1} is linear in the source term).
+    // sbit: bit c = 1 when corner row s_j0 + c is one of this item's rows and
+    // one of the corner columns lies in group q.
+    const int s_i0 = src.i0, s_j0 = src.j0;
+    unsigned sbit = 0;
+    if (active && s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int rr = s_j0 + c - z0;
+            if (rr >= r0 && rr < r1) sbit |= 1u << c;
+        }
+    // the item's role: 1 the first run of a CTA with a CTA above (sweeps down,
+    // hands its top rows up first), 2 the last of two or more runs of a CTA
+    // with a CTA below (sweeps up, hands its bottom rows down first), 0 any
+    // other run (sweeps down); tail: the only run of a CTA with a CTA below
+    // copies its bottom rows down after the sweep
+    const bool has_prev = crank > 0, has_next = crank < C - 1;
+    int role = 0;
+    bool tail = false;
+    if (active) {
+        if (nseg > 1 && seg == nseg - 1) role = has_next ? 2 : 0;
+        else if (seg == 0) role = has_prev ? 1 : 0;
+        tail = nseg == 1 && has_next;
+    }
 
     // neighbours' views of both time-level buffers
     float4 *prev_A = nullptr, *prev_B = nullptr, *next_A = nullptr, *next_B = nullptr;
@@ -188,13 +308,12 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         next_A = cluster.map_shared_rank(A4, base + crank + 1);
         next_B = cluster.map_shared_rank(B4, base + crank + 1);
     }
-    const bool top_item = r0 < R;                        // may hold halo rows of the CTA above
-    const bool bot_item = r0 + ROWS > rows_c - R;        // ... of the CTA below
 
     // history: this item's first row in slot n + 1 (advanced one field per step)
     float4 *hrow = nullptr;
+    const int hp4 = pitch / 4;
     if (HIST && active)
-        hrow = reinterpret_cast<float4 *>(in.hist) + (size_t)(z0 + r0 + HALO) * (pitch / 4) + 1 + q;
+        hrow = reinterpret_cast<float4 *>(in.hist) + (size_t)(z0 + r0 + HALO) * hp4 + HALO4 + q;
     float4 *cur = A4, *nxt = B4;
     for (int n = 0; n <= nt; ++n) {
         if (HIST) hrow += gs.field / 4;
@@ -203,73 +322,58 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         {
             const int iw = n + 1, ir = n;
             if (tid == 0 && iw < nt) cp_async4(wring + iw % DEPTH, gwav + iw);
-            if (dobs && ir < nt)
+            if (has_rec && dobs && ir < nt)
                 for (int r = tid; r < nrec; r += nth)
                     if (rec_k[r] >= 0)
                         cp_async4(dring + (ir % DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
             cp_async_commit();
         }
         if (n < nt && active) {
-            const float rn = wring[n % DEPTH];
+            const float4 *cq = cur + 1 + q;           // group q of shared row 0
+            float4 *nq = nxt + 1 + q;
+            const float4 *mq = M4 + q;
             const bool even = (n & 1) == 0;           // nxt is B4 on even steps, A4 on odd
-            float4 *prevA = even ? prev_B : prev_A;
-            float4 *nextA = even ? next_B : next_A;
-            float4 w[2 * R + 1];
+            float4 *pq = has_prev ? (even ? prev_B : prev_A) + 1 + q : nullptr;
+            float4 *xq = has_next ? (even ? next_B : next_A) + 1 + q : nullptr;
+            // the first run sweeps down and hands its top rows to the CTA above
+            // first; the last run sweeps up and hands its bottom rows to the
+            // CTA below first; a middle run has no halo rows
+            float4 *peer = role == 1 ? pq : (role == 2 ? xq : nullptr);
+            const int D = role == 2 ? -1 : 1;
+            const int poff = role == 2 ? -rows_c : rows_c;
+            if (zpad)
+                sweep_item<R, RW, true, HIST>(cq, nq, mq, ezs, sp4, NQ, r0, r1 - r0, D, cx, cz, cres, gx01, gx23,
+                                              hx01, hx23, hrow, hp4, peer, poff);
+            else
+                sweep_item<R, RW, false, HIST>(cq, nq, mq, ezs, sp4, NQ, r0, r1 - r0, D, cx, cz, cres, gx01,
+                                               gx23, hx01, hx23, hrow, hp4, peer, poff);
+            if (tail)
+                for (int rr = max(r0, rows_c - R); rr < r1; ++rr) xq[(R + rr - rows_c) * sp4] = nq[(R + rr) * sp4];
+            if (sbit) {   // the source term of the item's corner rows
+                const float rn = wring[n % DEPTH];
+                for (int c = 0; c < 2; ++c) {
+                    if (!((sbit >> c) & 1u)) continue;
+                    const int rr = s_j0 + c - z0, lr = R + rr;
+                    float4 v = nq[lr * sp4];
+                    const float4 av = mq[rr * NQ];
+                    float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float b0 = src.w[2 * c] * rn, b1 = src.w[2 * c + 1] * rn;
 #pragma unroll
-            for (int m = 0; m < 2 * R; ++m) w[m] = cur[(r0 + m) * sp4 + 1 + q];
-#pragma unroll
-            for (int k = 0; k < ROWS; ++k) {
-                {
-                    const int lr = R + r0 + k;           // shared row of the output
-                    w[2 * R] = cur[(lr + R) * sp4 + 1 + q];
-                    const float4 lft = cur[lr * sp4 + q];
-                    const float4 rgt = cur[lr * sp4 + 2 + q];
-                    const float4 um = nxt[lr * sp4 + 1 + q];
-                    const float4 av = M4[(r0 + k) * NQ + q];
-                    // Laplacian of lanes (0,1) and (2,3) with packed FP32x2 arithmetic;
-                    // x and z parts accumulate separately (two independent chains)
-                    const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
-                    float xs[12];
-                    xline1(lft, w[R], rgt, xs);
-                    float2 lap01, lap23;
-                    lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
-                    if (src_here && (k == ks || k == ks + 1)) {
-                        const float4 sb = (k == ks) ? sb0 : sb1;
-                        lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);
-                        lap23 = __ffma2_rn(make_float2(sb.z, sb.w), make_float2(rn, rn), lap23);
+                    for (int l = 0; l < 4; ++l) {
+                        const int I = 4 * q + l;
+                        set_comp(b, l, (I == s_i0 ? b0 : 0.f) + (I == s_i0 + 1 ? b1 : 0.f));
                     }
-                    // u^{n+1} = [2 u^n - (1 - t) u^{n-1} + a lap] / (1 + t)
-                    //         = g (u^n - u^{n-1}) + u^{n-1} + (a f) lap,  g = 2 f, f = 1 / (1 + t)
-                    // (a f is the pre-scaled model slab); one branch-free form for
-                    // interior and damping layer, g per lane and row
-                    const float ezk = ezs[r0 + k];
-                    float2 g01 = gx01, g23 = gx23;
-                    if (ezk != 0.f) {
-                        g01 = make_float2(__fdividef(2.f, 1.f + (ex.x + ezk)), __fdividef(2.f, 1.f + (ex.y + ezk)));
-                        g23 = make_float2(__fdividef(2.f, 1.f + (ex.z + ezk)), __fdividef(2.f, 1.f + (ex.w + ezk)));
-                    }
-                    const float2 um01 = make_float2(um.x, um.y), um23 = make_float2(um.z, um.w);
-                    const float2 o01 = __ffma2_rn(g01, __fadd2_rn(c01, make_float2(-um.x, -um.y)),
-                                                  __ffma2_rn(make_float2(av.x, av.y), lap01, um01));
-                    const float2 o23 = __ffma2_rn(g23, __fadd2_rn(c23, make_float2(-um.z, -um.w)),
-                                                  __ffma2_rn(make_float2(av.z, av.w), lap23, um23));
-                    const float4 out = make_float4(o01.x, o01.y, o23.x, o23.y);
-                    if (k >= kfirst && k < klast) {
-                        nxt[lr * sp4 + 1 + q] = out;
-                        if (HIST) __stcs(hrow + k * (pitch / 4), out);   // written once: evict first
-                        // halo rows of the neighbours
-                        const int rr = r0 + k;
-                        if (top_item && prevA && rr < R) prevA[(rr + rows_c + R) * sp4 + 1 + q] = out;
-                        if (bot_item && nextA && rr >= rows_c - R)
-                            nextA[(rr - rows_c + R) * sp4 + 1 + q] = out;
-                    }
+                    v = make_float4(fmaf(av.x, b.x, v.x), fmaf(av.y, b.y, v.y), fmaf(av.z, b.z, v.z),
+                                    fmaf(av.w, b.w, v.w));
+                    nq[lr * sp4] = v;
+                    if (HIST) __stcs(hrow + (rr - r0) * hp4, v);
+                    if (pq && rr < R) pq[(lr + rows_c) * sp4] = v;
+                    if (xq && rr >= rows_c - R) xq[(lr - rows_c) * sp4] = v;
                 }
-#pragma unroll
-                for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
             }
         }
         // receivers sample u^n (record n - 1)
-        if (n >= 1) {
+        if (has_rec && n >= 1) {
             const float *cf = reinterpret_cast<const float *>(cur);
             const int sp = 4 * sp4;
             for (int r = tid; r < nrec; r += nth) {
@@ -289,6 +393,7 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
                 accf = 0.f;
             }
         }
+
         // this step's copies have landed; the barrier publishes them
         cp_async_wait<0>();
         cluster.sync();
@@ -323,9 +428,15 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
 // ranks C/2 .. C - 1 instance b, both of the same grid (so both halves pass
 // the same number of cluster barriers).  Launches with no halved unit use the
 // PAIRS = false instantiation, where the whole-cluster layout is constant.
-// HIST (never with PAIRS) also writes the wavefield history.
-template <int R, int NT, bool PAIRS, bool HIST>
-__global__ void __launch_bounds__(NT, 1)
+// HIST (never with PAIRS) also writes the wavefield history.  NT threads at
+// most: registers per thread are capped so that NT / 128 warps per scheduler
+// fit its quarter of the register file.
+template <int NT> struct RegCap {
+    static constexpr int v = (16384 / (((NT / 32) + 3) / 4 * 32)) / 8 * 8;
+};
+
+template <int R, int NT, int RW, bool PAIRS, bool HIST>
+__global__ void __launch_bounds__(NT) __maxnreg__(RegCap<NT>::v)
 wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts,
                      const int4 *__restrict__ units, int n_units, int *counter, int ring_pitch,
                      double *partial)
@@ -335,6 +446,7 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
     __shared__ double cred[16];
     __shared__ double wred[NT / 32];
     __shared__ GridDev sg;
+    __shared__ SrcInfo src;
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -363,17 +475,29 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float *dring = wring + 4 * ((DEPTH + 3) / 4);
         float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
         int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
-        resident_instance<R, HIST>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, ring_pitch, Ce,
-                             ce, sub * Ce, cluster, cred, wred, partial);
+        resident_instance<R, RW, HIST>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, src, Ce, ce,
+                                       sub * Ce, cluster, cred, wred, partial);
     }
 }
 
-constexpr int RES_NT = 512;
+// The two shapes: rows per thread and thread bound
+constexpr int RW_A = 8, NT_A = 512;
+constexpr int RW_B = 13, NT_B = 384;
+
+int shape_threads(int rows) { return rows == RW_B ? NT_B : NT_A; }
 
 }  // namespace
 
-int resident_max_threads() { return RES_NT; }
-int resident_rows_per_thread() { return ROWS; }
+int resident_max_threads(int rows) { return shape_threads(rows); }
+int resident_default_rows() { return RW_A; }
+bool resident_rows_supported(int rows) { return rows == RW_A || rows == RW_B; }
+
+// threads of the work items of grid g on C CTAs with runs of at most `rows` rows
+int resident_threads(const GridDev &g, int C, int rows)
+{
+    const int rows_c = (g.NZ + C - 1) / C;
+    return (g.NQ * ((rows_c + rows - 1) / rows) + 31) / 32 * 32;
+}
 
 // two time levels with halo rows, the slab of the model field, its damping
 // rows, the staging buffers (wavelet samples, observed records) and the
@@ -387,70 +511,66 @@ size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch)
            (sizeof(float4) + sizeof(int)) * (size_t)ring_pitch;
 }
 
-// Does grid g run on a cluster of C CTAs?  Each CTA needs at least R rows (so
-// halos come from the nearest neighbour only), no CTA may be empty, the work
-// items must fit one thread each, and the two time levels plus the model slab
-// the shared memory.
-bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit)
+// Does grid g run on a cluster of C CTAs with runs of at most `rows` rows?
+// Each CTA needs at least R rows (so halos come from the nearest neighbour
+// only), no CTA may be empty, the work items must fit one thread each, and
+// the two time levels plus the model slab the shared memory.
+bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit, int rows)
 {
     const int rows_c = (g.NZ + C - 1) / C;
-    if (rows_c < g.R || rows_c < ROWS) return false;
+    if (rows_c < g.R || !resident_rows_supported(rows)) return false;
     if ((C - 1) * rows_c >= g.NZ) return false;
-    const int nseg = (rows_c + ROWS - 1) / ROWS;
-    if (g.NQ * nseg > RES_NT) return false;
+    if (resident_threads(g, C, rows) > shape_threads(rows)) return false;
     return resident_smem_bytes(g, C, ring_pitch) <= smem_limit;
 }
 
 namespace {
-template <int R, bool PAIRS, bool HIST>
-cudaError_t configure_rp(size_t smem_bytes, int C)
-{
-    cudaError_t e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS, HIST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    if (C > 8)
-        e = cudaFuncSetAttribute(wave_resident_kernel<R, RES_NT, PAIRS, HIST>,
-                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    return e;
-}
-
-template <int R>
-cudaError_t configure_r(size_t smem_bytes, int C)
-{
-    cudaError_t e = configure_rp<R, false, false>(smem_bytes, C);
-    if (e == cudaSuccess) e = configure_rp<R, true, false>(smem_bytes, C);
-    return e != cudaSuccess ? e : configure_rp<R, false, true>(smem_bytes, C);
-}
 
 using ResidentFn = void (*)(const GridDev *, const Inst *, const int4 *, int, int *, int, double *);
 
-ResidentFn resident_fn(int R, bool pairs, bool hist = false)
+template <int NT, int RW>
+ResidentFn resident_fn_shape(int R, bool pairs, bool hist)
 {
     if (hist) {
-        if (R == 4) return wave_resident_kernel<4, RES_NT, false, true>;
-        if (R == 2) return wave_resident_kernel<2, RES_NT, false, true>;
-        return wave_resident_kernel<1, RES_NT, false, true>;
+        if (R == 4) return wave_resident_kernel<4, NT, RW, false, true>;
+        if (R == 2) return wave_resident_kernel<2, NT, RW, false, true>;
+        return R == 1 ? wave_resident_kernel<1, NT, RW, false, true> : nullptr;
     }
     if (pairs) {
-        if (R == 4) return wave_resident_kernel<4, RES_NT, true, false>;
-        if (R == 2) return wave_resident_kernel<2, RES_NT, true, false>;
-        return wave_resident_kernel<1, RES_NT, true, false>;
+        if (R == 4) return wave_resident_kernel<4, NT, RW, true, false>;
+        if (R == 2) return wave_resident_kernel<2, NT, RW, true, false>;
+        return R == 1 ? wave_resident_kernel<1, NT, RW, true, false> : nullptr;
     }
-    if (R == 4) return wave_resident_kernel<4, RES_NT, false, false>;
-    if (R == 2) return wave_resident_kernel<2, RES_NT, false, false>;
-    return wave_resident_kernel<1, RES_NT, false, false>;
+    if (R == 4) return wave_resident_kernel<4, NT, RW, false, false>;
+    if (R == 2) return wave_resident_kernel<2, NT, RW, false, false>;
+    if (R == 1) return wave_resident_kernel<1, NT, RW, false, false>;
+    return nullptr;
+}
+
+ResidentFn resident_fn(int R, bool pairs, bool hist, int rows)
+{
+    return rows == RW_B ? resident_fn_shape<NT_B, RW_B>(R, pairs, hist)
+                        : resident_fn_shape<NT_A, RW_A>(R, pairs, hist);
 }
 }  // namespace
 
 cudaError_t resident_configure(int R, size_t smem_bytes, int C)
 {
-    if (R == 4) return configure_r<4>(smem_bytes, C);
-    if (R == 2) return configure_r<2>(smem_bytes, C);
-    return configure_r<1>(smem_bytes, C);
+    for (const int rows : {RW_A, RW_B})
+        for (const bool pairs : {false, true})
+            for (const bool hist : {false, true}) {
+                if (pairs && hist) continue;
+                const ResidentFn f = resident_fn(R, pairs, hist, rows);
+                cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem_bytes);
+                if (e == cudaSuccess && C > 8)
+                    e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                if (e != cudaSuccess) return e;
+            }
+    return cudaSuccess;
 }
 
-int resident_max_clusters(int R, int C, int threads, size_t smem_bytes)
+int resident_max_clusters(int R, int C, int threads, size_t smem_bytes, int rows, bool hist)
 {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -464,7 +584,7 @@ int resident_max_clusters(int R, int C, int threads, size_t smem_bytes)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, resident_fn(R, false), &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, resident_fn(R, false, hist, rows), &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -473,8 +593,8 @@ int resident_max_clusters(int R, int C, int threads, size_t smem_bytes)
 
 cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *insts, const int4 *units,
                                  int n_units, bool pairs, int *counter, int C, int n_clusters, int threads,
-                                 int ring_pitch, size_t smem_bytes, double *partial, cudaStream_t st,
-                                 bool hist)
+                                 int rows, int ring_pitch, size_t smem_bytes, double *partial,
+                                 cudaStream_t st, bool hist)
 {
     if (n_units <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
@@ -489,8 +609,8 @@ cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *in
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, resident_fn(R, pairs && !hist, hist), grids_dev, insts, units, n_units, counter,
-                              ring_pitch, partial);
+    return cudaLaunchKernelEx(&cfg, resident_fn(R, pairs && !hist, hist, rows), grids_dev, insts, units,
+                              n_units, counter, ring_pitch, partial);
 }
 
 }  // namespace empso

@@ -208,7 +208,7 @@ __device__ void stream_instance(const GridDev &g, const Inst &in, float *bufA, f
             wait_m(k);
             if (k == 0 && active) {
 #pragma unroll
-                for (int m = 0; m < 2 * R; ++m) w[m] = urow(m - R)[1 + q];
+                for (int m = 0; m < 2 * R; ++m) w[m] = urow(m - R)[HALO4 + q];
             }
             const unsigned ms = (mcount + (unsigned)k) % RG::MC;
 #pragma unroll
@@ -216,12 +216,12 @@ __device__ void stream_instance(const GridDev &g, const Inst &in, float *bufA, f
                 const int J = J0 + b;
                 const bool live = J < NZ;
                 if (active) {
-                    w[2 * R] = urow(J + R)[1 + q];
+                    w[2 * R] = urow(J + R)[HALO4 + q];
                     const float4 *crow = urow(J);
-                    const float4 lft = crow[q];
-                    const float4 rgt = crow[2 + q];
-                    const float4 um = mring[((size_t)ms * RB + b) * sp4 + 1 + q];
-                    const float4 av = aring[((size_t)ms * RB + b) * sp4 + 1 + q];
+                    const float4 lft = crow[HALO4 - 1 + q];
+                    const float4 rgt = crow[HALO4 + 1 + q];
+                    const float4 um = mring[((size_t)ms * RB + b) * sp4 + HALO4 + q];
+                    const float4 av = aring[((size_t)ms * RB + b) * sp4 + HALO4 + q];
                     const float ezj = live ? __ldg(g.ez + J + HALO) : 0.f;
                     float s[12];
                     xline1(lft, w[R], rgt, s);
@@ -240,11 +240,11 @@ __device__ void stream_instance(const GridDev &g, const Inst &in, float *bufA, f
                             lap = fmaf(bw, rn, lap);
                         }
                         const float t = lane4(ex, l) + ezj;
-                        const float num = fmaf(lane4(av, l), lap, fmaf(2.f, s[4 + l], -(1.f - t) * lane4(um, l)));
+                        const float num = fmaf(lane4(av, l), lap, fmaf(2.f, s[4 * XGroups<R>::G + l], -(1.f - t) * lane4(um, l)));
                         o[l] = (t == 0.f) ? num : __fdividef(num, 1.f + t);
                     }
                     if (live)
-                        reinterpret_cast<float4 *>(nxt + (size_t)(J + HALO) * g.pitch)[1 + q] =
+                        reinterpret_cast<float4 *>(nxt + (size_t)(J + HALO) * g.pitch)[HALO4 + q] =
                             make_float4(o[0], o[1], o[2], o[3]);
                 }
                 // receivers with lower corner row J sample u^n (record n - 1)
@@ -378,7 +378,7 @@ StreamFn stream_fn(int R)
 {
     if (R == 4) return wave_stream_kernel<4>;
     if (R == 2) return wave_stream_kernel<2>;
-    return wave_stream_kernel<1>;
+    return R == 1 ? wave_stream_kernel<1> : nullptr;
 }
 
 }  // namespace

@@ -94,7 +94,8 @@ def test_host_functions_through_the_binding(lib):
 @pytest.mark.parametrize("order,nx,nz,h,T,vmax", [(2, 37, 29, 10.0, 0.3, 3200.0),
                                                    (4, 101, 101, 10.0, 0.5, 2625.0),
                                                    (8, 461, 151, 20.0, 3.0, 4700.0),
-                                                   (8, 921, 301, 10.0, 4.0, 4700.0)])
+                                                   (8, 921, 301, 10.0, 4.0, 4700.0),
+                                                   (16, 301, 121, 10.0, 2.0, 4700.0)])
 def test_context_free_time_axis_matches_oracle(lib, order, nx, nz, h, T, vmax):
     """Host logic only (no device work): the library's CFL time axis for a
     grid equals the oracle's, and invalid grids are refused with the codes

@@ -117,6 +117,45 @@ def test_gradient_field_matches_oracle_at_every_node(B, order, kernel):
     ctx.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_gradient_order16_matches_oracle(B, kernel):
+    """The gradient with the 16th-order operator of the paper's local FWI
+    (per-step forward and adjoint launches) against central differences of
+    the oracle misfit: a dense direction and one node on the model's edge."""
+    nx, nz, h, pad, T, f0, vmax = 41, 31, 10.0, 10, 0.25, 15.0, 3000.0
+    og = oracle.Grid(nx, nz, h, h, pad, 16, T, f0, vmax)
+    v = synth.layered_faulted_model(nx, nz, h, h, seed=5, vmin=1500.0, vmax=2800.0)
+    v_true = synth.layered_faulted_model(nx, nz, h, h, seed=6, vmin=1500.0, vmax=2800.0)
+    shots = np.array([[105.0, 23.0], [297.0, 41.0]])
+    rec = synth.receiver_line(nx, h, 27.0)[:-1] + np.array([3.7, 0.0])
+    nrec = len(rec)
+    rb, rc = [0, 0], [nrec, nrec]
+    _, obs = oracle.shot_batch(og, v_true, shots, rec, rb, rc, want_traces=True)
+
+    def phi(vel):
+        p, _ = oracle.shot_batch(og, vel, shots, rec, rb, rc, dobs=obs)
+        return float(np.sum(p[0]))
+
+    ctx = B.Context([B.make_grid(nx, nz, h, h, pad, 16, T, f0, 1500.0, vmax)], rec)
+    ctx.set_kernel(kernel)
+    g = torch.zeros(1, nz, nx, device="cuda")
+    mis = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.gradient(_dev(v[None]), B.make_shots(shots, rb, rc),
+                 _dev(np.concatenate([o.ravel() for o in obs])), g, mis)
+    G = g[0].cpu().numpy().astype(np.float64)
+    assert mis.item() == pytest.approx(phi(v), rel=1e-4)
+    rng = np.random.default_rng(16)
+    cases = [(rng.normal(size=(nz, nx)), 1.0, 2e-3)]
+    d = np.zeros((nz, nx))
+    d[20, 0] = 1.0
+    cases.append((d, 5.0, 1e-2))
+    for d, eps, tol in cases:
+        fd = (phi(v + eps * d) - phi(v - eps * d)) / (2 * eps)
+        ad = float(np.sum(G * d))
+        assert abs(ad - fd) <= tol * abs(fd), (ad, fd)
+    ctx.close()
+
+
 def test_gradient_batch_of_models_equals_single_calls(B):
     nx, nz, h = 37, 29, 10.0
     grid = B.make_grid(nx, nz, h, h, 6, 4, 0.2, 15.0, 1500.0, 3000.0)
@@ -175,9 +214,13 @@ def test_gradient_edge_cases(B):
     ctx.close()
 
 
-def test_fwi_descends_and_improves_the_model(B):
+@pytest.mark.parametrize("order", [4, 16])
+def test_fwi_descends_and_improves_the_model(B, order):
+    """Steepest descent with the BB step and backtracking (section "Testing
+    approach", local FWI) from a smoothed model; order 16 is the paper's
+    operator for it (line-search misfits on the gradient's forward pass)."""
     nx, nz, h, pad = 61, 41, 10.0, 10
-    grid = B.make_grid(nx, nz, h, h, pad, 4, 0.45, 12.0, 1400.0, 3000.0)
+    grid = B.make_grid(nx, nz, h, h, pad, order, 0.45, 12.0, 1400.0, 3000.0)
     rec = synth.receiver_line(nx, h, 20.0)
     ctx = B.Context([grid], rec)
     _, nt = ctx.grid_info(0)

@@ -90,6 +90,65 @@ def test_traces_match_oracle(B, kind, order, nx, nz, pad, h):
     ctx.close()
 
 
+@pytest.mark.parametrize("rows", [8, 13])
+@pytest.mark.parametrize("order,nx,nz,pad,h,C", [
+    (8, 70, 61, 9, 15.0, 3),     # 79 rows on 3 CTAs: runs of unequal length
+    (4, 61, 45, 10, 12.5, 5),    # 13 rows per CTA, a short last CTA
+    (2, 37, 29, 7, 10.0, 2),
+])
+def test_on_chip_row_shapes_match_oracle(B, rows, order, nx, nz, pad, h, C):
+    """Both rows-per-thread shapes of the on-chip kernel against the oracle,
+    with the source and receivers off the grid nodes."""
+    vmax = 3200.0
+    og = oracle.Grid(nx, nz, h, h, pad, order, 0.3, 12.0, vmax)
+    vel = synth.layered_faulted_model(nx, nz, h, h, seed=order + nx, vmin=1500.0, vmax=vmax)
+    shots, rec = _geometry(nx, nz, h, 3, 2.5 * h, 1.5 * h, off_grid=True)
+    nrec = len(rec)
+    _, ref = oracle.shot_batch(og, vel, shots, rec, [0] * 3, [nrec] * 3, want_traces=True)
+    ctx = B.Context([B.make_grid(nx, nz, h, h, pad, order, 0.3, 12.0, 1500.0, vmax)], rec)
+    ctx.set_kernel(2)
+    ctx.set_cluster(C)
+    ctx.set_tile_rows(rows)
+    out = torch.zeros(3 * og.nt * nrec, device="cuda")
+    ctx.forward_traces(_dev(vel[None]), B.make_shots(shots, [0] * 3, [nrec] * 3), out)
+    assert ctx.last_launch() == (2, C) and ctx.last_tile_rows() == rows
+    got = out.cpu().numpy().reshape(3, og.nt, nrec)
+    for s in range(3):
+        assert _rel_l2(got[s], ref[s]) < TRACE_TOL, (s, _rel_l2(got[s], ref[s]))
+    with pytest.raises(B.EmpsoError):
+        ctx.set_tile_rows(7)
+    ctx.close()
+
+
+@pytest.mark.parametrize("nx,nz,pad,h", [(70, 33, 9, 15.0), (37, 29, 12, 10.0)])
+def test_order16_traces_match_oracle(B, nx, nz, pad, h):
+    """Order 16 in space (the local FWI's operator) runs on the plain
+    streaming kernel: traces against the oracle; the cluster kernels, which
+    hold radius-4 stencils, refuse it."""
+    vmax = 3200.0
+    og = oracle.Grid(nx, nz, h, h, pad, 16, 0.3, 12.0, vmax)
+    vel = synth.layered_faulted_model(nx, nz, h, h, seed=16 + nx, vmin=1500.0, vmax=vmax)
+    shots, rec = _geometry(nx, nz, h, 3, 2.5 * h, 1.5 * h, off_grid=True)
+    nrec = len(rec)
+    _, ref = oracle.shot_batch(og, vel, shots, rec, [0] * 3, [nrec] * 3, want_traces=True)
+    ctx = B.Context([B.make_grid(nx, nz, h, h, pad, 16, 0.3, 12.0, 1500.0, vmax)], rec)
+    dt, nt = ctx.grid_info(0)
+    assert nt == og.nt and dt == pytest.approx(og.dt, rel=1e-6)
+    out = torch.zeros(3 * og.nt * nrec, device="cuda")
+    sh = B.make_shots(shots, [0] * 3, [nrec] * 3)
+    ctx.forward_traces(_dev(vel[None]), sh, out)
+    assert ctx.last_launch() == (1, 1) and ctx.last_kernel_name() == "wave_kernel"
+    got = out.cpu().numpy().reshape(3, og.nt, nrec)
+    for s in range(3):
+        assert _rel_l2(got[s], ref[s]) < TRACE_TOL, (s, _rel_l2(got[s], ref[s]))
+    for kind in (2, 3):
+        ctx.set_kernel(kind)
+        with pytest.raises(B.EmpsoError) as e:
+            ctx.forward_traces(_dev(vel[None]), sh, out)
+        assert e.value.status == 6
+    ctx.close()
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_single_forward_two_layer(B, kind):
     """Two-layer model (1500/2500 m/s, interface at 500 m) on 101 x 101 at 10 m
