@@ -44,6 +44,13 @@ METRIC = ("grid-pt updates/s + PSO fitness evals/s at 1 GB300; wall-clock to tar
           "surrogate vs plain")
 WORKLOAD = "empso-461x151-P32-S16"
 BYTES_PER_UPDATE = 16          # read u^n, u^{n-1}, a; write u^{n+1} (FP32)
+# FP32 lane operations per grid-point update of the on-chip kernel (an FMA
+# counts one), from its ncu instruction counters: 2 (FADD2 + FFMA2 + FMUL2) +
+# FADD per update = 2 (3.739 + 8.044 + 1.006) + 3.273 (profiles/
+# wave_resident_kernel_empso-461x151.md); the FP32 pipes retire 128 lane
+# operations per SM per clock
+FP32_OPS_PER_UPDATE = {"wave_resident_kernel": 28.85}
+FP32_LANES_PER_SM = 128
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -67,6 +74,8 @@ def _args():
     ap.add_argument("--surrogate-seeds", type=int, default=9)
     ap.add_argument("--trials", type=int, default=5, help="PSO vs EMPSO comparison trials")
     ap.add_argument("--bands", type=int, default=0, help="fwi workload: number of bands (0: all six)")
+    ap.add_argument("--no-sub-workloads", action="store_true",
+                    help="default run: skip the bounded uneven and hires sub-results")
     ap.add_argument("--gradient-case", type=int, default=0,
                     help="time one adjoint gradient of this many shots")
     ap.add_argument("--surrogate-case", type=int, default=0,
@@ -343,6 +352,21 @@ def run_ours(a):
     achieved = BYTES_PER_UPDATE * upd_step / (wave_mean / 1e3) / 1e9
     kname = ctx.last_kernel_name()
     traffic = _traffic_from_profile(kname)
+    rows = ctx.last_tile_rows()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    roof_sm = None
+    if kname in FP32_OPS_PER_UPDATE:
+        ops = FP32_OPS_PER_UPDATE[kname]
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        busy = launch[1] * ctx.last_clusters() if launch[0] == 2 else sm_count
+        peak_ops = sm_count * FP32_LANES_PER_SM * mhz * 1e6
+        ach_ops = ops * upd_step / (wave_mean / 1e3)
+        roof_sm = {"kernel": kname, "bound": "fp32", "achieved": ach_ops / 1e12,
+                   "peak": peak_ops / 1e12, "unit": "T FP32 ops/s (FMA = 1)",
+                   "frac": ach_ops / peak_ops, "ops_per_update": ops,
+                   "peak_from": f"{sm_count} SMs x {FP32_LANES_PER_SM} lanes x {mhz:.0f} MHz (median under load)",
+                   "sms_busy": busy, "frac_of_busy_sms": ach_ops / (busy * FP32_LANES_PER_SM * mhz * 1e6)}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -350,6 +374,14 @@ def run_ours(a):
     sur = None
     if rank == 0 and not a.no_surrogate:
         sur = surrogate_vs_plain(a.surrogate_seeds)
+    subs = {}
+    if rank == 0 and world == 1 and not a.no_sub_workloads:
+        # bounded sub-results: one uneven generation of the mixed-resolution
+        # batch (planner's shape) and a 2 x 64 sample of the hires generation
+        # (autotuned over the L2 cluster kernel's sizes)
+        subs["uneven"] = _uneven_result("uneven-P256-S16x2", steps=2, warmup=1, tune=False)
+        subs["hires"] = _hires_result("hires-921x301-P512-S64", P=2, steps=2, warmup=1, tune_kind=3,
+                                      prescreen=False)
 
     if rank == 0:
         line = {
@@ -368,7 +400,9 @@ def run_ours(a):
                     "d2h_bytes_per_step": int(mis.numel() * 8),
                     "fitness_evals_per_s": world * wl.P * a.steps / (e2e_total / 1e3)},
             "kernel": {"kind": {1: "streaming", 2: "on-chip cluster", 3: "L2 cluster"}.get(launch[0], "?"),
-                       "cluster_ctas": launch[1], "autotuned": list(tuned),
+                       "cluster_ctas": launch[1], "rows_per_thread": rows, "autotuned": list(tuned),
+                       "sm_count": sm_count,
+                       "sms_busy": launch[1] * ctx.last_clusters() if launch[0] == 2 else None,
                        "step": "CUDA graph: interpolation, persistent modelling launch, "
                                "misfit reduction, EMPSO step"},
             "roofline": {"kernel": kname,
@@ -377,18 +411,21 @@ def run_ours(a):
                          "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": BYTES_PER_UPDATE * upd_step,
                          "kernel_ms": wave_mean},
+            "roofline_sm": roof_sm,
             "gpu_launches": 4 * a.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
             "surrogate_vs_plain": sur,
         }
+        line.update(subs)
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
 
 
-def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch=512, overlap=True):
+def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch=512, overlap=True,
+                       recent=4096, min_rank_corr=0.5):
     """Wall-clock to a target misfit, surrogate-assisted vs plain EMPSO.
 
     Problem: the 101 x 101 / 10 m / order-4 / 0.5 s / 10 Hz grid with a
@@ -401,7 +438,9 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
     network beside the modelling (`overlap`), and stops when it reaches the
     target.  Both times include a host read of the best misfit every
     generation.  One untimed run of each comes first (module loading, first
-    launches)."""
+    launches).  Policy: half of every minibatch from the newest `recent`
+    pairs; the whole swarm is modelled after a pre-screened generation whose
+    rank correlation fell below `min_rank_corr`."""
     import torch
     from paper_1905_12795_gb300 import binding as B
     wl = synth.workloads()["surrogate-101x101-P1024"]
@@ -437,13 +476,16 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
         ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
         ctx.surrogate_init(hidden=256, capacity=50000, lr=1e-3, seed=seed + 1)
         ctx.surrogate_set_overlap(overlap)
+        ctx.surrogate_set_policy(recent, min_rank_corr)
         ctx.pso_init()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        best_s, modelled, g, t_sur = float("inf"), 0, 0, None
+        best_s, modelled, g, t_sur, full = float("inf"), 0, 0, None, 0
         while g < 4 * n_gens:
-            modelled += ctx.surrogate_generation(sh, dobs, keep, warm=P, train_steps=train_steps,
-                                                 batch=batch, misfit_out=mis)
+            n_mod = ctx.surrogate_generation(sh, dobs, keep, warm=P, train_steps=train_steps,
+                                             batch=batch, misfit_out=mis)
+            modelled += n_mod
+            full += n_mod == P
             g += 1
             best_s = min(best_s, mis.min().item())
             if best_s <= target:
@@ -465,6 +507,7 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
         ctx.close()
         return {"seed": seed, "target_misfit": target, "plain_s": t_plain, "plain_models": P * n_gens,
                 "surrogate_s": t_sur, "surrogate_generations": g, "surrogate_models": modelled,
+                "full_generations": full,
                 "surrogate_best": best_s, "surrogate_error": err}
 
     one(-1, 5)                                   # untimed
@@ -474,7 +517,8 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
     mean = lambda v: float(np.mean(v)) if v else None  # noqa: E731
     return {"problem": "101x101 order 4, 1 shot, swarm 1024, 100 plain generations, keep 25 %",
             "training": {"steps_per_generation": train_steps, "batch": batch,
-                         "beside_modelling": overlap},
+                         "beside_modelling": overlap, "recent_pairs": recent,
+                         "min_rank_corr": min_rank_corr},
             "seeds": seeds, "reached": len(reached),
             "median_plain_s": med([r["plain_s"] for r in runs]),
             "median_surrogate_s": med([r["surrogate_s"] for r in reached]),
@@ -489,12 +533,17 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
 
 
 def run_uneven(a):
+    print(json.dumps(_uneven_result(a.workload, a.steps, a.warmup, tune=True)), flush=True)
+
+
+def _uneven_result(workload, steps, warmup, tune):
     """Uneven batching: 256 particles x 32 shots, 16 shots on a 40 m / 3 Hz /
     4 s grid and 16 on a 20 m / 6 Hz / 3 s grid, in one persistent launch per
-    generation (graph replay); shot weights 1 / E of each band."""
+    generation (graph replay); shot weights 1 / E of each band.  `tune`: the
+    autotuner picks the kernel shape first (else the planner's choice)."""
     import torch
     from paper_1905_12795_gb300 import binding as B
-    wl = synth.workloads()[a.workload]
+    wl = synth.workloads()[workload]
     coarse, fine = wl.grids
     grids = [B.make_grid(g.nx, g.nz, g.hx, g.hz, g.pad, g.order, g.T, g.f0, g.vmin, g.vmax,
                          kx=g.kx, kz=g.kz) for g in (coarse, fine)]
@@ -527,10 +576,10 @@ def run_uneven(a):
     mis = torch.zeros(wl.P, dtype=torch.float64, device="cuda")
     x = torch.zeros(wl.P, K, device="cuda")
     ctx.pso_init(x)
-    tuned = ctx.autotune(x, sh, dobs, mis)
+    tuned = ctx.autotune(x, sh, dobs, mis) if tune else None
     ctx.pso_init()
     ctx.set_timing(True)
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         ctx.generation(sh, dobs, mis)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -538,7 +587,7 @@ def run_uneven(a):
     clocks = _Clocks(torch.cuda.current_device())
     clocks.start()
     ms, wave = [], []
-    for _ in range(a.steps):
+    for _ in range(steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -554,26 +603,27 @@ def run_uneven(a):
     total = sum(ms)
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_UPDATE * upd / (np.mean(wave) / 1e3) / 1e9
-    line = {"metric": METRIC, "value": upd * a.steps / (total / 1e3), "unit": "grid-pt updates/s",
-            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": total / a.steps,
+    line = {"metric": METRIC, "value": upd * steps / (total / 1e3), "unit": "grid-pt updates/s",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": total / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": a.workload, "grids": [f"{g.nx}x{g.nz}@{g.hx:g}m/{g.f0:g}Hz/"
+            "config": {"workload": workload, "grids": [f"{g.nx}x{g.nz}@{g.hx:g}m/{g.f0:g}Hz/"
                                                          f"{g.T:g}s nt={nt}" for g, nt in
                                                          zip((coarse, fine), nts)],
                        "particles": wl.P, "shots": list(wl.shots_per_grid),
                        "instances_per_step": wl.P * sum(wl.shots_per_grid),
                        "updates_per_step": upd, "l2": "flushed between timed steps"},
-            "fitness_evals_per_s": wl.P * a.steps / (total / 1e3),
+            "fitness_evals_per_s": wl.P * steps / (total / 1e3),
             "kernel": {"kind": {1: "streaming", 2: "on-chip cluster", 3: "L2 cluster"}.get(launch[0], "?"),
-                       "cluster_ctas": launch[1], "autotuned": list(tuned)},
+                       "cluster_ctas": launch[1], "rows_per_thread": ctx.last_tile_rows(),
+                       "autotuned": list(tuned) if tuned else "planner's choice"},
             "roofline": {"kernel": ctx.last_kernel_name(),
                          "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "kernel_ms": float(np.mean(wave))},
-            "gpu_launches": 4 * a.steps, "clocks": clk}
-    print(json.dumps(line), flush=True)
+            "gpu_launches": 4 * steps, "clocks": clk}
     ctx.close()
+    return line
 
 
 def _hires_prescreen(ctx_model, B, gs, rec, sh, dobs, P=32, shots=4, gens=3):
@@ -611,16 +661,20 @@ def _hires_prescreen(ctx_model, B, gs, rec, sh, dobs, P=32, shots=4, gens=3):
 
 
 def run_hires(a):
+    print(json.dumps(_hires_result(a.workload, a.particles or 8, a.steps, a.warmup, tune_kind=0,
+                                   prescreen=True)), flush=True)
+
+
+def _hires_result(workload, P, steps, warmup, tune_kind, prescreen):
     """High-resolution grid (921 x 301 at 10 m + 60 damping cells, order 8,
-    12 Hz, 4 s): a bounded sample of the generation, `--particles` x 64 shots
+    12 Hz, 4 s): a bounded sample of the generation, P particles x 64 shots
     in one launch.  The instance does not fit on chip: the autotuner times the
-    streaming kernel and the L2 cluster kernel's cluster sizes on this batch
-    first and keeps the fastest."""
+    kernels of kind `tune_kind` (0: every kind) on this batch first and keeps
+    the fastest."""
     import torch
     from paper_1905_12795_gb300 import binding as B
-    wl = synth.workloads()[a.workload]
+    wl = synth.workloads()[workload]
     gs = wl.grids[0]
-    P = a.particles or 8
     S = wl.shots_per_grid[0]
     rec = synth.receiver_line(gs.nx, gs.hx, wl.rec_z)
     shots = synth.shot_line(S, (gs.nx - 1) * gs.hx, wl.src_z)
@@ -635,16 +689,17 @@ def run_hires(a):
     x = torch.tensor(synth.random_particles(P, gs.kx * gs.kz, wl.xmin, wl.xmax, wl.seed_pso),
                      dtype=torch.float32, device="cuda")
     mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+    ctx.set_kernel(tune_kind)
     tuned = ctx.autotune(x, sh, dobs, mis)
     ctx.set_timing(True)
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         ctx.eval_fitness(x, sh, dobs, mis)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     ms, wave = [], []
     clocks = _Clocks(torch.cuda.current_device())
     clocks.start()
-    for _ in range(a.steps):
+    for _ in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ctx.eval_fitness(x, sh, dobs, mis)
@@ -658,15 +713,15 @@ def run_hires(a):
     total = sum(ms)
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_UPDATE * upd / (np.mean(wave) / 1e3) / 1e9
-    line = {"metric": METRIC, "value": upd * a.steps / (total / 1e3), "unit": "grid-pt updates/s",
-            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": total / a.steps,
+    line = {"metric": METRIC, "value": upd * steps / (total / 1e3), "unit": "grid-pt updates/s",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": total / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": a.workload, "grid": f"{gs.nx}x{gs.nz} (+{gs.pad} damping)",
+            "config": {"workload": workload, "grid": f"{gs.nx}x{gs.nz} (+{gs.pad} damping)",
                        "nt": nt, "sample": f"{P} particles x {S} shots of the {wl.P} x {S} "
                                            "generation (bounded sample)",
                        "updates_per_step": upd, "l2": "inputs larger than L2"},
-            "fitness_evals_per_s": P * a.steps / (total / 1e3),
+            "fitness_evals_per_s": P * steps / (total / 1e3),
             "kernel": {"kind": {1: "streaming", 2: "on-chip cluster", 3: "L2 cluster"}.get(launch[0], "?"),
                        "cluster_ctas": launch[1], "autotuned": list(tuned)},
             "roofline": {"kernel": ctx.last_kernel_name(),
@@ -674,10 +729,11 @@ def run_hires(a):
                          "unit": "GB/s", "frac": achieved / peak,
                          "traffic": _traffic_from_profile(ctx.last_kernel_name(), "hires-921x301"),
                          "kernel_ms": float(np.mean(wave))},
-            "gpu_launches": 3 * a.steps, "clocks": clk}
-    line["surrogate_prescreen"] = _hires_prescreen(ctx, B, gs, rec, sh, dobs)
-    print(json.dumps(line), flush=True)
+            "gpu_launches": 3 * steps, "clocks": clk}
+    if prescreen:
+        line["surrogate_prescreen"] = _hires_prescreen(ctx, B, gs, rec, sh, dobs)
     ctx.close()
+    return line
 
 
 def run_compare(a):

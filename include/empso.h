@@ -200,13 +200,16 @@ empso_status pso_set_state(empso_ctx *ctx, const double *x, const double *v,
 empso_status empso_generation(empso_ctx *ctx, const empso_shot *shots, int32_t S,
                               const float *d_obs, double *misfit_out, void *stream);
 
-/* Autotuner: times the streaming kernel and the on-chip kernel at every
- * cluster size the batch fits (one warm-up and one timed launch each, CUDA
- * events on `stream`) on this exact batch (particles device [P][K], shots,
- * d_obs; misfit device [P] is used as scratch output), and keeps the fastest
- * for every later batch with the same grids, shot counts and P.  The choice
- * is returned in *kind_out / *cluster_out (host, may be NULL) and appended to
- * the tuning cache file if one is set.  Synchronises `stream`. */
+/* Autotuner: times the streaming kernel, the on-chip kernel at every cluster
+ * size and rows-per-thread shape the batch fits, and the L2 cluster kernel at
+ * cluster sizes 4, 8, 10, 12 and 16 (one warm-up and one timed launch each,
+ * CUDA events on `stream`) on this exact batch (particles device [P][K],
+ * shots, d_obs; misfit device [P] is used as scratch output), and keeps the
+ * fastest for every later batch with the same grids, shot counts and P.  With
+ * a kernel kind selected (empso_set_kernel), only that kind's candidates are
+ * timed.  The choice is returned in *kind_out / *cluster_out (host, may be
+ * NULL) and appended to the tuning cache file (with its rows per thread) if
+ * one is set.  Synchronises `stream`. */
 empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
                             const empso_shot *shots, int32_t S, const float *d_obs,
                             double *misfit, int32_t *kind_out, int32_t *cluster_out,
@@ -246,6 +249,22 @@ empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, fl
  * pairs of the earlier generations on a second stream while the selected
  * particles are modelled (one generation of lag, shorter generations). */
 empso_status surrogate_set_overlap(empso_ctx *ctx, int32_t enable);
+
+/* Pre-screening policy (engineering choices of this library; the paper has
+ * no surrogate): recent > 0 draws half of every training minibatch from the
+ * newest `recent` pairs of the replay buffer (the swarm's current
+ * neighbourhood), the other half from all of it (0: all uniform, the
+ * default).  min_rank_corr > 0: after a pre-screened generation whose
+ * predictions rank its modelled particles with a Spearman correlation below
+ * min_rank_corr against their true misfits, the next surrogate_generation
+ * models the whole swarm (true modelling stays the fallback; 0: never, the
+ * default).  Errors: INVALID_ARG (recent < 0, min_rank_corr outside [-1, 1]),
+ * NOT_INITIALIZED. */
+empso_status surrogate_set_policy(empso_ctx *ctx, int32_t recent, float min_rank_corr);
+
+/* Spearman correlation of the last pre-screened generation (predicted vs
+ * true misfit of its modelled particles).  rho: host; synchronises `stream`. */
+empso_status surrogate_last_rank_corr(empso_ctx *ctx, float *rho, void *stream);
 
 /* Tensor-core path of this context's dense layers: 1 = tcgen05.mma with
  * the accumulator in tensor memory (default), 0 = mma.sync.  Both compute
@@ -323,6 +342,11 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas);
  * thread).  An engineering choice of this library (the paper has no such
  * parameter).  Errors: INVALID_ARG for any other value. */
 empso_status empso_set_tile_rows(empso_ctx *ctx, int32_t rows);
+
+/* Co-resident groups of the last modelling launch: thread-block clusters of
+ * the cluster kernels (times the cluster size = SMs busy), CTAs of the
+ * streaming kernels.  groups: host. */
+empso_status empso_last_clusters(const empso_ctx *ctx, int32_t *groups);
 
 /* Rows per thread of the last on-chip launch (0 if the last launch used
  * another kernel).  rows: host. */

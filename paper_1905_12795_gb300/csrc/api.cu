@@ -60,6 +60,7 @@ struct empso_ctx {
     int last_path = 0;              // 1 streaming, 2 resident, 3 bulk-copy streaming (last launch)
     int last_C = 0;
     int last_rows = 0;              // on-chip launch: rows per thread
+    int last_groups = 0;            // co-resident clusters (CTAs for the streaming kernels)
     int last_paired = 0;            // on-chip launch: units running two instances
     int *dev_err = nullptr;         // device status word set by bounded waits that give up
     unsigned long long *nonfinite = nullptr;  // non-finite misfits: {running, this call}
@@ -98,6 +99,9 @@ struct empso_ctx {
     cudaEvent_t sur_fork = nullptr, sur_done = nullptr;
     bool sur_done_rec = false;
     bool sur_overlap = false;            // train prescreen generations beside their modelling
+    float sur_rho_min = 0.f;             // > 0: model the whole swarm after a pre-screened generation
+                                         // whose rank correlation fell below this
+    bool sur_screened = false;           // the last surrogate generation was pre-screened
     int *sel_rows = nullptr;        // [P] indices of the modelled particles
     float *xk = nullptr;            // [P][D] their positions
     double *fk = nullptr;           // [P] their misfits
@@ -435,9 +439,9 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
     // kernel and cluster size: explicit settings, else the tuned choice, else
     // the on-chip kernel with the cluster size that keeps the most SMs busy
     int kind = ctx->kernel_kind, forcedC = ctx->forced_C, forcedRows = ctx->forced_rows;
-    if (kind == EMPSO_KERNEL_AUTO && forcedC == 0 && forcedRows == 0) {
+    if (forcedC == 0 && forcedRows == 0) {
         auto it = ctx->tuned.find(batch_key(ctx, shots, S, M));
-        if (it != ctx->tuned.end()) {
+        if (it != ctx->tuned.end() && (kind == EMPSO_KERNEL_AUTO || kind == it->second.kind)) {
             kind = it->second.kind;
             forcedC = it->second.C;
             forcedRows = it->second.rows;
@@ -696,6 +700,7 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
         ctx->last_path = 2;
         ctx->last_C = p.resC;
         ctx->last_rows = p.res_rows;
+        ctx->last_groups = p.res_clusters;
         ctx->last_paired = p.n_paired;
     } else if (p.l2) {
         CK(ctx, launch_wave_l2(p.resR, ctx->grids_dev, p.insts,
@@ -704,17 +709,20 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
                                p.l2_smem, ctx->partial, st));
         ctx->last_path = 4;
         ctx->last_C = p.l2C;
+        ctx->last_groups = p.l2_clusters;
     } else if (p.stream_tma) {
         CK(ctx, launch_wave_stream(p.st_R, ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter,
                                    ctx->slots, 2 * p.maxfield, p.n_ctas, p.st_threads, p.st_smem,
                                    p.rec_max, ctx->dev_err, ctx->partial, st));
         ctx->last_path = 3;
         ctx->last_C = 1;
+        ctx->last_groups = p.n_ctas;
     } else {
         CK(ctx, launch_wave(ctx->grids_dev, p.insts, (int)p.n_inst, ctx->counter, ctx->slots,
                             2 * p.maxfield, p.n_ctas, ctx->wave_threads, ctx->partial, st));
         ctx->last_path = 1;
         ctx->last_C = 1;
+        ctx->last_groups = p.n_ctas;
     }
     if (ctx->timing) CK(ctx, mark(ctx->tev[2], st));
     if (misfit)
@@ -1751,10 +1759,15 @@ empso_status empso_autotune(empso_ctx *ctx, const float *particles, int32_t P,
     CK(ctx, cudaEventCreate(&e1));
     // candidates: the streaming kernel, every cluster size and rows-per-thread
     // shape of the on-chip one, and the usual cluster sizes of the L2 one
-    std::vector<empso_ctx::Tuned> cand = {{EMPSO_KERNEL_STREAMING, 0, 0}};
-    for (int C = 1; C <= 16; ++C)
-        for (const int rows : {13, 8}) cand.push_back({EMPSO_KERNEL_RESIDENT, C, rows});
-    for (int C : {4, 8, 10, 12, 16}) cand.push_back({EMPSO_KERNEL_CLUSTER_L2, C, 0});
+    // (only those of the selected kind when a kind is selected)
+    const int only = ctx->kernel_kind;
+    std::vector<empso_ctx::Tuned> cand;
+    if (only == EMPSO_KERNEL_AUTO || only == EMPSO_KERNEL_STREAMING) cand.push_back({EMPSO_KERNEL_STREAMING, 0, 0});
+    if (only == EMPSO_KERNEL_AUTO || only == EMPSO_KERNEL_RESIDENT)
+        for (int C = 1; C <= 16; ++C)
+            for (const int rows : {13, 8}) cand.push_back({EMPSO_KERNEL_RESIDENT, C, rows});
+    if (only == EMPSO_KERNEL_AUTO || only == EMPSO_KERNEL_CLUSTER_L2)
+        for (int C : {4, 8, 10, 12, 16}) cand.push_back({EMPSO_KERNEL_CLUSTER_L2, C, 0});
     float best = 1e30f;
     empso_ctx::Tuned choice;
     choice.kind = EMPSO_KERNEL_AUTO;
@@ -1831,6 +1844,13 @@ empso_status empso_set_tile_rows(empso_ctx *ctx, int32_t rows)
     if (rows != 0 && !resident_rows_supported(rows))
         return fail(ctx, EMPSO_INVALID_ARG, "rows per thread must be 0 (automatic), 8 or 13");
     ctx->forced_rows = rows;
+    return EMPSO_OK;
+}
+
+empso_status empso_last_clusters(const empso_ctx *ctx, int32_t *groups)
+{
+    if (!ctx || !groups) return EMPSO_INVALID_ARG;
+    *groups = ctx->last_groups;
     return EMPSO_OK;
 }
 
@@ -1978,6 +1998,7 @@ empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, fl
     CK(ctx, alloc((void **)&s.xbuf, 4 * (size_t)capacity * K));
     CK(ctx, alloc((void **)&s.ybuf, 4 * (size_t)capacity));
     CK(ctx, alloc((void **)&s.count, 4));
+    CK(ctx, alloc((void **)&s.rho, 4));
     CK(ctx, alloc((void **)&ctx->sel_rows, 4 * (size_t)P));
     CK(ctx, alloc((void **)&ctx->xk, 4 * (size_t)P * K));
     CK(ctx, alloc((void **)&ctx->fk, 8 * (size_t)P));
@@ -1997,6 +2018,7 @@ empso_status surrogate_init(empso_ctx *ctx, int32_t hidden, int32_t capacity, fl
     CK(ctx, cudaMemset(s.m, 0, 4 * np));
     CK(ctx, cudaMemset(s.v, 0, 4 * np));
     CK(ctx, cudaMemset(s.count, 0, 4));
+    CK(ctx, cudaMemset(s.rho, 0, 4));
     CK(ctx, cudaMemcpy(s.stats, stats0, 8, cudaMemcpyHostToDevice));
     CK(ctx, sur_refresh_bf16(s, 0));
     CK(ctx, sur_prepare_tc());
@@ -2028,6 +2050,26 @@ empso_status surrogate_set_overlap(empso_ctx *ctx, int32_t enable)
 {
     NEED_SUR(ctx);
     ctx->sur_overlap = enable != 0;
+    return EMPSO_OK;
+}
+
+empso_status surrogate_set_policy(empso_ctx *ctx, int32_t recent, float min_rank_corr)
+{
+    NEED_SUR(ctx);
+    if (recent < 0 || !(min_rank_corr >= -1.f && min_rank_corr <= 1.f))
+        return fail(ctx, EMPSO_INVALID_ARG, "need recent >= 0 and -1 <= min_rank_corr <= 1");
+    ctx->sur.recent = recent;
+    ctx->sur_rho_min = min_rank_corr;
+    return EMPSO_OK;
+}
+
+empso_status surrogate_last_rank_corr(empso_ctx *ctx, float *rho, void *stream)
+{
+    NEED_SUR(ctx);
+    if (!rho) return fail(ctx, EMPSO_INVALID_ARG, "null rho");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(ctx, cudaMemcpyAsync(rho, ctx->sur.rho, sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
     return EMPSO_OK;
 }
 
@@ -2124,12 +2166,20 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
     JOIN_SUR(ctx, st);
     // how many pairs the replay buffer holds (host read: decides the branch)
     int have = 0;
+    float rho = 1.f;
     CK(ctx, cudaMemcpyAsync(&have, s.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (ctx->sur_rho_min > 0.f && ctx->sur_screened)
+        CK(ctx, cudaMemcpyAsync(&rho, s.rho, sizeof(float), cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaStreamSynchronize(st));
     if ((rc = strict_begin(ctx, st))) return rc;
     Models mod;
     int k;
-    if (have < warm) {
+    // the whole swarm is modelled while the buffer warms up, and after a
+    // pre-screened generation whose predictions ranked the modelled particles
+    // too poorly (rank correlation below the policy's minimum)
+    const bool fallback = ctx->sur_rho_min > 0.f && ctx->sur_screened && rho < ctx->sur_rho_min;
+    ctx->sur_screened = false;
+    if (have < warm || fallback) {
         // warm-up: model every particle, then train on everything so far
         k = P;
         mod.particles = ctx->xf;
@@ -2163,6 +2213,8 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
         mod.particles = ctx->xk;
         mod.M = k;
         if ((rc = run_batch(ctx, mod, shots, S, d_obs, nullptr, ctx->fk, st))) return rc;
+        CK(ctx, sur_rank_corr(ctx->fk, ctx->sel_rows, ctx->logphi, k, s.rho, st));
+        ctx->sur_screened = true;
         CK(ctx, sur_append(s, ctx->xf, ctx->fk, ctx->sel_rows, k, st));
         CK(ctx, sur_scatter(ctx->sel_rows, ctx->fk, k, ctx->logphi, P, ctx->fit_full, ctx->rank_full, st));
         if (train_steps > 0 && !ctx->sur_overlap) CK(ctx, sur_train(s, train_steps, batch, st));
@@ -2202,6 +2254,7 @@ empso_status empso_nonfinite_count(empso_ctx *ctx, int64_t *count, int32_t reset
 //   swarm:     i32 P, D | u64 seed | i32 g, k | f64 xmin[D], xmax[D]
 //              | f64 x[P D], v[P D], p[P D], pf[P] | i32 order[P]
 //   surrogate: i32 K, H, cap | u64 seed | i32 t, sample_step, count
+//              | i32 screened | f32 rank correlation of that generation
 //              | f32 stats[2] | f32 params[n], m[n], v[n]
 //              | f32 xbuf[rows K], ybuf[rows] with rows = min(count, cap)
 //   u64 FNV-1a hash of every preceding byte
@@ -2211,7 +2264,7 @@ empso_status empso_nonfinite_count(empso_ctx *ctx, int64_t *count, int32_t reset
 namespace {
 
 const char CK_MAGIC[8] = {'E', 'M', 'P', 'S', 'O', 'C', 'K', '1'};
-constexpr uint32_t CK_VERSION = 1;
+constexpr uint32_t CK_VERSION = 2;
 
 uint64_t fnv1a(const unsigned char *p, size_t n)
 {
@@ -2298,6 +2351,10 @@ empso_status empso_save(empso_ctx *ctx, const char *path)
         o.val<int32_t>(s.t);
         o.val<int32_t>(s.sample_step);
         o.val<int32_t>(count);
+        float rho = 0.f;
+        CK(ctx, cudaMemcpy(&rho, s.rho, sizeof rho, cudaMemcpyDeviceToHost));
+        o.val<int32_t>(ctx->sur_screened ? 1 : 0);
+        o.val<float>(rho);
         CK(ctx, dev_put(o, s.stats, 2));
         CK(ctx, dev_put(o, s.p, (size_t)s.n_params));
         CK(ctx, dev_put(o, s.m, (size_t)s.n_params));
@@ -2375,9 +2432,9 @@ empso_status empso_load(empso_ctx *ctx, const char *path)
             return fail(ctx, EMPSO_INVALID_ARG, "checkpoint search bounds differ from this context's");
     }
     // surrogate part: validated in full before anything is written
-    int32_t sK = 0, sH = 0, scap = 0, st_t = 0, st_step = 0, count = 0;
+    int32_t sK = 0, sH = 0, scap = 0, st_t = 0, st_step = 0, count = 0, screened = 0;
     uint64_t sseed = 0;
-    float stats[2];
+    float stats[2], rho = 0.f;
     std::vector<float> sp, sm, sv, xb, yb;
     const bool file_sur = (parts & 2u) != 0;
     if (file_sur) {
@@ -2385,11 +2442,13 @@ empso_status empso_load(empso_ctx *ctx, const char *path)
             return fail(ctx, EMPSO_NOT_INITIALIZED, "checkpoint holds a surrogate; call surrogate_init first");
         const SurDev &s = ctx->sur;
         if (!in.val(sK) || !in.val(sH) || !in.val(scap) || !in.val(sseed) || !in.val(st_t) ||
-            !in.val(st_step) || !in.val(count) || !in.get(stats, sizeof stats))
+            !in.val(st_step) || !in.val(count) || !in.val(screened) || !in.val(rho) ||
+            !in.get(stats, sizeof stats))
             return corrupt("surrogate header");
         if (sK != s.K || sH != s.H || scap != s.cap)
             return fail(ctx, EMPSO_INVALID_ARG, "checkpoint surrogate (K, H, capacity) differs from this context's");
-        if (count < 0 || st_t < 0 || st_step < 0) return corrupt("surrogate counters");
+        if (count < 0 || st_t < 0 || st_step < 0 || (screened != 0 && screened != 1))
+            return corrupt("surrogate counters");
         const size_t np = (size_t)s.n_params, rows = (size_t)std::min(count, scap);
         sp.resize(np);
         sm.resize(np);
@@ -2417,6 +2476,8 @@ empso_status empso_load(empso_ctx *ctx, const char *path)
         CK(ctx, cudaMemcpy(s.v, sv.data(), 4 * sv.size(), cudaMemcpyHostToDevice));
         CK(ctx, cudaMemcpy(s.stats, stats, sizeof stats, cudaMemcpyHostToDevice));
         CK(ctx, cudaMemcpy(s.count, &count, sizeof count, cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(s.rho, &rho, sizeof rho, cudaMemcpyHostToDevice));
+        ctx->sur_screened = screened != 0;
         if (!xb.empty()) {
             CK(ctx, cudaMemcpy(s.xbuf, xb.data(), 4 * xb.size(), cudaMemcpyHostToDevice));
             CK(ctx, cudaMemcpy(s.ybuf, yb.data(), 4 * yb.size(), cudaMemcpyHostToDevice));

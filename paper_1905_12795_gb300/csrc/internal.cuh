@@ -232,6 +232,9 @@ struct SurDev {
     int *count = nullptr;
     uint64_t seed = 0;
     int sample_step = 0, t = 0;
+    int recent = 0;          // > 0: half of every minibatch from the newest `recent` pairs
+    float *rho = nullptr;    // Spearman correlation of predicted and true misfits of the
+                             // last pre-screened generation's modelled particles
     float lr = 1e-3f, beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
     int tc = 1;              // dense layers: 1 = tcgen05 (TMEM accumulator), 0 = mma.sync
     int *err = nullptr;      // status word for a tcgen05 completion wait that gives up
@@ -250,6 +253,10 @@ cudaError_t sur_append(const SurDev &s, const float *x, const double *misfit, co
 // have < 0: on the rows the device count says are filled
 cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st, int have = -1);
 cudaError_t sur_select(const float *key, int P, int k, int *rows, cudaStream_t st);
+// rank correlation of fk[j] (true misfits of the k modelled particles) with
+// logphi[rows[j]] (their predictions) into *rho (one block)
+cudaError_t sur_rank_corr(const double *fk, const int *rows, const float *logphi, int k, float *rho,
+                          cudaStream_t st);
 cudaError_t sur_prepare_tc();
 cudaError_t sur_gather(const float *x, const int *rows, int k, int K, float *out, cudaStream_t st);
 cudaError_t sur_scatter(const int *rows, const double *fk, int k, const float *logphi, int P,

@@ -547,16 +547,57 @@ __device__ __forceinline__ uint4 philox_s(uint4 c, uint32_t k0, uint32_t k1)
 }
 
 // batch rows drawn uniformly from the filled part of the replay buffer (its
-// first min(have_host, cap) rows when have_host >= 0, else the device count's)
+// first min(have_host, cap) rows when have_host >= 0, else the device count's);
+// with recent > 0 the second half of the batch comes from the newest
+// min(recent, filled) pairs instead (the swarm's current neighbourhood)
 __global__ void sample_kernel(int *rows, int B, const int *count, int have_host, int cap, uint64_t seed,
-                              int step)
+                              int step, int recent)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const int have = min(have_host >= 0 ? have_host : *count, cap);
+    const int total = have_host >= 0 ? have_host : *count;   // pairs appended so far
+    const int have = min(total, cap);
     const uint4 w = philox_s(make_uint4((uint32_t)step, (uint32_t)b, 0x5u, 0x7u), (uint32_t)seed,
                              (uint32_t)(seed >> 32));
+    if (recent > 0 && b >= B / 2 && have > 0) {
+        const int span = min(recent, have);
+        const int j = (int)(((unsigned long long)w.x * (unsigned long long)span) >> 32);
+        rows[b] = (int)(((long long)total - 1 - j) % cap);
+        return;
+    }
     rows[b] = have > 0 ? (int)(((unsigned long long)w.x * (unsigned long long)have) >> 32) : 0;
+}
+
+// Spearman rank correlation of the k modelled particles' true misfits fk
+// and predictions logphi[rows]: ranks by counting (ties by index), one block
+__global__ void rank_corr_kernel(const double *__restrict__ fk, const int *__restrict__ rows,
+                                 const float *__restrict__ logphi, int k, float *rho)
+{
+    __shared__ double red[32];
+    double d2 = 0.0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double ti = fk[i];
+        const float pi = logphi[rows[i]];
+        int rt = 0, rp = 0;
+        for (int j = 0; j < k; ++j) {
+            const double tj = fk[j];
+            const float pj = logphi[rows[j]];
+            rt += (tj < ti) || (tj == ti && j < i);
+            rp += (pj < pi) || (pj == pi && j < i);
+        }
+        const double d = (double)(rt - rp);
+        d2 += d * d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d2 += __shfl_down_sync(0xffffffffu, d2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) s += red[w];
+        const double kk = (double)k;
+        *rho = k > 1 ? (float)(1.0 - 6.0 * s / (kk * (kk * kk - 1.0))) : 1.f;
+    }
 }
 
 // standardised targets of the batch: (log phi - mu) / sigma
@@ -827,7 +868,7 @@ cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st, int have)
     stats_kernel<<<1, 256, 0, st>>>(s.ybuf, s.count, have, s.cap, s.stats);
     for (int i = 0; i < steps; ++i) {
         sample_kernel<<<(B + 255) / 256, 256, 0, st>>>(s.rows, B, s.count, have, s.cap, s.seed,
-                                                       s.sample_step++);
+                                                       s.sample_step++, s.recent);
         targets_kernel<<<(B + 255) / 256, 256, 0, st>>>(s.ybuf, s.rows, B, s.stats, s.tb);
         // the buffer holds raw positions: scale the batch rows to [-1, 1] in BF16
         if ((e = sur_normalize(s, s.xbuf, s.rows, B, s.Xb, st))) return e;
@@ -840,6 +881,13 @@ cudaError_t sur_train(SurDev &s, int steps, int B, cudaStream_t st, int have)
 cudaError_t sur_select(const float *key, int P, int k, int *rows, cudaStream_t st)
 {
     select_kernel<<<1, 1024, 0, st>>>(key, P, k, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_rank_corr(const double *fk, const int *rows, const float *logphi, int k, float *rho,
+                          cudaStream_t st)
+{
+    rank_corr_kernel<<<1, 256, 0, st>>>(fk, rows, logphi, k, rho);
     return cudaGetLastError();
 }
 

@@ -217,22 +217,43 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     }
 
     // work item: column group q and rows [r0, r1) of the slab, the slab's rows
-    // split into nseg runs of at most RW rows each (lengths differ by one at most)
+    // split into nseg runs of at most RW rows each (lengths differ by one at
+    // most), item i = seg NQ + q on thread i.  When the launch has fewer
+    // threads than items (a multiple of four warps, so that the SM's four
+    // schedulers carry equal work), the last `left` items (the last columns
+    // of the last run) are split into single rows instead, one extra row on
+    // each of the first left * len_last threads.
     const int nseg = (my_rows + RW - 1) / RW;
-    const bool active = tid < NQ * nseg;
+    const int items = NQ * nseg;
+    const int nmain = min(items, nth);
+    const int left = items - nmain;
+    const int r0_last = (nseg - 1) * my_rows / nseg, len_last = my_rows - r0_last;
+    const bool active = tid < nmain;
     const int q = active ? tid % NQ : 0;
     const int seg = active ? tid / NQ : 0;
     const int r0 = active ? seg * my_rows / nseg : 0;
     const int r1 = active ? (seg + 1) * my_rows / nseg : 0;
+    const bool extra = tid < left * len_last;
+    const int qe = extra ? NQ - left + tid / len_last : 0;
+    const int re = extra ? r0_last + tid % len_last : 0;
+    // a launch shape the planner did not mean (leftover items outside the last
+    // run, or more extra rows than threads) would leave rows uncomputed: the
+    // instance then reports a NaN misfit (the work and barriers run as usual)
+    const bool bad_shape = left > NQ || left * len_last > nth;
 
-    float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ex = make_float4(0.f, 0.f, 0.f, 0.f), exe = ex;
     if (active) ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
+    if (extra) exe = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + qe);
     // update weight g = 2 / (1 + t) of rows without z-damping: per lane,
     // constant over the instance (g = 2 in the interior); hx for the others
     const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));
     const float2 gx23 = make_float2(2.f / (1.f + ex.z), 2.f / (1.f + ex.w));
     const float2 hx01 = make_float2(0.5f * (1.f + ex.x), 0.5f * (1.f + ex.y));
     const float2 hx23 = make_float2(0.5f * (1.f + ex.z), 0.5f * (1.f + ex.w));
+    const float2 gxe01 = make_float2(2.f / (1.f + exe.x), 2.f / (1.f + exe.y));
+    const float2 gxe23 = make_float2(2.f / (1.f + exe.z), 2.f / (1.f + exe.w));
+    const float2 hxe01 = make_float2(0.5f * (1.f + exe.x), 0.5f * (1.f + exe.y));
+    const float2 hxe23 = make_float2(0.5f * (1.f + exe.z), 0.5f * (1.f + exe.w));
     float cx[R + 1], cz[R + 1];
 #pragma unroll
     for (int m = 0; m <= R; ++m) {
@@ -277,13 +298,13 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     // sbit: bit c = 1 when corner row s_j0 + c is one of this item's rows and
     // one of the corner columns lies in group q.
     const int s_i0 = src.i0, s_j0 = src.j0;
-    unsigned sbit = 0;
-    if (active && s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3)
+    unsigned sbit = 0, sbit_e = 0;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int rr = s_j0 + c - z0;
-            if (rr >= r0 && rr < r1) sbit |= 1u << c;
-        }
+    for (int c = 0; c < 2; ++c) {
+        const int rr = s_j0 + c - z0;
+        if (active && s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3 && rr >= r0 && rr < r1) sbit |= 1u << c;
+        if (extra && s_i0 >= 4 * qe - 1 && s_i0 <= 4 * qe + 3 && rr == re) sbit_e |= 1u << c;
+    }
     // the item's role: 1 the first run of a CTA with a CTA above (sweeps down,
     // hands its top rows up first), 2 the last of two or more runs of a CTA
     // with a CTA below (sweeps up, hands its bottom rows down first), 0 any
@@ -310,13 +331,46 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     }
 
     // history: this item's first row in slot n + 1 (advanced one field per step)
-    float4 *hrow = nullptr;
+    float4 *hrow = nullptr, *hrow_e = nullptr;
     const int hp4 = pitch / 4;
     if (HIST && active)
         hrow = reinterpret_cast<float4 *>(in.hist) + (size_t)(z0 + r0 + HALO) * hp4 + HALO4 + q;
+    if (HIST && extra)
+        hrow_e = reinterpret_cast<float4 *>(in.hist) + (size_t)(z0 + re + HALO) * hp4 + HALO4 + qe;
     float4 *cur = A4, *nxt = B4;
+    int step = 0;
+    // The source term of a piece's corner rows (column group qq, first row
+    // pr0, corner-row bits sb), added after its sweep; also to the history and
+    // to a neighbour's halo copy of the row
+    auto add_source = [&](int qq, int pr0, unsigned sb, float4 *nq, const float4 *mq, float4 *hr, float4 *pq,
+                          float4 *xq) {
+        const float rn = wring[step % DEPTH];
+        for (int c = 0; c < 2; ++c) {
+            if (!((sb >> c) & 1u)) continue;
+            const int rr = s_j0 + c - z0, lr = R + rr;
+            float4 v = nq[lr * sp4];
+            const float4 av = mq[rr * NQ];
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float b0 = src.w[2 * c] * rn, b1 = src.w[2 * c + 1] * rn;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int I = 4 * qq + l;
+                set_comp(b, l, (I == s_i0 ? b0 : 0.f) + (I == s_i0 + 1 ? b1 : 0.f));
+            }
+            v = make_float4(fmaf(av.x, b.x, v.x), fmaf(av.y, b.y, v.y), fmaf(av.z, b.z, v.z),
+                            fmaf(av.w, b.w, v.w));
+            nq[lr * sp4] = v;
+            if (HIST) __stcs(hr + (rr - pr0) * hp4, v);
+            if (pq && rr < R) pq[(lr + rows_c) * sp4] = v;
+            if (xq && rr >= rows_c - R) xq[(lr - rows_c) * sp4] = v;
+        }
+    };
     for (int n = 0; n <= nt; ++n) {
-        if (HIST) hrow += gs.field / 4;
+        step = n;
+        if (HIST) {
+            hrow += gs.field / 4;
+            hrow_e += gs.field / 4;
+        }
         // stage wavelet sample n + 1 and record n (sampled in step n + 1); their
         // slots were last read in step n - 1, which the previous barrier closed
         {
@@ -349,28 +403,24 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
                                                gx23, hx01, hx23, hrow, hp4, peer, poff);
             if (tail)
                 for (int rr = max(r0, rows_c - R); rr < r1; ++rr) xq[(R + rr - rows_c) * sp4] = nq[(R + rr) * sp4];
-            if (sbit) {   // the source term of the item's corner rows
-                const float rn = wring[n % DEPTH];
-                for (int c = 0; c < 2; ++c) {
-                    if (!((sbit >> c) & 1u)) continue;
-                    const int rr = s_j0 + c - z0, lr = R + rr;
-                    float4 v = nq[lr * sp4];
-                    const float4 av = mq[rr * NQ];
-                    float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float b0 = src.w[2 * c] * rn, b1 = src.w[2 * c + 1] * rn;
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        const int I = 4 * q + l;
-                        set_comp(b, l, (I == s_i0 ? b0 : 0.f) + (I == s_i0 + 1 ? b1 : 0.f));
-                    }
-                    v = make_float4(fmaf(av.x, b.x, v.x), fmaf(av.y, b.y, v.y), fmaf(av.z, b.z, v.z),
-                                    fmaf(av.w, b.w, v.w));
-                    nq[lr * sp4] = v;
-                    if (HIST) __stcs(hrow + (rr - r0) * hp4, v);
-                    if (pq && rr < R) pq[(lr + rows_c) * sp4] = v;
-                    if (xq && rr >= rows_c - R) xq[(lr - rows_c) * sp4] = v;
-                }
-            }
+            if (sbit) add_source(q, r0, sbit, nq, mq, hrow, pq, xq);
+        }
+        if (n < nt && extra) {   // the thread's single extra row
+            const float4 *cq = cur + 1 + qe;
+            float4 *nq = nxt + 1 + qe;
+            const float4 *mq = M4 + qe;
+            const bool even = (n & 1) == 0;
+            float4 *pq = has_prev ? (even ? prev_B : prev_A) + 1 + qe : nullptr;
+            float4 *xq = has_next ? (even ? next_B : next_A) + 1 + qe : nullptr;
+            float4 *peer = re < R ? pq : (re >= rows_c - R ? xq : nullptr);
+            const int poff = re < R ? rows_c : -rows_c;
+            if (zpad)
+                sweep_item<R, 1, true, HIST>(cq, nq, mq, ezs, sp4, NQ, re, 1, 1, cx, cz, cres, gxe01, gxe23,
+                                             hxe01, hxe23, hrow_e, hp4, peer, poff);
+            else
+                sweep_item<R, 1, false, HIST>(cq, nq, mq, ezs, sp4, NQ, re, 1, 1, cx, cz, cres, gxe01, gxe23,
+                                              hxe01, hxe23, hrow_e, hp4, peer, poff);
+            if (sbit_e) add_source(qe, re, sbit_e, nq, mq, hrow_e, pq, xq);
         }
         // receivers sample u^n (record n - 1)
         if (has_rec && n >= 1) {
@@ -404,6 +454,7 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     cp_async_wait<0>();
     if (!dobs) accf = 0.f, acc = 0.0;
     acc += (double)accf;
+    if (bad_shape) acc = __longlong_as_double(0x7ff8000000000000LL);
     // fixed-order reduction: warps -> CTA -> cluster rank 0 (ranks in order)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -492,11 +543,21 @@ int resident_max_threads(int rows) { return shape_threads(rows); }
 int resident_default_rows() { return RW_A; }
 bool resident_rows_supported(int rows) { return rows == RW_A || rows == RW_B; }
 
-// threads of the work items of grid g on C CTAs with runs of at most `rows` rows
+// Threads of the work items of grid g on C CTAs with runs of at most `rows`
+// rows: one per item, or, when that is not a multiple of four warps, the
+// multiple of four warps below it with the leftover items (the last columns
+// of the last run) done as single extra rows -- so that the SM's four
+// schedulers get the same number of warps -- when they fit (at most NQ
+// leftover items, at most one extra row per thread).
 int resident_threads(const GridDev &g, int C, int rows)
 {
     const int rows_c = (g.NZ + C - 1) / C;
-    return (g.NQ * ((rows_c + rows - 1) / rows) + 31) / 32 * 32;
+    const int nseg = (rows_c + rows - 1) / rows;
+    const int items = g.NQ * nseg;
+    const int lo = items / 128 * 128;
+    const int left = items - lo;
+    if (lo > 0 && left > 0 && left <= g.NQ && left * rows <= lo) return lo;
+    return (items + 31) / 32 * 32;
 }
 
 // two time levels with halo rows, the slab of the model field, its damping

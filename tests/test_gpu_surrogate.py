@@ -263,3 +263,31 @@ def test_surrogate_gains_at_equal_modelling_budget(B):
         sur.close()
         wins += best_sur < best_plain
     assert wins >= 2
+
+
+def test_rank_correlation_fallback_models_the_whole_swarm(B):
+    """After a pre-screened generation whose predictions rank the modelled
+    particles with a Spearman correlation below the policy's minimum, the
+    next generation models the whole swarm; without the policy it does not."""
+    P = 64
+    for rho_min, expect in ((0.999, P), (0.0, 16)):
+        ctx, sh, dobs = _search_problem(B, P, 4)
+        ctx.surrogate_init(hidden=64, capacity=4096, lr=1e-3, seed=4)
+        ctx.surrogate_set_policy(recent=128, min_rank_corr=rho_min)
+        ctx.pso_init()
+        mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+        assert ctx.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=5, batch=64,
+                                        misfit_out=mis) == P
+        assert ctx.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=5, batch=64,
+                                        misfit_out=mis) == 16
+        rho = ctx.surrogate_last_rank_corr()
+        assert -1.0 <= rho <= 1.0 and rho < 0.999
+        assert ctx.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=5, batch=64,
+                                        misfit_out=mis) == expect
+        assert torch.isfinite(mis).sum().item() == expect
+        # a fallback generation is not pre-screened: the one after it screens again
+        assert ctx.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=5, batch=64,
+                                        misfit_out=mis) == 16
+        with pytest.raises(B.EmpsoError):
+            ctx.surrogate_set_policy(recent=-1)
+        ctx.close()
