@@ -68,6 +68,8 @@ def _args():
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 streaming, 2 on-chip, 3 L2 cluster")
     ap.add_argument("--cluster", type=int, default=0, help="--case: CTAs per instance (0 automatic)")
     ap.add_argument("--rows", type=int, default=0, help="--case: on-chip rows per thread (0 automatic)")
+    ap.add_argument("--chains", type=int, default=0,
+                    help="--gradient-case: backward chains (0: the library default)")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-vs-plain wall-clock comparison")
@@ -425,7 +427,7 @@ def run_ours(a):
 
 
 def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch=512, overlap=True,
-                       recent=4096, min_rank_corr=0.5):
+                       recent=4096, min_rank_corr=0.0, patience=0):
     """Wall-clock to a target misfit, surrogate-assisted vs plain EMPSO.
 
     Problem: the 101 x 101 / 10 m / order-4 / 0.5 s / 10 Hz grid with a
@@ -440,7 +442,9 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
     generation.  One untimed run of each comes first (module loading, first
     launches).  Policy: half of every minibatch from the newest `recent`
     pairs; the whole swarm is modelled after a pre-screened generation whose
-    rank correlation fell below `min_rank_corr`."""
+    rank correlation fell below `min_rank_corr` (0: never) and after
+    `patience` pre-screened generations in a row without a new best (0:
+    never)."""
     import torch
     from paper_1905_12795_gb300 import binding as B
     wl = synth.workloads()["surrogate-101x101-P1024"]
@@ -476,7 +480,7 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
         ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
         ctx.surrogate_init(hidden=256, capacity=50000, lr=1e-3, seed=seed + 1)
         ctx.surrogate_set_overlap(overlap)
-        ctx.surrogate_set_policy(recent, min_rank_corr)
+        ctx.surrogate_set_policy(recent, min_rank_corr, patience)
         ctx.pso_init()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -518,7 +522,7 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=10, batch
     return {"problem": "101x101 order 4, 1 shot, swarm 1024, 100 plain generations, keep 25 %",
             "training": {"steps_per_generation": train_steps, "batch": batch,
                          "beside_modelling": overlap, "recent_pairs": recent,
-                         "min_rank_corr": min_rank_corr},
+                         "min_rank_corr": min_rank_corr, "patience": patience},
             "seeds": seeds, "reached": len(reached),
             "median_plain_s": med([r["plain_s"] for r in runs]),
             "median_surrogate_s": med([r["surrogate_s"] for r in reached]),
@@ -1052,7 +1056,8 @@ def run_case(a):
         torch.cuda.synchronize()
         ms = ctx.read_timing()[1]
         print(f"rep {r}: modelling kernel {ms:.3f} ms, {upd / ms / 1e6:.1f} G updates/s, "
-              f"launch {ctx.last_launch()} rows {ctx.last_tile_rows()} {ctx.last_kernel_name()}",
+              f"launch {ctx.last_launch()} rows {ctx.last_tile_rows()} clusters {ctx.last_clusters()} "
+              f"{ctx.last_kernel_name()}",
               flush=True)
     ctx.close()
 
@@ -1069,6 +1074,9 @@ def run_gradient_case(a):
     shots = synth.shot_line(S, (gs.nx - 1) * gs.hx, wl.src_z)
     grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin, gs.vmax)
     ctx = B.Context([grid], rec)
+    if a.chains:
+        ctx.set_gradient_chains(a.chains)
+    ctx.set_cluster(a.cluster)
     _, nt = ctx.grid_info(0)
     sh = B.make_shots(shots, [0] * S, [len(rec)] * S)
     v = torch.tensor(true, dtype=torch.float32, device="cuda")[None].contiguous()

@@ -258,9 +258,12 @@ empso_status surrogate_set_overlap(empso_ctx *ctx, int32_t enable);
  * predictions rank its modelled particles with a Spearman correlation below
  * min_rank_corr against their true misfits, the next surrogate_generation
  * models the whole swarm (true modelling stays the fallback; 0: never, the
- * default).  Errors: INVALID_ARG (recent < 0, min_rank_corr outside [-1, 1]),
- * NOT_INITIALIZED. */
-empso_status surrogate_set_policy(empso_ctx *ctx, int32_t recent, float min_rank_corr);
+ * default).  patience > 0: after that many pre-screened generations in a row
+ * that did not lower the swarm's best misfit, the next surrogate_generation
+ * models the whole swarm (0: never, the default); each call synchronises
+ * `stream` once more to read the best misfit.  Errors: INVALID_ARG (recent <
+ * 0, min_rank_corr outside [-1, 1], patience < 0), NOT_INITIALIZED. */
+empso_status surrogate_set_policy(empso_ctx *ctx, int32_t recent, float min_rank_corr, int32_t patience);
 
 /* Spearman correlation of the last pre-screened generation (predicted vs
  * true misfit of its modelled particles).  rho: host; synchronises `stream`. */
@@ -498,6 +501,18 @@ empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t n
 empso_status empso_gradient(empso_ctx *ctx, const float *vel, int32_t M,
                             const empso_shot *shots, int32_t S, const float *d_obs,
                             double *misfit, float *grad, void *stream);
+
+/* Chains of the gradient's backward pass: its (model, shot) instances are
+ * independent, so they run as n chains (1..4) of consecutive instances on
+ * separate streams inside the captured graph, one chain's memory waits and
+ * launch gaps overlapping another's work; 0 (default): 4 chains from 16
+ * instances up, else 1 (measured on the 461 x 151 grid: 16 shots 35.6 ->
+ * 33.3 ms with 4 chains, 4 shots 15.7 -> 18.1 ms).  Results do not depend on
+ * n (each instance's arithmetic is the same).  A cluster size set by
+ * empso_set_cluster also applies to the gradient's on-chip forward pass.
+ * An engineering choice of this library (the paper has no such parameter).
+ * Errors: INVALID_ARG outside 0..4. */
+empso_status empso_set_gradient_chains(empso_ctx *ctx, int32_t chains);
 
 /* Steepest-descent FWI of one model vel device [nz][nx] (in place), the
  * paper's local inversion: iteration k moves v <- clip(v - alpha g, vmin,

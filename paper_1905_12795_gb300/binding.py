@@ -27,7 +27,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA_ERROR", 4: "NONFINITE",
 
 EXPORTS = ["empso_create", "empso_destroy", "empso_grid_info", "empso_time_axis", "empso_interp", "forward_traces",
            "eval_models", "eval_fitness", "pso_init", "pso_step", "pso_get_state",
-           "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_set_tile_rows",
+           "pso_set_state", "empso_set_kernel", "empso_set_cluster", "empso_set_tile_rows", "empso_set_gradient_chains",
            "empso_last_tile_rows", "empso_last_clusters", "empso_last_launch", "empso_device_error", "empso_set_timing", "empso_read_timing", "eval_models_noalloc",
            "empso_generation", "empso_autotune", "empso_set_tuning_cache",
            "pso_step_ranked", "surrogate_init", "surrogate_set_backend", "surrogate_set_overlap", "surrogate_set_policy", "surrogate_last_rank_corr", "surrogate_predict", "surrogate_add",
@@ -109,6 +109,7 @@ def load():
     L.empso_set_kernel.argtypes = [_vp, _i32]
     L.empso_set_cluster.argtypes = [_vp, _i32]
     L.empso_set_tile_rows.argtypes = [_vp, _i32]
+    L.empso_set_gradient_chains.argtypes = [_vp, _i32]
     L.empso_last_tile_rows.argtypes = [_vp, P(_i32)]
     L.empso_last_clusters.argtypes = [_vp, P(_i32)]
     L.empso_device_error.argtypes = [_vp, P(_i32), _vp]
@@ -122,7 +123,7 @@ def load():
     L.surrogate_init.argtypes = [_vp, _i32, _i32, _f32, ctypes.c_uint64]
     L.surrogate_set_backend.argtypes = [_vp, _i32]
     L.surrogate_set_overlap.argtypes = [_vp, _i32]
-    L.surrogate_set_policy.argtypes = [_vp, _i32, _f32]
+    L.surrogate_set_policy.argtypes = [_vp, _i32, _f32, _i32]
     L.surrogate_last_rank_corr.argtypes = [_vp, P(_f32), _vp]
     L.empso_nonfinite_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _i32, _vp]
     L.empso_set_strict.argtypes = [_vp, _i32]
@@ -304,6 +305,10 @@ class Context:
         """Rows per thread of the on-chip kernel: 0 automatic, 8 or 13."""
         self._check(self._L.empso_set_tile_rows(self._h, int(rows)))
 
+    def set_gradient_chains(self, chains: int):
+        """Independent chains of instances in the gradient's backward pass (1..4; 0 automatic)."""
+        self._check(self._L.empso_set_gradient_chains(self._h, int(chains)))
+
     def last_clusters(self) -> int:
         """Co-resident clusters (streaming kernels: CTAs) of the last launch."""
         r = _i32()
@@ -419,9 +424,11 @@ class Context:
     def surrogate_init(self, hidden=256, capacity=50000, lr=1e-3, seed=1):
         self._check(self._L.surrogate_init(self._h, hidden, capacity, lr, seed))
 
-    def surrogate_set_policy(self, recent=0, min_rank_corr=0.0):
-        """Recency share of the minibatches and the rank-correlation fallback."""
-        self._check(self._L.surrogate_set_policy(self._h, int(recent), float(min_rank_corr)))
+    def surrogate_set_policy(self, recent=0, min_rank_corr=0.0, patience=0):
+        """Recency share of the minibatches, the rank-correlation fallback and
+        the stagnation fallback (whole swarm after `patience` screened
+        generations in a row without a new best)."""
+        self._check(self._L.surrogate_set_policy(self._h, int(recent), float(min_rank_corr), int(patience)))
 
     def surrogate_last_rank_corr(self) -> float:
         r = _f32()

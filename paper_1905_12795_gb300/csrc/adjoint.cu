@@ -531,12 +531,13 @@ cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_in
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
+cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int n_all, int rec_threads,
                                 cudaStream_t st)
 {
     // the receiver term of step nt first; each step's extra block then
-    // scatters the next step's
-    const int tz = adj_rows_per_thread(g, n_inst);
+    // scatters the next step's.  The rows per thread follow the instances of
+    // all chains that run at once (n_all).
+    const int tz = adj_rows_per_thread(g, n_all);
     const dim3 grid(tile_count(g, 8 * tz) + 1, n_inst);
     const StepFn fn = step_fn(g.R, tz);
     adj_scatter_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);

@@ -88,6 +88,13 @@ struct empso_ctx {
     };
     std::vector<GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
+    // the gradient's backward pass as independent chains of instances, each
+    // on its own captured stream, so that one chain's memory waits and launch
+    // gaps overlap another's work
+    static constexpr int MAX_CHAINS = 4;
+    int grad_chains = 0;            // 0: four chains from 16 instances up, else one
+    cudaStream_t chain_stream[MAX_CHAINS - 1] = {};
+    cudaEvent_t chain_fork = nullptr, chain_join[MAX_CHAINS - 1] = {};
     float *xf = nullptr;            // float copy of the swarm positions [P][D]
     double *gen_misfit = nullptr;   // misfit of the last captured generation [P]
 
@@ -102,6 +109,10 @@ struct empso_ctx {
     float sur_rho_min = 0.f;             // > 0: model the whole swarm after a pre-screened generation
                                          // whose rank correlation fell below this
     bool sur_screened = false;           // the last surrogate generation was pre-screened
+    int sur_patience = 0;                // > 0: model the whole swarm after this many pre-screened
+                                         // generations in a row without a new best misfit
+    int sur_stall = 0;                   // such generations so far
+    double sur_best = HUGE_VAL;          // best misfit when the count was last updated
     int *sel_rows = nullptr;        // [P] indices of the modelled particles
     float *xk = nullptr;            // [P][D] their positions
     double *fk = nullptr;           // [P] their misfits
@@ -829,6 +840,11 @@ void free_ctx(empso_ctx *c)
         cudaFree(e.table);
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (int i = 0; i < empso_ctx::MAX_CHAINS - 1; ++i) {
+        if (c->chain_stream[i]) cudaStreamDestroy(c->chain_stream[i]);
+        if (c->chain_join[i]) cudaEventDestroy(c->chain_join[i]);
+    }
+    if (c->chain_fork) cudaEventDestroy(c->chain_fork);
     for (void *p : c->sur_mem) cudaFree(p);
     if (c->sur_stream) cudaStreamDestroy(c->sur_stream);
     if (c->sur_fork) cudaEventDestroy(c->sur_fork);
@@ -897,17 +913,11 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         ctx->grids[i].spec = grids[i];
         if ((rc = setup_grid(ctx, ctx->grids[i], i)) != EMPSO_OK) return bail(rc);
     }
-    std::vector<GridDev> gd(ngrids);
-    for (int i = 0; i < ngrids; ++i) gd[i] = ctx->grids[i].dev;
     auto ck = [&](cudaError_t e, const char *what) {
         if (e == cudaSuccess) return EMPSO_OK;
         ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? EMPSO_OOM : EMPSO_CUDA_ERROR;
     };
-    if ((rc = ck(cudaMalloc(&ctx->grids_dev, sizeof(GridDev) * ngrids), "grid table")) ||
-        (rc = ck(cudaMemcpy(ctx->grids_dev, gd.data(), sizeof(GridDev) * ngrids,
-                            cudaMemcpyHostToDevice), "grid table copy")))
-        return bail(rc);
     ctx->nrec_total = nrec_total;
     ctx->rec_host.assign(rec_xz, rec_xz + 2 * (size_t)nrec_total);
     if ((rc = ck(cudaMalloc(&ctx->rec_dev, sizeof(float2) * std::max(1, nrec_total)), "receivers")))
@@ -915,6 +925,12 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
     if (nrec_total > 0 &&
         (rc = ck(cudaMemcpy(ctx->rec_dev, rec_xz, sizeof(float2) * nrec_total,
                             cudaMemcpyHostToDevice), "receiver copy")))
+        return bail(rc);
+    std::vector<GridDev> gd(ngrids);
+    for (int i = 0; i < ngrids; ++i) gd[i] = ctx->grids[i].dev;
+    if ((rc = ck(cudaMalloc(&ctx->grids_dev, sizeof(GridDev) * ngrids), "grid table")) ||
+        (rc = ck(cudaMemcpy(ctx->grids_dev, gd.data(), sizeof(GridDev) * ngrids,
+                            cudaMemcpyHostToDevice), "grid table copy")))
         return bail(rc);
     if ((rc = ck(cudaMalloc(&ctx->counter, sizeof(int)), "counter")) ||
         (rc = ck(cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming), "event")))
@@ -924,7 +940,7 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
         // keep room for the kernel's static shared memory
-        ctx->smem_optin = optin > 2048 ? (size_t)optin - 2048 : 0;
+        ctx->smem_optin = optin > 1024 ? (size_t)optin - 1024 : 0;
         for (int R : {1, 2, 4}) {
             if ((rc = ck(resident_configure(R, ctx->smem_optin, 16), "on-chip kernel attributes")))
                 return bail(rc);
@@ -990,8 +1006,13 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
             (rc = ck(cudaMemset(ctx->pso_int, 0, sizeof(int) * (p.P + 2)), "swarm ints")))
             return bail(rc);
     }
-    if ((rc = ck(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream")))
+    if ((rc = ck(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream")) ||
+        (rc = ck(cudaEventCreateWithFlags(&ctx->chain_fork, cudaEventDisableTiming), "chain event")))
         return bail(rc);
+    for (int i = 0; i < empso_ctx::MAX_CHAINS - 1; ++i)
+        if ((rc = ck(cudaStreamCreateWithFlags(&ctx->chain_stream[i], cudaStreamNonBlocking), "chain stream")) ||
+            (rc = ck(cudaEventCreateWithFlags(&ctx->chain_join[i], cudaEventDisableTiming), "chain event")))
+            return bail(rc);
     if ((rc = ck(cudaDeviceSynchronize(), "setup kernels"))) return bail(rc);
     *out = ctx;
     return EMPSO_OK;
@@ -1172,6 +1193,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         long long best = 0;
         for (int C = 1; C <= 16; ++C)
             for (const int rows : {13, 8}) {
+                if (ctx->forced_C > 0 && C != ctx->forced_C) continue;
                 if (ctx->forced_rows > 0 && rows != ctx->forced_rows) continue;
                 if (!resident_fits(g, C, rec_max, ctx->smem_optin, rows)) continue;
                 const size_t sm = resident_smem_bytes(g, C, rec_max);
@@ -1285,7 +1307,8 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     // the two time loops replay as one graph
     std::ostringstream key;
     key << gid << "|" << I << "|" << rec_threads << "|" << (const void *)W.insts << "|" << rC << "|" << lC
-        << "|" << (const void *)W.rtab << "|" << (const void *)W.slots << "|" << forward_only;
+        << "|" << (const void *)W.rtab << "|" << (const void *)W.slots << "|" << forward_only << "|"
+        << ctx->grad_chains;
     cudaGraphExec_t exec = nullptr;
     for (auto &e : W.graphs)
         if (e.first == key.str()) exec = e.second;
@@ -1311,8 +1334,24 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         } else {
             ce = launch_adj_forward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
         }
-        if (ce == cudaSuccess && !forward_only)
-            ce = launch_adj_backward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
+        if (ce == cudaSuccess && !forward_only) {
+            // instances [c I / n, (c + 1) I / n) on chain c (chain 0 on the
+            // capture stream), forked after the forward pass and joined at the end
+            const int want = ctx->grad_chains > 0 ? ctx->grad_chains : (I >= 16 ? 4 : 1);
+            const int n = (int)std::max<long long>(1, std::min<long long>(want, I));
+            if (n > 1) ce = cudaEventRecord(ctx->chain_fork, ctx->cap_stream);
+            for (int c = 1; c < n && ce == cudaSuccess; ++c)
+                ce = cudaStreamWaitEvent(ctx->chain_stream[c - 1], ctx->chain_fork, 0);
+            for (int c = 0; c < n && ce == cudaSuccess; ++c) {
+                const long long i0 = c * I / n, i1 = (c + 1) * I / n;
+                ce = launch_adj_backward(g, W.insts + i0, (int)(i1 - i0), (int)I, rec_threads,
+                                         c == 0 ? ctx->cap_stream : ctx->chain_stream[c - 1]);
+            }
+            for (int c = 1; c < n && ce == cudaSuccess; ++c) {
+                ce = cudaEventRecord(ctx->chain_join[c - 1], ctx->chain_stream[c - 1]);
+                if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->cap_stream, ctx->chain_join[c - 1], 0);
+            }
+        }
         const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
         if (ce == cudaSuccess) ce = ee;
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -1837,6 +1876,16 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas)
     return EMPSO_OK;
 }
 
+empso_status empso_set_gradient_chains(empso_ctx *ctx, int32_t chains)
+{
+    if (!ctx) return EMPSO_INVALID_ARG;
+    ctx->err.clear();
+    if (chains < 0 || chains > empso_ctx::MAX_CHAINS)
+        return fail(ctx, EMPSO_INVALID_ARG, "gradient chains must be 0..4");
+    ctx->grad_chains = chains;
+    return EMPSO_OK;
+}
+
 empso_status empso_set_tile_rows(empso_ctx *ctx, int32_t rows)
 {
     if (!ctx) return EMPSO_INVALID_ARG;
@@ -2053,13 +2102,15 @@ empso_status surrogate_set_overlap(empso_ctx *ctx, int32_t enable)
     return EMPSO_OK;
 }
 
-empso_status surrogate_set_policy(empso_ctx *ctx, int32_t recent, float min_rank_corr)
+empso_status surrogate_set_policy(empso_ctx *ctx, int32_t recent, float min_rank_corr, int32_t patience)
 {
     NEED_SUR(ctx);
-    if (recent < 0 || !(min_rank_corr >= -1.f && min_rank_corr <= 1.f))
-        return fail(ctx, EMPSO_INVALID_ARG, "need recent >= 0 and -1 <= min_rank_corr <= 1");
+    if (recent < 0 || !(min_rank_corr >= -1.f && min_rank_corr <= 1.f) || patience < 0)
+        return fail(ctx, EMPSO_INVALID_ARG, "need recent >= 0, -1 <= min_rank_corr <= 1 and patience >= 0");
     ctx->sur.recent = recent;
     ctx->sur_rho_min = min_rank_corr;
+    ctx->sur_patience = patience;
+    ctx->sur_stall = 0;
     return EMPSO_OK;
 }
 
@@ -2167,17 +2218,31 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
     // how many pairs the replay buffer holds (host read: decides the branch)
     int have = 0;
     float rho = 1.f;
+    int gk[2] = {0, 0};
     CK(ctx, cudaMemcpyAsync(&have, s.count, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (ctx->sur_rho_min > 0.f && ctx->sur_screened)
         CK(ctx, cudaMemcpyAsync(&rho, s.rho, sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (ctx->sur_patience > 0) CK(ctx, cudaMemcpyAsync(gk, ctx->pso.gk, sizeof gk, cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaStreamSynchronize(st));
+    // stagnation: pre-screened generations in a row after which the swarm's
+    // best misfit (its global best) did not improve
+    if (ctx->sur_patience > 0) {
+        double best = HUGE_VAL;
+        CK(ctx, cudaMemcpyAsync(&best, ctx->pso.pf + gk[0], sizeof best, cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaStreamSynchronize(st));
+        ctx->sur_stall = ctx->sur_screened && !(best < ctx->sur_best) ? ctx->sur_stall + 1 : 0;
+        ctx->sur_best = best;
+    }
     if ((rc = strict_begin(ctx, st))) return rc;
     Models mod;
     int k;
-    // the whole swarm is modelled while the buffer warms up, and after a
+    // the whole swarm is modelled while the buffer warms up, after a
     // pre-screened generation whose predictions ranked the modelled particles
-    // too poorly (rank correlation below the policy's minimum)
-    const bool fallback = ctx->sur_rho_min > 0.f && ctx->sur_screened && rho < ctx->sur_rho_min;
+    // too poorly (rank correlation below the policy's minimum), and after
+    // `patience` pre-screened generations in a row without a new best
+    const bool stalled = ctx->sur_patience > 0 && ctx->sur_stall >= ctx->sur_patience;
+    const bool fallback = (ctx->sur_rho_min > 0.f && ctx->sur_screened && rho < ctx->sur_rho_min) || stalled;
+    if (stalled) ctx->sur_stall = 0;
     ctx->sur_screened = false;
     if (have < warm || fallback) {
         // warm-up: model every particle, then train on everything so far
@@ -2198,21 +2263,21 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
         // first `have` rows) runs on a second stream beside this generation's
         // modelling, which appends only behind those rows; when the append
         // would wrap the ring onto them it runs first instead (same data,
-        // same result).  Default: train after the append, on every pair.
-        if (train_steps > 0 && ctx->sur_overlap) {
-            if ((long long)have + k <= s.cap) {
-                CK(ctx, cudaEventRecord(ctx->sur_fork, st));
-                CK(ctx, cudaStreamWaitEvent(ctx->sur_stream, ctx->sur_fork, 0));
-                CK(ctx, sur_train(s, train_steps, batch, ctx->sur_stream, have));
-                CK(ctx, cudaEventRecord(ctx->sur_done, ctx->sur_stream));
-                ctx->sur_done_rec = true;
-            } else {
-                CK(ctx, sur_train(s, train_steps, batch, st, have));
-            }
-        }
+        // same result).  Default: train after the append, on every pair.  The
+        // modelling is enqueued before the training's many small launches, so
+        // that the GPU starts on it while the host is still issuing them.
+        const bool beside = train_steps > 0 && ctx->sur_overlap && (long long)have + k <= s.cap;
+        if (train_steps > 0 && ctx->sur_overlap && !beside) CK(ctx, sur_train(s, train_steps, batch, st, have));
+        if (beside) CK(ctx, cudaEventRecord(ctx->sur_fork, st));
         mod.particles = ctx->xk;
         mod.M = k;
         if ((rc = run_batch(ctx, mod, shots, S, d_obs, nullptr, ctx->fk, st))) return rc;
+        if (beside) {
+            CK(ctx, cudaStreamWaitEvent(ctx->sur_stream, ctx->sur_fork, 0));
+            CK(ctx, sur_train(s, train_steps, batch, ctx->sur_stream, have));
+            CK(ctx, cudaEventRecord(ctx->sur_done, ctx->sur_stream));
+            ctx->sur_done_rec = true;
+        }
         CK(ctx, sur_rank_corr(ctx->fk, ctx->sel_rows, ctx->logphi, k, s.rho, st));
         ctx->sur_screened = true;
         CK(ctx, sur_append(s, ctx->xf, ctx->fk, ctx->sel_rows, k, st));
@@ -2255,6 +2320,7 @@ empso_status empso_nonfinite_count(empso_ctx *ctx, int64_t *count, int32_t reset
 //              | f64 x[P D], v[P D], p[P D], pf[P] | i32 order[P]
 //   surrogate: i32 K, H, cap | u64 seed | i32 t, sample_step, count
 //              | i32 screened | f32 rank correlation of that generation
+//              | i32 stalled generations | f64 best misfit of the stall count
 //              | f32 stats[2] | f32 params[n], m[n], v[n]
 //              | f32 xbuf[rows K], ybuf[rows] with rows = min(count, cap)
 //   u64 FNV-1a hash of every preceding byte
@@ -2264,7 +2330,7 @@ empso_status empso_nonfinite_count(empso_ctx *ctx, int64_t *count, int32_t reset
 namespace {
 
 const char CK_MAGIC[8] = {'E', 'M', 'P', 'S', 'O', 'C', 'K', '1'};
-constexpr uint32_t CK_VERSION = 2;
+constexpr uint32_t CK_VERSION = 3;
 
 uint64_t fnv1a(const unsigned char *p, size_t n)
 {
@@ -2355,6 +2421,8 @@ empso_status empso_save(empso_ctx *ctx, const char *path)
         CK(ctx, cudaMemcpy(&rho, s.rho, sizeof rho, cudaMemcpyDeviceToHost));
         o.val<int32_t>(ctx->sur_screened ? 1 : 0);
         o.val<float>(rho);
+        o.val<int32_t>(ctx->sur_stall);
+        o.val<double>(ctx->sur_best);
         CK(ctx, dev_put(o, s.stats, 2));
         CK(ctx, dev_put(o, s.p, (size_t)s.n_params));
         CK(ctx, dev_put(o, s.m, (size_t)s.n_params));
@@ -2432,8 +2500,9 @@ empso_status empso_load(empso_ctx *ctx, const char *path)
             return fail(ctx, EMPSO_INVALID_ARG, "checkpoint search bounds differ from this context's");
     }
     // surrogate part: validated in full before anything is written
-    int32_t sK = 0, sH = 0, scap = 0, st_t = 0, st_step = 0, count = 0, screened = 0;
+    int32_t sK = 0, sH = 0, scap = 0, st_t = 0, st_step = 0, count = 0, screened = 0, stall = 0;
     uint64_t sseed = 0;
+    double sbest = HUGE_VAL;
     float stats[2], rho = 0.f;
     std::vector<float> sp, sm, sv, xb, yb;
     const bool file_sur = (parts & 2u) != 0;
@@ -2442,12 +2511,12 @@ empso_status empso_load(empso_ctx *ctx, const char *path)
             return fail(ctx, EMPSO_NOT_INITIALIZED, "checkpoint holds a surrogate; call surrogate_init first");
         const SurDev &s = ctx->sur;
         if (!in.val(sK) || !in.val(sH) || !in.val(scap) || !in.val(sseed) || !in.val(st_t) ||
-            !in.val(st_step) || !in.val(count) || !in.val(screened) || !in.val(rho) ||
-            !in.get(stats, sizeof stats))
+            !in.val(st_step) || !in.val(count) || !in.val(screened) || !in.val(rho) || !in.val(stall) ||
+            !in.val(sbest) || !in.get(stats, sizeof stats))
             return corrupt("surrogate header");
         if (sK != s.K || sH != s.H || scap != s.cap)
             return fail(ctx, EMPSO_INVALID_ARG, "checkpoint surrogate (K, H, capacity) differs from this context's");
-        if (count < 0 || st_t < 0 || st_step < 0 || (screened != 0 && screened != 1))
+        if (count < 0 || st_t < 0 || st_step < 0 || (screened != 0 && screened != 1) || stall < 0)
             return corrupt("surrogate counters");
         const size_t np = (size_t)s.n_params, rows = (size_t)std::min(count, scap);
         sp.resize(np);
@@ -2478,6 +2547,8 @@ empso_status empso_load(empso_ctx *ctx, const char *path)
         CK(ctx, cudaMemcpy(s.count, &count, sizeof count, cudaMemcpyHostToDevice));
         CK(ctx, cudaMemcpy(s.rho, &rho, sizeof rho, cudaMemcpyHostToDevice));
         ctx->sur_screened = screened != 0;
+        ctx->sur_stall = stall;
+        ctx->sur_best = sbest;
         if (!xb.empty()) {
             CK(ctx, cudaMemcpy(s.xbuf, xb.data(), 4 * xb.size(), cudaMemcpyHostToDevice));
             CK(ctx, cudaMemcpy(s.ybuf, yb.data(), 4 * yb.size(), cudaMemcpyHostToDevice));

@@ -119,7 +119,9 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
 // that wrote its traces there)
 cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_inst, int rec_max,
                                 cudaStream_t st);
-cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
+// the backward pass of instances insts[0 .. n_inst), one of several chains
+// that together run n_all instances at once
+cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int n_all, int rec_threads,
                                 cudaStream_t st);
 // T: scratch of max(M * NZ * nx floats, M * S * 64 doubles), 8-byte aligned
 // (the misfit partials, then the x-folded gradient)
@@ -170,6 +172,16 @@ cudaError_t launch_finalize(const double *partial, const float *weights, int P, 
 int wave_max_ctas_per_sm(int threads);
 
 // On-chip variant (wave_resident.cu): one thread-block cluster per instance.
+// float4 per slab row of its damping table: one for the column groups outside
+// the x-damping layer and one per group with a lane in it
+__host__ __device__ inline int resident_gtab_width(const GridDev &g)
+{
+    const int qa = g.NQ < (g.pad + 3) / 4 ? g.NQ : (g.pad + 3) / 4;
+    int qb = (g.NX - g.pad) / 4;
+    qb = qb > g.NQ ? g.NQ : qb;
+    qb = qb < qa ? qa : qb;
+    return 1 + qa + (g.NQ - qb);
+}
 // `rows`: the rows-per-thread shape (8 or 13).
 int resident_max_threads(int rows);
 int resident_default_rows();

@@ -72,12 +72,19 @@ __device__ __forceinline__ void corners(float x, float z, const GridDev &g, int 
     w[3] = ax * az;
 }
 
-// 1 / x to the hardware reciprocal's accuracy (one MUFU operation)
-__device__ __forceinline__ float rcp_approx(float x)
+// Column groups with a lane in the x-damping layer (columns [0, pad) and
+// [NX - pad, NX)): groups [0, qa) and [qb, NQ)
+__device__ __forceinline__ void xpad_groups(const GridDev &g, int &qa, int &qb)
 {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+    qa = min(g.NQ, (g.pad + 3) / 4);
+    qb = max(qa, min(g.NQ, (g.NX - g.pad) / 4));
+}
+
+// slot of column group q in a row of the damping table: 0 for the groups
+// outside the x-damping layer, 1 .. for the others
+__device__ __forceinline__ int gslot(int q, int qa, int qb)
+{
+    return q < qa ? 1 + q : (q >= qb ? 1 + qa + (q - qb) : 0);
 }
 
 // Source position of the instance, shared by the CTA: bilinear corner (padded
@@ -90,19 +97,19 @@ struct SrcInfo {
 // One step of a work item: rows r0 .. r0 + nrows - 1 (nrows <= RW) of column
 // group q (cq / nq / mq point at group q of row 0 of u^n, u^{n-1} -> u^{n+1}
 // and the pre-scaled model slab).  ZPAD (the same for a whole CTA): some row
-// of the slab lies in the z-damping layer, so g = 1 / (hx + hz) per row;
-// otherwise g is the per-lane constant gx.  The rows are swept downwards
+// of the slab lies in the z-damping layer, so g comes from the CTA's table
+// (gq: the group's column of it, gst float4 per row); otherwise g is the
+// per-lane constant gx.  The rows are swept downwards
 // (D = 1) or upwards (D = -1, the window mirrored; the stencil is symmetric
 // in z), one instruction stream for both.  The first R rows swept are also
 // halo rows of a neighbouring CTA when `peer` is set: they go to its buffer
 // (shared-row offset peer_off) as soon as they are computed, so the remote
 // stores complete under the rest of the sweep.
 template <int R, int RW, bool ZPAD, bool HIST>
-__device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const float4 *mq, const float *ezs,
-                                           int sp4, int NQ, int r0, int nrows, int D, const float *cx,
+__device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const float4 *mq, const float4 *gq,
+                                           int gst, int sp4, int NQ, int r0, int nrows, int D, const float *cx,
                                            const float *cz, float cres, float2 gx01, float2 gx23,
-                                           float2 hx01, float2 hx23, float4 *hrow, int hp4, float4 *peer,
-                                           int peer_off)
+                                           float4 *hrow, int hp4, float4 *peer, int peer_off)
 {
     const float2 m1 = splat2(-1.f);
     const int rs = D > 0 ? r0 : r0 + nrows - 1; // first slab row swept
@@ -117,21 +124,23 @@ __device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const f
     for (int m = 0; m < 2 * R; ++m) w[m] = cp[(m - R) * ds];
     // the inputs of the next row are read before this row is stored
     // (software pipelined: the loads need not wait behind the store)
+    const int dg = D * gst;
+    const float4 *gp = ZPAD ? gq + rs * gst : nullptr;   // the row's update weights
     float4 p_w = cp[R * ds], p_l = cp[-1], p_r = cp[1], p_um = *np, p_av = *ap;
-    float p_hz = ZPAD ? ezs[rs] : 0.f;
+    float4 p_g = ZPAD ? *gp : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
         if (k >= nrows) break;
         w[2 * R] = p_w;
         const float4 lft = p_l, rgt = p_r, um = p_um, av = p_av;
-        const float hz = p_hz;
+        const float4 gv = p_g;
         if (k + 1 < RW) {
             p_w = cp[(R + 1) * ds];
             p_l = cp[ds - 1];
             p_r = cp[ds + 1];
             p_um = np[ds];
             p_av = ap[dm];
-            if (ZPAD) p_hz = ezs[rs + D * (k + 1)];
+            if (ZPAD) p_g = gp[(k + 1) * dg];
         }
         const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
         float xs[12];
@@ -143,9 +152,8 @@ __device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const f
         // (a f is the pre-scaled model slab)
         float2 g01 = gx01, g23 = gx23;
         if (ZPAD) {
-            const float2 d01 = __fadd2_rn(hx01, splat2(hz)), d23 = __fadd2_rn(hx23, splat2(hz));
-            g01 = make_float2(rcp_approx(d01.x), rcp_approx(d01.y));
-            g23 = make_float2(rcp_approx(d23.x), rcp_approx(d23.y));
+            g01 = lo2(gv);
+            g23 = hi2(gv);
         }
         const float2 um01 = lo2(um), um23 = hi2(um);
         const float2 o01 = __ffma2_rn(g01, __ffma2_rn(um01, m1, c01), __ffma2_rn(lo2(av), lap01, um01));
@@ -172,7 +180,7 @@ __device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const f
 // them) run instance `in`; with HIST every u^{n+1} also goes to in.hist
 template <int R, int RW, bool HIST>
 __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
-                                  float4 *M4, float *ezs, float *wring, float *dring, float4 *rec_w,
+                                  float4 *M4, float4 *G4, float *wring, float *dring, float4 *rec_w,
                                   int *rec_k, SrcInfo &src, int C, int crank, int base,
                                   cg::cluster_group &cluster, double *cred, double *wred, double *partial)
 {
@@ -202,9 +210,30 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         M4[r * NQ + qq] = make_float4(av.x / (1.f + (exq.x + ez)), av.y / (1.f + (exq.y + ez)),
                                       av.z / (1.f + (exq.z + ez)), av.w / (1.f + (exq.w + ez)));
     }
-    // half the z-damping of each slab row: g = 2 / (1 + t) = 1 / (hx + hz) with
-    // hx = (1 + t_x) / 2 per lane and hz = t_z / 2 per row
-    for (int r = tid; r < my_rows; r += nth) ezs[r] = 0.5f * __ldg(gez + z0 + r + HALO);
+    // some row of the slab in the z-damping layer (rows of the layer are the
+    // first and last of the grid, so the slab's end rows tell); the same path
+    // for every thread of the CTA
+    const bool zpad =
+        my_rows > 0 && (__ldg(gez + z0 + HALO) != 0.f || __ldg(gez + z0 + my_rows - 1 + HALO) != 0.f);
+    // Such a CTA tabulates g = 2 / (1 + t) of its rows once per instance: per
+    // row one value for the column groups outside the x-damping layer (t = t_z
+    // there) in slot 0, and one per lane for each group with a lane in it
+    // (slots 1 ..), so that its sweep reads g instead of dividing per point.
+    int qa, qb;
+    xpad_groups(gs, qa, qb);
+    const int gst = 1 + qa + (NQ - qb);
+    if (zpad)
+        for (int e = tid; e < my_rows * gst; e += nth) {
+            const int r = e / gst, sl = e % gst;
+            const float tz = __ldg(gez + z0 + r + HALO);
+            float4 exq = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sl > 0) {
+                const int qq = sl - 1 < qa ? sl - 1 : qb + (sl - 1 - qa);
+                exq = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + qq);
+            }
+            G4[e] = make_float4(2.f / (1.f + (exq.x + tz)), 2.f / (1.f + (exq.y + tz)),
+                                2.f / (1.f + (exq.z + tz)), 2.f / (1.f + (exq.w + tz)));
+        }
     if (tid == 0) {
         int i0, j0;
         float sw[4];
@@ -248,12 +277,10 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     // constant over the instance (g = 2 in the interior); hx for the others
     const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));
     const float2 gx23 = make_float2(2.f / (1.f + ex.z), 2.f / (1.f + ex.w));
-    const float2 hx01 = make_float2(0.5f * (1.f + ex.x), 0.5f * (1.f + ex.y));
-    const float2 hx23 = make_float2(0.5f * (1.f + ex.z), 0.5f * (1.f + ex.w));
     const float2 gxe01 = make_float2(2.f / (1.f + exe.x), 2.f / (1.f + exe.y));
     const float2 gxe23 = make_float2(2.f / (1.f + exe.z), 2.f / (1.f + exe.w));
-    const float2 hxe01 = make_float2(0.5f * (1.f + exe.x), 0.5f * (1.f + exe.y));
-    const float2 hxe23 = make_float2(0.5f * (1.f + exe.z), 0.5f * (1.f + exe.w));
+    // the damping-table columns of the thread's groups
+    const float4 *gq = G4 + gslot(q, qa, qb), *gq_e = G4 + gslot(qe, qa, qb);
     float cx[R + 1], cz[R + 1];
 #pragma unroll
     for (int m = 0; m <= R; ++m) {
@@ -289,10 +316,6 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
 
     cluster.sync();                                      // zeroed everywhere before halo stores
 
-    // some row of the slab in the z-damping layer (rows of the layer are the
-    // first and last of the grid, so the slab's end rows tell); the same path
-    // for every thread of the CTA
-    const bool zpad = my_rows > 0 && (ezs[0] != 0.f || ezs[my_rows - 1] != 0.f);
     // The source: the items holding a row of its corners add (a f) b r(t_n) to
     // those points after their rows (u^{n+1} is linear in the source term).
     // sbit: bit c = 1 when corner row s_j0 + c is one of this item's rows and
@@ -396,11 +419,11 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
             const int D = role == 2 ? -1 : 1;
             const int poff = role == 2 ? -rows_c : rows_c;
             if (zpad)
-                sweep_item<R, RW, true, HIST>(cq, nq, mq, ezs, sp4, NQ, r0, r1 - r0, D, cx, cz, cres, gx01, gx23,
-                                              hx01, hx23, hrow, hp4, peer, poff);
+                sweep_item<R, RW, true, HIST>(cq, nq, mq, gq, gst, sp4, NQ, r0, r1 - r0, D, cx, cz, cres, gx01,
+                                              gx23, hrow, hp4, peer, poff);
             else
-                sweep_item<R, RW, false, HIST>(cq, nq, mq, ezs, sp4, NQ, r0, r1 - r0, D, cx, cz, cres, gx01,
-                                               gx23, hx01, hx23, hrow, hp4, peer, poff);
+                sweep_item<R, RW, false, HIST>(cq, nq, mq, gq, gst, sp4, NQ, r0, r1 - r0, D, cx, cz, cres, gx01,
+                                               gx23, hrow, hp4, peer, poff);
             if (tail)
                 for (int rr = max(r0, rows_c - R); rr < r1; ++rr) xq[(R + rr - rows_c) * sp4] = nq[(R + rr) * sp4];
             if (sbit) add_source(q, r0, sbit, nq, mq, hrow, pq, xq);
@@ -415,11 +438,11 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
             float4 *peer = re < R ? pq : (re >= rows_c - R ? xq : nullptr);
             const int poff = re < R ? rows_c : -rows_c;
             if (zpad)
-                sweep_item<R, 1, true, HIST>(cq, nq, mq, ezs, sp4, NQ, re, 1, 1, cx, cz, cres, gxe01, gxe23,
-                                             hxe01, hxe23, hrow_e, hp4, peer, poff);
+                sweep_item<R, 1, true, HIST>(cq, nq, mq, gq_e, gst, sp4, NQ, re, 1, 1, cx, cz, cres, gxe01,
+                                             gxe23, hrow_e, hp4, peer, poff);
             else
-                sweep_item<R, 1, false, HIST>(cq, nq, mq, ezs, sp4, NQ, re, 1, 1, cx, cz, cres, gxe01, gxe23,
-                                              hxe01, hxe23, hrow_e, hp4, peer, poff);
+                sweep_item<R, 1, false, HIST>(cq, nq, mq, gq_e, gst, sp4, NQ, re, 1, 1, cx, cz, cres, gxe01,
+                                              gxe23, hrow_e, hp4, peer, poff);
             if (sbit_e) add_source(qe, re, sbit_e, nq, mq, hrow_e, pq, xq);
         }
         // receivers sample u^n (record n - 1)
@@ -521,12 +544,12 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float4 *A4 = smem4;
         float4 *B4 = A4 + (size_t)(rows_c + 2 * R) * (sg.NQ + 2);
         float4 *M4 = B4 + (size_t)(rows_c + 2 * R) * (sg.NQ + 2);
-        float *ezs = reinterpret_cast<float *>(M4 + (size_t)rows_c * sg.NQ);
-        float *wring = ezs + (rows_c + 3) / 4 * 4;
+        float4 *G4 = M4 + (size_t)rows_c * sg.NQ;
+        float *wring = reinterpret_cast<float *>(G4 + (size_t)rows_c * resident_gtab_width(sg));
         float *dring = wring + 4 * ((DEPTH + 3) / 4);
         float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
         int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
-        resident_instance<R, RW, HIST>(sg, in, A4, B4, M4, ezs, wring, dring, rec_w, rec_k, src, Ce, ce,
+        resident_instance<R, RW, HIST>(sg, in, A4, B4, M4, G4, wring, dring, rec_w, rec_k, src, Ce, ce,
                                        sub * Ce, cluster, cred, wred, partial);
     }
 }
@@ -561,14 +584,14 @@ int resident_threads(const GridDev &g, int C, int rows)
 }
 
 // two time levels with halo rows, the slab of the model field, its damping
-// rows, the staging buffers (wavelet samples, observed records) and the
+// table, the staging buffers (wavelet samples, observed records) and the
 // receiver tables, for shots of up to ring_pitch receivers
 size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch)
 {
     const int rows_c = (g.NZ + C - 1) / C;
-    return sizeof(float4) * (2 * (size_t)(rows_c + 2 * g.R) * (g.NQ + 2) + (size_t)rows_c * g.NQ) +
-           sizeof(float) * ((rows_c + 3) / 4 * 4 + 4 * ((DEPTH + 3) / 4) +
-                            ((size_t)DEPTH * ring_pitch + 3) / 4 * 4) +
+    return sizeof(float4) * (2 * (size_t)(rows_c + 2 * g.R) * (g.NQ + 2) + (size_t)rows_c * g.NQ +
+                             (size_t)rows_c * resident_gtab_width(g)) +
+           sizeof(float) * (4 * ((DEPTH + 3) / 4) + ((size_t)DEPTH * ring_pitch + 3) / 4 * 4) +
            (sizeof(float4) + sizeof(int)) * (size_t)ring_pitch;
 }
 

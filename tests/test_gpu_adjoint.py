@@ -185,6 +185,32 @@ def test_gradient_batch_of_models_equals_single_calls(B):
     ctx.close()
 
 
+def test_gradient_chains_give_identical_results(B):
+    """The backward pass split into 1..4 concurrent chains of instances (5
+    instances: uneven chains) computes every instance the same way."""
+    nx, nz, h = 37, 29, 10.0
+    grid = B.make_grid(nx, nz, h, h, 6, 8, 0.2, 15.0, 1500.0, 3000.0)
+    rec = synth.receiver_line(nx, h, 20.0)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    xs = [60.0, 120.0, 180.0, 240.0, 300.0]
+    sh = B.make_shots([(x, 20.0) for x in xs], [0] * 5, [nx] * 5, weights=[1.0, 0.5, 2.0, 1.0, 0.25])
+    dobs = torch.randn(5 * nt * nx, device="cuda") * 1e-3
+    v = _dev(synth.layered_faulted_model(nx, nz, h, h, seed=4, vmin=1500.0, vmax=2800.0)[None])
+    out = []
+    for chains in (1, 2, 3, 4):
+        ctx.set_gradient_chains(chains)
+        g = torch.zeros(1, nz, nx, device="cuda")
+        m = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.gradient(v, sh, dobs, g, m)
+        out.append((g, m.item()))
+    for g, m in out[1:]:
+        assert torch.equal(g, out[0][0]) and m == out[0][1]
+    with pytest.raises(B.EmpsoError):
+        ctx.set_gradient_chains(5)
+    ctx.close()
+
+
 def test_gradient_edge_cases(B):
     nx, nz, h = 37, 29, 10.0
     grid = B.make_grid(nx, nz, h, h, 6, 8, 0.2, 15.0, 1500.0, 3000.0)

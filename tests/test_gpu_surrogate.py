@@ -291,3 +291,30 @@ def test_rank_correlation_fallback_models_the_whole_swarm(B):
         with pytest.raises(B.EmpsoError):
             ctx.surrogate_set_policy(recent=-1)
         ctx.close()
+
+
+def test_stagnation_fallback_models_the_whole_swarm(B):
+    """With patience 1, a generation follows the whole-swarm rule exactly:
+    after a pre-screened generation that did not lower the best misfit
+    (tracked on the host as the minimum of every modelled misfit, which is
+    the swarm's global best), the whole swarm is modelled; after one that
+    did, it is pre-screened again."""
+    P = 64
+    ctx, sh, dobs = _search_problem(B, P, 5)
+    ctx.surrogate_init(hidden=64, capacity=4096, lr=1e-3, seed=5)
+    ctx.surrogate_set_policy(recent=0, min_rank_corr=0.0, patience=1)
+    ctx.pso_init()
+    mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+    best, prev_screened, prev_improved, fallbacks = np.inf, False, True, 0
+    for _ in range(40):
+        n = ctx.surrogate_generation(sh, dobs, 0.25, warm=P, train_steps=3, batch=64, misfit_out=mis)
+        if prev_screened:
+            assert n == (16 if prev_improved else P)
+            fallbacks += n == P
+        m = mis.min().item()
+        prev_improved, prev_screened = m < best, n < P
+        best = min(best, m)
+    assert fallbacks >= 1
+    with pytest.raises(B.EmpsoError):
+        ctx.surrogate_set_policy(patience=-1)
+    ctx.close()
