@@ -37,6 +37,12 @@ the other readings of the paper in the design notes):
   seeded layered/faulted model (the paper's Marmousi data are not
   available).
 
+One group the paper does not have: an optional ``surrogate`` dictionary
+(``keep`` fraction modelled per generation, ``hidden``, ``capacity``, ``lr``,
+``train_steps``, ``batch``, ``recent``, ``patience``) runs the generations
+with the learned pre-screen; its log records then also carry the number of
+particles modelled and the surrogate's rank correlation on them.
+
 The arithmetic of the method runs in the CUDA library; this module only
 converts units and drives the library's calls.
 """
@@ -87,6 +93,7 @@ class RunConfig:
     em_start: int
     seed: int
     shotfile: str = ""
+    surrogate: dict | None = None    # learned pre-screen settings (not in the paper)
     raw: dict = field(default_factory=dict)
 
     @property
@@ -158,7 +165,24 @@ def load(src, overrides: dict | None = None) -> RunConfig:
                      em_start=int(ps.get("em_start", PAPER_DEFAULTS["em_start"])),
                      seed=int(ps.get("seed", PAPER_DEFAULTS["seed"])),
                      shotfile=os.path.join(base_dir, raw["shotfile"]) if raw.get("shotfile") else "",
-                     raw=raw)
+                     surrogate=_surrogate_settings(raw.get("surrogate")), raw=raw)
+
+
+SURROGATE_DEFAULTS = {"keep": 0.25, "hidden": 256, "capacity": 50000, "lr": 1e-3, "train_steps": 5,
+                      "batch": 512, "recent": 4096, "patience": 0}
+
+
+def _surrogate_settings(sur):
+    if sur is None:
+        return None
+    bad = set(sur) - set(SURROGATE_DEFAULTS)
+    if bad:
+        raise KeyError(f"run configuration: unknown surrogate keys {sorted(bad)}")
+    out = dict(SURROGATE_DEFAULTS)
+    out.update(sur)
+    if not 0.0 < float(out["keep"]) <= 1.0:
+        raise ValueError("run configuration: surrogate.keep must lie in (0, 1]")
+    return out
 
 
 def open_context(cfg: RunConfig):
@@ -211,25 +235,44 @@ def run(cfg: RunConfig, log_path: str | None = None, gens: int | None = None, do
         updates = float(cfg.npop) * len(cfg.shots) * NX * NZ * nt
         mis = torch.zeros(cfg.npop, dtype=torch.float64, device="cuda")
         ctx.set_timing(True)
+        sur = cfg.surrogate
+        if sur:
+            ctx.surrogate_init(hidden=int(sur["hidden"]), capacity=int(sur["capacity"]), lr=float(sur["lr"]),
+                               seed=cfg.seed)
+            ctx.surrogate_set_overlap(True)
+            ctx.surrogate_set_policy(recent=int(sur["recent"]), patience=int(sur["patience"]))
         ctx.pso_init()
         G = cfg.gens if gens is None else gens
         records = []
         log = open(log_path, "w") if log_path else None
         t_start = time.perf_counter()
+        evaluations = 0
         for k in range(1, G + 1):
-            ctx.generation(shots, dobs, mis)
+            rho = None
+            if sur:
+                n_mod = ctx.surrogate_generation(shots, dobs, float(sur["keep"]), warm=cfg.npop,
+                                                 train_steps=int(sur["train_steps"]),
+                                                 batch=int(sur["batch"]), misfit_out=mis)
+                if n_mod < cfg.npop:
+                    rho = ctx.surrogate_last_rank_corr()
+            else:
+                ctx.generation(shots, dobs, mis)
+                n_mod = cfg.npop
+            evaluations += n_mod
             m = mis.cpu().numpy()
             kernel_ms = ctx.read_timing()[1]
-            fin = m[np.isfinite(m)]
+            fin = m[np.isfinite(m)]     # the modelled particles' misfits
             pf = torch.zeros(cfg.npop, dtype=torch.float64, device="cuda")
             gk = torch.zeros(2, dtype=torch.int32, device="cuda")
             ctx.pso_get_state(pf=pf, gk=gk)
             rec = {"generation": k, "best_misfit": float(fin.min()) if fin.size else None,
                    "mean_misfit": float(fin.mean()) if fin.size else None,
                    "gbest_misfit": float(pf[int(gk[0].item())].item()), "gbest": int(gk[0].item()),
-                   "evaluations": k * cfg.npop, "nonfinite": int(m.size - fin.size),
-                   "modelling_ms": kernel_ms, "updates_per_s": updates / (kernel_ms * 1e-3),
-                   "wall_s": time.perf_counter() - t_start}
+                   "modelled": n_mod, "evaluations": evaluations,
+                   "nonfinite": int(n_mod - fin.size) if not sur else None,
+                   "modelling_ms": kernel_ms,
+                   "updates_per_s": updates * n_mod / cfg.npop / (kernel_ms * 1e-3),
+                   "surrogate_rank_corr": rho, "wall_s": time.perf_counter() - t_start}
             records.append(rec)
             if log:
                 log.write(json.dumps(rec) + "\n")

@@ -11,16 +11,19 @@
 // w.  Its exact discrete adjoint, for k = nt .. 1 with mu^{nt+1} = mu^{nt+2} = 0:
 //   mu^k = w R^T e_{k-1} + 2 f mu^{k+1} + L (f a mu^{k+1}) - g mu^{k+2},
 //   dphi/da = sum_{k=1..nt} mu^k f (L u^{k-1} + s^{k-1}).
-// The forward pass keeps the whole history u^0 .. u^nt in HBM (no
-// checkpointing: a shot of the 461 x 151 grid takes 0.78 GB).  Then
-// dphi/da of the padded grid is folded back onto the physical nodes (the
-// transpose of the edge extension into the damping pad) and chained to the
-// velocity: dphi/dv = 2 v dt^2 dphi/da.
+// The forward pass keeps a whole history in HBM (no checkpointing: a shot
+// of the 461 x 151 grid takes 0.78 GB).  Then dphi/da of the padded grid is
+// folded back onto the physical nodes (the transpose of the edge extension
+// into the damping pad) and chained to the velocity: dphi/dv = 2 v dt^2
+// dphi/da.
 //
-// The forward pass normally runs on the on-chip modelling kernel, which
-// streams the history out (wave_resident.cu) and leaves its traces for
-// adj_residual_kernel; adj_fwd_kernel is the per-step form for grids it
-// cannot hold.  The per-step kernels here run over all instances at once
+// The forward pass normally runs on the on-chip (or L2) cluster modelling
+// kernel, which streams out L u^n of every step, the only part of the
+// forward field the adjoint pass needs (its gradient term then costs one
+// pointwise read per point-step instead of a staged tile and a second
+// Laplacian), and leaves its traces for adj_residual_kernel;
+// adj_fwd_kernel is the per-step form for grids neither can hold, whose
+// history is the time levels u^0 .. u^nt themselves.  The per-step kernels here run over all instances at once
 // (blockIdx.y = instance), one launch per time step (the time loops replay as
 // one CUDA graph).  They stage the fields their Laplacians read in
 // shared-memory tiles and give each thread a few rows of one float4 group.
@@ -291,13 +294,15 @@ __global__ void adj_scatter_kernel(GridDev g, const AdjInst *__restrict__ insts,
 //   G += mu^k f (L u^{k-1} + s^{k-1}),
 // with Q^{k+1} = f a mu^{k+1} formed as the tile is staged.  J is read only
 // on the instance's receiver rows.  Block 0 meanwhile scatters J^{k-1} into
-// the other J slot for the next step.
-template <int R, int TZ>
+// the other J slot for the next step.  HLAP: the history holds L u^{k-1} (in
+// slot k, written by a cluster kernel's forward pass), read per point; else
+// it holds u^{k-1} (slot k - 1), staged as a tile and differentiated here.
+template <int R, int TZ, bool HLAP>
 __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts,
                                                                    int k)
 {
     constexpr int W = Tile<R>::W, XG = Tile<R>::XG, TT = 8 * TZ;
-    __shared__ float4 SQ[(TT + 2 * R) * W], SU[(TT + 2 * R) * W];
+    __shared__ float4 SQ[(TT + 2 * R) * W], SU[HLAP ? 1 : (TT + 2 * R) * W];
     const AdjInst in = insts[blockIdx.y];
     if (blockIdx.x == 0) {
         if (k >= 2) scatter_receiver_term(g, in, k - 1);
@@ -310,10 +315,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
     const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 3) * g.field);
     const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 3) * g.field);
     float4 *J4 = reinterpret_cast<float4 *>(in.J + (long long)(k % 2) * g.field);
-    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(k - 1) * g.field);
+    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(HLAP ? k : k - 1) * g.field);
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
     float4 *G4 = reinterpret_cast<float4 *>(in.G);
-    stage_tile<R, TT>(SU, u, J0, q0, g);                  // in flight during the product tile
+    if (!HLAP) stage_tile<R, TT>(SU, u, J0, q0, g);      // in flight during the product tile
     stage_tile_product<R, TT>(SQ, B4, m1, J0, q0, g);
     cp_async_wait_all();
     __syncthreads();
@@ -329,7 +334,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
         const int sr = ly * TZ + r + R;
         const long long k4 = (long long)(J + HALO) * p4 + HALO4 + q;
         const float4 lq = lap4_tile_sum<R>(SQ, sr, lx + XG, g);
-        const float4 lu = lap4_tile_sum<R>(SU, sr, lx + XG, g);
+        const float4 lu = HLAP ? u[k4] : lap4_tile_sum<R>(SU, sr, lx + XG, g);
         const float4 a1 = m1[k4], a2 = m2[k4];
         const bool jrow = J >= in.jr0 && J <= in.jr1;
         const float4 jj = jrow ? J4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -480,14 +485,19 @@ StepFn fwd_fn(int R)
     if (R == 4) return adj_fwd_kernel<4, 1>;
     return R == 2 ? adj_fwd_kernel<2, 1> : adj_fwd_kernel<1, 1>;
 }
-template <int TZ>
+template <int TZ, bool HLAP>
 StepFn step_fn_z(int R)
 {
-    if (R == 8) return adj_step_kernel<8, TZ>;
-    if (R == 4) return adj_step_kernel<4, TZ>;
-    return R == 2 ? adj_step_kernel<2, TZ> : adj_step_kernel<1, TZ>;
+    if (R == 8) return adj_step_kernel<8, TZ, HLAP>;
+    if (R == 4) return adj_step_kernel<4, TZ, HLAP>;
+    return R == 2 ? adj_step_kernel<2, TZ, HLAP> : adj_step_kernel<1, TZ, HLAP>;
 }
-StepFn step_fn(int R, int TZ) { return TZ == 4 ? step_fn_z<4>(R) : (TZ == 2 ? step_fn_z<2>(R) : step_fn_z<1>(R)); }
+template <bool HLAP>
+StepFn step_fn_h(int R, int TZ)
+{
+    return TZ == 4 ? step_fn_z<4, HLAP>(R) : (TZ == 2 ? step_fn_z<2, HLAP>(R) : step_fn_z<1, HLAP>(R));
+}
+StepFn step_fn(int R, int TZ, bool hlap) { return hlap ? step_fn_h<true>(R, TZ) : step_fn_h<false>(R, TZ); }
 
 // rows per thread of an adjoint-step launch over n_inst instances: 4 while
 // that gives every SM 7 tile blocks (one wave at 8 resident), else 2 while
@@ -532,14 +542,14 @@ cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_in
 }
 
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int n_all, int rec_threads,
-                                cudaStream_t st)
+                                bool hlap, cudaStream_t st)
 {
     // the receiver term of step nt first; each step's extra block then
     // scatters the next step's.  The rows per thread follow the instances of
     // all chains that run at once (n_all).
     const int tz = adj_rows_per_thread(g, n_all);
     const dim3 grid(tile_count(g, 8 * tz) + 1, n_inst);
-    const StepFn fn = step_fn(g.R, tz);
+    const StepFn fn = step_fn(g.R, tz, hlap);
     adj_scatter_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
     for (int k = g.nt; k >= 1; --k) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, k);
     return cudaGetLastError();

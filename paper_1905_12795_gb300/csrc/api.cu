@@ -1344,7 +1344,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
                 ce = cudaStreamWaitEvent(ctx->chain_stream[c - 1], ctx->chain_fork, 0);
             for (int c = 0; c < n && ce == cudaSuccess; ++c) {
                 const long long i0 = c * I / n, i1 = (c + 1) * I / n;
-                ce = launch_adj_backward(g, W.insts + i0, (int)(i1 - i0), (int)I, rec_threads,
+                ce = launch_adj_backward(g, W.insts + i0, (int)(i1 - i0), (int)I, rec_threads, rC || lC,
                                          c == 0 ? ctx->cap_stream : ctx->chain_stream[c - 1]);
             }
             for (int c = 1; c < n && ce == cudaSuccess; ++c) {

@@ -120,9 +120,10 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
 cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_inst, int rec_max,
                                 cudaStream_t st);
 // the backward pass of instances insts[0 .. n_inst), one of several chains
-// that together run n_all instances at once
+// that together run n_all instances at once; hlap: the history holds L u^n in
+// slot n + 1 (cluster kernels' forward pass), else u^n in slot n
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int n_all, int rec_threads,
-                                cudaStream_t st);
+                                bool hlap, cudaStream_t st);
 // T: scratch of max(M * NZ * nx floats, M * S * 64 doubles), 8-byte aligned
 // (the misfit partials, then the x-folded gradient)
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,

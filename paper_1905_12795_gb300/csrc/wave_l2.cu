@@ -68,7 +68,9 @@ __device__ __forceinline__ void bilinear_corner(float x, float z, const GridDev 
     w[3] = ax * az;
 }
 
-// with HIST every u^{n+1} also goes to in.hist (slot n + 1, buffer layout)
+// with HIST the Laplacian L u^n of every step (without the source term) also
+// goes to in.hist (slot n + 1, buffer layout), the history the gradient's
+// adjoint pass reads
 template <int R, bool HIST>
 __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float4 *U1, float *wring,
                             float *dring, float4 *rec_w, int *rec_k, int C, int crank,
@@ -179,6 +181,7 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
                     xline1(lft, w[R], rgt, xs);
                     float2 lap01, lap23;
                     lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
+                    const float4 lap_u = make_float4(lap01.x, lap01.y, lap23.x, lap23.y);   // L u^n
                     if (src_here && (k == ks || k == ks + 1)) {
                         const float4 sb = (k == ks) ? sb0 : sb1;
                         lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);
@@ -201,10 +204,10 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
                     if (k >= kfirst && k < klast) {
                         const float4 out = make_float4(o01.x, o01.y, o23.x, o23.y);
                         nxt[lr * sp4 + 1 + q] = out;
-                        if (HIST)   // written once, read back by a later pass: evict first
+                        if (HIST)   // L u^n for the adjoint pass (written once: evict first)
                             __stcs(reinterpret_cast<float4 *>(in.hist + (size_t)(n + 1) * gs.field) +
                                        (size_t)(zr + HALO) * ap4 + HALO4 + q,
-                                   out);
+                                   lap_u);
                     }
 #pragma unroll
                     for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];

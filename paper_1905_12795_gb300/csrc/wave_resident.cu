@@ -164,8 +164,8 @@ __device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const f
             *pp = out;
             pp += ds;
         }
-        if (HIST) {
-            __stcs(hp, out);                         // written once: evict first
+        if (HIST) {   // the gradient's history: L u^n (written once: evict first)
+            __stcs(hp, make_float4(lap01.x, lap01.y, lap23.x, lap23.y));
             hp += dh;
         }
         cp += ds;
@@ -177,7 +177,8 @@ __device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const f
 }
 
 // C CTAs (ranks base .. base + C - 1 of the cluster; crank is the rank among
-// them) run instance `in`; with HIST every u^{n+1} also goes to in.hist
+// them) run instance `in`; with HIST the Laplacian L u^n of every step (the
+// source term excluded) also goes to in.hist, slot n + 1
 template <int R, int RW, bool HIST>
 __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
                                   float4 *M4, float4 *G4, float *wring, float *dring, float4 *rec_w,
@@ -362,11 +363,10 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         hrow_e = reinterpret_cast<float4 *>(in.hist) + (size_t)(z0 + re + HALO) * hp4 + HALO4 + qe;
     float4 *cur = A4, *nxt = B4;
     int step = 0;
-    // The source term of a piece's corner rows (column group qq, first row
-    // pr0, corner-row bits sb), added after its sweep; also to the history and
-    // to a neighbour's halo copy of the row
-    auto add_source = [&](int qq, int pr0, unsigned sb, float4 *nq, const float4 *mq, float4 *hr, float4 *pq,
-                          float4 *xq) {
+    // The source term of a piece's corner rows (column group qq, corner-row
+    // bits sb), added after its sweep; also to a neighbour's halo copy of the
+    // row (the history holds L u^n without it)
+    auto add_source = [&](int qq, unsigned sb, float4 *nq, const float4 *mq, float4 *pq, float4 *xq) {
         const float rn = wring[step % DEPTH];
         for (int c = 0; c < 2; ++c) {
             if (!((sb >> c) & 1u)) continue;
@@ -383,7 +383,6 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
             v = make_float4(fmaf(av.x, b.x, v.x), fmaf(av.y, b.y, v.y), fmaf(av.z, b.z, v.z),
                             fmaf(av.w, b.w, v.w));
             nq[lr * sp4] = v;
-            if (HIST) __stcs(hr + (rr - pr0) * hp4, v);
             if (pq && rr < R) pq[(lr + rows_c) * sp4] = v;
             if (xq && rr >= rows_c - R) xq[(lr - rows_c) * sp4] = v;
         }
@@ -426,7 +425,7 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
                                                gx23, hrow, hp4, peer, poff);
             if (tail)
                 for (int rr = max(r0, rows_c - R); rr < r1; ++rr) xq[(R + rr - rows_c) * sp4] = nq[(R + rr) * sp4];
-            if (sbit) add_source(q, r0, sbit, nq, mq, hrow, pq, xq);
+            if (sbit) add_source(q, sbit, nq, mq, pq, xq);
         }
         if (n < nt && extra) {   // the thread's single extra row
             const float4 *cq = cur + 1 + qe;
@@ -443,7 +442,7 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
             else
                 sweep_item<R, 1, false, HIST>(cq, nq, mq, gq_e, gst, sp4, NQ, re, 1, 1, cx, cz, cres, gxe01,
                                               gxe23, hrow_e, hp4, peer, poff);
-            if (sbit_e) add_source(qe, re, sbit_e, nq, mq, hrow_e, pq, xq);
+            if (sbit_e) add_source(qe, sbit_e, nq, mq, pq, xq);
         }
         // receivers sample u^n (record n - 1)
         if (has_rec && n >= 1) {
@@ -502,7 +501,8 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
 // ranks C/2 .. C - 1 instance b, both of the same grid (so both halves pass
 // the same number of cluster barriers).  Launches with no halved unit use the
 // PAIRS = false instantiation, where the whole-cluster layout is constant.
-// HIST (never with PAIRS) also writes the wavefield history.  NT threads at
+// HIST (never with PAIRS) also writes the history the gradient's adjoint pass
+// reads: L u^n of every step n into slot n + 1.  NT threads at
 // most: registers per thread are capped so that NT / 128 warps per scheduler
 // fit its quarter of the register file.
 template <int NT> struct RegCap {

@@ -46,6 +46,14 @@ def test_overrides_and_missing_keys():
     del raw["pso"]
     with pytest.raises(KeyError):
         config.load(raw)
+    # the optional surrogate group (not in the paper): defaults filled, keys checked
+    sur = config.load(EXAMPLE, {"surrogate": {"keep": 0.5}}).surrogate
+    assert sur["keep"] == 0.5 and sur["hidden"] == 256 and sur["train_steps"] == 5
+    assert config.load(EXAMPLE).surrogate is None
+    with pytest.raises(KeyError):
+        config.load(EXAMPLE, {"surrogate": {"keeep": 0.5}})
+    with pytest.raises(ValueError):
+        config.load(EXAMPLE, {"surrogate": {"keep": 0.0}})
 
 
 @pytest.mark.gpu
@@ -68,3 +76,21 @@ def test_one_generation_from_the_paper_example(tmp_path):
     assert len(lines) == 2
     final = json.loads(lines[-1])
     assert len(final["final_swarm"]) == 4 and len(final["final_swarm"][0]) == cfg.K
+
+
+@pytest.mark.gpu
+def test_surrogate_generations_from_the_paper_example(tmp_path):
+    """The same reduced example with the surrogate group: a warm-up
+    generation models all 8 particles, the next ones the predicted-best
+    quarter, and their records carry the surrogate's rank correlation."""
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    from paper_1905_12795_gb300 import config
+    cfg = config.load(EXAMPLE, {"nshots": 1, "tn": 1000.0, "pso": {"npop": 8},
+                                "surrogate": {"hidden": 64, "capacity": 256, "batch": 8}})
+    recs = config.run(cfg, str(tmp_path / "run.jsonl"), gens=3)
+    assert [r["modelled"] for r in recs] == [8, 2, 2]
+    assert [r["evaluations"] for r in recs] == [8, 10, 12]
+    assert recs[0]["surrogate_rank_corr"] is None
+    assert all(-1.0 <= r["surrogate_rank_corr"] <= 1.0 for r in recs[1:])
+    assert all(r["gbest_misfit"] <= r["best_misfit"] for r in recs)
