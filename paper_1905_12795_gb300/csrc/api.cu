@@ -1181,8 +1181,14 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 6 * I, st));
     // The forward pass runs on the on-chip cluster kernel, which streams the
     // history out beside its usual work, when the kernel selection allows it
-    // and the grid fits a cluster's shared memory (the cluster size that
-    // keeps the most SMs busy); else one tiled launch per step.
+    // and the grid fits a cluster's shared memory; else one tiled launch per
+    // step.  Its cluster size: a gradient has few instances (shots x models),
+    // so the rounds of clusters matter, not only the SMs busy: the fewest
+    // rounds x rows per CTA (a round's time follows the rows a CTA sweeps),
+    // then the most SMs busy, over C <= 12 when some such size fits (13..16
+    // measured slower at every shot count: 16 shots on the 461 x 151 grid
+    // took 28.5 ms at C = 12, 30.2 at the 15 clusters of C = 9, 31.3-32.4 at
+    // C = 13..16).
     int rC = 0, r_threads = 0, r_nc = 0, r_rows = 0;
     size_t r_smem = 0;
     // (the cluster kernels hold stencils up to radius 4: order 16 takes the
@@ -1190,8 +1196,10 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     const bool want_res = g.R <= MAX_R_FAST &&
                           (ctx->kernel_kind == EMPSO_KERNEL_AUTO || ctx->kernel_kind == EMPSO_KERNEL_RESIDENT);
     if (want_res) {
-        long long best = 0;
-        for (int C = 1; C <= 16; ++C)
+        long long best_cost = 0, best_sms = 0;
+        // C <= 12 first; 13 .. 16 only for grids that need them
+        for (int pass = 0; pass < 2 && !rC; ++pass)
+        for (int C = pass == 0 ? 1 : 13; C <= (pass == 0 ? 12 : 16); ++C)
             for (const int rows : {13, 8}) {
                 if (ctx->forced_C > 0 && C != ctx->forced_C) continue;
                 if (ctx->forced_rows > 0 && rows != ctx->forced_rows) continue;
@@ -1199,8 +1207,12 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
                 const size_t sm = resident_smem_bytes(g, C, rec_max);
                 const int threads = resident_threads(g, C, rows);
                 const int nc = (int)std::min<long long>(resident_max_clusters(g.R, C, threads, sm, rows, true), I);
-                if (nc > 0 && (long long)nc * C > best) {
-                    best = (long long)nc * C;
+                if (nc <= 0) continue;
+                const long long cost = (I + nc - 1) / nc * (long long)((g.NZ + C - 1) / C);
+                const long long sms = (long long)nc * C;
+                if (!rC || cost < best_cost || (cost == best_cost && sms > best_sms)) {
+                    best_cost = cost;
+                    best_sms = sms;
                     rC = C;
                     r_rows = rows;
                     r_threads = threads;
