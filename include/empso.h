@@ -340,10 +340,11 @@ empso_status empso_set_cluster(empso_ctx *ctx, int32_t ctas);
 
 /* Rows per thread of the on-chip kernel (EMPSO_KERNEL_RESIDENT): each thread
  * updates a run of at most `rows` consecutive rows of one 4-point column
- * group per step.  0 (default): the planner's or the autotuner's choice;
- * 8 (up to 512 threads per CTA) or 13 (up to 384 threads, more registers per
- * thread).  An engineering choice of this library (the paper has no such
- * parameter).  Errors: INVALID_ARG for any other value. */
+ * group per step.  0 (default): the planner's or the autotuner's choice
+ * (among 13, 11, 9, 8, 6); 4..8 run with up to 512 threads per CTA, 9..13
+ * with up to 384 (more registers per thread).  An engineering choice of this
+ * library (the paper has no such parameter).  Errors: INVALID_ARG for any
+ * other value. */
 empso_status empso_set_tile_rows(empso_ctx *ctx, int32_t rows);
 
 /* Co-resident groups of the last modelling launch: thread-block clusters of

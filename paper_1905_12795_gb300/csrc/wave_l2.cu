@@ -20,9 +20,9 @@
 // thread's centre is its neighbours' x-stencil, and the first rows of one run
 // of rows are the last rows of the run above, and both come from L1 instead of
 // a second L2 read (30.9 -> 21.1 B of L2 traffic per update on the grid
-// above).  The level being overwritten is read past L1.  Threads loop over work items (float4 column group x
-// run of ROWS rows), each with its z-stencil in a register window and packed
-// FP32x2 arithmetic.
+// above).  The level being overwritten is read past L1.  Each thread sweeps
+// one run of rows of a float4 column group (plus at most one single row),
+// with its z-stencil in a register window and packed FP32x2 arithmetic.
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
@@ -36,6 +36,7 @@ namespace {
 
 constexpr int L2_ROWS = 8;
 constexpr int L2_NT = 512;
+constexpr int L2_CHUNK = 8;   // rows per unrolled chunk of a run
 constexpr int L2_DEPTH = 2;
 
 __device__ __forceinline__ void set_lane(float4 &v, int l, float x)
@@ -126,8 +127,17 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
     cp_wait_all();
     float accf = 0.f;
     double acc = 0.0;
-    const int nseg = (my_rows + L2_ROWS - 1) / L2_ROWS;
-    const int items = NQ * nseg;
+    // Work split: the slab's rows in nseg runs per column group, nseg the
+    // smallest count that gives every thread an item, item i = seg NQ + q on
+    // thread i (consecutive threads on consecutive groups: coalesced rows).
+    // When that makes more items than threads, the last `left` items (the
+    // last columns of the last run) are done as single rows, one extra row per
+    // thread, so that no thread sweeps more than one run plus one row.  (A
+    // loop over 8-row items left a fraction of the threads a whole item more
+    // than the rest: 327 G updates/s on the 921 x 301 grid against 375.)
+    const int nseg = max(1, min(my_rows, (nth + NQ - 1) / NQ));
+    const int items = NQ * nseg, nmain = min(items, nth), left = items - nmain;
+    const int r0_last = (nseg - 1) * my_rows / nseg, len_last = my_rows - r0_last;
     const float4 *__restrict__ arow = reinterpret_cast<const float4 *>(in.a + (size_t)HALO * pitch + HALO);
     const int ap4 = pitch / 4;
 
@@ -143,77 +153,8 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
                     if (rec_k[r] >= 0) cp4(dring + (ir % L2_DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
             cp_commit();
         }
-        if (n < nt) {
-            const float rn = wring[n % L2_DEPTH];
-            for (int it = tid; it < items; it += nth) {
-                const int q = it % NQ, seg = it / NQ;
-                const int r0 = max(0, min(seg * L2_ROWS, my_rows - L2_ROWS));
-                const int kfirst = seg * L2_ROWS - r0, klast = my_rows - r0;
-                const float4 ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
-                const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));
-                const float2 gx23 = make_float2(2.f / (1.f + ex.z), 2.f / (1.f + ex.w));
-                const int ks = s_j0 - (z0 + r0);
-                const bool src_here = s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3 && ks + 1 >= 0 && ks < L2_ROWS;
-                float4 sb0 = make_float4(0.f, 0.f, 0.f, 0.f), sb1 = sb0;
-                if (src_here) {
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        const int I = 4 * q + l;
-                        const float bx0 = (I == s_i0 ? 1.f : 0.f), bx1 = (I == s_i0 + 1 ? 1.f : 0.f);
-                        set_lane(sb0, l, (bx0 * sw[0] + bx1 * sw[1]) * inv_cell);
-                        set_lane(sb1, l, (bx0 * sw[2] + bx1 * sw[3]) * inv_cell);
-                    }
-                }
-                float4 w[2 * R + 1];
-#pragma unroll
-                for (int m = 0; m < 2 * R; ++m) w[m] = *(cur + (r0 + m) * sp4 + 1 + q);
-#pragma unroll
-                for (int k = 0; k < L2_ROWS; ++k) {
-                    const int lr = R + r0 + k;
-                    w[2 * R] = *(cur + (lr + R) * sp4 + 1 + q);
-                    const float4 lft = *(cur + lr * sp4 + q);
-                    const float4 rgt = *(cur + lr * sp4 + 2 + q);
-                    const float4 um = __ldcg(nxt + lr * sp4 + 1 + q);
-                    const int zr = z0 + r0 + k;                   // padded row of the output
-                    const float4 av = __ldg(arow + (size_t)min(zr, NZ - 1) * ap4 + q);
-                    const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
-                    float xs[12];
-                    xline1(lft, w[R], rgt, xs);
-                    float2 lap01, lap23;
-                    lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
-                    const float4 lap_u = make_float4(lap01.x, lap01.y, lap23.x, lap23.y);   // L u^n
-                    if (src_here && (k == ks || k == ks + 1)) {
-                        const float4 sb = (k == ks) ? sb0 : sb1;
-                        lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);
-                        lap23 = __ffma2_rn(make_float2(sb.z, sb.w), make_float2(rn, rn), lap23);
-                    }
-                    // u^{n+1} = g (u^n - u^{n-1}) + u^{n-1} + (a f) lap, g = 2 f, f = 1 / (1 + t)
-                    const float ezk = zr < NZ ? __ldg(gez + zr + HALO) : 0.f;
-                    float2 g01 = gx01, g23 = gx23;
-                    if (ezk != 0.f) {
-                        g01 = make_float2(__fdividef(2.f, 1.f + (ex.x + ezk)), __fdividef(2.f, 1.f + (ex.y + ezk)));
-                        g23 = make_float2(__fdividef(2.f, 1.f + (ex.z + ezk)), __fdividef(2.f, 1.f + (ex.w + ezk)));
-                    }
-                    const float2 af01 = __fmul2_rn(make_float2(av.x, av.y), __fmul2_rn(g01, make_float2(0.5f, 0.5f)));
-                    const float2 af23 = __fmul2_rn(make_float2(av.z, av.w), __fmul2_rn(g23, make_float2(0.5f, 0.5f)));
-                    const float2 um01 = make_float2(um.x, um.y), um23 = make_float2(um.z, um.w);
-                    const float2 o01 = __ffma2_rn(g01, __fadd2_rn(c01, make_float2(-um.x, -um.y)),
-                                                  __ffma2_rn(af01, lap01, um01));
-                    const float2 o23 = __ffma2_rn(g23, __fadd2_rn(c23, make_float2(-um.z, -um.w)),
-                                                  __ffma2_rn(af23, lap23, um23));
-                    if (k >= kfirst && k < klast) {
-                        const float4 out = make_float4(o01.x, o01.y, o23.x, o23.y);
-                        nxt[lr * sp4 + 1 + q] = out;
-                        if (HIST)   // L u^n for the adjoint pass (written once: evict first)
-                            __stcs(reinterpret_cast<float4 *>(in.hist + (size_t)(n + 1) * gs.field) +
-                                       (size_t)(zr + HALO) * ap4 + HALO4 + q,
-                                   lap_u);
-                    }
-#pragma unroll
-                    for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
-                }
-            }
-        }
+        // receivers sample u^n (record n - 1) before the sweep, so that their
+        // loads overlap the other warps' work instead of delaying the barrier
         if (n >= 1) {
             const float *cf = reinterpret_cast<const float *>(cur);
             const int sp = 4 * sp4;
@@ -233,6 +174,86 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
                 acc += (double)accf;
                 accf = 0.f;
             }
+        }
+        if (n < nt) {
+            const float rn = wring[n % L2_DEPTH];
+            // rows r0 .. r0 + len - 1 of column group q, swept downwards in
+            // chunks of L2_CHUNK rows, each with the z-stencil in a register
+            // window (its first 2R rows reloaded per chunk: they were read by
+            // this thread a moment before, so they come from L1; carrying the
+            // window across chunks made the compiler spill)
+            auto sweep = [&](const int q, const int r0, const int len) {
+                const float4 ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
+                const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));
+                const float2 gx23 = make_float2(2.f / (1.f + ex.z), 2.f / (1.f + ex.w));
+                const int ks = s_j0 - (z0 + r0);                  // run row of the source's first corner row
+                const bool src_here = s_i0 >= 4 * q - 1 && s_i0 <= 4 * q + 3 && ks + 1 >= 0 && ks < len;
+                float4 sb0 = make_float4(0.f, 0.f, 0.f, 0.f), sb1 = sb0;
+                if (src_here) {
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const int I = 4 * q + l;
+                        const float bx0 = (I == s_i0 ? 1.f : 0.f), bx1 = (I == s_i0 + 1 ? 1.f : 0.f);
+                        set_lane(sb0, l, (bx0 * sw[0] + bx1 * sw[1]) * inv_cell);
+                        set_lane(sb1, l, (bx0 * sw[2] + bx1 * sw[3]) * inv_cell);
+                    }
+                }
+                for (int k0 = 0; k0 < len; k0 += L2_CHUNK) {
+                    float4 w[2 * R + 1];
+#pragma unroll
+                    for (int m = 0; m < 2 * R; ++m) w[m] = *(cur + (r0 + k0 + m) * sp4 + 1 + q);
+#pragma unroll
+                    for (int j = 0; j < L2_CHUNK; ++j) {
+                        const int k = k0 + j;
+                        if (k >= len) break;
+                        const int lr = R + r0 + k;
+                        w[2 * R] = *(cur + (lr + R) * sp4 + 1 + q);
+                        const float4 lft = *(cur + lr * sp4 + q);
+                        const float4 rgt = *(cur + lr * sp4 + 2 + q);
+                        const float4 um = __ldcg(nxt + lr * sp4 + 1 + q);
+                        const int zr = z0 + r0 + k;                   // padded row of the output
+                        const float4 av = __ldg(arow + (size_t)min(zr, NZ - 1) * ap4 + q);
+                        const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
+                        float xs[12];
+                        xline1(lft, w[R], rgt, xs);
+                        float2 lap01, lap23;
+                        lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
+                        const float4 lap_u = make_float4(lap01.x, lap01.y, lap23.x, lap23.y);   // L u^n
+                        if (src_here && (k == ks || k == ks + 1)) {
+                            const float4 sb = (k == ks) ? sb0 : sb1;
+                            lap01 = __ffma2_rn(make_float2(sb.x, sb.y), make_float2(rn, rn), lap01);
+                            lap23 = __ffma2_rn(make_float2(sb.z, sb.w), make_float2(rn, rn), lap23);
+                        }
+                        // u^{n+1} = g (u^n - u^{n-1}) + u^{n-1} + (a f) lap, g = 2 f, f = 1 / (1 + t)
+                        const float ezk = zr < NZ ? __ldg(gez + zr + HALO) : 0.f;
+                        float2 g01 = gx01, g23 = gx23;
+                        if (ezk != 0.f) {
+                            g01 = make_float2(__fdividef(2.f, 1.f + (ex.x + ezk)), __fdividef(2.f, 1.f + (ex.y + ezk)));
+                            g23 = make_float2(__fdividef(2.f, 1.f + (ex.z + ezk)), __fdividef(2.f, 1.f + (ex.w + ezk)));
+                        }
+                        const float2 af01 = __fmul2_rn(make_float2(av.x, av.y), __fmul2_rn(g01, make_float2(0.5f, 0.5f)));
+                        const float2 af23 = __fmul2_rn(make_float2(av.z, av.w), __fmul2_rn(g23, make_float2(0.5f, 0.5f)));
+                        const float2 um01 = make_float2(um.x, um.y), um23 = make_float2(um.z, um.w);
+                        const float2 o01 = __ffma2_rn(g01, __fadd2_rn(c01, make_float2(-um.x, -um.y)),
+                                                      __ffma2_rn(af01, lap01, um01));
+                        const float2 o23 = __ffma2_rn(g23, __fadd2_rn(c23, make_float2(-um.z, -um.w)),
+                                                      __ffma2_rn(af23, lap23, um23));
+                        nxt[lr * sp4 + 1 + q] = make_float4(o01.x, o01.y, o23.x, o23.y);
+                        if (HIST)   // L u^n for the adjoint pass (written once: evict first)
+                            __stcs(reinterpret_cast<float4 *>(in.hist + (size_t)(n + 1) * gs.field) +
+                                       (size_t)(zr + HALO) * ap4 + HALO4 + q,
+                                   lap_u);
+#pragma unroll
+                        for (int m = 0; m < 2 * R; ++m) w[m] = w[m + 1];
+                    }
+                }
+            };
+            if (tid < nmain) {
+                const int seg = tid / NQ, r0 = seg * my_rows / nseg;
+                sweep(tid % NQ, r0, (seg + 1) * my_rows / nseg - r0);
+            }
+            for (int e = tid; e < left * len_last; e += nth)
+                sweep(NQ - left + e / len_last, r0_last + e % len_last, 1);
         }
         cp_wait_all();
         cluster.sync();
@@ -326,8 +347,8 @@ long long l2_slot_f4(const GridDev &g, int C)
 }
 
 // a cluster of C CTAs runs grid g when no CTA is left without rows and every
-// slab holds at least one full run of rows (a work item's reads then stay
-// inside the C rows_c + 2R rows of the buffer)
+// slab holds at least R rows (a slab's window reads stay inside the
+// C rows_c + 2R rows of the buffer in any case)
 bool l2_fits(const GridDev &g, int C)
 {
     const int rows_c = (g.NZ + C - 1) / C;

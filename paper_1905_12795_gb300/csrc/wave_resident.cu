@@ -17,9 +17,11 @@
 // all.  Global memory is touched only for the model field (once per
 // instance), the observed traces and the output.
 //
-// Two shapes of the same code: RW = 8 rows per thread with up to 512 threads
-// (128 registers), and RW = 13 with up to 384 threads (168 registers, fewer
-// and longer runs); the planner and the autotuner choose per batch.
+// Two instantiations of the same code: runs of up to RW = 8 rows per thread
+// with up to 512 threads (128 registers), and up to RW = 13 with up to 384
+// threads (168 registers); the run length itself (4 .. 13: the number of runs
+// a slab is cut into, hence the threads) is a launch parameter, chosen per
+// batch by the planner and the autotuner.
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
@@ -106,10 +108,12 @@ struct SrcInfo {
 // (shared-row offset peer_off) as soon as they are computed, so the remote
 // stores complete under the rest of the sweep.
 template <int R, int RW, bool ZPAD, bool HIST>
-__device__ __forceinline__ void sweep_item(const float4 *cq, float4 *nq, const float4 *mq, const float4 *gq,
+__device__ __forceinline__ void sweep_item(const float4 *__restrict__ cq, float4 *__restrict__ nq,
+                                           const float4 *__restrict__ mq, const float4 *__restrict__ gq,
                                            int gst, int sp4, int NQ, int r0, int nrows, int D, const float *cx,
                                            const float *cz, float cres, float2 gx01, float2 gx23,
-                                           float4 *hrow, int hp4, float4 *peer, int peer_off)
+                                           float4 *__restrict__ hrow, int hp4, float4 *__restrict__ peer,
+                                           int peer_off)
 {
     const float2 m1 = splat2(-1.f);
     const int rs = D > 0 ? r0 : r0 + nrows - 1; // first slab row swept
@@ -183,7 +187,8 @@ template <int R, int RW, bool HIST>
 __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4, float4 *B4,
                                   float4 *M4, float4 *G4, float *wring, float *dring, float4 *rec_w,
                                   int *rec_k, SrcInfo &src, int C, int crank, int base,
-                                  cg::cluster_group &cluster, double *cred, double *wred, double *partial)
+                                  cg::cluster_group &cluster, double *cred, double *wred, double *partial,
+                                  int run)
 {
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
@@ -247,13 +252,13 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     }
 
     // work item: column group q and rows [r0, r1) of the slab, the slab's rows
-    // split into nseg runs of at most RW rows each (lengths differ by one at
-    // most), item i = seg NQ + q on thread i.  When the launch has fewer
+    // split into nseg runs of at most `run` (<= RW) rows each (lengths differ
+    // by one at most), item i = seg NQ + q on thread i.  When the launch has fewer
     // threads than items (a multiple of four warps, so that the SM's four
     // schedulers carry equal work), the last `left` items (the last columns
     // of the last run) are split into single rows instead, one extra row on
     // each of the first left * len_last threads.
-    const int nseg = (my_rows + RW - 1) / RW;
+    const int nseg = (my_rows + run - 1) / run;
     const int items = NQ * nseg;
     const int nmain = min(items, nth);
     const int left = items - nmain;
@@ -404,6 +409,32 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
                         cp_async4(dring + (ir % DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
             cp_async_commit();
         }
+        // receivers sample u^n (record n - 1) first: u^n is complete since the
+        // last barrier and read-only in this step, and the sampling's chain of
+        // dependent shared-memory loads then overlaps the other warps' sweeps
+        // (at the end of the step it held back the barrier: 461 receivers in
+        // one CTA cost 10 % of the step)
+        if (has_rec && n >= 1) {
+            const float *cf = reinterpret_cast<const float *>(cur);
+            const int sp = 4 * sp4;
+            for (int r = tid; r < nrec; r += nth) {
+                const int k0 = rec_k[r];
+                if (k0 < 0) continue;
+                const float4 w4 = rec_w[r];
+                const float d = w4.x * cf[k0] + w4.y * cf[k0 + 1] + w4.z * cf[k0 + sp] +
+                                w4.w * cf[k0 + sp + 1];
+                if (in.traces) in.traces[(size_t)(n - 1) * nrec + r] = d;
+                if (dobs) {
+                    const float e = d - dring[((n - 1) % DEPTH) * nrec + r];
+                    accf = fmaf(e, e, accf);
+                }
+            }
+            if ((n & 31) == 0) {        // keep the FP32 partial short, carry in FP64
+                acc += (double)accf;
+                accf = 0.f;
+            }
+        }
+
         if (n < nt && active) {
             const float4 *cq = cur + 1 + q;           // group q of shared row 0
             float4 *nq = nxt + 1 + q;
@@ -444,28 +475,6 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
                                               gxe23, hrow_e, hp4, peer, poff);
             if (sbit_e) add_source(qe, sbit_e, nq, mq, pq, xq);
         }
-        // receivers sample u^n (record n - 1)
-        if (has_rec && n >= 1) {
-            const float *cf = reinterpret_cast<const float *>(cur);
-            const int sp = 4 * sp4;
-            for (int r = tid; r < nrec; r += nth) {
-                const int k0 = rec_k[r];
-                if (k0 < 0) continue;
-                const float4 w4 = rec_w[r];
-                const float d = w4.x * cf[k0] + w4.y * cf[k0 + 1] + w4.z * cf[k0 + sp] +
-                                w4.w * cf[k0 + sp + 1];
-                if (in.traces) in.traces[(size_t)(n - 1) * nrec + r] = d;
-                if (dobs) {
-                    const float e = d - dring[((n - 1) % DEPTH) * nrec + r];
-                    accf = fmaf(e, e, accf);
-                }
-            }
-            if ((n & 31) == 0) {        // keep the FP32 partial short, carry in FP64
-                acc += (double)accf;
-                accf = 0.f;
-            }
-        }
-
         // this step's copies have landed; the barrier publishes them
         cp_async_wait<0>();
         cluster.sync();
@@ -513,7 +522,7 @@ template <int R, int NT, int RW, bool PAIRS, bool HIST>
 __global__ void __launch_bounds__(NT) __maxnreg__(RegCap<NT>::v)
 wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__ insts,
                      const int4 *__restrict__ units, int n_units, int *counter, int ring_pitch,
-                     double *partial)
+                     double *partial, int run)
 {
     extern __shared__ float4 smem4[];
     __shared__ int s_q;
@@ -550,7 +559,7 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
         int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
         resident_instance<R, RW, HIST>(sg, in, A4, B4, M4, G4, wring, dring, rec_w, rec_k, src, Ce, ce,
-                                       sub * Ce, cluster, cred, wred, partial);
+                                       sub * Ce, cluster, cred, wred, partial, run);
     }
 }
 
@@ -558,13 +567,15 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
 constexpr int RW_A = 8, NT_A = 512;
 constexpr int RW_B = 13, NT_B = 384;
 
-int shape_threads(int rows) { return rows == RW_B ? NT_B : NT_A; }
+// the shape that runs runs of `rows` rows: up to RW_A rows on the 512-thread
+// instantiation, more on the 384-thread one
+int shape_threads(int rows) { return rows > RW_A ? NT_B : NT_A; }
 
 }  // namespace
 
 int resident_max_threads(int rows) { return shape_threads(rows); }
 int resident_default_rows() { return RW_A; }
-bool resident_rows_supported(int rows) { return rows == RW_A || rows == RW_B; }
+bool resident_rows_supported(int rows) { return rows >= 4 && rows <= RW_B; }
 
 // Threads of the work items of grid g on C CTAs with runs of at most `rows`
 // rows: one per item, or, when that is not a multiple of four warps, the
@@ -610,7 +621,7 @@ bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit, i
 
 namespace {
 
-using ResidentFn = void (*)(const GridDev *, const Inst *, const int4 *, int, int *, int, double *);
+using ResidentFn = void (*)(const GridDev *, const Inst *, const int4 *, int, int *, int, double *, int);
 
 template <int NT, int RW>
 ResidentFn resident_fn_shape(int R, bool pairs, bool hist)
@@ -633,8 +644,8 @@ ResidentFn resident_fn_shape(int R, bool pairs, bool hist)
 
 ResidentFn resident_fn(int R, bool pairs, bool hist, int rows)
 {
-    return rows == RW_B ? resident_fn_shape<NT_B, RW_B>(R, pairs, hist)
-                        : resident_fn_shape<NT_A, RW_A>(R, pairs, hist);
+    return rows > RW_A ? resident_fn_shape<NT_B, RW_B>(R, pairs, hist)
+                       : resident_fn_shape<NT_A, RW_A>(R, pairs, hist);
 }
 }  // namespace
 
@@ -694,7 +705,7 @@ cudaError_t launch_wave_resident(int R, const GridDev *grids_dev, const Inst *in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, resident_fn(R, pairs && !hist, hist, rows), grids_dev, insts, units,
-                              n_units, counter, ring_pitch, partial);
+                              n_units, counter, ring_pitch, partial, rows);
 }
 
 }  // namespace empso

@@ -105,7 +105,7 @@ def test_full_size_traces_elementwise(B, kind):
     assert ctx.last_launch()[0] == kind
     if kind == 2:
         # the planner's on-chip cluster for this batch: 9 or more CTAs hold this grid
-        assert ctx.last_launch()[1] >= 9 and ctx.last_tile_rows() in (8, 13)
+        assert ctx.last_launch()[1] >= 9 and 4 <= ctx.last_tile_rows() <= 13
     got = out.view(P, S, nt, nrec)
     errs = {}
     for (m, s) in _SAMPLE:
@@ -115,7 +115,7 @@ def test_full_size_traces_elementwise(B, kind):
     ctx.close()
 
 
-@pytest.mark.parametrize("C,rows", [(10, 8), (10, 13), (9, 13)])
+@pytest.mark.parametrize("C,rows", [(10, 8), (10, 13), (9, 13), (9, 9), (9, 11), (12, 7)])
 def test_full_size_traces_on_forced_cluster_shapes(B, C, rows):
     """The same comparison with the on-chip kernel forced onto clusters of
     C CTAs and runs of at most `rows` rows per thread (the shapes the

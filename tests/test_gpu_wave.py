@@ -90,15 +90,15 @@ def test_traces_match_oracle(B, kind, order, nx, nz, pad, h):
     ctx.close()
 
 
-@pytest.mark.parametrize("rows", [8, 13])
+@pytest.mark.parametrize("rows", [4, 6, 8, 9, 11, 13])
 @pytest.mark.parametrize("order,nx,nz,pad,h,C", [
     (8, 70, 61, 9, 15.0, 3),     # 79 rows on 3 CTAs: runs of unequal length
     (4, 61, 45, 10, 12.5, 5),    # 13 rows per CTA, a short last CTA
     (2, 37, 29, 7, 10.0, 2),
 ])
 def test_on_chip_row_shapes_match_oracle(B, rows, order, nx, nz, pad, h, C):
-    """Both rows-per-thread shapes of the on-chip kernel against the oracle,
-    with the source and receivers off the grid nodes."""
+    """Run lengths of both instantiations of the on-chip kernel against the
+    oracle, with the source and receivers off the grid nodes."""
     vmax = 3200.0
     og = oracle.Grid(nx, nz, h, h, pad, order, 0.3, 12.0, vmax)
     vel = synth.layered_faulted_model(nx, nz, h, h, seed=order + nx, vmin=1500.0, vmax=vmax)
@@ -115,8 +115,9 @@ def test_on_chip_row_shapes_match_oracle(B, rows, order, nx, nz, pad, h, C):
     got = out.cpu().numpy().reshape(3, og.nt, nrec)
     for s in range(3):
         assert _rel_l2(got[s], ref[s]) < TRACE_TOL, (s, _rel_l2(got[s], ref[s]))
-    with pytest.raises(B.EmpsoError):
-        ctx.set_tile_rows(7)
+    for bad in (3, 14):
+        with pytest.raises(B.EmpsoError):
+            ctx.set_tile_rows(bad)
     ctx.close()
 
 
