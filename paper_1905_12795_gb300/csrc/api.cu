@@ -20,9 +20,9 @@ using namespace empso;
 
 // run lengths (rows per thread) of the on-chip kernel that the planner and
 // the autotuner consider, in the planner's order of preference on a tie
-// (11 was fastest on the 461 x 151 grid at 9 CTAs: 527.7 G updates/s, 13:
-// 524.1, 9: 527.6, 8: 520.5)
-constexpr int RESIDENT_RUNS[] = {11, 13, 9, 8, 6};
+// (the 461 x 151 grid on 9-CTA clusters: 13 rows 568.1 G updates/s, 11 and
+// 9 rows 551.1)
+constexpr int RESIDENT_RUNS[] = {13, 11, 9, 8, 6};
 
 // the run lengths to consider: the forced one, else RESIDENT_RUNS
 std::vector<int> resident_runs(int forced)

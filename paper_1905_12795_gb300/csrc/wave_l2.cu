@@ -113,14 +113,18 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
     const float inv_cell = 1.f / (gs.hx * gs.hz);
     const int nrec = in.nrec;
     const float *__restrict__ dobs = in.dobs;
-    for (int r = tid; r < nrec; r += nth) {
+    // receivers: every CTA samples an equal share [rec_b, rec_e) of them,
+    // wherever their rows lie (the time levels are in global memory), so that
+    // no CTA holds back the barrier with all of a shot's receivers; rec_k is
+    // the corner's float index in a time-level buffer
+    const int rec_b = crank * nrec / C, rec_e = (crank + 1) * nrec / C;
+    for (int r = rec_b + tid; r < rec_e; r += nth) {
         const float2 pr = in.rec[r];
         int i0, j0;
         float w4[4];
         bilinear_corner(pr.x, pr.y, gs, i0, j0, w4);
-        const bool mine = j0 >= z0 && j0 < z0 + my_rows;
-        rec_k[r] = mine ? (j0 - z0 + R) * (4 * sp4) + 4 + i0 : -1;
-        rec_w[r] = make_float4(w4[0], w4[1], w4[2], w4[3]);
+        rec_k[r - rec_b] = (j0 + R) * (4 * sp4) + 4 + i0;
+        rec_w[r - rec_b] = make_float4(w4[0], w4[1], w4[2], w4[3]);
     }
     if (tid == 0 && nt > 0) cp4(wring, gwav);
     cp_commit();
@@ -149,19 +153,18 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
             const int iw = n + 1, ir = n;
             if (tid == 0 && iw < nt) cp4(wring + iw % L2_DEPTH, gwav + iw);
             if (dobs && ir < nt)
-                for (int r = tid; r < nrec; r += nth)
-                    if (rec_k[r] >= 0) cp4(dring + (ir % L2_DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
+                for (int r = rec_b + tid; r < rec_e; r += nth)
+                    cp4(dring + (ir % L2_DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
             cp_commit();
         }
         // receivers sample u^n (record n - 1) before the sweep, so that their
         // loads overlap the other warps' work instead of delaying the barrier
         if (n >= 1) {
-            const float *cf = reinterpret_cast<const float *>(cur);
+            const float *cf = reinterpret_cast<const float *>(cur - (long long)z0 * sp4);   // the level's buffer
             const int sp = 4 * sp4;
-            for (int r = tid; r < nrec; r += nth) {
-                const int k0 = rec_k[r];
-                if (k0 < 0) continue;
-                const float4 w4 = rec_w[r];
+            for (int r = rec_b + tid; r < rec_e; r += nth) {
+                const int k0 = rec_k[r - rec_b];
+                const float4 w4 = rec_w[r - rec_b];
                 const float d = w4.x * __ldcg(cf + k0) + w4.y * __ldcg(cf + k0 + 1) +
                                 w4.z * __ldcg(cf + k0 + sp) + w4.w * __ldcg(cf + k0 + sp + 1);
                 if (in.traces) in.traces[(size_t)(n - 1) * nrec + r] = d;

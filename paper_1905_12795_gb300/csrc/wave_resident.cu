@@ -295,24 +295,26 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     }
     const float cres = gs.cres;
 
-    // receivers: bilinear corners and weights of every receiver, computed once
-    // per instance; rec_k = float index of the lower-left corner in this CTA's
-    // slab, or -1 when another CTA holds the receiver's lower corner row
+    // receivers: every CTA samples an equal share of them, receivers
+    // [rec_b, rec_e), whichever CTA holds their rows (reading that CTA's u^n through
+    // distributed shared memory): one CTA holding all of a shot's receivers
+    // would hold back every barrier (461 receivers in one CTA cost 7-10 % of
+    // the step).  Per receiver of the share, computed once per instance: the
+    // bilinear weights, and the corner's float index in its holder's slab
+    // with the holder's rank in the top 8 bits.
     const int nrec = in.nrec;
     const float *__restrict__ dobs = in.dobs;
-    int owns = 0;
-    for (int r = tid; r < nrec; r += nth) {
+    const int rec_b = crank * nrec / C, rec_e = (crank + 1) * nrec / C;
+    for (int r = rec_b + tid; r < rec_e; r += nth) {
         const float2 pr = in.rec[r];
         int i0, j0;
         float w4[4];
         corners(pr.x, pr.y, gs, i0, j0, w4);
-        const bool mine = j0 >= z0 && j0 < z0 + my_rows;
-        owns |= mine;
-        rec_k[r] = mine ? (j0 - z0 + R) * (4 * sp4) + 4 + i0 : -1;
-        rec_w[r] = make_float4(w4[0], w4[1], w4[2], w4[3]);
+        const int holder = min(j0 / rows_c, C - 1);
+        rec_k[r - rec_b] = (holder << 24) | ((j0 - holder * rows_c + R) * (4 * sp4) + 4 + i0);
+        rec_w[r - rec_b] = make_float4(w4[0], w4[1], w4[2], w4[3]);
     }
-    // CTAs that hold no receiver skip the per-step receiver loops
-    const bool has_rec = __syncthreads_or(owns) != 0;
+    const bool has_rec = rec_e > rec_b;
     // staging prologue: the wavelet sample of step 0
     if (tid == 0 && nt > 0) cp_async4(wring, gwav);
     cp_async_commit();
@@ -404,9 +406,8 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
             const int iw = n + 1, ir = n;
             if (tid == 0 && iw < nt) cp_async4(wring + iw % DEPTH, gwav + iw);
             if (has_rec && dobs && ir < nt)
-                for (int r = tid; r < nrec; r += nth)
-                    if (rec_k[r] >= 0)
-                        cp_async4(dring + (ir % DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
+                for (int r = rec_b + tid; r < rec_e; r += nth)
+                    cp_async4(dring + (ir % DEPTH) * nrec + r, dobs + (size_t)ir * nrec + r);
             cp_async_commit();
         }
         // receivers sample u^n (record n - 1) first: u^n is complete since the
@@ -417,12 +418,11 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
         if (has_rec && n >= 1) {
             const float *cf = reinterpret_cast<const float *>(cur);
             const int sp = 4 * sp4;
-            for (int r = tid; r < nrec; r += nth) {
-                const int k0 = rec_k[r];
-                if (k0 < 0) continue;
-                const float4 w4 = rec_w[r];
-                const float d = w4.x * cf[k0] + w4.y * cf[k0 + 1] + w4.z * cf[k0 + sp] +
-                                w4.w * cf[k0 + sp + 1];
+            for (int r = rec_b + tid; r < rec_e; r += nth) {
+                const int kk = rec_k[r - rec_b], holder = kk >> 24, k0 = kk & 0xffffff;
+                const float *hf = holder == crank ? cf : cluster.map_shared_rank(cf, base + holder);
+                const float4 w4 = rec_w[r - rec_b];
+                const float d = w4.x * hf[k0] + w4.y * hf[k0 + 1] + w4.z * hf[k0 + sp] + w4.w * hf[k0 + sp + 1];
                 if (in.traces) in.traces[(size_t)(n - 1) * nrec + r] = d;
                 if (dobs) {
                     const float e = d - dring[((n - 1) % DEPTH) * nrec + r];
