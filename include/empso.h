@@ -504,7 +504,7 @@ empso_status empso_gradient(empso_ctx *ctx, const float *vel, int32_t M,
                             double *misfit, float *grad, void *stream);
 
 /* Chains of the gradient's backward pass: its (model, shot) instances are
- * independent, so they run as n chains (1..4) of consecutive instances on
+ * independent, so they run as n chains (1..8) of consecutive instances on
  * separate streams inside the captured graph, one chain's memory waits and
  * launch gaps overlapping another's work; 0 (default): 4 chains from 16
  * instances up, else 1 (measured on the 461 x 151 grid: 16 shots 35.6 ->
@@ -512,7 +512,7 @@ empso_status empso_gradient(empso_ctx *ctx, const float *vel, int32_t M,
  * n (each instance's arithmetic is the same).  A cluster size set by
  * empso_set_cluster also applies to the gradient's on-chip forward pass.
  * An engineering choice of this library (the paper has no such parameter).
- * Errors: INVALID_ARG outside 0..4. */
+ * Errors: INVALID_ARG outside 0..8. */
 empso_status empso_set_gradient_chains(empso_ctx *ctx, int32_t chains);
 
 /* Steepest-descent FWI of one model vel device [nz][nx] (in place), the

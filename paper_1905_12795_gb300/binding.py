@@ -306,7 +306,7 @@ class Context:
         self._check(self._L.empso_set_tile_rows(self._h, int(rows)))
 
     def set_gradient_chains(self, chains: int):
-        """Independent chains of instances in the gradient's backward pass (1..4; 0 automatic)."""
+        """Independent chains of instances in the gradient's backward pass (1..8; 0 automatic)."""
         self._check(self._L.empso_set_gradient_chains(self._h, int(chains)))
 
     def last_clusters(self) -> int:

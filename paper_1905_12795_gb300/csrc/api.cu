@@ -8,9 +8,11 @@
 #include <fstream>
 #include <random>
 #include <map>
+#include <mutex>
 #include <new>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <iterator>
 #include <vector>
 
@@ -23,6 +25,39 @@ using namespace empso;
 // (the 461 x 151 grid on 9-CTA clusters: 13 rows 568.1 G updates/s, 11 and
 // 9 rows 551.1)
 constexpr int RESIDENT_RUNS[] = {13, 11, 9, 8, 6};
+
+// Occupancy answers depend only on the device and the launch shape, and the
+// planner asks for every cluster size and run length of every batch (each
+// surrogate generation plans a batch): memoised process-wide.
+int memo_resident_clusters(int R, int C, int threads, size_t smem, int rows, bool hist = false)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, size_t, int, bool>, int> memo;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, R, C, threads, smem, rows, hist);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    const int n = resident_max_clusters(R, C, threads, smem, rows, hist);
+    memo[key] = n;
+    return n;
+}
+
+int memo_l2_clusters(int R, int C, int threads, size_t smem, bool hist = false)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, size_t, bool>, int> memo;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, R, C, threads, smem, hist);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    const int n = l2_max_clusters(R, C, threads, smem, hist);
+    if (n >= 0) memo[key] = n;       // errors (negative) are not kept
+    return n;
+}
 
 // the run lengths to consider: the forced one, else RESIDENT_RUNS
 std::vector<int> resident_runs(int forced)
@@ -105,7 +140,7 @@ struct empso_ctx {
     // the gradient's backward pass as independent chains of instances, each
     // on its own captured stream, so that one chain's memory waits and launch
     // gaps overlap another's work
-    static constexpr int MAX_CHAINS = 4;
+    static constexpr int MAX_CHAINS = 8;
     int grad_chains = 0;            // 0: four chains from 16 instances up, else one
     cudaStream_t chain_stream[MAX_CHAINS - 1] = {};
     cudaEvent_t chain_fork = nullptr, chain_join[MAX_CHAINS - 1] = {};
@@ -514,7 +549,7 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
                                 resident_smem_bytes(g, C / 2, ring_pitch) <= sm &&
                                 resident_threads(g, C / 2, rows) <= threads;
                 }
-            const int nc = (int)std::min<long long>(resident_max_clusters(resR, C, threads, sm, rows), p.n_inst);
+            const int nc = (int)std::min<long long>(memo_resident_clusters(resR, C, threads, sm, rows), p.n_inst);
             const long long sms = (long long)nc * C;
             if (nc > 0 && sms > best_sms) {
                 best_sms = sms;
@@ -559,7 +594,7 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
             const int threads = (int)std::min<long long>(l2_max_threads(), (items + 31) / 32 * 32);
             CK(ctx, l2_configure(resR, sm, C));
             const long long by_l2 = std::max<long long>(1, L2_BUDGET_BYTES / std::max<long long>(inst_bytes, 1));
-            const int occ = l2_max_clusters(resR, C, threads, sm);
+            const int occ = memo_l2_clusters(resR, C, threads, sm);
             if (occ < 0)
                 return fail(ctx, EMPSO_CUDA_ERROR,
                             std::string("L2 cluster kernel occupancy (C = ") + std::to_string(C) +
@@ -1218,7 +1253,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
                 if (!resident_fits(g, C, rec_max, ctx->smem_optin, rows)) continue;
                 const size_t sm = resident_smem_bytes(g, C, rec_max);
                 const int threads = resident_threads(g, C, rows);
-                const int nc = (int)std::min<long long>(resident_max_clusters(g.R, C, threads, sm, rows, true), I);
+                const int nc = (int)std::min<long long>(memo_resident_clusters(g.R, C, threads, sm, rows, true), I);
                 if (nc <= 0) continue;
                 const long long cost = (I + nc - 1) / nc * (long long)((g.NZ + C - 1) / C);
                 const long long sms = (long long)nc * C;
@@ -1253,7 +1288,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             const long long items = std::max<long long>(32, (long long)g.NQ * ((rows_c + 7) / 8));
             const int threads = (int)std::min<long long>(l2_max_threads(), (items + 31) / 32 * 32);
             CK(ctx, l2_configure(g.R, sm, C));
-            const int occ = l2_max_clusters(g.R, C, threads, sm, true);
+            const int occ = memo_l2_clusters(g.R, C, threads, sm, true);
             if (occ <= 0) continue;
             const long long by_l2 = std::max<long long>(1, L2_BUDGET_BYTES / inst_bytes);
             const int nc = (int)std::min<long long>(std::min<long long>(occ, I), by_l2);
@@ -1905,7 +1940,7 @@ empso_status empso_set_gradient_chains(empso_ctx *ctx, int32_t chains)
     if (!ctx) return EMPSO_INVALID_ARG;
     ctx->err.clear();
     if (chains < 0 || chains > empso_ctx::MAX_CHAINS)
-        return fail(ctx, EMPSO_INVALID_ARG, "gradient chains must be 0..4");
+        return fail(ctx, EMPSO_INVALID_ARG, "gradient chains must be 0..8");
     ctx->grad_chains = chains;
     return EMPSO_OK;
 }

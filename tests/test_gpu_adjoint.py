@@ -186,8 +186,9 @@ def test_gradient_batch_of_models_equals_single_calls(B):
 
 
 def test_gradient_chains_give_identical_results(B):
-    """The backward pass split into 1..4 concurrent chains of instances (5
-    instances: uneven chains) computes every instance the same way."""
+    """The backward pass split into 1..8 concurrent chains of instances (5
+    instances: uneven chains, and more chains than instances) computes every
+    instance the same way."""
     nx, nz, h = 37, 29, 10.0
     grid = B.make_grid(nx, nz, h, h, 6, 8, 0.2, 15.0, 1500.0, 3000.0)
     rec = synth.receiver_line(nx, h, 20.0)
@@ -198,7 +199,7 @@ def test_gradient_chains_give_identical_results(B):
     dobs = torch.randn(5 * nt * nx, device="cuda") * 1e-3
     v = _dev(synth.layered_faulted_model(nx, nz, h, h, seed=4, vmin=1500.0, vmax=2800.0)[None])
     out = []
-    for chains in (1, 2, 3, 4):
+    for chains in (1, 2, 3, 4, 8):
         ctx.set_gradient_chains(chains)
         g = torch.zeros(1, nz, nx, device="cuda")
         m = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -207,7 +208,7 @@ def test_gradient_chains_give_identical_results(B):
     for g, m in out[1:]:
         assert torch.equal(g, out[0][0]) and m == out[0][1]
     with pytest.raises(B.EmpsoError):
-        ctx.set_gradient_chains(5)
+        ctx.set_gradient_chains(9)
     ctx.close()
 
 
