@@ -391,6 +391,7 @@ def run_ours(a):
         subs["uneven"] = _uneven_result("uneven-P256-S16x2", steps=2, warmup=1, tune=False)
         subs["hires"] = _hires_result("hires-921x301-P512-S64", P=2, steps=2, warmup=1, tune_kind=3,
                                       prescreen=False)
+        subs["gradient"] = _gradient_result(16, reps=5)
 
     if rank == 0:
         line = {
@@ -1068,6 +1069,44 @@ def run_case(a):
               f"{ctx.last_kernel_name()}",
               flush=True)
     ctx.close()
+
+
+def _gradient_result(S, reps):
+    """The local FWI's adjoint gradient of S shots on the plain workload's
+    grid (the layered/faulted model against observed data of the model +5 %),
+    after one untimed call (workspace and graph): median device time, and the
+    rate at ADJ_BYTES_PER_UPDATE per point-step against the HBM peak."""
+    import torch
+    from paper_1905_12795_gb300 import binding as B
+    wl, gs, _, _, rec, true = _setup("empso-461x151-P32-S16")
+    shots = synth.shot_line(S, (gs.nx - 1) * gs.hx, wl.src_z)
+    grid = B.make_grid(gs.nx, gs.nz, gs.hx, gs.hz, gs.pad, gs.order, gs.T, gs.f0, gs.vmin, gs.vmax)
+    ctx = B.Context([grid], rec)
+    _, nt = ctx.grid_info(0)
+    sh = B.make_shots(shots, [0] * S, [len(rec)] * S)
+    v = torch.tensor(true, dtype=torch.float32, device="cuda")[None].contiguous()
+    dobs = torch.zeros(S * nt * len(rec), device="cuda")
+    ctx.forward_traces(v * 1.05, sh, dobs)
+    g = torch.zeros_like(v)
+    ctx.gradient(v, sh, dobs, g)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.gradient(v, sh, dobs, g)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ctx.close()
+    t = float(np.median(ms))
+    upd = S * _updates_per_instance(gs, nt)
+    peak, peak_kind = _peaks()
+    achieved = ADJ_BYTES_PER_UPDATE * upd / (t / 1e3) / 1e9
+    return {"workload": f"gradient-{gs.nx}x{gs.nz}-S{S}", "shots": S, "nt": nt, "ms": t,
+            "point_steps": upd,
+            "roofline": {"kernel": "adjoint path (on-chip forward with history, adj_step2_kernel)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "bytes_per_point_step": ADJ_BYTES_PER_UPDATE}}
 
 
 def run_gradient_case(a):

@@ -149,10 +149,9 @@ __device__ __forceinline__ void stage_tile_product(float4 *S, const float4 *__re
 }
 
 // the staged x-line of the group at tile row sr, column sc (XG groups each side)
-template <int R>
+template <int R, int W = Tile<R>::W>
 __device__ __forceinline__ void tile_xline(const float4 *S, int sr, int sc, float *xs)
 {
-    constexpr int W = Tile<R>::W;
     if (Tile<R>::XG == 1)
         xline1(S[sr * W + sc - 1], S[sr * W + sc], S[sr * W + sc + 1], xs);
     else
@@ -180,12 +179,12 @@ __device__ __forceinline__ float4 lap4_tile(const float4 *S, int sr, int sc, con
 // The same operator summed as written (centre weight c_0, pair sums): the
 // adjoint step's form, where its FP32 rounding only enters the gradient and
 // the differences would cost the step registers it does not have
-template <int R>
+template <int R, int W = Tile<R>::W>
 __device__ __forceinline__ float4 lap4_tile_sum(const float4 *S, int sr, int sc, const GridDev &g)
 {
-    constexpr int XG = Tile<R>::XG, O = 4 * XG, W = Tile<R>::W;
+    constexpr int XG = Tile<R>::XG, O = 4 * XG;
     float s[4 * (2 * XG + 1)];
-    tile_xline<R>(S, sr, sc, s);
+    tile_xline<R, W>(S, sr, sc, s);
     float o[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) o[i] = g.cxm[0] * s[O + i];
@@ -266,12 +265,13 @@ __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const 
     }
 }
 
-// Scatter of the receiver term J^kk = w R^T e_{kk-1} into J slot kk % 2 (zero
-// before; the adjoint step kk clears it again): corner c of every receiver in
-// pass c; receivers sharing a cell meet in an atomic add.  Run by one block.
+// Scatter of the receiver term J^kk = w R^T e_{kk-1} into J slot kk % 4 (zero
+// before; the one-step kernel clears it again after reading, the two-step
+// kernel's scatter zeroes it first): corner c of every receiver in pass c;
+// receivers sharing a cell meet in an atomic add.  Run by one block.
 __device__ __forceinline__ void scatter_receiver_term(const GridDev &g, const AdjInst &in, int kk)
 {
-    float *J = in.J + (long long)(kk % 2) * g.field;
+    float *J = in.J + (long long)(kk % 4) * g.field;
     for (int c = 0; c < 4; ++c) {
         for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
             const float2 p = in.rec[r];
@@ -287,6 +287,14 @@ __device__ __forceinline__ void scatter_receiver_term(const GridDev &g, const Ad
 __global__ void adj_scatter_kernel(GridDev g, const AdjInst *__restrict__ insts, int kk)
 {
     scatter_receiver_term(g, insts[blockIdx.x], kk);
+}
+
+// the receiver terms of the first two adjoint steps kk and kk - 1 (the first
+// two-step launch's)
+__global__ void adj_scatter2_kernel(GridDev g, const AdjInst *__restrict__ insts, int kk)
+{
+    scatter_receiver_term(g, insts[blockIdx.x], kk);
+    if (kk >= 2) scatter_receiver_term(g, insts[blockIdx.x], kk - 1);
 }
 
 // One adjoint step k, per point:
@@ -311,10 +319,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
     const int t = blockIdx.x - 1, ntx = tiles_x(g);
     const int q0 = (t % ntx) * TW, J0 = (t / ntx) * TT;
     const int p4 = g.pitch / 4;
-    float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 3) * g.field);
-    const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 3) * g.field);
-    const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 3) * g.field);
-    float4 *J4 = reinterpret_cast<float4 *>(in.J + (long long)(k % 2) * g.field);
+    float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 4) * g.field);
+    const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 4) * g.field);
+    const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 4) * g.field);
+    float4 *J4 = reinterpret_cast<float4 *>(in.J + (long long)(k % 4) * g.field);
     const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(HLAP ? k : k - 1) * g.field);
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
     float4 *G4 = reinterpret_cast<float4 *>(in.G);
@@ -355,6 +363,145 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
             go[i] = fmaf(m / (1.f + t), li, lane_of(gg, i));
         }
         mk[k4] = make_float4(mo[0], mo[1], mo[2], mo[3]);
+        G4[k4] = make_float4(go[0], go[1], go[2], go[3]);
+    }
+}
+
+// Two adjoint steps per launch, k and k - 1, for the pointwise history (the
+// cluster kernels' forward pass).  The block's tile T (rows J0 .. J0 + T2 - 1,
+// groups q0 .. q0 + TW - 1) needs mu^k on T and on one stencil halo around it
+// (region E) for the second step's L(f a mu^k), and mu^k on E needs
+// f a mu^{k+1} on two halos (region E2).  So the block stages
+// Q1 = f a mu^{k+1} on E2 (keeping mu^{k+1} on E), computes mu^k on E (the
+// halo part again where the neighbouring tiles compute it too, in the same
+// operation order, so with the same result), forms Q0 = f a mu^k on E in
+// shared memory and computes mu^{k-1} on T.  The gradient takes both steps'
+// terms on T, in the one-step order, with one read and one write of G.  mu
+// lives in four rolling slots (k mod 4): a launch reads mu^{k+1}, mu^{k+2} and
+// writes mu^k, mu^{k-1}, so a neighbour's halo reads never meet a slot being
+// written.  J^k and J^{k-1} are only read here (a neighbour tile reads a
+// cell's J in its halo); block 0 zeroes the next launch's two J slots on the
+// receiver rows and scatters J^{k-2}, J^{k-3} into them.
+constexpr int T2 = 32;            // rows of a two-step tile
+constexpr int T2_THREADS = 256;
+
+__device__ __forceinline__ void zero_receiver_rows(const GridDev &g, const AdjInst &in, int kk)
+{
+    float *J = in.J + (long long)(kk % 4) * g.field;
+    const long long r0 = (long long)(max(in.jr0, -HALO) + HALO) * g.pitch;
+    const long long n = (long long)(min(in.jr1, g.NZ + HALO - 1) - max(in.jr0, -HALO) + 1) * g.pitch;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) J[r0 + e] = 0.f;
+    __syncthreads();
+}
+
+template <int R>
+__global__ void __launch_bounds__(T2_THREADS, 4) adj_step2_kernel(GridDev g, const AdjInst *__restrict__ insts,
+                                                                  int k)
+{
+    constexpr int XG = Tile<R>::XG;
+    constexpr int W1 = TW + 4 * XG, H1 = T2 + 4 * R;     // region E2
+    constexpr int W0 = TW + 2 * XG, H0 = T2 + 2 * R;     // region E
+    __shared__ float4 S1[H1 * W1], S0[H0 * W0], M1[H0 * W0], MK[T2 * TW];
+    const AdjInst in = insts[blockIdx.y];
+    if (blockIdx.x == 0) {
+        for (int kk = k - 2; kk >= max(1, k - 3); --kk) {
+            zero_receiver_rows(g, in, kk);
+            scatter_receiver_term(g, in, kk);
+        }
+        return;
+    }
+    const int t = blockIdx.x - 1, ntx = tiles_x(g);
+    const int q0 = (t % ntx) * TW, J0 = (t / ntx) * T2;
+    const int p4 = g.pitch / 4;
+    float4 *mu0 = reinterpret_cast<float4 *>(in.mu + (long long)(k % 4) * g.field);          // mu^k
+    float4 *mu_1 = reinterpret_cast<float4 *>(in.mu + (long long)((k - 1) % 4) * g.field);   // mu^{k-1}
+    const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 4) * g.field);
+    const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 4) * g.field);
+    const float4 *J0f = reinterpret_cast<const float4 *>(in.J + (long long)(k % 4) * g.field);
+    const float4 *J1f = reinterpret_cast<const float4 *>(in.J + (long long)((k - 1) % 4) * g.field);
+    const float4 *P0 = reinterpret_cast<const float4 *>(in.H + (long long)k * g.field);          // L u^{k-1}
+    const float4 *P1 = reinterpret_cast<const float4 *>(in.H + (long long)(k - 1) * g.field);    // L u^{k-2}
+    const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
+    float4 *G4 = reinterpret_cast<float4 *>(in.G);
+    // Q1 = f a mu^{k+1} on E2 (zero outside the buffer), mu^{k+1} kept on E
+    for (int c = threadIdx.x; c < H1 * W1; c += T2_THREADS) {
+        const int tr = c / W1, tc = c % W1;
+        const int row = J0 - 2 * R + tr + HALO, grp = q0 - 2 * XG + HALO4 + tc;   // buffer coordinates
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f), y = v;
+        if (row >= 0 && row < g.rows && grp >= 0 && grp < p4) {
+            const float4 x = B4[(long long)row * p4 + grp];
+            y = m1[(long long)row * p4 + grp];
+            v = make_float4(x.x * y.x, x.y * y.y, x.z * y.z, x.w * y.w);
+        }
+        S1[c] = v;
+        if (tr >= R && tr < R + H0 && tc >= XG && tc < XG + W0) M1[(tr - R) * W0 + tc - XG] = y;
+    }
+    __syncthreads();
+    const SrcCorner sc = src_corner(in.sx, in.sz, g);
+    const float rn0 = g.wavelet[k - 1] / (g.hx * g.hz), rn1 = g.wavelet[k - 2] / (g.hx * g.hz);
+    // step k on E; Q0 = f a mu^k on E
+    for (int c = threadIdx.x; c < H0 * W0; c += T2_THREADS) {
+        const int er = c / W0, ec = c % W0;
+        const int J = J0 - R + er, q = q0 - XG + ec;
+        float4 mk = make_float4(0.f, 0.f, 0.f, 0.f), bq = mk;
+        if (J >= 0 && J < g.NZ && q >= 0 && q < g.NQ) {
+            const long long k4 = (long long)(J + HALO) * p4 + HALO4 + q;
+            const float4 lq = lap4_tile_sum<R, W1>(S1, er + R, ec + XG, g);
+            const float4 a1 = M1[c], a2 = m2[k4];
+            const bool jrow = J >= in.jr0 && J <= in.jr1;
+            const float4 jj = jrow ? J0f[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 ex = reinterpret_cast<const float4 *>(g.ex + HALO)[q];
+            const float ez = g.ez[J + HALO];
+            float mo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int I = 4 * q + i;
+                const float tt = lane_of(ex, i) + ez;
+                const float f = 1.f / (1.f + tt);
+                mo[i] = I < g.NX ? 2.f * f * lane_of(a1, i) + lane_of(lq, i) - (1.f - tt) * f * lane_of(a2, i) +
+                                       lane_of(jj, i)
+                                 : 0.f;
+            }
+            mk = make_float4(mo[0], mo[1], mo[2], mo[3]);
+            const float4 b = B4[k4];
+            bq = make_float4(b.x * mk.x, b.y * mk.y, b.z * mk.z, b.w * mk.w);
+            const int lr = J - J0, lx = q - q0;
+            if (lr >= 0 && lr < T2 && lx >= 0 && lx < TW) {
+                mu0[k4] = mk;
+                MK[lr * TW + lx] = mk;
+            }
+        }
+        S0[c] = bq;
+    }
+    __syncthreads();
+    // step k - 1 on T, and both steps' gradient terms
+    for (int c = threadIdx.x; c < T2 * TW; c += T2_THREADS) {
+        const int lr = c / TW, lx = c % TW;
+        const int J = J0 + lr, q = q0 + lx;
+        if (J >= g.NZ || q >= g.NQ) continue;
+        const long long k4 = (long long)(J + HALO) * p4 + HALO4 + q;
+        const float4 lq = lap4_tile_sum<R, W0>(S0, lr + R, lx + XG, g);
+        const float4 mk = MK[c], a1 = M1[(lr + R) * W0 + lx + XG];
+        const bool jrow = J >= in.jr0 && J <= in.jr1;
+        const float4 jj = jrow ? J1f[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 gg = G4[k4], p0 = P0[k4], p1 = P1[k4];
+        const float4 ex = reinterpret_cast<const float4 *>(g.ex + HALO)[q];
+        const float ez = g.ez[J + HALO];
+        float mo[4], go[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int I = 4 * q + i;
+            const float tt = lane_of(ex, i) + ez;
+            const float f = 1.f / (1.f + tt);
+            const float m = I < g.NX ? 2.f * f * lane_of(mk, i) + lane_of(lq, i) - (1.f - tt) * f * lane_of(a1, i) +
+                                           lane_of(jj, i)
+                                     : 0.f;
+            mo[i] = m;
+            const float w = src_weight(sc, I, J);
+            const float l0 = fmaf(w, rn0, lane_of(p0, i)), l1 = fmaf(w, rn1, lane_of(p1, i));
+            go[i] = fmaf(m / (1.f + tt), l1, fmaf(lane_of(mk, i) / (1.f + tt), l0, lane_of(gg, i)));
+        }
+        mu_1[k4] = make_float4(mo[0], mo[1], mo[2], mo[3]);
         G4[k4] = make_float4(go[0], go[1], go[2], go[3]);
     }
 }
@@ -499,6 +646,12 @@ StepFn step_fn_h(int R, int TZ)
 }
 StepFn step_fn(int R, int TZ, bool hlap) { return hlap ? step_fn_h<true>(R, TZ) : step_fn_h<false>(R, TZ); }
 
+StepFn step2_fn(int R)
+{
+    if (R == 4) return adj_step2_kernel<4>;
+    return R == 2 ? adj_step2_kernel<2> : adj_step2_kernel<1>;
+}
+
 // rows per thread of an adjoint-step launch over n_inst instances: 4 while
 // that gives every SM 7 tile blocks (one wave at 8 resident), else 2 while
 // that gives 3, else 1 (measured on the 461 x 151 grid: 16 shots run fastest
@@ -544,12 +697,32 @@ cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_in
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int n_all, int rec_threads,
                                 bool hlap, cudaStream_t st)
 {
+    const int tz = adj_rows_per_thread(g, n_all);
+    const StepFn fn = step_fn(g.R, tz, hlap);
+    // two steps per launch while its tiles (4 resident per SM: 46.6 KB of
+    // shared memory each) make at most two waves over all chains; beyond, the
+    // one-step kernel's 8 blocks per SM hide more latency (461 x 151 grid:
+    // 16 shots 28.4 -> 24.7 ms with two steps, 32 shots 43.8 -> 49.1)
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    const long long tiles2 = (long long)tiles_x(g) * ((g.NZ + T2 - 1) / T2);
+    if (hlap && g.R <= 4 && tiles2 * n_all <= 2LL * 4 * sms) {
+        // the receiver terms of steps nt and nt - 1 first, each launch's
+        // block 0 then scatters the next launch's two; an odd last step takes
+        // the one-step kernel
+        const dim3 grid2(tiles_x(g) * ((g.NZ + T2 - 1) / T2) + 1, n_inst);
+        const StepFn fn2 = step2_fn(g.R);
+        adj_scatter2_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
+        int k = g.nt;
+        for (; k >= 2; k -= 2) fn2<<<grid2, T2_THREADS, 0, st>>>(g, insts, k);
+        if (k == 1) fn<<<dim3(tile_count(g, 8 * tz) + 1, n_inst), TILE_THREADS, 0, st>>>(g, insts, 1);
+        return cudaGetLastError();
+    }
     // the receiver term of step nt first; each step's extra block then
     // scatters the next step's.  The rows per thread follow the instances of
     // all chains that run at once (n_all).
-    const int tz = adj_rows_per_thread(g, n_all);
     const dim3 grid(tile_count(g, 8 * tz) + 1, n_inst);
-    const StepFn fn = step_fn(g.R, tz, hlap);
     adj_scatter_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
     for (int k = g.nt; k >= 1; --k) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, k);
     return cudaGetLastError();

@@ -1211,8 +1211,9 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     W.B = W.a + F * M;
     if ((rc = adj_grow(ctx, &W.H, &W.H_cap, F * (size_t)(g.nt + 1) * I, &grewH))) return rc;
     // per instance: mu [3], G, J [2]
-    if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 6 * I, nullptr))) return rc;
-    W.G = W.mu + F * 3 * I;
+    // per instance: four rolling adjoint fields, the gradient, four receiver-term slots
+    if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 9 * I, nullptr))) return rc;
+    W.G = W.mu + F * 4 * I;
     // residuals in the modelling trace layout [model][shot][nt][nrec]
     std::vector<long long> doff(S + 1, 0);
     for (int s = 0; s < S; ++s) doff[s + 1] = doff[s] + (long long)g.nt * shots[s].nrec;
@@ -1226,7 +1227,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
         CK(ctx, cudaMemsetAsync(W.H, 0, sizeof(float) * F * (size_t)(g.nt + 1) * I, st));
         W.layout = lay.str();
     }
-    CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 6 * I, st));
+    CK(ctx, cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 9 * I, st));
     // The forward pass runs on the on-chip cluster kernel, which streams the
     // history out beside its usual work, when the kernel selection allows it
     // and the grid fits a cluster's shared memory; else one tiled launch per
@@ -1321,9 +1322,9 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
             in.a = W.a + F * m;
             in.B = W.B + F * m;
             in.H = W.H + F * (size_t)(g.nt + 1) * q;
-            in.mu = W.mu + F * 3 * q;
+            in.mu = W.mu + F * 4 * q;
             in.G = W.G + F * q;
-            in.J = W.mu + F * 4 * I + F * 2 * q;
+            in.J = W.mu + F * 5 * I + F * 4 * q;
             in.E = W.E + (size_t)doff[S] * m + doff[s];
             in.dobs = d_obs + doff[s];
             in.rec = ctx->rec_dev + shots[s].rec_begin;

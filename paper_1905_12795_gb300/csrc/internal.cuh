@@ -102,9 +102,9 @@ struct AdjInst {
     const float *a;      // model field a = v^2 dt^2 (buffer layout)
     const float *B;      // f a, f = 1 / (1 + t)
     float *H;            // wavefield history [nt + 1][field], H[n] = u^n
-    float *mu;           // adjoint fields, 3 rolling buffers [3][field]
+    float *mu;           // adjoint fields, 4 rolling buffers [4][field] (slot k mod 4)
     float *G;            // dphi/da of this shot [field]
-    float *J;            // receiver terms w R^T e of two adjoint steps [2][field], zero elsewhere
+    float *J;            // receiver terms w R^T e of adjoint steps [4][field] (slot k mod 4), zero elsewhere
     float *E;            // residuals [nt][nrec]
     const float *dobs;   // [nt][nrec]
     const float2 *rec;   // receiver positions

@@ -272,9 +272,11 @@ __device__ void resident_instance(const GridDev &gs, const Inst &in, float4 *A4,
     const int qe = extra ? NQ - left + tid / len_last : 0;
     const int re = extra ? r0_last + tid % len_last : 0;
     // a launch shape the planner did not mean (leftover items outside the last
-    // run, or more extra rows than threads) would leave rows uncomputed: the
-    // instance then reports a NaN misfit (the work and barriers run as usual)
-    const bool bad_shape = left > NQ || left * len_last > nth;
+    // run, more extra rows than threads, or runs shorter than the R halo rows
+    // they hand to a neighbour) would leave rows uncomputed or halos stale:
+    // the instance then reports a NaN misfit (the work and barriers run as
+    // usual)
+    const bool bad_shape = left > NQ || left * len_last > nth || (nseg > 1 && my_rows / nseg < R);
 
     float4 ex = make_float4(0.f, 0.f, 0.f, 0.f), exe = ex;
     if (active) ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
@@ -615,6 +617,13 @@ bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit, i
     const int rows_c = (g.NZ + C - 1) / C;
     if (rows_c < g.R || !resident_rows_supported(rows)) return false;
     if ((C - 1) * rows_c >= g.NZ) return false;
+    // a slab cut into several runs hands its first R rows up from its first
+    // run and its last R rows down from its last run, so every run must hold
+    // R rows (in the full slabs and in the last, shorter one)
+    for (const int my : {rows_c, g.NZ - (C - 1) * rows_c}) {
+        const int nseg = (my + rows - 1) / rows;
+        if (nseg > 1 && my / nseg < g.R) return false;
+    }
     if (resident_threads(g, C, rows) > shape_threads(rows)) return false;
     return resident_smem_bytes(g, C, ring_pitch) <= smem_limit;
 }

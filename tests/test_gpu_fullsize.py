@@ -256,6 +256,43 @@ def test_full_size_gradient_directional_derivative(B, kernel):
     ctx.close()
 
 
+def test_gradient_one_and_two_step_adjoint_kernels_agree(B):
+    """20 shots of the plain grid are more tiles than two waves of the
+    two-step adjoint kernel, so their backward pass runs one step per launch;
+    10 shots run two steps per launch.  Both compute every instance's steps
+    with the same arithmetic, so the 20-shot gradient equals the sum of the
+    two 10-shot halves' to FP32 rounding (the compiler may contract the same
+    expressions differently in the two kernels, and the shot sums group
+    differently), and so do the misfits (the 10-shot path is pinned to the
+    oracle above)."""
+    F = _plain()
+    gs, rec = F["gs"], F["rec"]
+    nrec = len(rec)
+    ctx = B.Context([_plain_grid(B, gs)], rec)
+    _, nt = ctx.grid_info(0)
+    xs = np.linspace(100.0, (gs.nx - 1) * gs.hx - 100.0, 20)
+    shots = np.stack([xs, np.full(20, 20.0)], axis=1)
+    v = _dev(F["true"][None])
+    dobs = torch.zeros(20 * nt * nrec, device="cuda")
+    ctx.forward_traces(v * 1.04, B.make_shots(shots, [0] * 20, [nrec] * 20), dobs)
+    d = dobs.view(20, nt * nrec)
+
+    def grad(idx):
+        g = torch.zeros(1, gs.nz, gs.nx, device="cuda")
+        m = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.gradient(v, B.make_shots(shots[idx], [0] * len(idx), [nrec] * len(idx)),
+                     d[idx].contiguous().view(-1), g, m)
+        return g[0].double(), m.item()
+
+    g20, m20 = grad(list(range(20)))
+    ga, ma = grad(list(range(10)))
+    gb, mb = grad(list(range(10, 20)))
+    assert float((g20 - (ga + gb)).norm() / g20.norm()) < 1e-4
+    assert m20 == pytest.approx(ma + mb, rel=1e-9)
+    assert ctx.device_error() == 0
+    ctx.close()
+
+
 def test_hires_gradient_on_l2_cluster_kernel(B):
     """The adjoint gradient on the high-resolution grid (record shortened to
     0.5 s), forward pass on the L2 cluster kernel with the history streamed

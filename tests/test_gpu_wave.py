@@ -110,6 +110,17 @@ def test_on_chip_row_shapes_match_oracle(B, rows, order, nx, nz, pad, h, C):
     ctx.set_cluster(C)
     ctx.set_tile_rows(rows)
     out = torch.zeros(3 * og.nt * nrec, device="cuda")
+    # a slab cut into runs hands its first and last R rows to its neighbours
+    # from its first and last runs: a run length that leaves a run shorter
+    # than R rows is refused
+    NZ, R = nz + 2 * pad, order // 2
+    rows_c = -(-NZ // C)
+    short = any(-(-my // rows) > 1 and my // -(-my // rows) < R for my in (rows_c, NZ - (C - 1) * rows_c))
+    if short:
+        with pytest.raises(B.EmpsoError):
+            ctx.forward_traces(_dev(vel[None]), B.make_shots(shots, [0] * 3, [nrec] * 3), out)
+        ctx.close()
+        return
     ctx.forward_traces(_dev(vel[None]), B.make_shots(shots, [0] * 3, [nrec] * 3), out)
     assert ctx.last_launch() == (2, C) and ctx.last_tile_rows() == rows
     got = out.cpu().numpy().reshape(3, og.nt, nrec)
@@ -466,4 +477,43 @@ def test_grid_too_large_for_chip_runs_on_l2_cluster_kernel(B):
         _check_misfit(got[kind], ref, [e] * 2)
     assert np.allclose(got[0], got[1], rtol=1e-5)
     assert ctx.device_error() == 0
+    ctx.close()
+
+
+def test_every_cluster_shape_matches_oracle(B):
+    """Every cluster size and run length the planner or the autotuner may pick
+    for a small grid (77 x 35 + 12 cells, order 8: slabs of 4 to 59 rows, the
+    last slab shorter) gives the oracle's misfits; the L2 cluster kernel's
+    sizes too."""
+    nx, nz, h, pad, P, S = 77, 35, 20.0, 12, 4, 2
+    grid = B.make_grid(nx, nz, h, h, pad, 8, 0.8, 6.0, 1500.0, 4700.0)
+    rec = synth.receiver_line(nx, h, 20.0)
+    shots = synth.shot_line(S, (nx - 1) * h, 20.0)
+    og = oracle.Grid(nx, nz, h, h, pad, 8, 0.8, 6.0, 4700.0)
+    true = synth.layered_faulted_model(nx, nz, h, h, seed=1905)
+    _, obs = oracle.shot_batch(og, true, shots, rec, [0] * S, [nx] * S, want_traces=True)
+    dobs = _dev(np.concatenate([o.ravel() for o in obs]))
+    x = _dev(synth.random_particles(P, 32, 1500.0, 4700.0, seed=2))
+    ctx = B.Context([grid], rec)
+    vel = torch.zeros(P, nz, nx, device="cuda")
+    ctx.interp(0, x, vel)
+    ref = np.array([oracle.shot_batch(og, vel[m].cpu().numpy().astype(np.float64), shots, rec, [0] * S,
+                                      [nx] * S, dobs=obs)[0].sum() for m in range(P)])
+    sh = B.make_shots(shots, [0] * S, [nx] * S)
+    mis = torch.zeros(P, dtype=torch.float64, device="cuda")
+    ran = 0
+    cands = [(2, C, r) for C in range(1, 17) for r in (13, 11, 9, 8, 6, 4)] + \
+            [(3, C, 0) for C in (1, 2, 4, 8, 10, 12, 16)]
+    for kind, C, rows in cands:
+        ctx.set_kernel(kind)
+        ctx.set_cluster(C)
+        ctx.set_tile_rows(rows)
+        try:
+            ctx.eval_fitness(x, sh, dobs, mis)
+        except B.EmpsoError:
+            continue                     # the shape does not fit this grid
+        got = mis.cpu().numpy()
+        assert np.all(np.abs(got / ref - 1.0) < 1e-4), (kind, C, rows, got, ref)
+        ran += 1
+    assert ran >= 40
     ctx.close()
