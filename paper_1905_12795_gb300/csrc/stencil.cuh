@@ -88,6 +88,69 @@ __device__ __forceinline__ void lap_group(const float4 *w, const float *xs, cons
     l23 = __fadd2_rn(x23, z23);
 }
 
+// lap_group for a thread that sweeps a run of rows: the z-differences from
+// the centre are carried from row to row instead of formed twice.  With
+// d_k = u_{k+1} - u_k and e_k = u_{k+2} - u_k (one rounding each, as dif
+// forms them), the m = 1 and m = 2 pair sums are d_k - d_{k-1} and
+// e_k - e_{k-2}: the same rounded operands as lap_group's
+// (u_{k-1} - u_k) + (u_{k+1} - u_k) and (u_{k-2} - u_k) + (u_{k+2} - u_k),
+// added in the other order, so the result is bit for bit lap_group's, with two
+// packed operations fewer per pair.  dm = d_{k-1}, em = e_{k-2} in; dk = d_k,
+// ek = e_k out (ek only for R >= 2).
+template <int R>
+__device__ __forceinline__ void lap_group_run(const float4 *w, const float *xs, const float *cx, const float *cz,
+                                              float cres, float2 dm01, float2 dm23, float2 em01, float2 em23,
+                                              float2 &dk01, float2 &dk23, float2 &ek01, float2 &ek23,
+                                              float2 &l01, float2 &l23)
+{
+    constexpr int O = 4 * XGroups<R>::G;
+    const float2 c01 = lo2(w[R]), c23 = hi2(w[R]);
+    const float2 m1 = splat2(-1.f);
+    dk01 = __ffma2_rn(c01, m1, lo2(w[R + 1]));
+    dk23 = __ffma2_rn(c23, m1, hi2(w[R + 1]));
+    float2 z01 = __fmul2_rn(splat2(cz[1]), __ffma2_rn(dm01, m1, dk01));
+    float2 z23 = __fmul2_rn(splat2(cz[1]), __ffma2_rn(dm23, m1, dk23));
+    if (R >= 2) {
+        ek01 = __ffma2_rn(c01, m1, lo2(w[R + 2]));
+        ek23 = __ffma2_rn(c23, m1, hi2(w[R + 2]));
+        z01 = __ffma2_rn(splat2(cz[2]), __ffma2_rn(em01, m1, ek01), z01);
+        z23 = __ffma2_rn(splat2(cz[2]), __ffma2_rn(em23, m1, ek23), z23);
+    }
+#pragma unroll
+    for (int m = 3; m <= R; ++m) {
+        z01 = __ffma2_rn(splat2(cz[m]), __fadd2_rn(lo2(w[R - m]), lo2(w[R + m])), z01);
+        z23 = __ffma2_rn(splat2(cz[m]), __fadd2_rn(hi2(w[R - m]), hi2(w[R + m])), z23);
+    }
+    float e[5];
+#pragma unroll
+    for (int j = -1; j <= 3; ++j) e[j + 1] = xs[O + j + 1] - xs[O + j];
+    float2 x01 = __fmul2_rn(splat2(cx[1]), f2(e[1] - e[0], e[2] - e[1]));
+    float2 x23 = __fmul2_rn(splat2(cx[1]), f2(e[3] - e[2], e[4] - e[3]));
+    auto dif = [&](const float2 &v, const float2 &c) { return __ffma2_rn(c, m1, v); };
+    if (R >= 2) {
+        x01 = __ffma2_rn(splat2(cx[2]), __fadd2_rn(dif(f2(xs[O + 2], xs[O + 3]), c01),
+                                                   dif(f2(xs[O - 2], xs[O - 1]), c01)), x01);
+        x23 = __ffma2_rn(splat2(cx[2]), __fadd2_rn(dif(f2(xs[O + 4], xs[O + 5]), c23),
+                                                   dif(f2(xs[O + 0], xs[O + 1]), c23)), x23);
+    }
+#pragma unroll
+    for (int m = 3; m <= R; ++m) {
+        const float2 s01 = (m & 1) ? f2(xs[O - m] + xs[O + m], xs[O + 1 - m] + xs[O + 1 + m])
+                                   : __fadd2_rn(f2(xs[O - m], xs[O + 1 - m]), f2(xs[O + m], xs[O + 1 + m]));
+        const float2 s23 = (m & 1) ? f2(xs[O + 2 - m] + xs[O + 2 + m], xs[O + 3 - m] + xs[O + 3 + m])
+                                   : __fadd2_rn(f2(xs[O + 2 - m], xs[O + 3 - m]),
+                                                f2(xs[O + 2 + m], xs[O + 3 + m]));
+        x01 = __ffma2_rn(splat2(cx[m]), s01, x01);
+        x23 = __ffma2_rn(splat2(cx[m]), s23, x23);
+    }
+    if (R >= 3) {
+        x01 = __ffma2_rn(splat2(cres), c01, x01);
+        x23 = __ffma2_rn(splat2(cres), c23, x23);
+    }
+    l01 = __fadd2_rn(x01, z01);
+    l23 = __fadd2_rn(x23, z23);
+}
+
 // The x-line of a group for R <= 8 from its float4 neighbours l2, l, r, r2.
 __device__ __forceinline__ void xline2(const float4 &l2, const float4 &l, const float4 &c, const float4 &r,
                                        const float4 &r2, float *xs)

@@ -36,7 +36,7 @@ namespace {
 
 constexpr int L2_ROWS = 8;
 constexpr int L2_NT = 512;
-constexpr int L2_CHUNK = 8;   // rows per unrolled chunk of a run
+constexpr int L2_CHUNK = 12;  // rows per unrolled chunk of a run (8: 383.2, 12: 389.1 G updates/s on the 921 x 301 grid; 16 spilled)
 constexpr int L2_DEPTH = 2;
 
 __device__ __forceinline__ void set_lane(float4 &v, int l, float x)
@@ -182,9 +182,9 @@ __device__ void l2_instance(const GridDev &gs, const Inst &in, float4 *U0, float
             const float rn = wring[n % L2_DEPTH];
             // rows r0 .. r0 + len - 1 of column group q, swept downwards in
             // chunks of L2_CHUNK rows, each with the z-stencil in a register
-            // window (its first 2R rows reloaded per chunk: they were read by
-            // this thread a moment before, so they come from L1; carrying the
-            // window across chunks made the compiler spill)
+            // window (its first 2R rows reloaded per chunk, mostly from L1:
+            // this thread read them a moment before; carrying the window
+            // across chunks made the compiler spill)
             auto sweep = [&](const int q, const int r0, const int len) {
                 const float4 ex = __ldg(reinterpret_cast<const float4 *>(gex + HALO) + q);
                 const float2 gx01 = make_float2(2.f / (1.f + ex.x), 2.f / (1.f + ex.y));

@@ -132,6 +132,22 @@ __device__ __forceinline__ void sweep_item(const float4 *__restrict__ cq, float4
     const float4 *gp = ZPAD ? gq + rs * gst : nullptr;   // the row's update weights
     float4 p_w = cp[R * ds], p_l = cp[-1], p_r = cp[1], p_um = *np, p_av = *ap;
     float4 p_g = ZPAD ? *gp : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the run's carried z-differences (lap_group_run, in the 13-row shape,
+    // whose registers hold them; bit for bit the same Laplacian as
+    // lap_group): d_{k-1} = u_k - u_{k-1}, e_{k-1} = u_{k+1} - u_{k-1},
+    // e_{k-2} = u_k - u_{k-2} at the first row
+    constexpr bool CARRY = RW > 8;
+    float2 dm01 = splat2(0.f), dm23 = dm01, e101 = dm01, e123 = dm01, e201 = dm01, e223 = dm01;
+    if (CARRY) {
+        dm01 = __ffma2_rn(lo2(w[R - 1]), m1, lo2(w[R]));
+        dm23 = __ffma2_rn(hi2(w[R - 1]), m1, hi2(w[R]));
+    }
+    if (CARRY && R >= 2) {
+        e101 = __ffma2_rn(lo2(w[R - 1]), m1, lo2(w[R + 1]));
+        e123 = __ffma2_rn(hi2(w[R - 1]), m1, hi2(w[R + 1]));
+        e201 = __ffma2_rn(lo2(w[R - 2]), m1, lo2(w[R]));
+        e223 = __ffma2_rn(hi2(w[R - 2]), m1, hi2(w[R]));
+    }
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
         if (k >= nrows) break;
@@ -150,7 +166,20 @@ __device__ __forceinline__ void sweep_item(const float4 *__restrict__ cq, float4
         float xs[12];
         xline1(lft, w[R], rgt, xs);
         float2 lap01, lap23;
-        lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
+        if (CARRY) {
+            float2 dk01, dk23, ek01, ek23;
+            lap_group_run<R>(w, xs, cx, cz, cres, dm01, dm23, e201, e223, dk01, dk23, ek01, ek23, lap01, lap23);
+            dm01 = dk01;
+            dm23 = dk23;
+            if (R >= 2) {
+                e201 = e101;
+                e223 = e123;
+                e101 = ek01;
+                e123 = ek23;
+            }
+        } else {
+            lap_group<R>(w, xs, cx, cz, cres, lap01, lap23);
+        }
         // u^{n+1} = [2 u^n - (1 - t) u^{n-1} + a lap] / (1 + t)
         //         = g (u^n - u^{n-1}) + u^{n-1} + (a f) lap,  g = 2 f, f = 1 / (1 + t)
         // (a f is the pre-scaled model slab)
