@@ -46,10 +46,10 @@ WORKLOAD = "empso-461x151-P32-S16"
 BYTES_PER_UPDATE = 16          # read u^n, u^{n-1}, a; write u^{n+1} (FP32)
 # FP32 lane operations per grid-point update of the on-chip kernel (an FMA
 # counts one), from its ncu instruction counters: 2 (FADD2 + FFMA2 + FMUL2) +
-# FADD + FFMA + FMUL per update = 2 (3.519 + 8.044 + 1.006) + 3.273 + 0.023
+# FADD + FFMA + FMUL per update = 2 (2.573 + 8.163 + 1.006) + 3.273 + 0.023
 # (profiles/wave_resident_kernel_empso-461x151.md); the FP32 pipes retire 128
 # lane operations per SM per clock
-FP32_OPS_PER_UPDATE = {"wave_resident_kernel": 28.43}
+FP32_OPS_PER_UPDATE = {"wave_resident_kernel": 26.78}
 FP32_LANES_PER_SM = 128
 FALLBACK_HBM_GBS = 6800.0
 
