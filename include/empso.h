@@ -483,10 +483,11 @@ empso_status empso_lowpass(empso_ctx *ctx, const float *in, int32_t S, int32_t n
  * empso_gradient: misfit phi_m = sum_s w_s / 2 |R u_s - d_obs,s|^2 and its
  * gradient dphi_m/dv at every physical node of M gridded models vel device
  * [M][nz][nx] (m/s), all shots on one grid.  Computed by the exact discrete
- * adjoint of the modelling scheme: a forward pass that keeps the whole
- * wavefield history u^0 .. u^nt of every (model, shot) in device memory
- * ((nt + 1) x padded-grid floats each, e.g. 0.78 GB per shot of a 461 x 151
- * grid with 40 damping cells and 1414 steps), then the adjoint pass backward
+ * adjoint of the modelling scheme: a forward pass that keeps, for every
+ * (model, shot), the Laplacian L u^n of every step in device memory (all the
+ * adjoint pass needs of the forward field; (nt + 1) x padded-grid floats
+ * each, e.g. 0.78 GB per shot of a 461 x 151 grid with 40 damping cells and
+ * 1414 steps), then the adjoint pass backward
  * in time accumulating sum_k mu^k f (L u^{k-1} + s^{k-1}), folded from the
  * damping pad onto the edge nodes and chained through a = v^2 dt^2.  The
  * forward pass runs on the on-chip kernel (history streamed out) when the

@@ -22,8 +22,9 @@
 // forward field the adjoint pass needs (its gradient term then costs one
 // pointwise read per point-step instead of a staged tile and a second
 // Laplacian), and leaves its traces for adj_residual_kernel;
-// adj_fwd_kernel is the per-step form for grids neither can hold, whose
-// history is the time levels u^0 .. u^nt themselves.  The per-step kernels here run over all instances at once
+// adj_fwd_kernel is the per-step form for grids neither can hold (and order
+// 16), which keeps its time levels in three rotating slots and writes the
+// same history.  The per-step kernels here run over all instances at once
 // (blockIdx.y = instance), one launch per time step (the time loops replay as
 // one CUDA graph).  They stage the fields their Laplacians read in
 // shared-memory tiles and give each thread a few rows of one float4 group.
@@ -206,7 +207,16 @@ __device__ __forceinline__ float lane_of(const float4 &v, int i)
 
 // Lanes past the last column (I >= NX) stay zero.
 
-// u^{n+1} of every instance into H[n+1]
+// One forward step n of every instance.  The time levels u^{n-1}, u^n,
+// u^{n+1} rotate through three of the instance's adjoint slots (free until
+// the backward pass, L2-resident), and the history slot n + 1 takes L u^n (the
+// source term excluded): the pointwise history the adjoint step reads, as the
+// cluster kernels' forward passes write it.
+__device__ __forceinline__ float *fwd_level(const GridDev &g, const AdjInst &in, int n)
+{
+    return in.mu + (long long)(n % 3) * g.field;
+}
+
 template <int R, int TZ>
 __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
 {
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const 
     // beside the other blocks' stencil work
     if (blockIdx.x == 0) {
         if (n < 1) return;
-        const float *uf = in.H + (long long)n * g.field;
+        const float *uf = fwd_level(g, in, n);
         for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
             const float2 p = in.rec[r];
             const SrcCorner c = src_corner(p.x, p.y, g);
@@ -231,9 +241,11 @@ __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const 
     const int t = blockIdx.x - 1, ntx = tiles_x(g);
     const int q0 = (t % ntx) * TW, J0 = (t / ntx) * TT;
     const int p4 = g.pitch / 4;
-    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)n * g.field);
-    const float4 *um = reinterpret_cast<const float4 *>(in.H + (long long)(n > 0 ? n - 1 : 0) * g.field);
-    float4 *u1 = reinterpret_cast<float4 *>(in.H + (long long)(n + 1) * g.field);
+    // u^{-1} is the zeroed third slot at n = 0
+    const float4 *u = reinterpret_cast<const float4 *>(fwd_level(g, in, n));
+    const float4 *um = reinterpret_cast<const float4 *>(fwd_level(g, in, n + 2));
+    float4 *u1 = reinterpret_cast<float4 *>(fwd_level(g, in, n + 1));
+    float4 *hl = reinterpret_cast<float4 *>(in.H + (long long)(n + 1) * g.field);
     const float4 *a4 = reinterpret_cast<const float4 *>(in.a);
     stage_tile<R, TT>(S, u, J0, q0, g);
     cp_async_wait_all();
@@ -262,6 +274,7 @@ __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const 
                             : 0.f;
         }
         u1[k4] = make_float4(o[0], o[1], o[2], o[3]);
+        __stcs(hl + k4, lap);                // written once, read by the backward pass
     }
 }
 
@@ -302,15 +315,14 @@ __global__ void adj_scatter2_kernel(GridDev g, const AdjInst *__restrict__ insts
 //   G += mu^k f (L u^{k-1} + s^{k-1}),
 // with Q^{k+1} = f a mu^{k+1} formed as the tile is staged.  J is read only
 // on the instance's receiver rows.  Block 0 meanwhile scatters J^{k-1} into
-// the other J slot for the next step.  HLAP: the history holds L u^{k-1} (in
-// slot k, written by a cluster kernel's forward pass), read per point; else
-// it holds u^{k-1} (slot k - 1), staged as a tile and differentiated here.
-template <int R, int TZ, bool HLAP>
+// the other J slot for the next step.  The history holds L u^{k-1} in slot k
+// (every forward pass writes it), read per point.
+template <int R, int TZ>
 __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts,
                                                                    int k)
 {
     constexpr int W = Tile<R>::W, XG = Tile<R>::XG, TT = 8 * TZ;
-    __shared__ float4 SQ[(TT + 2 * R) * W], SU[HLAP ? 1 : (TT + 2 * R) * W];
+    __shared__ float4 SQ[(TT + 2 * R) * W];
     const AdjInst in = insts[blockIdx.y];
     if (blockIdx.x == 0) {
         if (k >= 2) scatter_receiver_term(g, in, k - 1);
@@ -323,10 +335,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
     const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 4) * g.field);
     const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 4) * g.field);
     float4 *J4 = reinterpret_cast<float4 *>(in.J + (long long)(k % 4) * g.field);
-    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)(HLAP ? k : k - 1) * g.field);
+    const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)k * g.field);   // L u^{k-1}
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
     float4 *G4 = reinterpret_cast<float4 *>(in.G);
-    if (!HLAP) stage_tile<R, TT>(SU, u, J0, q0, g);      // in flight during the product tile
     stage_tile_product<R, TT>(SQ, B4, m1, J0, q0, g);
     cp_async_wait_all();
     __syncthreads();
@@ -342,7 +353,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
         const int sr = ly * TZ + r + R;
         const long long k4 = (long long)(J + HALO) * p4 + HALO4 + q;
         const float4 lq = lap4_tile_sum<R>(SQ, sr, lx + XG, g);
-        const float4 lu = HLAP ? u[k4] : lap4_tile_sum<R>(SU, sr, lx + XG, g);
+        const float4 lu = u[k4];
         const float4 a1 = m1[k4], a2 = m2[k4];
         const bool jrow = J >= in.jr0 && J <= in.jr1;
         const float4 jj = jrow ? J4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -506,11 +517,12 @@ __global__ void __launch_bounds__(T2_THREADS, 4) adj_step2_kernel(GridDev g, con
     }
 }
 
-// residual e_n = R u^{n+1} - d_obs,n (one block per instance)
+// residual e_n = R u^{n+1} - d_obs,n (one block per instance), u^{n+1} in the
+// rotating slots of the per-step forward pass
 __global__ void adj_record_kernel(GridDev g, const AdjInst *__restrict__ insts, int n)
 {
     const AdjInst in = insts[blockIdx.x];
-    const float *u = in.H + (long long)(n + 1) * g.field;
+    const float *u = fwd_level(g, in, n + 1);
     for (int r = threadIdx.x; r < in.nrec; r += blockDim.x) {
         const float2 p = in.rec[r];
         const SrcCorner c = src_corner(p.x, p.y, g);
@@ -632,19 +644,14 @@ StepFn fwd_fn(int R)
     if (R == 4) return adj_fwd_kernel<4, 1>;
     return R == 2 ? adj_fwd_kernel<2, 1> : adj_fwd_kernel<1, 1>;
 }
-template <int TZ, bool HLAP>
+template <int TZ>
 StepFn step_fn_z(int R)
 {
-    if (R == 8) return adj_step_kernel<8, TZ, HLAP>;
-    if (R == 4) return adj_step_kernel<4, TZ, HLAP>;
-    return R == 2 ? adj_step_kernel<2, TZ, HLAP> : adj_step_kernel<1, TZ, HLAP>;
+    if (R == 8) return adj_step_kernel<8, TZ>;
+    if (R == 4) return adj_step_kernel<4, TZ>;
+    return R == 2 ? adj_step_kernel<2, TZ> : adj_step_kernel<1, TZ>;
 }
-template <bool HLAP>
-StepFn step_fn_h(int R, int TZ)
-{
-    return TZ == 4 ? step_fn_z<4, HLAP>(R) : (TZ == 2 ? step_fn_z<2, HLAP>(R) : step_fn_z<1, HLAP>(R));
-}
-StepFn step_fn(int R, int TZ, bool hlap) { return hlap ? step_fn_h<true>(R, TZ) : step_fn_h<false>(R, TZ); }
+StepFn step_fn(int R, int TZ) { return TZ == 4 ? step_fn_z<4>(R) : (TZ == 2 ? step_fn_z<2>(R) : step_fn_z<1>(R)); }
 
 StepFn step2_fn(int R)
 {
@@ -695,10 +702,10 @@ cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_in
 }
 
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int n_all, int rec_threads,
-                                bool hlap, cudaStream_t st)
+                                cudaStream_t st)
 {
     const int tz = adj_rows_per_thread(g, n_all);
-    const StepFn fn = step_fn(g.R, tz, hlap);
+    const StepFn fn = step_fn(g.R, tz);
     // two steps per launch while its tiles (4 resident per SM: 46.6 KB of
     // shared memory each) make at most two waves over all chains; beyond, the
     // one-step kernel's 8 blocks per SM hide more latency (461 x 151 grid:
@@ -707,7 +714,7 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         sms = 1;
     const long long tiles2 = (long long)tiles_x(g) * ((g.NZ + T2 - 1) / T2);
-    if (hlap && g.R <= 4 && tiles2 * n_all <= 2LL * 4 * sms) {
+    if (g.R <= 4 && tiles2 * n_all <= 2LL * 4 * sms) {
         // the receiver terms of steps nt and nt - 1 first, each launch's
         // block 0 then scatters the next launch's two; an odd last step takes
         // the one-step kernel

@@ -1392,7 +1392,12 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
                                     ctx->cap_stream, true);
             if (ce == cudaSuccess) ce = launch_adj_residual(g, W.insts, (int)I, rec_max, ctx->cap_stream);
         } else {
+            // the per-step forward pass with its time levels in the (zeroed)
+            // adjoint slots and L u^n as the history; the slots are zeroed
+            // again for the backward pass
             ce = launch_adj_forward(g, W.insts, (int)I, rec_threads, ctx->cap_stream);
+            if (ce == cudaSuccess && !forward_only)
+                ce = cudaMemsetAsync(W.mu, 0, sizeof(float) * F * 4 * I, ctx->cap_stream);
         }
         if (ce == cudaSuccess && !forward_only) {
             // instances [c I / n, (c + 1) I / n) on chain c (chain 0 on the
@@ -1404,7 +1409,7 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
                 ce = cudaStreamWaitEvent(ctx->chain_stream[c - 1], ctx->chain_fork, 0);
             for (int c = 0; c < n && ce == cudaSuccess; ++c) {
                 const long long i0 = c * I / n, i1 = (c + 1) * I / n;
-                ce = launch_adj_backward(g, W.insts + i0, (int)(i1 - i0), (int)I, rec_threads, rC || lC,
+                ce = launch_adj_backward(g, W.insts + i0, (int)(i1 - i0), (int)I, rec_threads,
                                          c == 0 ? ctx->cap_stream : ctx->chain_stream[c - 1]);
             }
             for (int c = 1; c < n && ce == cudaSuccess; ++c) {

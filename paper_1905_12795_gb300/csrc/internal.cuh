@@ -79,7 +79,7 @@ struct Inst {
     float sx, sz;            // source position (m)
     int out;                 // slot of the partial misfit
     int pad_;
-    float *hist;             // [nt + 1][field] wavefield history (u^{n+1} into slot n + 1,
+    float *hist;             // [nt + 1][field] gradient history (L u^n into slot n + 1,
                              // buffer layout), or null; the HIST variants of the cluster
                              // kernels only
 };
@@ -101,7 +101,7 @@ cudaError_t launch_grid_tables(const GridDev &g, float *ex, float *ez, float *wa
 struct AdjInst {
     const float *a;      // model field a = v^2 dt^2 (buffer layout)
     const float *B;      // f a, f = 1 / (1 + t)
-    float *H;            // wavefield history [nt + 1][field], H[n] = u^n
+    float *H;            // history [nt + 1][field]: H[n + 1] = L u^n (H[0] unused)
     float *mu;           // adjoint fields, 4 rolling buffers [4][field] (slot k mod 4)
     float *G;            // dphi/da of this shot [field]
     float *J;            // receiver terms w R^T e of adjoint steps [4][field] (slot k mod 4), zero elsewhere
@@ -113,6 +113,9 @@ struct AdjInst {
     int jr0, jr1;        // padded rows that may hold a receiver term (J is zero elsewhere)
 };
 cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, cudaStream_t st);
+// the per-step forward pass: the time levels rotate through three of each
+// instance's adjoint slots (zeroed before) and the history takes L u^n in
+// slot n + 1
 cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                cudaStream_t st);
 // e = d - d_obs in place in every instance's E (after an on-chip forward pass
@@ -120,10 +123,10 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
 cudaError_t launch_adj_residual(const GridDev &g, const AdjInst *insts, int n_inst, int rec_max,
                                 cudaStream_t st);
 // the backward pass of instances insts[0 .. n_inst), one of several chains
-// that together run n_all instances at once; hlap: the history holds L u^n in
-// slot n + 1 (cluster kernels' forward pass), else u^n in slot n
+// that together run n_all instances at once; the history holds L u^n in slot
+// n + 1
 cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_inst, int n_all, int rec_threads,
-                                bool hlap, cudaStream_t st);
+                                cudaStream_t st);
 // T: scratch of max(M * NZ * nx floats, M * S * 64 doubles), 8-byte aligned
 // (the misfit partials, then the x-folded gradient)
 cudaError_t launch_adj_finish(const GridDev &g, const AdjInst *insts, int M, int S, const float *vel,
