@@ -73,7 +73,7 @@ def _args():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-vs-plain wall-clock comparison")
-    ap.add_argument("--surrogate-seeds", type=int, default=9)
+    ap.add_argument("--surrogate-seeds", type=int, default=18)
     ap.add_argument("--trials", type=int, default=5, help="PSO vs EMPSO comparison trials")
     ap.add_argument("--bands", type=int, default=0, help="fwi workload: number of bands (0: all six)")
     ap.add_argument("--no-sub-workloads", action="store_true",
@@ -422,7 +422,7 @@ def run_ours(a):
                          "algorithmic_bytes_per_launch": BYTES_PER_UPDATE * upd_step,
                          "kernel_ms": wave_mean},
             "roofline_sm": roof_sm,
-            "gpu_launches": 4 * a.steps,
+            "gpu_launches": 5 * a.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
             "surrogate_vs_plain": sur,
@@ -434,8 +434,8 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=2, batch=1024, overlap=True,
-                       recent=4096, min_rank_corr=0.0, patience=0):
+def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=6, batch=1024, overlap=True,
+                       recent=4096, min_rank_corr=0.0, patience=0, lr=1e-3):
     """Wall-clock to a target misfit, surrogate-assisted vs plain EMPSO.
 
     Problem: the 101 x 101 / 10 m / order-4 / 0.5 s / 10 Hz grid with a
@@ -486,7 +486,7 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=2, batch=
         target = best
         t_plain = next(t for t, b in hist if b <= target)
         ctx = B.Context([grid], rec, pso, wl.xmin, wl.xmax)
-        ctx.surrogate_init(hidden=256, capacity=50000, lr=1e-3, seed=seed + 1)
+        ctx.surrogate_init(hidden=256, capacity=50000, lr=lr, seed=seed + 1)
         ctx.surrogate_set_overlap(overlap)
         ctx.surrogate_set_policy(recent, min_rank_corr, patience)
         ctx.pso_init()
@@ -528,7 +528,7 @@ def surrogate_vs_plain(seeds, gens=100, P=1024, keep=0.25, train_steps=2, batch=
     med = lambda v: float(np.median(v)) if v else None  # noqa: E731
     mean = lambda v: float(np.mean(v)) if v else None  # noqa: E731
     return {"problem": f"101x101 order 4, 1 shot, swarm {P}, {gens} plain generations, keep {100 * keep:g} %",
-            "training": {"steps_per_generation": train_steps, "batch": batch,
+            "training": {"steps_per_generation": train_steps, "batch": batch, "lr": lr,
                          "beside_modelling": overlap, "recent_pairs": recent,
                          "min_rank_corr": min_rank_corr, "patience": patience},
             "seeds": seeds, "reached": len(reached),
@@ -634,7 +634,7 @@ def _uneven_result(workload, steps, warmup, tune):
                          "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "kernel_ms": float(np.mean(wave))},
-            "gpu_launches": 4 * steps, "clocks": clk}
+            "gpu_launches": 5 * steps, "clocks": clk}
     ctx.close()
     return line
 

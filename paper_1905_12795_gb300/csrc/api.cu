@@ -1023,7 +1023,7 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         ctx->pcfg = p;
         const size_t PD = (size_t)p.P * p.D;
         if ((rc = ck(cudaMalloc(&ctx->pso_mem, sizeof(double) * (3 * PD + p.P + 2 * p.D)), "swarm")) ||
-            (rc = ck(cudaMalloc(&ctx->pso_int, sizeof(int) * (p.P + 2)), "swarm ints")) ||
+            (rc = ck(cudaMalloc(&ctx->pso_int, sizeof(int) * (2 * p.P + 2)), "swarm ints")) ||
             (rc = ck(cudaMalloc(&ctx->xf, sizeof(float) * PD), "positions")) ||
             (rc = ck(cudaMalloc(&ctx->gen_misfit, sizeof(double) * p.P), "generation misfit")))
             return bail(rc);
@@ -1047,11 +1047,12 @@ empso_status empso_create(const empso_grid *grids, int32_t ngrids, const float *
         s.xmax = bounds + p.D;
         s.order = ctx->pso_int;
         s.gk = ctx->pso_int + p.P;
+        s.rank_of = ctx->pso_int + p.P + 2;
         s.xf = ctx->xf;
         if ((rc = ck(cudaMemcpy(bounds, xmin, sizeof(double) * p.D, cudaMemcpyHostToDevice), "xmin")) ||
             (rc = ck(cudaMemcpy(bounds + p.D, xmax, sizeof(double) * p.D, cudaMemcpyHostToDevice),
                      "xmax")) ||
-            (rc = ck(cudaMemset(ctx->pso_int, 0, sizeof(int) * (p.P + 2)), "swarm ints")))
+            (rc = ck(cudaMemset(ctx->pso_int, 0, sizeof(int) * (2 * p.P + 2)), "swarm ints")))
             return bail(rc);
     }
     if ((rc = ck(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream")) ||
@@ -2184,6 +2185,7 @@ empso_status surrogate_last_rank_corr(empso_ctx *ctx, float *rho, void *stream)
     NEED_SUR(ctx);
     if (!rho) return fail(ctx, EMPSO_INVALID_ARG, "null rho");
     cudaStream_t st = (cudaStream_t)stream;
+    JOIN_SUR(ctx, st);
     CK(ctx, cudaMemcpyAsync(rho, ctx->sur.rho, sizeof(float), cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaStreamSynchronize(st));
     return EMPSO_OK;
@@ -2345,7 +2347,7 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
         }
         CK(ctx, sur_rank_corr(ctx->fk, ctx->sel_rows, ctx->logphi, k, s.rho, st));
         ctx->sur_screened = true;
-        CK(ctx, sur_append(s, ctx->xf, ctx->fk, ctx->sel_rows, k, st));
+        CK(ctx, sur_append(s, ctx->xk, ctx->fk, nullptr, k, st));
         CK(ctx, sur_scatter(ctx->sel_rows, ctx->fk, k, ctx->logphi, P, ctx->fit_full, ctx->rank_full, st));
         if (train_steps > 0 && !ctx->sur_overlap) CK(ctx, sur_train(s, train_steps, batch, st));
         CK(ctx, launch_pso_step(ctx->pso, ctx->fit_full, nullptr, st, ctx->rank_full));

@@ -225,6 +225,7 @@ struct PsoDev {
     double *pf;                  // [P]
     int *order;                  // [P]
     int *gk;                     // {g, k}
+    int *rank_of;                // [P] EM rank of each particle in the current step
     float *xf;                   // [P][D] float copy of x (what generations evaluate)
 };
 cudaError_t launch_pso_init(const PsoDev &s, float *particles_out, cudaStream_t st);

@@ -178,16 +178,15 @@ __device__ __forceinline__ bool before(double fa, int ia, double fb, int ib)
     return fa < fb || (fa == fb && ia < ib);
 }
 
-// One generation in one CTA: bests, global best, EM sort, EM and Eq. 1-2.
+// One generation, first part, in one CTA: personal bests, global best and the
+// EM sort; the rank of every particle goes to s.rank_of for the second part.
 __global__ void __launch_bounds__(STEP_THREADS)
-pso_step_kernel(PsoDev s, const double *misfit, const double *rank, float *particles_out)
+pso_rank_kernel(PsoDev s, const double *misfit, const double *rank)
 {
     __shared__ double key[MAX_PSO_P];
     __shared__ int idx[MAX_PSO_P];
-    __shared__ int rank_of[MAX_PSO_P];
     __shared__ double bf[STEP_THREADS / 32];
     __shared__ int bi[STEP_THREADS / 32];
-    __shared__ int s_best;
     const int tid = threadIdx.x;
     const int P = s.P, D = s.D;
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
@@ -248,15 +247,14 @@ pso_step_kernel(PsoDev s, const double *misfit, const double *rank, float *parti
                 v = bf[w];
                 j = bi[w];
             }
-        // all-infinite pf: every index ties, the lowest one wins
-        s_best = (j == 0x7fffffff) ? 0 : j;
+        // all-infinite pf: every index ties, the lowest one wins (every
+        // thread read gk before the barrier above)
+        s.gk[0] = (j == 0x7fffffff) ? 0 : j;
+        s.gk[1] = k;
     }
-    __syncthreads();
-    const int g = s_best;
 
     // 4. EM: stable ascending sort of the fitness (bitonic on (f, i) pairs)
-    const int NM = s.NM;
-    const bool em = s.em_enabled && k >= s.em_start && NM > 0;
+    const bool em = s.em_enabled && k >= s.em_start && s.NM > 0;
     if (em) {
         for (int size = 2; size <= N; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -279,28 +277,38 @@ pso_step_kernel(PsoDev s, const double *misfit, const double *rank, float *parti
             }
         }
         for (int r = tid; r < P; r += STEP_THREADS) {
-            rank_of[idx[r]] = r;
+            s.rank_of[idx[r]] = r;
             s.order[r] = idx[r];
         }
     } else {
         for (int r = tid; r < P; r += STEP_THREADS) {
-            rank_of[r] = 0;
+            s.rank_of[r] = 0;
             s.order[r] = r;
         }
     }
-    __syncthreads();
+}
 
-    // 5. EM on the NM worst, Eq. 1 / Eq. 2 with clamps on the rest
+// One generation, second part, one thread per (particle, node) over the whole
+// GPU: EM on the NM worst, Eq. 1 / Eq. 2 with clamps on the rest.  Every
+// element's arithmetic is independent of the others', so spreading them over
+// CTAs changes no bit of the result.
+__global__ void pso_move_kernel(PsoDev s, float *particles_out)
+{
+    const int P = s.P, D = s.D;
+    const int g = s.gk[0], k = s.gk[1];
+    const int NM = s.NM;
+    const bool em = s.em_enabled && k >= s.em_start && NM > 0;
     const double phi = s.c1 + s.c2;
     const double chi = 2.0 / fabs(2.0 - phi - sqrt(phi * phi - 4.0 * phi));
     const double *gx = s.p + (size_t)g * D;
     const long long total = (long long)P * D;
-    for (long long e = tid; e < total; e += STEP_THREADS) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(e / D), d = (int)(e % D);
         const double lo = s.xmin[d], hi = s.xmax[d];
         const double vr = hi - lo;
         double x;
-        if (em && rank_of[i] >= P - NM) {
+        if (em && s.rank_of[i] >= P - NM) {
             const double u = uniform_at(s.seed, k, i, d, EM_U);
             double xn;
             if (u < s.p_em) xn = gx[d] + 0.1 * vr * normal_at(s.seed, k, i, d);
@@ -319,10 +327,6 @@ pso_step_kernel(PsoDev s, const double *misfit, const double *rank, float *parti
         s.x[e] = x;
         s.xf[e] = (float)x;
         if (particles_out) particles_out[e] = (float)x;
-    }
-    if (tid == 0) {
-        s.gk[0] = g;
-        s.gk[1] = k;
     }
 }
 
@@ -357,7 +361,13 @@ cudaError_t launch_xf_from_x(const PsoDev &s, cudaStream_t st)
 cudaError_t launch_pso_step(const PsoDev &s, const double *misfit, float *particles_out,
                             cudaStream_t st, const double *rank)
 {
-    pso_step_kernel<<<1, STEP_THREADS, 0, st>>>(s, misfit, rank, particles_out);
+    pso_rank_kernel<<<1, STEP_THREADS, 0, st>>>(s, misfit, rank);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // one element per thread, 256 threads a CTA (P D <= 2048 x 1024 elements)
+    const long long n = (long long)s.P * s.D;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8192));
+    pso_move_kernel<<<blocks, 256, 0, st>>>(s, particles_out);
     return cudaGetLastError();
 }
 

@@ -478,29 +478,47 @@ __global__ void relu_back_kernel(float *dA, const float *__restrict__ Z, long lo
     }
 }
 
-// column sums of an [n][H] FP32 matrix, optionally weighted per row by relu(Z)
-// (g[h] = sum_b X[b][h], fixed order per column)
-__global__ void colsum_kernel(const float *__restrict__ X, const float *__restrict__ wrow,
-                              const float *__restrict__ Zrelu, int n, int H, float *g)
+// Column sums g[h] = sum_b v[b][h] over the batch, v = X, or relu(Z) times
+// wrow[b]: one CTA of 32 x 32 threads per 32 columns; thread (x, y) sums rows
+// y, y + 32, ... of column x, then the 32 partial sums of a column are added
+// pairwise in a fixed tree (the same order on every call).
+constexpr int CS_T = 32;
+__global__ void __launch_bounds__(CS_T * CS_T)
+colsum_kernel(const float *__restrict__ X, const float *__restrict__ wrow,
+              const float *__restrict__ Zrelu, int n, int H, float *g)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= H) return;
+    __shared__ float red[CS_T][CS_T + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int h = blockIdx.x * CS_T + tx;
     float s = 0.f;
-    for (int b = 0; b < n; ++b) {
-        float v = X ? X[(size_t)b * H + h] : fmaxf(Zrelu[(size_t)b * H + h], 0.f);
-        if (wrow) v *= wrow[b];
-        s += v;
+    if (h < H)
+        for (int b = ty; b < n; b += CS_T) {
+            float v = X ? X[(size_t)b * H + h] : fmaxf(Zrelu[(size_t)b * H + h], 0.f);
+            if (wrow) v *= wrow[b];
+            s += v;
+        }
+    red[ty][tx] = s;
+    __syncthreads();
+    for (int st = CS_T / 2; st > 0; st >>= 1) {
+        if (ty < st) red[ty][tx] += red[ty + st][tx];
+        __syncthreads();
     }
-    g[h] = s;
+    if (ty == 0 && h < H) g[h] = red[0][tx];
 }
 
+// out = sum_i v[i]: one CTA, strided partial sums, then a fixed tree
 __global__ void sum_kernel(const float *__restrict__ v, int n, float *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        float s = 0.f;
-        for (int i = 0; i < n; ++i) s += v[i];
-        *out = s;
+    __shared__ float red[1024];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 // Adam on FP32 master weights, then BF16 copies of the two hidden matrices
@@ -569,19 +587,28 @@ __global__ void sample_kernel(int *rows, int B, const int *count, int have_host,
 }
 
 // Spearman rank correlation of the k modelled particles' true misfits fk
-// and predictions logphi[rows]: ranks by counting (ties by index), one block
-__global__ void rank_corr_kernel(const double *__restrict__ fk, const int *__restrict__ rows,
-                                 const float *__restrict__ logphi, int k, float *rho)
+// and predictions logphi[rows]: ranks by counting (ties by index), one block;
+// both keys are staged in shared memory first (k <= 2048)
+__global__ void __launch_bounds__(1024)
+rank_corr_kernel(const double *__restrict__ fk, const int *__restrict__ rows,
+                 const float *__restrict__ logphi, int k, float *rho)
 {
+    __shared__ double tk[2048];
+    __shared__ float pk[2048];
     __shared__ double red[32];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        tk[i] = fk[i];
+        pk[i] = logphi[rows[i]];
+    }
+    __syncthreads();
     double d2 = 0.0;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const double ti = fk[i];
-        const float pi = logphi[rows[i]];
+        const double ti = tk[i];
+        const float pi = pk[i];
         int rt = 0, rp = 0;
         for (int j = 0; j < k; ++j) {
-            const double tj = fk[j];
-            const float pj = logphi[rows[j]];
+            const double tj = tk[j];
+            const float pj = pk[j];
             rt += (tj < ti) || (tj == ti && j < i);
             rp += (pj < pi) || (pj == pi && j < i);
         }
@@ -642,42 +669,63 @@ __global__ void stats_kernel(const float *__restrict__ ybuf, const int *count, i
     }
 }
 
-// append (particle, log misfit) pairs; rows with a non-finite misfit are skipped
-__global__ void append_kernel(const float *__restrict__ x, const double *__restrict__ misfit,
-                              const int *__restrict__ rows, int n, int K, float *xbuf, float *ybuf,
-                              int *count, int cap)
+// append (particle, log misfit) pairs; rows with a non-finite misfit are
+// skipped.  One block of 1024 threads: the kept rows of each 1024-row chunk
+// take consecutive ring slots in row order (an exclusive scan of the keep
+// flags), so the buffer order is the same on every run.
+__global__ void __launch_bounds__(1024)
+append_kernel(const float *__restrict__ x, const double *__restrict__ misfit,
+              const int *__restrict__ rows, int n, int K, float *xbuf, float *ybuf, int *count, int cap)
 {
-    // single block, sequential slots keep the buffer order deterministic
-    __shared__ int base;
-    __shared__ int ok[1024];
+    __shared__ int wsum[32];
+    __shared__ int slot[1024];
+    __shared__ int base, kept;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base = *count;
+    __syncthreads();
     for (int c0 = 0; c0 < n; c0 += 1024) {
         const int m = min(1024, n - c0);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const double f = misfit[c0 + i];
-            ok[i] = (isfinite(f) && f > 0.0) ? 1 : 0;
+        int ok = 0;
+        if (tid < m) {
+            const double f = misfit[c0 + tid];
+            ok = (isfinite(f) && f > 0.0) ? 1 : 0;
         }
+        // inclusive scan within the warp, then over the warp totals
+        int v = ok;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) wsum[warp] = v;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int c = *count;
-            for (int i = 0; i < m; ++i) {
-                const int v = ok[i];
-                ok[i] = v ? c % cap : -1;
-                c += v;
+        if (warp == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
             }
-            base = c;
+            wsum[lane] = w;   // inclusive totals of warps 0..lane
+            if (lane == 31) kept = w;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const int slot = ok[i];
-            if (slot < 0) continue;
+        const int before = v - ok + (warp > 0 ? wsum[warp - 1] : 0);
+        slot[tid] = ok ? (base + before) % cap : -1;
+        if (tid < m && ok) ybuf[slot[tid]] = (float)log(misfit[c0 + tid]);
+        __syncthreads();
+        for (int e = tid; e < m * K; e += blockDim.x) {
+            const int i = e / K, kk = e % K;
+            const int sl = slot[i];
+            if (sl < 0) continue;
             const int src = rows ? rows[c0 + i] : c0 + i;
-            ybuf[slot] = (float)log(misfit[c0 + i]);
-            for (int k = 0; k < K; ++k) xbuf[(size_t)slot * K + k] = x[(size_t)src * K + k];
+            xbuf[(size_t)sl * K + kk] = x[(size_t)src * K + kk];
         }
         __syncthreads();
-        if (threadIdx.x == 0) *count = base;
+        if (tid == 0) base += kept;
         __syncthreads();
     }
+    if (tid == 0) *count = base;
 }
 
 // predictions back to log-misfit: out = y sigma + mu
@@ -795,12 +843,13 @@ cudaError_t sur_backward(const SurDev &s, const __nv_bfloat16 *Xb, const float *
     if ((e = sur_forward(s, Xb, n, s.y, st))) return e;
     loss_kernel<<<1, 256, 0, st>>>(s.y, t, n, s.dy, loss);
     // head: g_w3 = sum_b relu(Z2) dy, g_b3 = sum_b dy
-    colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(nullptr, s.dy, s.Z2, n, s.H, s.g + s.off_w3);
-    sum_kernel<<<1, 32, 0, st>>>(s.dy, n, s.g + s.off_b3);
+    const dim3 cs_grid((s.H + CS_T - 1) / CS_T), cs_block(CS_T, CS_T);
+    colsum_kernel<<<cs_grid, cs_block, 0, st>>>(nullptr, s.dy, s.Z2, n, s.H, s.g + s.off_w3);
+    sum_kernel<<<1, 1024, 0, st>>>(s.dy, n, s.g + s.off_b3);
     // layer 2
     dz2_kernel<<<blocks_for((long long)n * s.H), 256, 0, st>>>(s.dy, s.Z2, s.p + s.off_w3, n, s.H,
                                                              s.dZf, s.dZb);
-    colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(s.dZf, nullptr, nullptr, n, s.H, s.g + s.off_b2);
+    colsum_kernel<<<cs_grid, cs_block, 0, st>>>(s.dZf, nullptr, nullptr, n, s.H, s.g + s.off_b2);
     // g_W2[h][h'] = sum_b dZ2[b][h] A1[b][h']
     if ((e = gemm(s, st, s.H, s.H, n, s.dZb, s.H, 0, s.A1b, s.H, 0, nullptr, 0, s.g + s.off_W2, s.H,
                   nullptr, 0)))
@@ -810,7 +859,7 @@ cudaError_t sur_backward(const SurDev &s, const __nv_bfloat16 *Xb, const float *
         return e;
     relu_back_kernel<<<blocks_for((long long)n * s.H), 256, 0, st>>>(s.dA, s.Z1, (long long)n * s.H,
                                                                      s.dZb);
-    colsum_kernel<<<(s.H + 127) / 128, 128, 0, st>>>(s.dA, nullptr, nullptr, n, s.H, s.g + s.off_b1);
+    colsum_kernel<<<cs_grid, cs_block, 0, st>>>(s.dA, nullptr, nullptr, n, s.H, s.g + s.off_b1);
     // g_W1[h][k] = sum_b dZ1[b][h] X[b][k]
     if ((e = gemm(s, st, s.H, s.K, n, s.dZb, s.H, 0, Xb, s.K, 0, nullptr, 0, s.g + s.off_W1, s.K,
                   nullptr, 0)))
@@ -858,7 +907,7 @@ cudaError_t sur_predict(const SurDev &s, const float *x, int n, float *logphi, c
 cudaError_t sur_append(const SurDev &s, const float *x, const double *misfit, const int *rows, int n,
                        cudaStream_t st)
 {
-    append_kernel<<<1, 256, 0, st>>>(x, misfit, rows, n, s.K, s.xbuf, s.ybuf, s.count, s.cap);
+    append_kernel<<<1, 1024, 0, st>>>(x, misfit, rows, n, s.K, s.xbuf, s.ybuf, s.count, s.cap);
     return cudaGetLastError();
 }
 
@@ -887,7 +936,7 @@ cudaError_t sur_select(const float *key, int P, int k, int *rows, cudaStream_t s
 cudaError_t sur_rank_corr(const double *fk, const int *rows, const float *logphi, int k, float *rho,
                           cudaStream_t st)
 {
-    rank_corr_kernel<<<1, 256, 0, st>>>(fk, rows, logphi, k, rho);
+    rank_corr_kernel<<<1, 1024, 0, st>>>(fk, rows, logphi, k, rho);
     return cudaGetLastError();
 }
 

@@ -178,29 +178,53 @@ cudaError_t launch_level_taps(const GridDev &g, int L, const float *level_z, con
 // and in the alignment columns past NX.  Optionally also writes the physical
 // model [nz][nx] (m/s).
 __global__ void interp_kernel(GridDev g, const float *__restrict__ particles, float *a_fields,
-                              long long field_stride, float *vel_out)
+                              long long field_stride, float *vel_out, int col_blocks)
 {
     extern __shared__ float C[];
     const int p = blockIdx.y;
     const int K = g.K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) C[k] = particles[(size_t)p * K + k];
     __syncthreads();
+    // one buffer column per thread, a strided set of its rows per CTA
+    const int c = (blockIdx.x % col_blocks) * blockDim.x + threadIdx.x;
+    if (c >= g.pitch) return;
+    const int row_blocks = gridDim.x / col_blocks;
+    const int rows = (int)(g.field / g.pitch);
     float *a = a_fields + p * field_stride;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.field;
-         e += (long long)gridDim.x * blockDim.x) {
-        int r = (int)(e / g.pitch), c = (int)(e % g.pitch);
-        int I = c - HALO, J = r - HALO;
+    const int I = c - HALO;
+    const bool col_in = I >= 0 && I < g.NX;
+    const int i = min(max(I - g.pad, 0), g.nx - 1);
+    const float *wx = g.Wx + (size_t)i * g.kx;
+    // the column's x-sums t_kz = sum_kx C[kz][kx] Wx[i][kx] are the same for
+    // every row: with up to KZ_REG rows of nodes they are formed once, in
+    // registers, and each point takes only its kz-sum (the same operations in
+    // the same order as forming them per point)
+    constexpr int KZ_REG = 16;
+    const bool reg = g.mode != 2 && g.kz <= KZ_REG;
+    float T[KZ_REG];
+#pragma unroll
+    for (int kz = 0; kz < KZ_REG; ++kz) {
+        float t = 0.f;
+        if (reg && col_in && kz < g.kz)
+            for (int kx = 0; kx < g.kx; ++kx) t = fmaf(C[kz * g.kx + kx], wx[kx], t);
+        T[kz] = t;
+    }
+    for (int r = blockIdx.x / col_blocks; r < rows; r += row_blocks) {
+        const int J = r - HALO;
         float out = 0.f;
-        if (I >= 0 && I < g.NX && J >= 0 && J < g.NZ) {
-            int i = min(max(I - g.pad, 0), g.nx - 1);
-            int j = min(max(J - g.pad, 0), g.nz - 1);
+        if (col_in && J >= 0 && J < g.NZ) {
+            const int j = min(max(J - g.pad, 0), g.nz - 1);
             float v = 0.f;
-            if (g.mode == 2) {
+            if (reg) {
+                const float *wz = g.Wz + (size_t)j * g.kz;
+#pragma unroll
+                for (int kz = 0; kz < KZ_REG; ++kz)
+                    if (kz < g.kz) v = fmaf(__ldg(wz + kz), T[kz], v);
+            } else if (g.mode == 2) {
                 const int4 q = g.lidx[(size_t)j * g.nx + i];
                 const float4 w = g.lw[(size_t)j * g.nx + i];
                 v = fmaf(w.x, C[q.x], fmaf(w.y, C[q.y], fmaf(w.z, C[q.z], w.w * C[q.w])));
             } else {
-                const float *wx = g.Wx + (size_t)i * g.kx;
                 const float *wz = g.Wz + (size_t)j * g.kz;
                 for (int kz = 0; kz < g.kz; ++kz) {
                     float t = 0.f;
@@ -215,7 +239,7 @@ __global__ void interp_kernel(GridDev g, const float *__restrict__ particles, fl
             if (vel_out && I - g.pad == i && J - g.pad == j)
                 vel_out[(size_t)p * g.nx * g.nz + (size_t)j * g.nx + i] = v;
         }
-        a[e] = out;
+        a[(size_t)r * g.pitch + c] = out;
     }
 }
 
@@ -223,12 +247,16 @@ cudaError_t launch_interp(const GridDev &g, const float *particles, int P, float
                           long long field_stride, float *vel_out, cudaStream_t st)
 {
     if (P <= 0) return cudaSuccess;
-    int K = g.K;
-    int blocks = (int)((g.field + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
-    dim3 grid(blocks, P);
-    interp_kernel<<<grid, 256, K * sizeof(float), st>>>(g, particles, a_fields, field_stride,
-                                                         vel_out);
+    const int K = g.K;
+    const int T = 128;
+    const int col_blocks = (g.pitch + T - 1) / T;
+    const int rows = (int)(g.field / g.pitch);
+    // about 16 rows per thread, at least 2048 CTAs over the batch when the rows allow
+    int row_blocks = std::max((rows + 15) / 16, (2048 + P * col_blocks - 1) / (P * col_blocks));
+    row_blocks = std::min(row_blocks, rows);
+    dim3 grid(col_blocks * row_blocks, P);
+    interp_kernel<<<grid, T, K * sizeof(float), st>>>(g, particles, a_fields, field_stride, vel_out,
+                                                       col_blocks);
     return cudaGetLastError();
 }
 
