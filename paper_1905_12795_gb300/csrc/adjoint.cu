@@ -23,7 +23,7 @@
 // pointwise read per point-step instead of a staged tile and a second
 // Laplacian), and leaves its traces for adj_residual_kernel;
 // adj_fwd_kernel is the per-step form for grids neither can hold (and order
-// 16), which keeps its time levels in three rotating slots and writes the
+// 16), which keeps its time levels in two adjoint slots and writes the
 // same history.  The per-step kernels here run over all instances at once
 // (blockIdx.y = instance), one launch per time step (the time loops replay as
 // one CUDA graph).  They stage the fields their Laplacians read in
@@ -90,6 +90,7 @@ __global__ void adj_prep_kernel(GridDev g, const float *a, float *B)
 // TZ = 4 when that still gives every SM enough blocks (less halo re-read, one
 // wave), else 2 or 1 (more, smaller blocks to fill the GPU).
 constexpr int TW = 16, TILE_THREADS = TW * 8;
+constexpr int FWD_TZ8 = 4;   // forward rows per thread at radius 8 when the tiles fill the GPU
 
 template <int R> struct Tile {
     static constexpr int XG = (R + 3) / 4;     // halo groups each side
@@ -207,14 +208,15 @@ __device__ __forceinline__ float lane_of(const float4 &v, int i)
 
 // Lanes past the last column (I >= NX) stay zero.
 
-// One forward step n of every instance.  The time levels u^{n-1}, u^n,
-// u^{n+1} rotate through three of the instance's adjoint slots (free until
-// the backward pass, L2-resident), and the history slot n + 1 takes L u^n (the
+// One forward step n of every instance.  The time levels live in two of the
+// instance's adjoint slots (free until the backward pass, L2-resident): u^n in
+// slot n mod 2, and u^{n+1} overwrites u^{n-1} in the other one, point by
+// point by the thread that read it.  The history slot n + 1 takes L u^n (the
 // source term excluded): the pointwise history the adjoint step reads, as the
 // cluster kernels' forward passes write it.
 __device__ __forceinline__ float *fwd_level(const GridDev &g, const AdjInst &in, int n)
 {
-    return in.mu + (long long)(n % 3) * g.field;
+    return in.mu + (long long)(n % 2) * g.field;
 }
 
 template <int R, int TZ>
@@ -241,9 +243,10 @@ __global__ void __launch_bounds__(TILE_THREADS) adj_fwd_kernel(GridDev g, const 
     const int t = blockIdx.x - 1, ntx = tiles_x(g);
     const int q0 = (t % ntx) * TW, J0 = (t / ntx) * TT;
     const int p4 = g.pitch / 4;
-    // u^{-1} is the zeroed third slot at n = 0
+    // u^{n-1} (zero at n = 0) and u^{n+1} share a slot: no restrict, the
+    // read of a point comes before its write in the same thread
     const float4 *u = reinterpret_cast<const float4 *>(fwd_level(g, in, n));
-    const float4 *um = reinterpret_cast<const float4 *>(fwd_level(g, in, n + 2));
+    const float4 *um = reinterpret_cast<const float4 *>(fwd_level(g, in, n + 1));
     float4 *u1 = reinterpret_cast<float4 *>(fwd_level(g, in, n + 1));
     float4 *hl = reinterpret_cast<float4 *>(in.H + (long long)(n + 1) * g.field);
     const float4 *a4 = reinterpret_cast<const float4 *>(in.a);
@@ -316,10 +319,14 @@ __global__ void adj_scatter2_kernel(GridDev g, const AdjInst *__restrict__ insts
 // with Q^{k+1} = f a mu^{k+1} formed as the tile is staged.  J is read only
 // on the instance's receiver rows.  Block 0 meanwhile scatters J^{k-1} into
 // the other J slot for the next step.  The history holds L u^{k-1} in slot k
-// (every forward pass writes it), read per point.
+// (every forward pass writes it), read per point past L2's keep-set.  mu
+// rotates through `slots` slots: 4 beside the two-step kernel, else 2, where
+// mu^k overwrites mu^{k+2} point by point in the thread that read it (the
+// halo reads of neighbouring tiles are of mu^{k+1} only), which keeps the
+// backward pass's fields within L2 for more instances.
 template <int R, int TZ>
 __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, const AdjInst *__restrict__ insts,
-                                                                   int k)
+                                                                   int k, int slots)
 {
     constexpr int W = Tile<R>::W, XG = Tile<R>::XG, TT = 8 * TZ;
     __shared__ float4 SQ[(TT + 2 * R) * W];
@@ -331,9 +338,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
     const int t = blockIdx.x - 1, ntx = tiles_x(g);
     const int q0 = (t % ntx) * TW, J0 = (t / ntx) * TT;
     const int p4 = g.pitch / 4;
-    float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % 4) * g.field);
-    const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % 4) * g.field);
-    const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % 4) * g.field);
+    float4 *mk = reinterpret_cast<float4 *>(in.mu + (long long)(k % slots) * g.field);
+    const float4 *m1 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 1) % slots) * g.field);
+    const float4 *m2 = reinterpret_cast<const float4 *>(in.mu + (long long)((k + 2) % slots) * g.field);
     float4 *J4 = reinterpret_cast<float4 *>(in.J + (long long)(k % 4) * g.field);
     const float4 *u = reinterpret_cast<const float4 *>(in.H + (long long)k * g.field);   // L u^{k-1}
     const float4 *B4 = reinterpret_cast<const float4 *>(in.B);
@@ -353,7 +360,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 8) adj_step_kernel(GridDev g, co
         const int sr = ly * TZ + r + R;
         const long long k4 = (long long)(J + HALO) * p4 + HALO4 + q;
         const float4 lq = lap4_tile_sum<R>(SQ, sr, lx + XG, g);
-        const float4 lu = u[k4];
+        const float4 lu = __ldcs(u + k4);
         const float4 a1 = m1[k4], a2 = m2[k4];
         const bool jrow = J >= in.jr0 && J <= in.jr1;
         const float4 jj = jrow ? J4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -637,21 +644,22 @@ int grid_blocks(const GridDev &g)
 int tile_count(const GridDev &g, int TT) { return tiles_x(g) * ((g.NZ + TT - 1) / TT); }
 
 using StepFn = void (*)(GridDev, const AdjInst *, int);
+using Step1Fn = void (*)(GridDev, const AdjInst *, int, int);
 
-StepFn fwd_fn(int R)
+StepFn fwd_fn(int R, int TZ)
 {
-    if (R == 8) return adj_fwd_kernel<8, 1>;
+    if (R == 8) return TZ == 4 ? adj_fwd_kernel<8, 4> : (TZ == 2 ? adj_fwd_kernel<8, 2> : adj_fwd_kernel<8, 1>);
     if (R == 4) return adj_fwd_kernel<4, 1>;
     return R == 2 ? adj_fwd_kernel<2, 1> : adj_fwd_kernel<1, 1>;
 }
 template <int TZ>
-StepFn step_fn_z(int R)
+Step1Fn step_fn_z(int R)
 {
     if (R == 8) return adj_step_kernel<8, TZ>;
     if (R == 4) return adj_step_kernel<4, TZ>;
     return R == 2 ? adj_step_kernel<2, TZ> : adj_step_kernel<1, TZ>;
 }
-StepFn step_fn(int R, int TZ) { return TZ == 4 ? step_fn_z<4>(R) : (TZ == 2 ? step_fn_z<2>(R) : step_fn_z<1>(R)); }
+Step1Fn step_fn(int R, int TZ) { return TZ == 4 ? step_fn_z<4>(R) : (TZ == 2 ? step_fn_z<2>(R) : step_fn_z<1>(R)); }
 
 StepFn step2_fn(int R)
 {
@@ -673,6 +681,20 @@ int adj_rows_per_thread(const GridDev &g, int n_inst)
     return 1;
 }
 
+// rows per thread of the forward step: 1, except at radius 8, where a tile
+// of 8 rows stages 3 times its rows (2R = 16 halo rows): there 4 rows (1.5
+// times) while that gives every SM 7 tile blocks, else 2 while that gives 3
+int adj_fwd_rows_per_thread(const GridDev &g, int n_inst)
+{
+    if (g.R < 8) return 1;
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    if ((long long)tile_count(g, 32) * n_inst >= 7LL * sms) return FWD_TZ8;
+    if ((long long)tile_count(g, 16) * n_inst >= 3LL * sms) return 2;
+    return 1;
+}
+
 }  // namespace
 
 cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, cudaStream_t st)
@@ -686,8 +708,9 @@ cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_ins
 {
     // step n also records e_{n-1} (in an extra block); the last record
     // follows the loop
-    const dim3 grid(tile_count(g, 8) + 1, n_inst);
-    const StepFn fn = fwd_fn(g.R);
+    const int tz = adj_fwd_rows_per_thread(g, n_inst);
+    const dim3 grid(tile_count(g, 8 * tz) + 1, n_inst);
+    const StepFn fn = fwd_fn(g.R, tz);
     for (int n = 0; n < g.nt; ++n) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, n);
     adj_record_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt - 1);
     return cudaGetLastError();
@@ -705,7 +728,7 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
                                 cudaStream_t st)
 {
     const int tz = adj_rows_per_thread(g, n_all);
-    const StepFn fn = step_fn(g.R, tz);
+    const Step1Fn fn = step_fn(g.R, tz);
     // two steps per launch while its tiles (4 resident per SM: 46.6 KB of
     // shared memory each) make at most two waves over all chains; beyond, the
     // one-step kernel's 8 blocks per SM hide more latency (461 x 151 grid:
@@ -723,7 +746,7 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
         adj_scatter2_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
         int k = g.nt;
         for (; k >= 2; k -= 2) fn2<<<grid2, T2_THREADS, 0, st>>>(g, insts, k);
-        if (k == 1) fn<<<dim3(tile_count(g, 8 * tz) + 1, n_inst), TILE_THREADS, 0, st>>>(g, insts, 1);
+        if (k == 1) fn<<<dim3(tile_count(g, 8 * tz) + 1, n_inst), TILE_THREADS, 0, st>>>(g, insts, 1, 4);
         return cudaGetLastError();
     }
     // the receiver term of step nt first; each step's extra block then
@@ -731,7 +754,7 @@ cudaError_t launch_adj_backward(const GridDev &g, const AdjInst *insts, int n_in
     // all chains that run at once (n_all).
     const dim3 grid(tile_count(g, 8 * tz) + 1, n_inst);
     adj_scatter_kernel<<<n_inst, rec_threads, 0, st>>>(g, insts, g.nt);
-    for (int k = g.nt; k >= 1; --k) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, k);
+    for (int k = g.nt; k >= 1; --k) fn<<<grid, TILE_THREADS, 0, st>>>(g, insts, k, 2);
     return cudaGetLastError();
 }
 

@@ -1212,7 +1212,9 @@ empso_status gradient_impl(empso_ctx *ctx, const float *vel, int M, const empso_
     W.B = W.a + F * M;
     if ((rc = adj_grow(ctx, &W.H, &W.H_cap, F * (size_t)(g.nt + 1) * I, &grewH))) return rc;
     // per instance: mu [3], G, J [2]
-    // per instance: four rolling adjoint fields, the gradient, four receiver-term slots
+    // per instance: four adjoint-field slots (the two-step backward rotates
+    // through all four, the one-step backward and the per-step forward use
+    // two), the gradient, four receiver-term slots
     if ((rc = adj_grow(ctx, &W.mu, &W.mu_cap, F * 9 * I, nullptr))) return rc;
     W.G = W.mu + F * 4 * I;
     // residuals in the modelling trace layout [model][shot][nt][nrec]

@@ -102,7 +102,7 @@ struct AdjInst {
     const float *a;      // model field a = v^2 dt^2 (buffer layout)
     const float *B;      // f a, f = 1 / (1 + t)
     float *H;            // history [nt + 1][field]: H[n + 1] = L u^n (H[0] unused)
-    float *mu;           // adjoint fields, 4 rolling buffers [4][field] (slot k mod 4)
+    float *mu;           // adjoint fields [4][field]: slot k mod 4 (two-step backward) or k mod 2
     float *G;            // dphi/da of this shot [field]
     float *J;            // receiver terms w R^T e of adjoint steps [4][field] (slot k mod 4), zero elsewhere
     float *E;            // residuals [nt][nrec]
@@ -113,9 +113,9 @@ struct AdjInst {
     int jr0, jr1;        // padded rows that may hold a receiver term (J is zero elsewhere)
 };
 cudaError_t launch_adj_prep(const GridDev &g, const float *a, float *B, int M, cudaStream_t st);
-// the per-step forward pass: the time levels rotate through three of each
-// instance's adjoint slots (zeroed before) and the history takes L u^n in
-// slot n + 1
+// the per-step forward pass: the time levels live in two of each instance's
+// adjoint slots (zeroed before; u^{n+1} overwrites u^{n-1}) and the history
+// takes L u^n in slot n + 1
 cudaError_t launch_adj_forward(const GridDev &g, const AdjInst *insts, int n_inst, int rec_threads,
                                cudaStream_t st);
 // e = d - d_obs in place in every instance's E (after an on-chip forward pass
