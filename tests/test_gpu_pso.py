@@ -69,7 +69,8 @@ def test_init_bit_exact(B, P, D):
     ctx.close()
 
 
-@pytest.mark.parametrize("P,D,em_start", [(32, 32, 1), (33, 5, 1), (1024, 32, 1), (16, 8, 99)])
+@pytest.mark.parametrize("P,D,em_start", [(32, 32, 1), (33, 5, 1), (1024, 32, 1), (16, 8, 99), (2048, 64, 1),
+                                            (1000, 7, 1)])
 def test_step_from_given_state_bit_exact(B, P, D, em_start):
     rng = np.random.default_rng(P + D)
     lo, hi = -5.0, 5.0

@@ -239,6 +239,15 @@ def test_prescreen_models_the_predicted_best_quarter(B):
     assert modelled.sum() == 16
     order = np.lexsort((np.arange(P), pred.cpu().numpy()))
     assert set(np.where(modelled)[0]) == set(order[:16].tolist())
+    # the generation's Spearman correlation of true misfits and predictions
+    # over the modelled rows (in selection order, ties to the earlier row)
+    rows = order[:16]
+    def ranks(v):
+        return np.array([sum(1 for j in range(len(v)) if v[j] < v[i] or (v[j] == v[i] and j < i))
+                         for i in range(len(v))])
+    d = ranks(mis.cpu().numpy()[rows]) - ranks(pred.cpu().numpy()[rows])
+    rho = 1.0 - 6.0 * np.sum(d.astype(np.float64) ** 2) / (16 * (16 ** 2 - 1))
+    assert abs(ctx.surrogate_last_rank_corr() - rho) < 1e-6
     ctx.close()
 
 

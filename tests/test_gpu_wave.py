@@ -194,16 +194,19 @@ def test_single_forward_two_layer(B, kind):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-def test_interp_matches_oracle(B, mode):
+@pytest.mark.parametrize("kx,kz", [(8, 4), (4, 16), (3, 21)])
+def test_interp_matches_oracle(B, mode, kx, kz):
+    """Both tensor-product modes against the oracle, with node rows formed in
+    registers per column (kz <= 16) and per point (kz = 21)."""
     nx, nz, h = 93, 41, 20.0
-    grid = B.make_grid(nx, nz, h, h, 5, 8, 0.2, 6.0, 1500.0, 4700.0, kx=8, kz=4, mode=mode)
+    grid = B.make_grid(nx, nz, h, h, 5, 8, 0.2, 6.0, 1500.0, 4700.0, kx=kx, kz=kz, mode=mode)
     ctx = B.Context([grid], [[0.0, 0.0]])
-    parts = synth.random_particles(5, 32, 1000.0, 5200.0, seed=9)   # some nodes outside the clip
+    parts = synth.random_particles(5, kx * kz, 1000.0, 5200.0, seed=9)   # some nodes outside the clip
     out = torch.zeros(5, nz, nx, device="cuda")
     ctx.interp(0, _dev(parts), out)
     got = out.cpu().numpy()
     for p in range(5):
-        ref = oracle.interp_model(parts[p].reshape(4, 8), nz, nx, mode, 1500.0, 4700.0)
+        ref = oracle.interp_model(parts[p].reshape(kz, kx), nz, nx, mode, 1500.0, 4700.0)
         assert np.max(np.abs(got[p] - ref) / ref) < 2e-6
     ctx.close()
 
