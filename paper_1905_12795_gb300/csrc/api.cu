@@ -437,6 +437,7 @@ struct Plan {
     int resR = 0, resC = 0, res_threads = 0, res_clusters = 0, res_rows = 0, ring_pitch = 0;
     size_t res_smem = 0;
     std::vector<char> res_pair;        // per grid: two instances share a cluster (half each)
+    std::vector<int> res_run;          // per grid: rows per run of its instances (0: res_rows)
     const int4 *units = nullptr;       // device work units of the on-chip kernel
     int n_units = 0, n_paired = 0;
     int n_ctas = 0;
@@ -568,6 +569,14 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
     if (kind == EMPSO_KERNEL_RESIDENT && !p.resident)
         return fail(ctx, EMPSO_UNSUPPORTED,
                     "the batch does not fit the on-chip kernel (grid too large or mixed orders)");
+    // a grid whose work items fill few of the launch's threads (the smaller
+    // grid of an uneven batch) runs shorter runs, more per column
+    p.res_run.assign(ng, 0);
+    if (p.resident)
+        for (int gid = 0; gid < ng; ++gid)
+            if (p.fbase[gid] >= 0)
+                p.res_run[gid] = resident_grid_run(ctx->grids[gid].dev, p.res_pair[gid] ? p.resC / 2 : p.resC,
+                                                   p.res_threads, p.res_rows);
     // L2-resident cluster kernel for grids the on-chip kernel cannot hold:
     // the cluster size that keeps the most SMs busy while every instance in
     // flight (two time levels and the model field) stays within the L2 budget
@@ -686,6 +695,7 @@ empso_status plan_batch(empso_ctx *ctx, const Models &mod, const empso_shot *sho
         in.sx = sh.sx;
         in.sz = sh.sz;
         in.out = (int)q;
+        in.run = p.resident ? p.res_run[sh.grid_id] : 0;
         hi[k] = in;
     }
     float *wh = reinterpret_cast<float *>(ctx->stage_host + wofs);

@@ -78,7 +78,7 @@ struct Inst {
     int nrec;
     float sx, sz;            // source position (m)
     int out;                 // slot of the partial misfit
-    int pad_;
+    int run;                 // on-chip kernel: rows per run for this instance (0: the launch's)
     float *hist;             // [nt + 1][field] gradient history (L u^n into slot n + 1,
                              // buffer layout), or null; the HIST variants of the cluster
                              // kernels only
@@ -190,6 +190,7 @@ __host__ __device__ inline int resident_gtab_width(const GridDev &g)
 int resident_max_threads(int rows);
 int resident_default_rows();
 bool resident_rows_supported(int rows);
+int resident_grid_run(const GridDev &g, int Ce, int threads, int rows);
 int resident_threads(const GridDev &g, int C, int rows);
 size_t resident_smem_bytes(const GridDev &g, int C, int ring_pitch);
 bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit, int rows);

@@ -589,8 +589,10 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float *dring = wring + 4 * ((DEPTH + 3) / 4);
         float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
         int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
+        // rows per run: the instance's own (its grid's, set by the planner
+        // when shorter runs keep more of the launch's threads busy) or the launch's
         resident_instance<R, RW, HIST>(sg, in, A4, B4, M4, G4, wring, dring, rec_w, rec_k, src, Ce, ce,
-                                       sub * Ce, cluster, cred, wred, partial, run);
+                                       sub * Ce, cluster, cred, wred, partial, in.run > 0 ? in.run : run);
     }
 }
 
@@ -655,6 +657,31 @@ bool resident_fits(const GridDev &g, int C, int ring_pitch, size_t smem_limit, i
     }
     if (resident_threads(g, C, rows) > shape_threads(rows)) return false;
     return resident_smem_bytes(g, C, ring_pitch) <= smem_limit;
+}
+
+// Rows per run for grid g in a launch of `threads` threads with runs of at
+// most `rows` rows, on Ce CTAs per instance: the shortest run (most runs per
+// column, so the most threads) whose runs all hold R rows in the full and in
+// the last slab and whose work items need no more than the launch's threads,
+// when that gives more runs than `rows` does; else 0 (the launch's `rows`).
+// A small grid in a launch sized for a larger one (uneven batches) then uses
+// the threads the larger grid needs instead of leaving most of them idle.
+int resident_grid_run(const GridDev &g, int Ce, int threads, int rows)
+{
+    const int rows_c = (g.NZ + Ce - 1) / Ce;
+    const int last = g.NZ - (Ce - 1) * rows_c;
+    if (rows_c < 1 || last < 1) return 0;
+    const int nseg0 = (rows_c + rows - 1) / rows;
+    int best = 0;
+    for (int run = rows - 1; run >= g.R; --run) {
+        const int nseg = (rows_c + run - 1) / run;
+        if (nseg <= nseg0 || (long long)g.NQ * nseg > threads) continue;
+        if (nseg > 1 && rows_c / nseg < g.R) continue;
+        const int nl = (last + run - 1) / run;
+        if (nl > 1 && last / nl < g.R) continue;
+        best = run;
+    }
+    return best;
 }
 
 namespace {

@@ -322,6 +322,29 @@ def test_uneven_batch_pairs_the_small_grid(B):
     ctx.close()
 
 
+def test_uneven_batch_every_cluster_size(B):
+    """Every cluster size that holds both grids of the uneven batch: the
+    coarse grid's instances run shorter runs than the launch's (more runs per
+    column, sized by the fine grid's threads) wherever the planner finds such
+    runs; the misfits match the oracle at each size."""
+    grids, rec, sh, dobs, parts, ref, e = _uneven_problem(B)
+    ctx = B.Context(grids, rec)
+    ctx.set_kernel(2)
+    ran = 0
+    for C in range(2, 8):
+        ctx.set_cluster(C)
+        mis = torch.zeros(5, dtype=torch.float64, device="cuda")
+        try:
+            ctx.eval_fitness(_dev(parts), sh, dobs, mis)
+        except B.EmpsoError:
+            continue                      # this size does not hold one of the grids
+        assert ctx.last_launch() == (2, C)
+        _check_misfit(mis.cpu().numpy(), ref, [e] * 5)
+        ran += 1
+    assert ran >= 4
+    ctx.close()
+
+
 def test_edge_cases(B):
     nx, nz, h = 41, 31, 10.0
     grid = B.make_grid(nx, nz, h, h, 5, 4, 0.2, 10.0, 1500.0, 3000.0)
