@@ -763,7 +763,9 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
     CK(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int), st));
     if (ctx->timing) CK(ctx, mark(ctx->tev[1], st));
     if (p.resident) {
-        CK(ctx, launch_wave_resident(p.resR, ctx->grids_dev, p.insts, p.units, p.n_units, p.n_paired > 0,
+        // the variant for several grids: paired units, or a grid with its own run length
+        const bool multi = p.n_paired > 0 || std::any_of(p.res_run.begin(), p.res_run.end(), [](int r) { return r > 0; });
+        CK(ctx, launch_wave_resident(p.resR, ctx->grids_dev, p.insts, p.units, p.n_units, multi,
                                      ctx->counter, p.resC, p.res_clusters, p.res_threads, p.res_rows,
                                      p.ring_pitch, p.res_smem, ctx->partial, st));
         ctx->last_path = 2;

@@ -589,10 +589,14 @@ wave_resident_kernel(const GridDev *__restrict__ grids, const Inst *__restrict__
         float *dring = wring + 4 * ((DEPTH + 3) / 4);
         float4 *rec_w = reinterpret_cast<float4 *>(dring + (DEPTH * ring_pitch + 3) / 4 * 4);
         int *rec_k = reinterpret_cast<int *>(rec_w + ring_pitch);
-        // rows per run: the instance's own (its grid's, set by the planner
-        // when shorter runs keep more of the launch's threads busy) or the launch's
+        // rows per run: in a launch over several grids (the PAIRS variant),
+        // the instance's own when the planner set one (shorter runs that keep
+        // more of the launch's threads busy), else the launch's.  A single-grid
+        // launch keeps the launch-wide value (reading it per instance cost
+        // that launch 0.75 %)
+        const int irun = PAIRS && in.run > 0 ? in.run : run;
         resident_instance<R, RW, HIST>(sg, in, A4, B4, M4, G4, wring, dring, rec_w, rec_k, src, Ce, ce,
-                                       sub * Ce, cluster, cred, wred, partial, in.run > 0 ? in.run : run);
+                                       sub * Ce, cluster, cred, wred, partial, irun);
     }
 }
 
