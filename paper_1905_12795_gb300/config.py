@@ -168,8 +168,8 @@ def load(src, overrides: dict | None = None) -> RunConfig:
                      surrogate=_surrogate_settings(raw.get("surrogate")), raw=raw)
 
 
-SURROGATE_DEFAULTS = {"keep": 0.25, "hidden": 256, "capacity": 50000, "lr": 1e-3, "train_steps": 5,
-                      "batch": 512, "recent": 4096, "patience": 0}
+SURROGATE_DEFAULTS = {"keep": 0.25, "hidden": 256, "capacity": 50000, "lr": 1e-3, "train_steps": 6,
+                      "batch": 1024, "recent": 4096, "patience": 0}
 
 
 def _surrogate_settings(sur):

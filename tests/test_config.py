@@ -48,7 +48,7 @@ def test_overrides_and_missing_keys():
         config.load(raw)
     # the optional surrogate group (not in the paper): defaults filled, keys checked
     sur = config.load(EXAMPLE, {"surrogate": {"keep": 0.5}}).surrogate
-    assert sur["keep"] == 0.5 and sur["hidden"] == 256 and sur["train_steps"] == 5
+    assert sur["keep"] == 0.5 and sur["hidden"] == 256 and sur["train_steps"] == 6 and sur["batch"] == 1024
     assert config.load(EXAMPLE).surrogate is None
     with pytest.raises(KeyError):
         config.load(EXAMPLE, {"surrogate": {"keeep": 0.5}})
