@@ -749,7 +749,7 @@ cudaError_t mark(cudaEvent_t ev, cudaStream_t st)
 // Enqueue the planned launch: model fields, queue reset, persistent
 // modelling kernel, misfit reduction (when `misfit` is given).
 empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, double *misfit,
-                           cudaStream_t st)
+                           cudaStream_t st, cudaEvent_t before_model = nullptr)
 {
     const int ng = (int)ctx->grids.size();
     if (ctx->timing) CK(ctx, mark(ctx->tev[0], st));
@@ -762,6 +762,7 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
     }
     CK(ctx, cudaMemsetAsync(ctx->counter, 0, sizeof(int), st));
     if (ctx->timing) CK(ctx, mark(ctx->tev[1], st));
+    if (before_model) CK(ctx, cudaEventRecord(before_model, st));
     if (p.resident) {
         // the variant for several grids: paired units, or a grid with its own run length
         const bool multi = p.n_paired > 0 || std::any_of(p.res_run.begin(), p.res_run.end(), [](int r) { return r > 0; });
@@ -806,12 +807,13 @@ empso_status enqueue_batch(empso_ctx *ctx, const Models &mod, const Plan &p, dou
 }
 
 empso_status run_batch(empso_ctx *ctx, const Models &mod, const empso_shot *shots, int S,
-                       const float *d_obs, float *traces, double *misfit, cudaStream_t st)
+                       const float *d_obs, float *traces, double *misfit, cudaStream_t st,
+                       cudaEvent_t before_model = nullptr)
 {
     Plan p;
     empso_status rc = plan_batch(ctx, mod, shots, S, d_obs, traces, p, nullptr, st);
     if (rc) return rc;
-    return enqueue_batch(ctx, mod, p, misfit, st);
+    return enqueue_batch(ctx, mod, p, misfit, st, before_model);
 }
 
 // Strict mode: zero the per-call count of non-finite misfits before the
@@ -2349,10 +2351,12 @@ empso_status surrogate_generation(empso_ctx *ctx, const empso_shot *shots, int32
         // that the GPU starts on it while the host is still issuing them.
         const bool beside = train_steps > 0 && ctx->sur_overlap && (long long)have + k <= s.cap;
         if (train_steps > 0 && ctx->sur_overlap && !beside) CK(ctx, sur_train(s, train_steps, batch, st, have));
-        if (beside) CK(ctx, cudaEventRecord(ctx->sur_fork, st));
+        // the training's fork is recorded once the model fields are written,
+        // just before the modelling launch
         mod.particles = ctx->xk;
         mod.M = k;
-        if ((rc = run_batch(ctx, mod, shots, S, d_obs, nullptr, ctx->fk, st))) return rc;
+        if ((rc = run_batch(ctx, mod, shots, S, d_obs, nullptr, ctx->fk, st, beside ? ctx->sur_fork : nullptr)))
+            return rc;
         if (beside) {
             CK(ctx, cudaStreamWaitEvent(ctx->sur_stream, ctx->sur_fork, 0));
             CK(ctx, sur_train(s, train_steps, batch, ctx->sur_stream, have));
